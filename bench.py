@@ -1,0 +1,350 @@
+"""Benchmark of the FP32-accurate GEMM path on one GB300 (or N replicas).
+
+One step = one call g3_gemm(F32_3XBF16) on the square FP32 problem
+m = n = k = 16384, alpha = 1, beta = 0.5, uniform [-1, 1] inputs from seed 0:
+the hi/lo split pre-pass of both operands (packing) followed by one persistent
+tcgen05 kernel (blocking, TMA staging, 3 MMAs per k-step, alpha/beta epilogue).
+The inputs (1 GiB per operand) exceed the 129 MB L2, so no flush is needed
+between steps.  The plain FP32 SIMT kernel is timed on the same problem for the
+speedup, and both results are checked on sampled rows against the binary64
+oracle.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--size S] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the problem has
+no exchange step): value = total flops of all ranks / max elapsed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GEMM TFLOPS & % dtype peak; 3xBF16-FP32 vs SIMT-FP32 speedup at equal error"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(p, target_s=12.0, max_rows=512):
+    """Time the binary64 oracle on a bounded sample: whole rows of C."""
+    import oracle
+    A64 = p.A.astype(np.float64)
+    B64 = p.B.astype(np.float64)
+    rows = 16
+    t0 = time.perf_counter()
+    oracle.gemm(A64[:rows], B64, None, 1.0, 0.0)
+    dt = time.perf_counter() - t0
+    more = int(min(max_rows, max(rows, rows * (target_s / max(dt, 1e-3)))))
+    sel = np.arange(rows, rows + more) % p.m
+    t0 = time.perf_counter()
+    oracle.gemm(A64, B64, p.C, p.alpha, p.beta, rows=sel)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * more * p.n * p.k
+    return {"value": flops / dt / 1e12, "unit": "TFLOPS", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{more} full rows of C of the {p.m}x{p.n}x{p.k} problem, binary64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the same workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2310_20347_gb300 import synth
+    import oracle
+    oracle.build()
+    p = synth.uniform_problem(args.size, args.size, args.size, seed=0, alpha=1.0, beta=0.5)
+    A64 = p.A.astype(np.float64)
+    B64 = p.B.astype(np.float64)
+    rows_per_step = max(1, args.ref_rows)
+    for w in range(args.warmup):
+        oracle.gemm(A64, B64, p.C, 1.0, 0.5, rows=np.arange(rows_per_step) % p.m)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.gemm(A64, B64, p.C, 1.0, 0.5, rows=(np.arange(rows_per_step) + s * rows_per_step) % p.m)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * rows_per_step * p.n * p.k * args.steps
+    val = flops / dt / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"square FP32 GEMM m=n=k={args.size}, alpha=1, beta=0.5, uniform [-1,1], "
+                                   f"seed 0", "inputs": "larger than L2 (no flush needed)"},
+            "cpu_baseline": {"value": val, "unit": "TFLOPS", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{rows_per_step} rows of C per step"},
+            "e2e": {"value": val, "unit": "TFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--size", type=int, default=16384)
+    ap.add_argument("--impl", default="g3", choices=["g3", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--simt-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    import paper_2310_20347_gb300 as pkg
+    from paper_2310_20347_gb300 import G3_F32, G3_F32_3XBF16, _lib, synth, torch_api
+    pkg.load()
+    n = args.size
+    p = synth.uniform_problem(n, n, n, seed=0, alpha=1.0, beta=0.5)
+    A = torch.from_numpy(p.A).cuda()
+    B = torch.from_numpy(p.B).cuda()
+    C0 = torch.from_numpy(p.C).cuda()
+    C = C0.clone()
+    stream = torch.cuda.current_stream()
+    flops = 2.0 * n * n * n
+
+    def step(dtype, out):
+        torch_api.gemm(A, B, out, 1.0, 0.5, dtype=dtype, stream=stream)
+
+    # --- correctness on sampled rows of the full-size problem (same launch config)
+    import oracle
+    sample_rows = np.array([0, 1, n // 3, n // 2, n - 2, n - 1])
+    errs = {}
+    if rank == 0:
+        A64, B64 = p.A.astype(np.float64), p.B.astype(np.float64)
+        ref = oracle.gemm(A64, B64, p.C, 1.0, 0.5, rows=sample_rows)
+        D = oracle.absprod(A64, B64, 1.0, rows=sample_rows)
+    for name, dt in (("3xbf16", G3_F32_3XBF16), ("simt", G3_F32)):
+        C.copy_(C0)
+        step(dt, C)
+        torch.cuda.synchronize()
+        if rank == 0:
+            got = C[torch.from_numpy(sample_rows).cuda()].cpu().numpy().astype(np.float64)
+            errs[name] = float(np.max(np.abs(got - ref) / D))
+
+    # --- timed region: K steps of the 3xBF16 path
+    for _ in range(args.warmup):
+        step(G3_F32_3XBF16, C)
+    torch.cuda.synchronize()
+    _lib.g3_kernel_timing(True)
+    _lib.g3_kernel_time_ms(reset=True)
+    clocks = Clocks(local)
+    barrier(world)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    launches0 = _lib.g3_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(G3_F32_3XBF16, C)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.g3_launch_count() - launches0
+    clk = clocks.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = _lib.g3_kernel_time_ms(reset=True)
+    _lib.g3_kernel_timing(False)
+    ms_max = max_over_ranks(ms, world)
+    value = world * flops * args.steps / (ms_max * 1e-3) / 1e12
+
+    # --- SIMT on the same problem (the plain method), for the speedup
+    for _ in range(1):
+        step(G3_F32, C)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.simt_steps):
+        step(G3_F32, C)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    simt_ms = s0.elapsed_time(s1) / args.simt_steps
+
+    # --- end to end through the public API with host buffers
+    hA = torch.from_numpy(p.A).pin_memory()
+    hB = torch.from_numpy(p.B).pin_memory()
+    hC = torch.from_numpy(p.C).pin_memory()
+    hOut = torch.empty_like(hC).pin_memory()
+    dA, dB, dC = torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)
+
+    def e2e_step():
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        dC.copy_(hC, non_blocking=True)
+        torch_api.gemm(dA, dB, dC, 1.0, 0.5, dtype=G3_F32_3XBF16, stream=stream)
+        hOut.copy_(dC, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    barrier(world)
+    x0 = torch.cuda.Event(enable_timing=True)
+    x1 = torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1), world)
+    e2e_val = world * flops * e2e_steps / (e2e_ms * 1e-3) / 1e12
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = load_peaks()
+    per_launch_ms = kern_ms / max(kern_n, 1)
+    tensor_flops = 3.0 * flops                  # three bf16 products per FP32-equivalent flop
+    achieved = tensor_flops / (per_launch_ms * 1e-3) / 1e12
+    peak = float(peaks["bf16_tflops"])
+    st = _lib.g3_plan_query(n, n, n, G3_F32_3XBF16)
+    member = _lib.g3_family_describe(st[1]) if st[0] == 0 and st[1] >= 0 else "?"
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    simt_tflops = flops / (simt_ms * 1e-3) / 1e12
+    sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
+    simt_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32", "data": "synthetic",
+        "config": {"workload": f"square FP32 GEMM m=n=k={n}, alpha=1, beta=0.5, uniform [-1,1], seed 0, "
+                               f"F32_3XBF16 (split pre-pass + tcgen05 kernel)",
+                   "member": member, "l2": "inputs 1 GiB/operand > L2, no flush",
+                   "flops_per_step": flops},
+        "rel_err": {"3xbf16": errs.get("3xbf16"), "simt": errs.get("simt"), "tolerance": 2e-6,
+                    "sample": f"rows {sample_rows.tolist()} vs binary64 oracle"},
+        "simt": {"tflops": simt_tflops, "ms": simt_ms, "peak_tflops_at_clock": simt_peak,
+                 "frac": simt_tflops / simt_peak},
+        "speedup_vs_simt": simt_ms / (ms_max / args.steps),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "tc_gemm_kernel<256,2,TC_3XBF16>",
+                     "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
+                     "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", peak)),
+                     "per_launch_ms": per_launch_ms, "launches_timed": kern_n,
+                     "algorithmic": "6 n^3 bf16 tensor flops per launch"},
+        "e2e": {"value": e2e_val, "unit": "TFLOPS", "h2d_bytes_per_step": 3 * n * n * 4,
+                "d2h_bytes_per_step": n * n * 4},
+        "gpu_launches": int(launches),
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                   "samples": clk["samples"]},
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_oracle_sample(p)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

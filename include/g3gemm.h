@@ -1,0 +1,224 @@
+/*
+ * g3gemm.h -- C ABI of a GB300 (sm_103a) blocked general matrix multiplication.
+ *
+ * The operation is the one the paper "Automatic Generators for a Family of
+ * Matrix Multiplication Routines with Apache TVM" (Alaejos et al.) builds its
+ * family of blocked algorithms for (Section 3.1): C = C + A B with A m x k,
+ * B k x n, C m x n, generalised to the usual C := beta*C + alpha*A*B.  Every
+ * variant of that family computes the same product; they differ in blocking,
+ * packing and which operand stays resident where (Sections 3-4, 7).  This
+ * library implements the family on one GPU: a plain FP32 kernel on the CUDA
+ * cores (the C-resident micro-kernel of Section 4.1) and tensor-core kernels
+ * (tcgen05, TMA, TMEM) in several precisions, selected per problem shape in
+ * the spirit of the paper's micro-kernel search (Section 8.4).
+ *
+ * Conventions for every call:
+ *   - Matrices are ROW-MAJOR: element (i,p) of A is A[i*lda + p], (p,j) of B is
+ *     B[p*ldb + j], (i,j) of C is C[i*ldc + j].  Leading dimensions are in
+ *     elements and must satisfy lda >= max(1,k), ldb >= max(1,n),
+ *     ldc >= max(1,n).  A column-major caller computes C^T = B^T A^T by
+ *     swapping the operands.
+ *   - A, B and C are DEVICE pointers owned by the caller; the library never
+ *     frees them and keeps no reference after the call returns (a grouped plan
+ *     keeps them until it is destroyed).
+ *   - Calls are asynchronous on the library's current stream (g3_set_stream)
+ *     or on the stream passed explicitly; none synchronises the host except
+ *     g3_get_last_device_status and first-use workspace growth.
+ *   - Errors: a negative g3_status is returned and nothing is launched.  An
+ *     invalid argument at position i (1-based, in the order of the g3_gemm
+ *     signature) returns -(100 + i), in the manner of BLAS xerbla.  Device-side
+ *     failures (a bounded wait that expired) are recorded in a device status
+ *     word and reported by g3_get_last_device_status().
+ *   - Edge rules: m == 0 or n == 0 is a no-op; k == 0 or alpha == 0 computes
+ *     C := beta*C without reading A or B; beta == 0 never reads C (NaN in C is
+ *     overwritten).
+ */
+#ifndef G3GEMM_H
+#define G3GEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define G3_API __attribute__((visibility("default")))
+#else
+#define G3_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Arithmetic of a call.  Inputs/outputs per dtype:
+ *   G3_F32         A, B, C float32; FP32 FFMA on the CUDA cores.
+ *   G3_F32_3XBF16  A, B, C float32; each operand split into hi + lo bfloat16
+ *                  parts, C += Ahi*Bhi + Ahi*Blo + Alo*Bhi on the tensor cores
+ *                  with FP32 accumulation (the lo*lo term is dropped).
+ *   G3_BF16        A, B bfloat16 (raw 16-bit patterns); C float32.
+ *   G3_FP8_E4M3    A, B OCP E4M3 bytes with per-tensor scales (g3_gemm_ex);
+ *                  C float32 = alpha*scale_a*scale_b*(Aq Bq) + beta*C.
+ *   G3_INT8        A, B int8; C int32; alpha must be 1 and beta 0 or 1; exact
+ *                  (k <= 131072 so that no int32 overflow is possible). */
+typedef enum {
+  G3_F32 = 0,
+  G3_F32_3XBF16 = 1,
+  G3_BF16 = 2,
+  G3_FP8_E4M3 = 3,
+  G3_INT8 = 4
+} g3_dtype;
+
+typedef enum {
+  G3_OK = 0,
+  G3_ERR_ARG = -1,          /* generic invalid argument (positional: -(100+i)) */
+  G3_ERR_UNSUPPORTED = -2,  /* valid but not supported (e.g. INT8 with alpha != 1) */
+  G3_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  G3_ERR_NOMEM = -4,        /* workspace could not be allocated */
+  G3_ERR_TIMEOUT = -5,      /* a device-side bounded wait expired */
+  G3_ERR_NOT_INIT = -6      /* no usable CUDA device */
+} g3_status;
+
+/* C := beta*C + alpha*A*B on the current stream (Section 3.1).
+ * `dtype` is a g3_dtype; alpha and beta are converted to float.  For
+ * G3_FP8_E4M3 the scales are 1; use g3_gemm_ex to pass scales.  May allocate
+ * library workspace on first use of a size class (3xBF16 operand planes,
+ * split-K partials, re-packed operands).                                   */
+G3_API int g3_gemm(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B,
+            int64_t ldb, double beta, void* C, int64_t ldc, int dtype);
+
+/* Set the stream later calls without an explicit stream use (a cudaStream_t;
+ * NULL = legacy default stream).  The setting is per process.             */
+G3_API int g3_set_stream(void* cuda_stream);
+
+/* Extended arguments.  Fields beyond the g3_gemm signature:
+ *   scale_a, scale_b   device pointers to one float each (FP8 per-tensor
+ *                      scales; NULL means 1); ignored for other dtypes.
+ *   workspace, workspace_bytes   optional caller-owned device scratch; when
+ *                      non-NULL and large enough (g3_gemm_workspace_size) the
+ *                      call allocates nothing; too small -> G3_ERR_ARG.
+ *   config             -1: the planner's choice; otherwise the index of a
+ *                      member of the generated kernel family (g3_family_*).
+ *   split_k            0: the planner's choice; >= 1 forces that many splits.
+ *   raster             0: the planner's choice; >= 1 the band width (in tiles)
+ *                      of the tile walk.                                    */
+typedef struct g3_gemm_args {
+  int64_t m, n, k;
+  double alpha, beta;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+  int dtype;
+  const float* scale_a;
+  const float* scale_b;
+  void* workspace;
+  size_t workspace_bytes;
+  int config;
+  int split_k;
+  int raster;
+} g3_gemm_args;
+
+/* Initialise the optional fields of `args` to their defaults (config = -1,
+ * everything else 0/NULL).                                                  */
+G3_API void g3_gemm_args_init(g3_gemm_args* args);
+
+/* g3_gemm with the extended arguments on an explicit stream (NULL = the
+ * current stream).                                                          */
+G3_API int g3_gemm_ex(const g3_gemm_args* args, void* cuda_stream);
+
+/* Bytes of device scratch g3_gemm_ex needs for these arguments with the
+ * planner's (or the forced) configuration; 0 when none.  Returns 0 and sets
+ * *bytes on success.                                                         */
+G3_API int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes);
+
+/* --- Operand preparation (the packing step of Section 5.3) ----------------
+ * x: device float32 rows x cols, leading dimension ldx.  Outputs are device
+ * buffers owned by the caller with leading dimension ldy (elements).        */
+
+/* y = bfloat16(x), round to nearest even (raw 16-bit patterns).             */
+G3_API int g3_convert_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* y, int64_t ldy,
+                    void* cuda_stream);
+
+/* hi = bf16(x), lo = bf16(x - hi): the split of the FP32-accurate mode.     */
+G3_API int g3_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo, int64_t ldy,
+                  void* cuda_stream);
+
+/* Per-tensor E4M3 quantisation: scale = amax|x| / 448 (1 when x == 0),
+ * q = e4m3_satfinite(x / scale) with the quotient rounded in float32.
+ * `scale` is a device float written by the call; q has leading dimension ldq. */
+G3_API int g3_quantize_fp8(const float* x, int64_t rows, int64_t cols, int64_t ldx, uint8_t* q, int64_t ldq,
+                    float* scale, void* cuda_stream);
+
+/* --- Grouped GEMM: many independent problems in one persistent launch ------
+ * One descriptor per problem, same conventions as g3_gemm; all problems of a
+ * call share one dtype (G3_BF16 or G3_F32_3XBF16).                          */
+typedef struct g3_gemm_desc {
+  int64_t m, n, k;
+  int64_t lda, ldb, ldc;
+  double alpha, beta;
+  const void* A;
+  const void* B;
+  void* C;
+} g3_gemm_desc;
+
+typedef struct g3_grouped_plan g3_grouped_plan;
+
+/* Validate the descriptors, bucket the shapes, encode the per-problem tensor
+ * maps into a device table and allocate the plan's workspace.  Synchronous.
+ * The caller must keep A, B, C of every problem alive until the plan is
+ * destroyed.  Descriptor i with an invalid field returns -(100 + i) clipped
+ * to G3_ERR_ARG for i >= 900.                                               */
+G3_API int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** plan);
+
+/* Run every problem of the plan: pre-passes (if any) and ONE persistent
+ * kernel launch.  No host synchronisation and no allocation, so the call can
+ * be captured into a CUDA graph.                                            */
+G3_API int g3_grouped_plan_execute(g3_grouped_plan* plan, void* cuda_stream);
+
+G3_API int g3_grouped_plan_destroy(g3_grouped_plan* plan);
+
+/* Convenience: create, execute, destroy (synchronises on destroy).          */
+G3_API int g3_gemm_grouped(int count, const g3_gemm_desc* descs, int dtype, void* cuda_stream);
+
+/* --- Status, introspection, timing ----------------------------------------*/
+
+/* Synchronise the device, return G3_ERR_TIMEOUT if any kernel since the last
+ * call reported an expired wait (G3_OK otherwise) and clear the word.  The
+ * raw device code is stored in *code when code != NULL.                      */
+G3_API int g3_get_last_device_status(int* code);
+
+G3_API const char* g3_status_string(int status);
+
+/* Number of members of the generated tensor-core kernel family, and a
+ * one-line description ("mode=bf16 bm=256 stages=4 smem=197888") of member
+ * `index` written to buf (NUL-terminated, truncated to len).               */
+G3_API int g3_family_size(void);
+G3_API int g3_family_describe(int index, char* buf, size_t len);
+
+/* Which configuration the planner picks for a problem (index into the family,
+ * split count, raster band); -1 in *config for the FP32 SIMT kernel.        */
+G3_API int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* split_k, int* raster);
+
+/* Kernel launches issued by the library since the process started.         */
+G3_API uint64_t g3_launch_count(void);
+
+/* When enabled, the library brackets its main GEMM kernel launch with CUDA
+ * events on the launching stream; g3_kernel_time_ms returns (after
+ * synchronising) the summed device time of those kernels since the last
+ * reset and the number of launches timed.                                   */
+G3_API int g3_kernel_timing(int enable);
+G3_API int g3_kernel_time_ms(double* total_ms, int* launches, int reset);
+
+/* Failure-detection test hook.  The next tensor-core GEMM launch withholds
+ * the producer's arrive on its first k-block, so the MMA thread's bounded
+ * wait expires after timeout_ms (1..10000): the kernel records the watchdog
+ * code, every role leaves its loop, in-flight copies and MMAs are drained and
+ * TMEM is freed; nothing hangs or faults.  That call's C is left undefined and
+ * g3_get_last_device_status() then returns G3_ERR_TIMEOUT.                   */
+G3_API int g3_debug_withhold_next(int64_t timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* G3GEMM_H */

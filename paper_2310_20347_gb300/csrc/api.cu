@@ -1,0 +1,687 @@
+// api.cu -- the C ABI of include/g3gemm.h: argument validation, the planner
+// (per-shape choice of a member of the generated kernel family, split-K and
+// raster), library workspace, TMA descriptor encoding and dispatch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "g3gemm.h"
+#include "family_gen.inc"
+#include "internal.h"
+
+namespace g3 {
+
+__device__ int g_device_status;   // first watchdog code raised since the last query
+uint64_t launch_count();
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct DevState {
+  bool init = false;
+  int sms = 0;
+  int* status = nullptr;   // device address of g_device_status
+  void* ws = nullptr;      // library-owned workspace
+  size_t ws_bytes = 0;
+};
+
+std::mutex g_mu;
+DevState g_dev[kMaxDevices];
+cudaStream_t g_stream = nullptr;
+FamilyEntry g_family[G3_FAMILY_SIZE];
+bool g_family_ready = false;
+bool g_timing = false;
+bool g_withhold_next = false;              // failure-detection test hook
+unsigned long long g_withhold_timeout_ns = 0;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_events;
+
+unsigned long long watchdog_ns() {
+  static unsigned long long ns = [] {
+    const char* e = std::getenv("G3_WATCHDOG_MS");
+    long long ms = e ? std::atoll(e) : 2000;
+    if (ms <= 0) ms = 2000;
+    return (unsigned long long)ms * 1000000ULL;
+  }();
+  return ns;
+}
+
+void family_init() {
+  if (g_family_ready) return;
+  std::memset(g_family, 0, sizeof(g_family));
+  register_family_bf16(g_family);
+  register_family_3xbf16(g_family);
+  register_family_fp8(g_family);
+  g_family_ready = true;
+}
+
+int ensure_device(DevState** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return G3_ERR_NOT_INIT;
+  }
+  DevState& d = g_dev[dev];
+  if (!d.init) {
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return G3_ERR_NOT_INIT;
+    }
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) {
+      cudaGetLastError();
+      return G3_ERR_CUDA;
+    }
+    d.status = static_cast<int*>(p);
+    d.init = true;
+  }
+  family_init();
+  *out = &d;
+  return G3_OK;
+}
+
+// ---------------------------------------------------------------- TMA descriptors
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// A row-major matrix of `outer` rows x `inner` elements (leading dimension ld
+// elements) as a 2-D tensor, loaded in boxes of box_inner x box_outer with the
+// 128-byte swizzle; out-of-range elements of a box read as zero.
+int encode_2d(CUtensorMap* map, const void* base, int esize, uint64_t inner, uint64_t outer, uint64_t ld,
+              uint32_t box_inner, uint32_t box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return G3_ERR_CUDA;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld * (uint64_t)esize};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUtensorMapDataType dt = esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
+}
+
+bool tma_ok(const void* p, int64_t ld, int esize) {
+  return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((ld * esize) % 16 == 0);
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------- planner
+int tc_mode_of(int dtype) {
+  switch (dtype) {
+    case G3_BF16: return TC_BF16;
+    case G3_F32_3XBF16: return TC_3XBF16;
+    case G3_FP8_E4M3: return TC_FP8;
+    case G3_INT8: return TC_BF16;   // exact emulation: int8 values are exact in bfloat16
+    default: return -1;
+  }
+}
+
+struct Plan {
+  int member = -1;
+  int splits = 1;
+  int kb_per_split = 1;
+  int num_kb = 1;
+  int tiles_m = 1, tiles_n = 1;
+  int raster = 8;
+};
+
+// Relative throughput of one SM with an MMA of N = bm (smem bandwidth per flop
+// grows as N shrinks; values from the operand bytes each MMA reads).
+double tile_efficiency(int bm) { return bm >= 256 ? 1.0 : (bm >= 128 ? 0.8 : 0.55); }
+
+Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_member, int force_split,
+               int force_raster) {
+  Plan pl;
+  const int mode = tc_mode_of(dtype);
+  const int bk = (mode == TC_FP8) ? 128 : 64;
+  pl.num_kb = (int)((k + bk - 1) / bk);
+  pl.tiles_n = (int)((n + 127) / 128);
+  if (force_member >= 0 && force_member < G3_FAMILY_SIZE && g_family[force_member].mode == mode &&
+      g_family[force_member].launch) {
+    pl.member = force_member;
+  } else {
+    double best = 1e300;
+    for (int i = 0; i < G3_FAMILY_SIZE; ++i) {
+      const FamilyEntry& f = g_family[i];
+      if (!f.launch || f.mode != mode) continue;
+      if (pl.member >= 0 && g_family[pl.member].bm == f.bm) continue;   // first (deepest) variant per bm
+      const long long tiles = ((m + f.bm - 1) / f.bm) * (long long)pl.tiles_n;
+      const long long waves = (tiles + sms - 1) / sms;
+      const double cost = (double)waves * f.bm / tile_efficiency(f.bm);
+      if (cost < best * 0.999) {
+        best = cost;
+        pl.member = i;
+      }
+    }
+  }
+  if (pl.member < 0) return pl;
+  const int bm = g_family[pl.member].bm;
+  pl.tiles_m = (int)((m + bm - 1) / bm);
+  const long long tiles = (long long)pl.tiles_m * pl.tiles_n;
+  int splits = 1;
+  if (force_split > 0) {
+    splits = force_split;
+  } else if (tiles * 2 <= sms && pl.num_kb >= 8) {
+    splits = (int)std::min<long long>(sms / tiles, std::min(pl.num_kb / 4, 16));
+    splits = std::max(splits, 1);
+  }
+  if (dtype == G3_INT8) splits = std::max(splits, (pl.num_kb + 15) / 16);   // k-chunks of <= 1024
+  splits = std::min(splits, pl.num_kb);
+  pl.kb_per_split = (pl.num_kb + splits - 1) / splits;
+  if (dtype == G3_INT8) pl.kb_per_split = std::min(pl.kb_per_split, 16);
+  pl.splits = (pl.num_kb + pl.kb_per_split - 1) / pl.kb_per_split;
+  pl.raster = force_raster > 0 ? force_raster : 8;
+  pl.raster = std::max(1, std::min(pl.raster, pl.tiles_m));
+  return pl;
+}
+
+// ---------------------------------------------------------------- workspace layout
+struct Layout {
+  bool pack_a = false, pack_b = false;
+  int64_t lda_p = 0, ldb_p = 0;   // leading dimensions of re-packed / converted operands
+  size_t a_hi = 0, a_lo = 0, b_hi = 0, b_lo = 0, partial = 0, amax = 0;
+  size_t total = 0;
+};
+
+Layout make_layout(const g3_gemm_args& a, const Plan& pl) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const int64_t m = a.m, n = a.n, k = a.k;
+  switch (a.dtype) {
+    case G3_F32_3XBF16:
+      L.lda_p = round_up(k, 8);
+      L.ldb_p = round_up(n, 8);
+      L.a_hi = take((size_t)m * L.lda_p * 2);
+      L.a_lo = take((size_t)m * L.lda_p * 2);
+      L.b_hi = take((size_t)k * L.ldb_p * 2);
+      L.b_lo = take((size_t)k * L.ldb_p * 2);
+      break;
+    case G3_INT8:
+      L.pack_a = L.pack_b = true;
+      L.lda_p = round_up(k, 8);
+      L.ldb_p = round_up(n, 8);
+      L.a_hi = take((size_t)m * L.lda_p * 2);
+      L.b_hi = take((size_t)k * L.ldb_p * 2);
+      break;
+    case G3_BF16:
+    case G3_FP8_E4M3: {
+      const int es = a.dtype == G3_BF16 ? 2 : 1;
+      L.pack_a = !tma_ok(a.A, a.lda, es);
+      L.pack_b = !tma_ok(a.B, a.ldb, es);
+      L.lda_p = L.pack_a ? round_up(k, 16 / es) : a.lda;
+      L.ldb_p = L.pack_b ? round_up(n, 16 / es) : a.ldb;
+      if (L.pack_a) L.a_hi = take((size_t)m * L.lda_p * es);
+      if (L.pack_b) L.b_hi = take((size_t)k * L.ldb_p * es);
+      break;
+    }
+    default:
+      break;
+  }
+  if (a.dtype != G3_F32 && pl.splits > 1) L.partial = take((size_t)pl.splits * m * n * 4);
+  L.total = off;
+  return L;
+}
+
+int get_workspace(DevState& d, const g3_gemm_args& a, size_t need, uint8_t** out) {
+  *out = nullptr;
+  if (need == 0) return G3_OK;
+  if (a.workspace) {
+    if (a.workspace_bytes < need) return -(100 + 15);
+    *out = static_cast<uint8_t*>(a.workspace);
+    return G3_OK;
+  }
+  if (d.ws_bytes < need) {
+    if (d.ws) {
+      cudaDeviceSynchronize();
+      cudaFree(d.ws);
+      d.ws = nullptr;
+      d.ws_bytes = 0;
+    }
+    const size_t sz = std::max<size_t>(round_up((int64_t)need, 64 << 20), 64 << 20);
+    if (cudaMalloc(&d.ws, sz) != cudaSuccess) {
+      cudaGetLastError();
+      d.ws = nullptr;
+      return G3_ERR_NOMEM;
+    }
+    d.ws_bytes = sz;
+  }
+  *out = static_cast<uint8_t*>(d.ws);
+  return G3_OK;
+}
+
+// ---------------------------------------------------------------- timing
+struct TimedRegion {
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  explicit TimedRegion(cudaStream_t st) : s(st) {
+    if (!g_timing) return;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  ~TimedRegion() {
+    if (!e0) return;
+    cudaEventRecord(e1, s);
+    g_events.emplace_back(e0, e1);
+  }
+};
+
+#define G3_CHECK_CUDA(expr)                   \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) {                  \
+      if (std::getenv("G3_LOG"))              \
+        std::fprintf(stderr, "g3gemm: %s: %s\n", #expr, cudaGetErrorString(_e)); \
+      return G3_ERR_CUDA;                     \
+    }                                         \
+  } while (0)
+
+// ---------------------------------------------------------------- validation
+int validate(const g3_gemm_args& a) {
+  if (a.m < 0) return -101;
+  if (a.n < 0) return -102;
+  if (a.k < 0) return -103;
+  if (a.dtype < G3_F32 || a.dtype > G3_INT8) return -112;
+  if (a.lda < std::max<int64_t>(1, a.k)) return -106;
+  if (a.ldb < std::max<int64_t>(1, a.n)) return -108;
+  if (a.ldc < std::max<int64_t>(1, a.n)) return -111;
+  if (a.m == 0 || a.n == 0) return G3_OK;
+  if (!a.C) return -110;
+  if (a.k > 0 && a.alpha != 0.0) {
+    if (!a.A) return -105;
+    if (!a.B) return -107;
+  }
+  if (a.m > INT32_MAX || a.n > INT32_MAX || a.k > INT32_MAX) return G3_ERR_UNSUPPORTED;
+  if (a.dtype == G3_INT8) {
+    if (a.alpha != 1.0 && a.k > 0) return G3_ERR_UNSUPPORTED;
+    if (a.beta != 0.0 && a.beta != 1.0) return G3_ERR_UNSUPPORTED;
+    if (a.k > 131072) return G3_ERR_UNSUPPORTED;
+  }
+  return G3_OK;
+}
+
+int run_simt(const g3_gemm_args& a, cudaStream_t s) {
+  SimtParams p;
+  p.m = (int)a.m;
+  p.n = (int)a.n;
+  p.k = (int)a.k;
+  p.alpha = (float)a.alpha;
+  p.beta = (float)a.beta;
+  p.A = static_cast<const float*>(a.A);
+  p.lda = a.lda;
+  p.B = static_cast<const float*>(a.B);
+  p.ldb = a.ldb;
+  p.C = static_cast<float*>(a.C);
+  p.ldc = a.ldc;
+  const bool vec = (reinterpret_cast<uintptr_t>(a.A) % 16 == 0) && (reinterpret_cast<uintptr_t>(a.B) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(a.C) % 16 == 0) && a.lda % 4 == 0 && a.ldb % 4 == 0 &&
+                   a.ldc % 4 == 0;
+  TimedRegion tr(s);
+  G3_CHECK_CUDA(launch_simt(p, vec, s));
+  return G3_OK;
+}
+
+int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
+  const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d.sms, a.config, a.split_k, a.raster);
+  if (pl.member < 0) return G3_ERR_UNSUPPORTED;
+  const FamilyEntry& fam = g_family[pl.member];
+  const Layout L = make_layout(a, pl);
+  uint8_t* ws = nullptr;
+  int st = get_workspace(d, a, L.total, &ws);
+  if (st != G3_OK) return st;
+
+  const int64_t m = a.m, n = a.n, k = a.k;
+  const int es = (a.dtype == G3_FP8_E4M3) ? 1 : 2;
+  const void *A_hi = a.A, *A_lo = nullptr, *B_hi = a.B, *B_lo = nullptr;
+  int64_t lda = a.lda, ldb = a.ldb;
+
+  // a1: operand preparation
+  if (a.dtype == G3_F32_3XBF16) {
+    uint16_t *ah = (uint16_t*)(ws + L.a_hi), *al = (uint16_t*)(ws + L.a_lo);
+    uint16_t *bh = (uint16_t*)(ws + L.b_hi), *bl = (uint16_t*)(ws + L.b_lo);
+    G3_CHECK_CUDA(launch_split_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p, s));
+    G3_CHECK_CUDA(launch_split_bf16((const float*)a.B, (int)k, (int)n, a.ldb, bh, bl, L.ldb_p, s));
+    A_hi = ah; A_lo = al; B_hi = bh; B_lo = bl;
+    lda = L.lda_p;
+    ldb = L.ldb_p;
+  } else if (a.dtype == G3_INT8) {
+    uint16_t *ah = (uint16_t*)(ws + L.a_hi), *bh = (uint16_t*)(ws + L.b_hi);
+    G3_CHECK_CUDA(launch_int8_to_bf16((const int8_t*)a.A, (int)m, (int)k, a.lda, ah, L.lda_p, s));
+    G3_CHECK_CUDA(launch_int8_to_bf16((const int8_t*)a.B, (int)k, (int)n, a.ldb, bh, L.ldb_p, s));
+    A_hi = ah; B_hi = bh;
+    lda = L.lda_p;
+    ldb = L.ldb_p;
+  } else {
+    if (L.pack_a) {
+      G3_CHECK_CUDA(launch_pack_rows(a.A, (int)m, k * es, a.lda * es, ws + L.a_hi, L.lda_p * es, s));
+      A_hi = ws + L.a_hi;
+      lda = L.lda_p;
+    }
+    if (L.pack_b) {
+      G3_CHECK_CUDA(launch_pack_rows(a.B, (int)k, n * es, a.ldb * es, ws + L.b_hi, L.ldb_p * es, s));
+      B_hi = ws + L.b_hi;
+      ldb = L.ldb_p;
+    }
+  }
+
+  // TMA descriptors: A as (k inner, m rows) in boxes of BK x bm; B as (n inner,
+  // k rows) in boxes of (128 bytes of n) x BK.
+  const uint32_t bk = 128 / es, boxn = 128 / es;
+  CUtensorMap maps[4];
+  std::memset(maps, 0, sizeof(maps));
+  if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+  if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
+  if (a.dtype == G3_F32_3XBF16) {
+    if ((st = encode_2d(&maps[2], A_lo, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[3], B_lo, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
+  } else {
+    maps[2] = maps[0];
+    maps[3] = maps[1];
+  }
+
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.m = (int)m;
+  p.n = (int)n;
+  p.k = (int)k;
+  p.tiles_m = pl.tiles_m;
+  p.tiles_n = pl.tiles_n;
+  p.splits = pl.splits;
+  p.kb_per_split = pl.kb_per_split;
+  p.num_kb = pl.num_kb;
+  p.raster = pl.raster;
+  p.alpha = (float)a.alpha;
+  p.beta = (float)a.beta;
+  p.scale_a = (a.dtype == G3_FP8_E4M3) ? a.scale_a : nullptr;
+  p.scale_b = (a.dtype == G3_FP8_E4M3) ? a.scale_b : nullptr;
+  p.C = a.C;
+  p.ldc = a.ldc;
+  p.timeout_ns = watchdog_ns();
+  p.status = d.status;
+  p.debug_withhold = -1;
+  if (g_withhold_next) {
+    p.debug_withhold = 0;
+    p.timeout_ns = g_withhold_timeout_ns;
+    g_withhold_next = false;
+  }
+  const bool is_int = a.dtype == G3_INT8;
+  if (pl.splits > 1) {
+    p.out_mode = OUT_PARTIAL;
+    p.partial = reinterpret_cast<float*>(ws + L.partial);
+  } else {
+    p.out_mode = is_int ? OUT_I32 : OUT_F32;
+  }
+  const long long total_tiles = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
+  const int grid = (int)std::min<long long>(total_tiles, d.sms);
+  {
+    TimedRegion tr(s);
+    G3_CHECK_CUDA(fam.launch(maps, p, grid, s));
+  }
+  if (pl.splits > 1) {
+    float alpha = (float)a.alpha;
+    if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b)) {
+      // scales live on the device: fold them in with a one-split reduce pass
+      // is not possible on the host, so FP8 never splits (see make_plan callers)
+      return G3_ERR_UNSUPPORTED;
+    }
+    G3_CHECK_CUDA(launch_splitk_reduce(p.partial, pl.splits, (int)m, (int)n, alpha, (float)a.beta, a.C, a.ldc,
+                                       is_int, s));
+  }
+  return G3_OK;
+}
+
+int gemm_impl(g3_gemm_args a, cudaStream_t s) {
+  int st = validate(a);
+  if (st != G3_OK) return st;
+  if (a.m == 0 || a.n == 0) return G3_OK;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DevState* d = nullptr;
+  if ((st = ensure_device(&d)) != G3_OK) return st;
+  const bool is_int = a.dtype == G3_INT8;
+  if (a.k == 0 || a.alpha == 0.0) {
+    if (is_int && a.beta == 1.0) return G3_OK;
+    G3_CHECK_CUDA(launch_scale_c(a.C, is_int, (int)a.m, (int)a.n, a.ldc, (float)a.beta, s));
+    return G3_OK;
+  }
+  if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b)) a.split_k = 1;   // scales apply in the kernel epilogue
+  if (a.dtype == G3_F32) return run_simt(a, s);
+  return run_tc(*d, a, s);
+}
+
+}  // namespace
+}  // namespace g3
+
+using namespace g3;
+
+extern "C" {
+
+void g3_gemm_args_init(g3_gemm_args* a) {
+  if (!a) return;
+  std::memset(a, 0, sizeof(*a));
+  a->config = -1;
+}
+
+int g3_gemm(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+            double beta, void* C, int64_t ldc, int dtype) {
+  g3_gemm_args a;
+  g3_gemm_args_init(&a);
+  a.m = m; a.n = n; a.k = k;
+  a.alpha = alpha; a.beta = beta;
+  a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = ldc;
+  a.dtype = dtype;
+  return gemm_impl(a, g_stream);
+}
+
+int g3_set_stream(void* stream) {
+  g_stream = static_cast<cudaStream_t>(stream);
+  return G3_OK;
+}
+
+int g3_gemm_ex(const g3_gemm_args* args, void* stream) {
+  if (!args) return G3_ERR_ARG;
+  return gemm_impl(*args, stream ? static_cast<cudaStream_t>(stream) : g_stream);
+}
+
+int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
+  if (!args || !bytes) return G3_ERR_ARG;
+  *bytes = 0;
+  int st = validate(*args);
+  if (st != G3_OK) return st;
+  if (args->m == 0 || args->n == 0 || args->k == 0 || args->alpha == 0.0 || args->dtype == G3_F32) return G3_OK;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DevState* d = nullptr;
+  if ((st = ensure_device(&d)) != G3_OK) return st;
+  g3_gemm_args a = *args;
+  if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b)) a.split_k = 1;
+  const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d->sms, a.config, a.split_k, a.raster);
+  *bytes = make_layout(a, pl).total;
+  return G3_OK;
+}
+
+static int prep_check(const void* x, int64_t rows, int64_t cols, int64_t ldx, const void* y, int64_t ldy) {
+  if (rows < 0) return -102;
+  if (cols < 0) return -103;
+  if (ldx < std::max<int64_t>(1, cols)) return -104;
+  if (rows > INT32_MAX || cols > INT32_MAX) return G3_ERR_UNSUPPORTED;
+  if (rows > 0 && cols > 0 && (!x || !y)) return x ? -105 : -101;
+  if (ldy < std::max<int64_t>(1, cols)) return -106;
+  return G3_OK;
+}
+
+int g3_convert_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* y, int64_t ldy, void* stream) {
+  int st = prep_check(x, rows, cols, ldx, y, ldy);
+  if (st != G3_OK || rows == 0 || cols == 0) return st;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  G3_CHECK_CUDA(launch_convert_bf16(x, (int)rows, (int)cols, ldx, static_cast<uint16_t*>(y), ldy, s));
+  return G3_OK;
+}
+
+int g3_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo, int64_t ldy,
+                  void* stream) {
+  int st = prep_check(x, rows, cols, ldx, hi, ldy);
+  if (st != G3_OK) return st;
+  if (rows > 0 && cols > 0 && !lo) return -106;
+  if (rows == 0 || cols == 0) return G3_OK;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  G3_CHECK_CUDA(launch_split_bf16(x, (int)rows, (int)cols, ldx, static_cast<uint16_t*>(hi),
+                                  static_cast<uint16_t*>(lo), ldy, s));
+  return G3_OK;
+}
+
+int g3_quantize_fp8(const float* x, int64_t rows, int64_t cols, int64_t ldx, uint8_t* q, int64_t ldq, float* scale,
+                    void* stream) {
+  int st = prep_check(x, rows, cols, ldx, q, ldq);
+  if (st != G3_OK) return st;
+  if (!scale) return -107;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DevState* d = nullptr;
+  if ((st = ensure_device(&d)) != G3_OK) return st;
+  g3_gemm_args dummy;
+  g3_gemm_args_init(&dummy);
+  uint8_t* ws = nullptr;
+  if ((st = get_workspace(*d, dummy, 256, &ws)) != G3_OK) return st;
+  G3_CHECK_CUDA(launch_quantize_e4m3(x, (int)rows, (int)cols, ldx, reinterpret_cast<unsigned int*>(ws), q, ldq,
+                                     scale, s));
+  return G3_OK;
+}
+
+int g3_grouped_plan_create(int, const g3_gemm_desc*, int, g3_grouped_plan** plan) {
+  if (plan) *plan = nullptr;
+  return G3_ERR_UNSUPPORTED;
+}
+int g3_grouped_plan_execute(g3_grouped_plan*, void*) { return G3_ERR_UNSUPPORTED; }
+int g3_grouped_plan_destroy(g3_grouped_plan*) { return G3_OK; }
+int g3_gemm_grouped(int, const g3_gemm_desc*, int, void*) { return G3_ERR_UNSUPPORTED; }
+
+int g3_get_last_device_status(int* code) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  DevState* d = nullptr;
+  int st = ensure_device(&d);
+  if (st != G3_OK) return st;
+  G3_CHECK_CUDA(cudaDeviceSynchronize());
+  int v = 0;
+  G3_CHECK_CUDA(cudaMemcpy(&v, d->status, sizeof(int), cudaMemcpyDeviceToHost));
+  const int zero = 0;
+  G3_CHECK_CUDA(cudaMemcpy(d->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  if (code) *code = v;
+  return v ? G3_ERR_TIMEOUT : G3_OK;
+}
+
+const char* g3_status_string(int s) {
+  switch (s) {
+    case G3_OK: return "ok";
+    case G3_ERR_ARG: return "invalid argument";
+    case G3_ERR_UNSUPPORTED: return "unsupported";
+    case G3_ERR_CUDA: return "CUDA error";
+    case G3_ERR_NOMEM: return "out of device memory";
+    case G3_ERR_TIMEOUT: return "device wait timed out";
+    case G3_ERR_NOT_INIT: return "no usable CUDA device";
+    default: return s <= -100 ? "invalid argument (positional)" : "unknown status";
+  }
+}
+
+int g3_family_size(void) { return G3_FAMILY_SIZE; }
+
+int g3_family_describe(int index, char* buf, size_t len) {
+  if (index < 0 || index >= G3_FAMILY_SIZE) return -101;
+  if (!buf || len == 0) return -102;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    family_init();
+  }
+  const FamilyEntry& f = g_family[index];
+  static const char* names[] = {"bf16", "3xbf16", "fp8"};
+  std::snprintf(buf, len, "mode=%s bm=%d bn=128 stages=%d smem=%d", names[f.mode], f.bm, f.stages, f.smem);
+  return G3_OK;
+}
+
+int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* split_k, int* raster) {
+  if (m < 0) return -101;
+  if (n < 0) return -102;
+  if (k < 0) return -103;
+  if (dtype < G3_F32 || dtype > G3_INT8) return -104;
+  if (dtype == G3_F32) {
+    if (config) *config = -1;
+    if (split_k) *split_k = 1;
+    if (raster) *raster = 0;
+    return G3_OK;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  DevState* d = nullptr;
+  int sms = 152;
+  family_init();
+  if (ensure_device(&d) == G3_OK) sms = d->sms;
+  const Plan pl = make_plan(m, n, std::max<int64_t>(k, 1), dtype, sms, -1, 0, 0);
+  if (config) *config = pl.member;
+  if (split_k) *split_k = pl.splits;
+  if (raster) *raster = pl.raster;
+  return G3_OK;
+}
+
+uint64_t g3_launch_count(void) { return g3::launch_count(); }
+
+int g3_debug_withhold_next(int64_t timeout_ms) {
+  if (timeout_ms <= 0 || timeout_ms > 10000) return -101;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_withhold_next = true;
+  g_withhold_timeout_ns = (unsigned long long)timeout_ms * 1000000ULL;
+  return G3_OK;
+}
+
+int g3_kernel_timing(int enable) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_timing = enable != 0;
+  return G3_OK;
+}
+
+int g3_kernel_time_ms(double* total_ms, int* launches, int reset) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  double sum = 0.0;
+  for (auto& ev : g_events) {
+    cudaEventSynchronize(ev.second);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) sum += ms;
+    else cudaGetLastError();
+  }
+  if (total_ms) *total_ms = sum;
+  if (launches) *launches = (int)g_events.size();
+  if (reset) {
+    for (auto& ev : g_events) {
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+    g_events.clear();
+  }
+  return G3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "simt_sgemm.cuh"
+#include "tc_gemm.cuh"
+
+namespace g3 {
+
+using TcLaunchFn = cudaError_t (*)(const CUtensorMap* maps, const TcParams& p, int grid, cudaStream_t s);
+
+// One member of the generated tensor-core kernel family.
+struct FamilyEntry {
+  int index;
+  int mode;     // TcMode
+  int bm;       // output rows per tile (= MMA N)
+  int stages;   // shared-memory ring depth
+  int smem;     // dynamic shared memory bytes
+  TcLaunchFn launch;
+};
+
+void register_family_bf16(FamilyEntry* table);
+void register_family_3xbf16(FamilyEntry* table);
+void register_family_fp8(FamilyEntry* table);
+
+// kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
+// launch's cudaError_t; sizes are validated by the caller.
+cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s);
+cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* lo,
+                              long long ldy, cudaStream_t s);
+cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
+                                cudaStream_t s);
+cudaError_t launch_int8_to_bf16(const int8_t* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
+                                cudaStream_t s);
+cudaError_t launch_pack_rows(const void* x, int rows, long long row_bytes, long long ldx_bytes, void* y,
+                             long long ldy_bytes, cudaStream_t s);
+cudaError_t launch_quantize_e4m3(const float* x, int rows, int cols, long long ldx, unsigned int* amax_bits,
+                                 uint8_t* q, long long ldq, float* scale, cudaStream_t s);
+cudaError_t launch_scale_c(void* C, bool is_int, int rows, int cols, long long ldc, float beta, cudaStream_t s);
+cudaError_t launch_splitk_reduce(const float* P, int splits, int rows, int cols, float alpha, float beta, void* C,
+                                 long long ldc, bool is_int, cudaStream_t s);
+
+// Number of kernel launches the library has issued (all translation units).
+void count_launch(int n = 1);
+
+}  // namespace g3

@@ -1,0 +1,164 @@
+// prepass.cuh -- memory-bound operand preparation and epilogue-only kernels.
+//
+// These are the GPU form of the paper's packing step (Section 5.3): copies that
+// put an operand in the layout and number format the blocked kernel consumes,
+// paid once per operand so that the O(mnk) work reads a friendly layout.
+//   split_bf16      FP32 -> (hi, lo) bfloat16 planes for the FP32-accurate mode
+//   convert_bf16    FP32 -> bfloat16 (round to nearest even)
+//   int8_to_bf16    int8 -> bfloat16 (exact)
+//   pack_rows       byte copy of a strided matrix into a 16-byte-aligned one
+//   absmax / quantize_e4m3   per-tensor FP8 scaling
+//   scale_c         C := beta*C (the k == 0 / alpha == 0 cases)
+//   splitk_reduce   C := alpha * sum_s P[s] + beta*C in a fixed split order
+// Rows go to blockIdx.y (grid-stride) and columns to threads, 4 per thread, so
+// that every warp reads and writes contiguous runs of a row.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cstdint>
+
+namespace g3 {
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_value(uint16_t b) {
+  return __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+// hi = bf16(x), lo = bf16(x - hi); x - hi is exact in FP32.
+__global__ void split_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                  uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, long long ldy) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = x + r * ldx;
+    uint16_t* hr = hi + r * ldy;
+    uint16_t* lr = lo + r * ldy;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < cols; c += gridDim.x * blockDim.x * 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (c + u < cols) {
+          const float v = xr[c + u];
+          const uint16_t h = bf16_bits(v);
+          hr[c + u] = h;
+          lr[c + u] = bf16_bits(v - bf16_value(h));
+        }
+      }
+    }
+  }
+}
+
+__global__ void convert_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                    uint16_t* __restrict__ y, long long ldy) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = x + r * ldx;
+    uint16_t* yr = y + r * ldy;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < cols; c += gridDim.x * blockDim.x * 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c + u < cols) yr[c + u] = bf16_bits(xr[c + u]);
+    }
+  }
+}
+
+__global__ void int8_to_bf16_kernel(const int8_t* __restrict__ x, int rows, int cols, long long ldx,
+                                    uint16_t* __restrict__ y, long long ldy) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int8_t* xr = x + r * ldx;
+    uint16_t* yr = y + r * ldy;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < cols; c += gridDim.x * blockDim.x * 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c + u < cols) yr[c + u] = bf16_bits(static_cast<float>(xr[c + u]));
+    }
+  }
+}
+
+// Copy `cols` elements of `esize` bytes per row from a strided source into a
+// destination whose rows start on 16-byte boundaries.
+__global__ void pack_rows_kernel(const uint8_t* __restrict__ x, int rows, long long row_bytes, long long ldx_bytes,
+                                 uint8_t* __restrict__ y, long long ldy_bytes) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const uint8_t* xr = x + r * ldx_bytes;
+    uint8_t* yr = y + r * ldy_bytes;
+    for (long long c = blockIdx.x * blockDim.x + threadIdx.x; c < row_bytes; c += (long long)gridDim.x * blockDim.x)
+      yr[c] = xr[c];
+  }
+}
+
+// amax of |x| as the bit pattern of a non-negative float (monotone as unsigned).
+__global__ void absmax_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                              unsigned int* __restrict__ amax_bits) {
+  float m = 0.f;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = x + r * ldx;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+      const float a = fabsf(xr[c]);
+      m = (a > m) ? a : m;   // NaN never wins the comparison
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  __shared__ float wmax[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) wmax[w] = m;
+  __syncthreads();
+  if (w == 0) {
+    m = (l < (int)(blockDim.x >> 5)) ? wmax[l] : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (l == 0) atomicMax(amax_bits, __float_as_uint(m));
+  }
+}
+
+// scale = amax / 448 (1 when amax == 0); code = e4m3_satfinite(x / scale).
+__global__ void quantize_e4m3_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                     const unsigned int* __restrict__ amax_bits, uint8_t* __restrict__ q,
+                                     long long ldq, float* __restrict__ scale_out) {
+  const float amax = __uint_as_float(*amax_bits);
+  const float scale = (amax > 0.f) ? __fdiv_rn(amax, 448.0f) : 1.0f;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && scale_out) *scale_out = scale;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = x + r * ldx;
+    uint8_t* qr = q + r * ldq;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
+      qr[c] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(__fdiv_rn(xr[c], scale), __NV_SATFINITE, __NV_E4M3));
+  }
+}
+
+template <typename TC>
+__global__ void scale_c_kernel(TC* __restrict__ C, int rows, int cols, long long ldc, float beta) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    TC* cr = C + r * ldc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+      if (beta == 0.f) cr[c] = TC(0);
+      else cr[c] = static_cast<TC>(beta * static_cast<float>(cr[c]));
+    }
+  }
+}
+
+// Deterministic split-K reduction: partial sums are added in split order 0..S-1.
+// INT: partials hold integer values exactly (|x| <= 2^24); they are converted
+// and summed in int32, then C (beta in {0, 1}) is added.
+template <bool INT>
+__global__ void splitk_reduce_kernel(const float* __restrict__ P, int splits, int rows, int cols, float alpha,
+                                     float beta, void* C, long long ldc) {
+  const long long plane = (long long)rows * cols;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+      const long long off = (long long)r * cols + c;
+      if (INT) {
+        int s32 = 0;
+        for (int s = 0; s < splits; ++s) s32 += __float2int_rn(P[s * plane + off]);
+        int* cp = static_cast<int*>(C) + r * ldc + c;
+        *cp = (beta != 0.f) ? (*cp + s32) : s32;
+      } else {
+        float sum = 0.f;
+        for (int s = 0; s < splits; ++s) sum += P[s * plane + off];
+        float* cp = static_cast<float*>(C) + r * ldc + c;
+        *cp = (beta != 0.f) ? fmaf(alpha, sum, beta * *cp) : alpha * sum;
+      }
+    }
+  }
+}
+
+}  // namespace g3

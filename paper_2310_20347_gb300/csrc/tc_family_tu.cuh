@@ -1,0 +1,33 @@
+// tc_family_tu.cuh -- instantiates the members of the generated family whose
+// mode is G3_TU_MODE and registers their launchers under G3_TU_REGISTER.
+#include "family_gen.inc"
+#include "internal.h"
+
+namespace g3 {
+namespace {
+
+template <int BM, int ST, int MODE>
+cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int grid, cudaStream_t s) {
+  using Cfg = TcConfig<BM, ST, MODE>;
+  auto kern = tc_gemm_kernel<BM, ST, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, Cfg::kThreads, Cfg::kSmemBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int IDX, int MODE, int BM, int ST>
+void add_member(FamilyEntry* t) {
+  if constexpr (MODE == G3_TU_MODE) {
+    t[IDX] = FamilyEntry{IDX, MODE, BM, ST, (int)TcConfig<BM, ST, MODE>::kSmemBytes, &launch_tc<BM, ST, MODE>};
+  }
+}
+
+}  // namespace
+
+#define G3_ADD_MEMBER(idx, mode, bm, st) add_member<idx, mode, bm, st>(table);
+void G3_TU_REGISTER(FamilyEntry* table) { G3_FAMILY_LIST(G3_ADD_MEMBER) }
+#undef G3_ADD_MEMBER
+
+}  // namespace g3

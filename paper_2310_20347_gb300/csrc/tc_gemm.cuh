@@ -1,0 +1,336 @@
+// tc_gemm.cuh -- the tensor-core member of the blocked-GEMM family (sm_103a).
+//
+// C := beta*C + alpha*A*B with A (m x k) and B (k x n) row-major, computed by a
+// persistent, warp-specialised kernel:
+//
+//   warp 0      TMA producer: streams k-blocks of A and B into a STAGES-deep ring
+//               of 128-byte-swizzled shared-memory tiles (the packed buffers Ac, Bc
+//               of the paper's Section 3.1 / Figure "packing": TMA writes them in
+//               exactly the layout the tensor core reads, so packing costs no pass)
+//   warp 1      MMA issuer: one thread issues tcgen05.mma per 16-element (BF16) or
+//               32-element (FP8) k-step; the accumulator micro-tile lives in TMEM
+//               (the "C resident" micro-kernel of Section 4.1 with TMEM in place of
+//               the register file), double-buffered across output tiles
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, alpha/beta, stores
+//
+// Orientation.  The MMA computes D = Bt * At, i.e. the transpose of the C tile:
+// TMEM lane = column j of C (128 per tile), TMEM column = row i of C (BM_T per
+// tile).  The MMA's A operand is the k x 128 slice of B (stored n-contiguous, so
+// "MN-major"), its B operand the BM_T x k slice of A (k-contiguous, "K-major").
+// Each epilogue thread then owns one column of C and a warp's store of one row
+// is 32 consecutive floats: every global store is a full 128-byte line.
+//
+// The blocked loops of the paper's baseline algorithm (Figure "B3A2C0") map to:
+// L1/L3 (jc, ic) -> the persistent tile walk with a banded raster (a band of
+// `raster` m-tiles walked m-fastest keeps that band's A panels and the current
+// B panels in L2); L2 (pc) -> the k-block loop, optionally split across CTAs
+// (split-K, the analogue of the C-in-cache variants of Section 7); L4/L5 (jr, ir)
+// -> the 128 x BM_T tile of one MMA; L6 (pr) -> the k-steps of the MMA.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "ptx.cuh"
+
+namespace g3 {
+
+enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2 };
+enum OutMode : int { OUT_F32 = 0, OUT_I32 = 1, OUT_PARTIAL = 2 };
+
+// Watchdog status codes (written to the device status word; see g3gemm.h).
+enum : int {
+  WD_PRODUCER_EMPTY = 0x101,
+  WD_MMA_FULL = 0x102,
+  WD_MMA_TMEM_EMPTY = 0x103,
+  WD_EPI_TMEM_FULL = 0x104,
+  WD_DRAIN = 0x105,
+};
+
+struct TcParams {
+  int m, n, k;
+  int tiles_m, tiles_n;   // ceil(m / BM_T), ceil(n / 128)
+  int splits;             // number of k-splits (1 = none)
+  int kb_per_split;       // k-blocks handled by one split
+  int num_kb;             // ceil(k / BK)
+  int raster;             // band width, in m-tiles, of the tile walk
+  float alpha, beta;
+  const float* scale_a;   // FP8 per-tensor scales (device, may be null = 1)
+  const float* scale_b;
+  void* C;                // float (OUT_F32) or int32 (OUT_I32)
+  long long ldc;
+  float* partial;         // OUT_PARTIAL: [splits][m][n] float
+  int out_mode;
+  unsigned long long timeout_ns;
+  int* status;
+  int debug_withhold;     // test hook: producer iteration whose stage never fills (-1: none)
+};
+
+template <int MODE>
+struct TcTraits {
+  static constexpr int kPlanes = (MODE == TC_3XBF16) ? 2 : 1;   // hi/lo operand planes
+  static constexpr int kElem = (MODE == TC_FP8) ? 1 : 2;        // bytes per element
+  static constexpr int kBK = 128 / kElem;                        // k per block: one 128-B row
+  static constexpr int kKStep = 32 / kElem;                      // k per MMA instruction
+  static constexpr int kKSteps = kBK / kKStep;                   // = 4
+  static constexpr int kBoxN = 128 / kElem;                      // n per TMA box of B
+  static constexpr int kNBoxes = 128 / kBoxN;                    // boxes per 128-wide n tile
+  static constexpr uint32_t kBtBytes = 128 * 128;                // 128 n x 128 bytes of k
+  static constexpr uint32_t kAFmt = (MODE == TC_FP8) ? 0u : 1u;  // E4M3 : BF16
+  // Leading byte offset of the MN-major Bt operand: the distance between its
+  // 128-byte-wide n groups (one TMA box each).  With a single group (FP8) the
+  // field is unused; 1024 keeps every address inside the stage either way.
+  static constexpr uint32_t kBtLBO = (kNBoxes > 1) ? kBK * 128 : 1024;
+};
+
+template <int BM_T, int STAGES, int MODE>
+struct TcConfig {
+  using T = TcTraits<MODE>;
+  static constexpr uint32_t kABytes = BM_T * 128;                      // BM_T rows x 128 B
+  static constexpr uint32_t kPlaneBytes = T::kBtBytes + kABytes;       // one plane of a stage
+  static constexpr uint32_t kStageBytes = T::kPlanes * kPlaneBytes;
+  static constexpr uint32_t kTmemCols = 2 * BM_T;                      // two accumulators
+  static constexpr uint32_t kBarBytes = 256;
+  static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kBarBytes;
+  static constexpr int kThreads = 192;
+  static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
+  static_assert(kSmemBytes <= 232448, "shared memory budget");
+  static_assert(8 * (2 * STAGES + 5) + 8 <= (int)kBarBytes, "barrier area");
+};
+
+__device__ __forceinline__ void decode_tile(int t, const TcParams& p, int& tm, int& tn, int& s) {
+  const int per_split = p.tiles_m * p.tiles_n;
+  s = t / per_split;
+  const int r = t - s * per_split;
+  const int G = p.raster;
+  const int band = r / (G * p.tiles_n);
+  const int in_band = r - band * G * p.tiles_n;
+  const int rows = min(G, p.tiles_m - band * G);
+  tm = band * G + in_band % rows;
+  tn = in_band / rows;
+}
+
+template <int BM_T, int STAGES, int MODE>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
+                   const TcParams p) {
+  using T = TcTraits<MODE>;
+  using Cfg = TcConfig<BM_T, STAGES, MODE>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::kStageBytes);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tmem_full = empty + STAGES;
+  uint64_t* tmem_empty = tmem_full + 2;
+  uint64_t* drain = tmem_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tmem_full[a], 1);
+      mbar_init(&tmem_empty[a], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+    if (MODE == TC_3XBF16) {
+      tma_prefetch_desc(&tmA_lo);
+      tma_prefetch_desc(&tmB_lo);
+    }
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  Watchdog wd{p.timeout_ns, p.status, abort_flag};
+  const int total_tiles = p.tiles_m * p.tiles_n * p.splits;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
+        int tm, tn, s;
+        decode_tile(t, p, tm, tn, s);
+        const int kb0 = s * p.kb_per_split;
+        const int kb1 = min(p.num_kb, kb0 + p.kb_per_split);
+        const int m0 = tm * BM_T, n0 = tn * 128;
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
+          if (!wait_parity(&empty[stage], ph ^ 1u, wd, WD_PRODUCER_EMPTY)) { ok = false; break; }
+          if ((int)it == p.debug_withhold) continue;   // failure-detection test: never arrive
+          mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+          uint8_t* st = smem + stage * Cfg::kStageBytes;
+          const int k0 = kb * T::kBK;
+#pragma unroll
+          for (int pl = 0; pl < T::kPlanes; ++pl) {
+            uint8_t* bt = st + pl * Cfg::kPlaneBytes;
+            uint8_t* at = bt + T::kBtBytes;
+            const CUtensorMap* mb = (pl == 0) ? &tmB : &tmB_lo;
+            const CUtensorMap* ma = (pl == 0) ? &tmA : &tmA_lo;
+#pragma unroll
+            for (int h = 0; h < T::kNBoxes; ++h)
+              tma_load_2d(bt + h * (T::kBK * 128), mb, n0 + h * T::kBoxN, k0, &full[stage]);
+            tma_load_2d(at, ma, k0, m0, &full[stage]);
+          }
+        }
+      }
+      // Let every load already issued land before the CTA can retire.
+      const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+      for (uint32_t j = first; j < it; ++j) {
+        uint64_t t0 = globaltimer_ns();
+        while (!mbar_try_wait(&full[j % STAGES], (j / STAGES) & 1u))
+          if (globaltimer_ns() - t0 > p.timeout_ns) { atomicCAS(p.status, 0, WD_DRAIN); break; }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/true, /*b_mn=*/false, 128, BM_T);
+      uint32_t it = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++lt) {
+        int tm, tn, s;
+        decode_tile(t, p, tm, tn, s);
+        const int kb0 = s * p.kb_per_split;
+        const int kb1 = min(p.num_kb, kb0 + p.kb_per_split);
+        const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+        if (!wait_parity(&tmem_empty[acc], aph ^ 1u, wd, WD_MMA_TMEM_EMPTY)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * BM_T;
+        uint32_t accumulate = 0;
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
+          if (!wait_parity(&full[stage], ph, wd, WD_MMA_FULL)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + stage * Cfg::kStageBytes);
+#pragma unroll
+          for (int ks = 0; ks < T::kKSteps; ++ks) {
+            // MN-major Bt: a k-step is kKStep whole 128-byte rows (kKStep/8 atoms);
+            // LBO = distance between 64-/128-wide n boxes, SBO = 8 rows.
+            // K-major A: a k-step is 32 bytes inside the swizzled 128-byte row.
+            const uint32_t bt_off = ks * T::kKStep * 128;
+            const uint32_t a_off = T::kBtBytes + ks * 32;
+            const uint64_t bt_hi = smem_desc_sw128(st + bt_off, T::kBtLBO, 1024);
+            const uint64_t a_hi = smem_desc_sw128(st + a_off, 16, 1024);
+            if (MODE == TC_3XBF16) {
+              const uint32_t lo = Cfg::kPlaneBytes;
+              const uint64_t bt_lo = smem_desc_sw128(st + lo + bt_off, T::kBtLBO, 1024);
+              const uint64_t a_lo = smem_desc_sw128(st + lo + a_off, 16, 1024);
+              // small terms first: Bhi*Alo, Blo*Ahi, then Bhi*Ahi (Blo*Alo dropped)
+              mma_f16(d_tmem, bt_hi, a_lo, idesc, accumulate);
+              mma_f16(d_tmem, bt_lo, a_hi, idesc, 1u);
+              mma_f16(d_tmem, bt_hi, a_hi, idesc, 1u);
+            } else if (MODE == TC_FP8) {
+              mma_f8(d_tmem, bt_hi, a_hi, idesc, accumulate);
+            } else {
+              mma_f16(d_tmem, bt_hi, a_hi, idesc, accumulate);
+            }
+            accumulate = 1u;
+          }
+          mma_commit(&empty[stage]);   // frees the stage when these MMAs finish
+        }
+        if (!ok) break;
+        mma_commit(&tmem_full[acc]);   // accumulator ready for the epilogue
+      }
+      // Make sure no MMA is in flight before TMEM is released.
+      mma_commit(drain);
+      uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain, 0))
+        if (globaltimer_ns() - t0 > p.timeout_ns) { atomicCAS(p.status, 0, WD_DRAIN); break; }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                  // TMEM lane quarter this warp may access
+    float alpha = p.alpha;
+    if (MODE == TC_FP8) {
+      const float sa = p.scale_a ? *p.scale_a : 1.0f;
+      const float sb = p.scale_b ? *p.scale_b : 1.0f;
+      alpha = alpha * (sa * sb);
+    }
+    const float beta = p.beta;
+    uint32_t lt = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
+      int tm, tn, s;
+      decode_tile(t, p, tm, tn, s);
+      const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+      bool ok = wait_parity(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      const int m0 = tm * BM_T;
+      const int j = tn * 128 + q * 32 + lane;              // column of C owned by this thread
+      const bool jok = j < p.n;
+      const int rows_here = min(BM_T, p.m - m0);
+      const int nchunks = (rows_here + 31) >> 5;
+      const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BM_T;
+      for (int c = 0; c < nchunks; ++c) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tbase + c * 32, r);
+        tmem_ld_wait();
+        if (c == nchunks - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tmem_empty[acc]);
+        }
+        const int i0 = m0 + c * 32;
+        const int iend = min(32, p.m - i0);
+        if (jok) {
+          if (p.out_mode == OUT_F32) {
+            float* cp = static_cast<float*>(p.C) + (long long)i0 * p.ldc + j;
+            if (beta != 0.0f) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                if (i < iend) cp[i * p.ldc] = fmaf(alpha, __uint_as_float(r[i]), beta * cp[i * p.ldc]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                if (i < iend) cp[i * p.ldc] = alpha * __uint_as_float(r[i]);
+            }
+          } else if (p.out_mode == OUT_I32) {
+            int* cp = static_cast<int*>(p.C) + (long long)i0 * p.ldc + j;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if (i < iend) {
+                const int v = __float2int_rn(__uint_as_float(r[i]));
+                cp[i * p.ldc] = (beta != 0.0f) ? (cp[i * p.ldc] + v) : v;
+              }
+            }
+          } else {
+            float* pp = p.partial + (long long)s * p.m * p.n + (long long)i0 * p.n + j;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < iend) pp[(long long)i * p.n] = __uint_as_float(r[i]);
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+  }
+}
+
+}  // namespace g3

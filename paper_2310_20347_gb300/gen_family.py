@@ -1,0 +1,102 @@
+"""Generator of the tensor-core kernel family (run at build time).
+
+The paper's contribution is a generator that emits a whole family of blocked
+GEMM routines and micro-kernels from a few parameters (Sections 5-7), plus a
+search that keeps the best member per problem shape (Section 8.4).  This
+script plays the generator's role for the GPU kernels: it enumerates the
+parameter space
+
+    mode     bf16 | 3xbf16 | fp8      operand format of the MMA
+    bm       64 | 128 | 256           output rows per tile = MMA N (tile is bm x 128)
+    stages   2 .. 8                   depth of the shared-memory k-block ring
+
+filters it with the hardware's analytical limits -- the shared-memory budget
+of one CTA and the 512 TMEM columns of an SM, the GPU counterpart of the cache
+model that fixes (mc, nc, kc) in Section 8.2 -- keeps the deepest pipeline that
+fits plus one shallower variant, and writes
+
+    csrc/family_gen.inc   an X-macro list the library instantiates
+    family.json           the same list for the planner's tests and tooling
+
+Split-K and the raster band are run-time knobs of every member, and the
+operand "residency" of the paper's variant names (which operand stays in which
+memory level) is expressed by the raster: a band walked m-fastest keeps B's
+panels hot in L2 (B3A2C0-like), the transposed walk keeps A's (A3B2C0-like).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+SMEM_LIMIT = 232448          # bytes of dynamic shared memory per CTA (227 KiB)
+TMEM_COLUMNS = 512           # 32-bit columns per SM
+BAR_BYTES = 256
+ALIGN_SLACK = 1024
+
+MODES = {            # name: (planes, element bytes)
+    "bf16": (1, 2),
+    "3xbf16": (2, 2),
+    "fp8": (1, 1),
+}
+MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8"}
+BMS = (256, 128, 64)
+
+
+def stage_bytes(mode: str, bm: int) -> int:
+    planes, _elem = MODES[mode]
+    bt = 128 * 128           # 128 columns of B x 128 bytes of k
+    a = bm * 128             # bm rows of A x 128 bytes of k
+    return planes * (bt + a)
+
+
+def smem_bytes(mode: str, bm: int, stages: int) -> int:
+    return ALIGN_SLACK + stages * stage_bytes(mode, bm) + BAR_BYTES
+
+
+def enumerate_family():
+    members = []
+    for mode in MODES:
+        for bm in BMS:
+            if 2 * bm > TMEM_COLUMNS:
+                continue
+            fits = [s for s in range(2, 9) if smem_bytes(mode, bm, s) <= SMEM_LIMIT]
+            if not fits:
+                continue
+            chosen = [max(fits)]
+            if max(fits) - 1 in fits and max(fits) > 3:
+                chosen.append(max(fits) - 1)
+            for st in chosen:
+                members.append({"mode": mode, "bm": bm, "stages": st,
+                                "smem": smem_bytes(mode, bm, st)})
+    for i, m in enumerate(members):
+        m["index"] = i
+    return members
+
+
+def write(out_dir: str) -> list:
+    members = enumerate_family()
+    lines = ["// Generated by gen_family.py -- do not edit.",
+             "// X(index, mode, bm, stages)",
+             "#define G3_FAMILY_LIST(X) \\"]
+    for m in members:
+        lines.append(f"  X({m['index']}, {MODE_ENUM[m['mode']]}, {m['bm']}, {m['stages']}) \\")
+    lines.append("")
+    lines.append(f"#define G3_FAMILY_SIZE {len(members)}")
+    text = "\n".join(lines) + "\n"
+    inc = os.path.join(out_dir, "csrc", "family_gen.inc")
+    old = open(inc).read() if os.path.exists(inc) else None
+    if old != text:
+        with open(inc, "w") as f:
+            f.write(text)
+    js = os.path.join(out_dir, "family.json")
+    jtext = json.dumps(members, indent=1) + "\n"
+    old = open(js).read() if os.path.exists(js) else None
+    if old != jtext:
+        with open(js, "w") as f:
+            f.write(jtext)
+    return members
+
+
+if __name__ == "__main__":
+    for m in write(os.path.dirname(os.path.abspath(__file__))):
+        print(m)

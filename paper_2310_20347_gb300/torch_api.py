@@ -1,0 +1,94 @@
+"""Torch-tensor front end of the C ABI: shapes, strides, devices and streams in,
+status codes out.  PyTorch supplies device memory and streams only; every step
+of the computation runs in libg3gemm.so.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+from ._lib import G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP8_E4M3, G3_INT8, check
+
+_ELEM = {G3_F32: (torch.float32, torch.float32), G3_F32_3XBF16: (torch.float32, torch.float32),
+         G3_BF16: (torch.bfloat16, torch.float32), G3_FP8_E4M3: (torch.uint8, torch.float32),
+         G3_INT8: (torch.int8, torch.int32)}
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _ld(t: torch.Tensor, name: str) -> int:
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    return max(t.stride(0), t.shape[1], 1)
+
+
+def _ptr(t):
+    return t.data_ptr() if t is not None else None
+
+
+def gemm_args(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, scale_a=None, scale_b=None, config=-1,
+              split_k=0, raster=0, workspace=None):
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or tuple(C.shape) != (m, n):
+        raise ValueError(f"shape mismatch: A {tuple(A.shape)} B {tuple(B.shape)} C {tuple(C.shape)}")
+    in_t, out_t = _ELEM[dtype]
+    for t, want, name in ((A, in_t, "A"), (B, in_t, "B"), (C, out_t, "C")):
+        if t.dtype != want and not (dtype == G3_FP8_E4M3 and t.dtype == torch.float8_e4m3fn and name != "C"):
+            raise TypeError(f"{name} must be {want} for dtype {dtype}, got {t.dtype}")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    a = _lib.g3_gemm_args_init()
+    a.m, a.n, a.k = m, n, k
+    a.alpha, a.beta = float(alpha), float(beta)
+    a.A, a.lda = _ptr(A), _ld(A, "A")
+    a.B, a.ldb = _ptr(B), _ld(B, "B")
+    a.C, a.ldc = _ptr(C), _ld(C, "C")
+    a.dtype = dtype
+    a.scale_a, a.scale_b = _ptr(scale_a), _ptr(scale_b)
+    if workspace is not None:
+        a.workspace, a.workspace_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    a.config, a.split_k, a.raster = config, split_k, raster
+    return a
+
+
+def gemm(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, stream=None, **kw):
+    """C := beta*C + alpha*A@B in place through g3_gemm_ex; returns C."""
+    a = gemm_args(A, B, C, alpha, beta, dtype, **kw)
+    check(_lib.g3_gemm_ex(a, _stream(stream)), "g3_gemm_ex")
+    return C
+
+
+def convert_bf16(x: torch.Tensor, stream=None) -> torch.Tensor:
+    y = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    check(_lib.g3_convert_bf16(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), y.data_ptr(),
+                               max(x.shape[1], 1), _stream(stream)), "g3_convert_bf16")
+    return y
+
+
+def split_bf16(x: torch.Tensor, stream=None):
+    hi = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    lo = torch.empty_like(hi)
+    check(_lib.g3_split_bf16(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), hi.data_ptr(),
+                             lo.data_ptr(), max(x.shape[1], 1), _stream(stream)), "g3_split_bf16")
+    return hi, lo
+
+
+def quantize_fp8(x: torch.Tensor, stream=None):
+    """(codes uint8 like x, scale float32 tensor of one element)."""
+    q = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    s = torch.empty(1, dtype=torch.float32, device=x.device)
+    check(_lib.g3_quantize_fp8(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), q.data_ptr(),
+                               max(x.shape[1], 1), s.data_ptr(), _stream(stream)), "g3_quantize_fp8")
+    return q, s
+
+
+def device_status():
+    st, code = _lib.g3_get_last_device_status()
+    return st, code

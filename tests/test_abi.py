@@ -1,0 +1,95 @@
+"""CPU checks of the boundary: the library builds, loads and exports every
+symbol include/g3gemm.h declares; argument validation returns the documented
+positional codes without touching a GPU; the generated family and the planner
+(host logic) behave as specified."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_20347_gb300 import _lib, build
+    build()
+    return _lib
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "g3gemm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(g3_\w+)\s*\(", text)))
+
+
+def test_exports_match_header(lib):
+    declared = header_symbols()
+    assert sorted(lib.EXPORTED) == declared
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in declared:
+        assert hasattr(so, name), name
+
+
+def test_library_has_no_oracle_dependency(lib):
+    # the product library must not link or embed the test oracle
+    data = open(lib.LIB_PATH, "rb").read()
+    assert b"oracle_gemm" not in data and b"liboracle" not in data
+
+
+def test_argument_errors(lib):
+    L = lib
+    p = 16  # any non-null "device" address: validation fails before any use
+    assert L.g3_gemm(-1, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, 0) == -101
+    assert L.g3_gemm(4, -1, 4, 1.0, p, 4, p, 4, 0.0, p, 4, 0) == -102
+    assert L.g3_gemm(4, 4, -1, 1.0, p, 4, p, 4, 0.0, p, 4, 0) == -103
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 7, p, 4, 0.0, p, 4, 0) == -106
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 3, 0.0, p, 4, 0) == -108
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 3, 0) == -111
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 9) == -112
+    assert L.g3_gemm(4, 4, 8, 1.0, None, 8, p, 4, 0.0, p, 4, 0) == -105
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, None, 4, 0.0, p, 4, 0) == -107
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, None, 4, 0) == -110
+    # INT8 accepts only alpha == 1 and beta in {0, 1}
+    assert L.g3_gemm(4, 4, 8, 2.0, p, 8, p, 4, 0.0, p, 4, 4) == L.G3_ERR_UNSUPPORTED
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.5, p, 4, 4) == L.G3_ERR_UNSUPPORTED
+    assert L.g3_gemm(4, 4, 131073, 1.0, p, 131073, p, 4, 0.0, p, 4, 4) == L.G3_ERR_UNSUPPORTED
+    # m == 0 or n == 0: a no-op, even with null pointers
+    assert L.g3_gemm(0, 4, 8, 1.0, None, 8, None, 4, 0.0, None, 4, 0) == 0
+    assert L.g3_gemm(4, 0, 8, 1.0, None, 8, None, 1, 0.0, None, 1, 0) == 0
+    assert L.g3_status_string(-5) == "device wait timed out"
+    assert L.g3_debug_withhold_next(0) == -101
+
+
+def test_family_matches_generator(lib):
+    from paper_2310_20347_gb300 import gen_family
+    members = gen_family.enumerate_family()
+    assert lib.g3_family_size() == len(members)
+    with open(os.path.join(ROOT, "paper_2310_20347_gb300", "family.json")) as f:
+        assert json.load(f) == members
+    for m in members:
+        d = lib.g3_family_describe(m["index"])
+        assert f"mode={m['mode']} bm={m['bm']} " in d and f"stages={m['stages']}" in d
+        assert m["smem"] <= gen_family.SMEM_LIMIT and 2 * m["bm"] <= gen_family.TMEM_COLUMNS
+
+
+def test_planner_choices(lib):
+    from paper_2310_20347_gb300 import gen_family
+    fam = gen_family.enumerate_family()
+    L = lib
+    # large square: the widest tile
+    st, cfg, sk, rs = L.g3_plan_query(16384, 16384, 16384, L.G3_F32_3XBF16)
+    assert st == 0 and fam[cfg]["mode"] == "3xbf16" and fam[cfg]["bm"] == 256 and sk == 1
+    # Cout = 64 convolution layer: a 64-row tile, no split
+    st, cfg, sk, rs = L.g3_plan_query(64, 200704, 147, L.G3_BF16)
+    assert fam[cfg]["bm"] == 64 and sk == 1
+    # few output tiles, deep k: split-K
+    st, cfg, sk, rs = L.g3_plan_query(512, 49, 4608, L.G3_BF16)
+    assert sk > 1
+    # INT8 is exact only in k-chunks of at most 1024
+    st, cfg, sk, rs = L.g3_plan_query(8192, 8192, 8192, L.G3_INT8)
+    assert sk == 8
+    st, cfg, sk, rs = L.g3_plan_query(128, 128, 100, L.G3_F32)
+    assert cfg == -1

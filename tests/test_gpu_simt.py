@@ -1,0 +1,95 @@
+"""Parity of the FP32 SIMT kernel (the plain method) with the binary64 oracle:
+max |C - C_ref| / (|alpha| |A| |B|) <= 2e-6, bit-exact on integer inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import check_guard, dev, guarded, rel_err
+from paper_2310_20347_gb300 import G3_F32, synth, torch_api
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-6
+
+
+def run(p, ldpad=(0, 0, 0)):
+    A = dev(p.A)
+    B = dev(p.B)
+    if ldpad[0]:
+        A = torch.zeros(p.m, p.k + ldpad[0], device="cuda")[:, :p.k].copy_(A) if p.k else A
+    if ldpad[1]:
+        B = torch.zeros(p.k, p.n + ldpad[1], device="cuda")[:, :p.n].copy_(B) if p.n else B
+    full, C = guarded(p.m, p.n, p.C, pad_cols=max(5, ldpad[2]))
+    torch_api.gemm(A, B, C, p.alpha, p.beta, dtype=G3_F32)
+    torch.cuda.synchronize()
+    check_guard(full, p.m, p.n, pad_cols=max(5, ldpad[2]))
+    return C.cpu().numpy()
+
+
+def check(p, tol=TOL, **kw):
+    got = run(p, **kw)
+    ref = oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta)
+    D = oracle.absprod(p.A, p.B, p.alpha)
+    e = rel_err(got, ref, D, None if p.C is None else p.beta * p.C.astype(np.float64))
+    assert e <= tol, e
+    return e
+
+
+def test_config_512_cube():
+    # plain FP32 GEMM C := A*B, m = n = k = 512, uniform [-1, 1] from seed 0, beta = 0
+    p = synth.uniform_problem(512, 512, 512, seed=0)
+    e = check(p)
+    print(f"simt 512^3 rel-err {e:.3e}")
+
+
+EDGE = (1, 2, 3, 15, 16, 17, 63, 64, 65, 127, 128, 129, 255, 257)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_edge_shapes(seed):
+    r = np.random.default_rng(100 + seed)
+    for _ in range(8):
+        m, n, k = (int(x) for x in r.choice(EDGE, 3))
+        p = synth.uniform_problem(m, n, k, seed=seed, alpha=-0.5, beta=0.5)
+        check(p)
+
+
+def test_integer_inputs_bit_exact():
+    p = synth.small_int_problem(200, 300, 1000, seed=3, alpha=1.0, beta=2.0)
+    got = run(p)
+    ref = oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta)
+    assert np.array_equal(got.astype(np.float64), ref)
+
+
+def test_unaligned_leading_dimensions():
+    p = synth.uniform_problem(131, 67, 301, seed=4, alpha=1.5, beta=-1.0)
+    check(p, ldpad=(1, 3, 6))
+
+
+def test_beta_zero_overwrites_nan():
+    p = synth.uniform_problem(70, 90, 40, seed=5)
+    A, B = dev(p.A), dev(p.B)
+    full, C = guarded(p.m, p.n, np.full((p.m, p.n), np.nan, np.float32))
+    torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_F32)
+    assert torch.isfinite(C).all()
+    check_guard(full, p.m, p.n)
+
+
+def test_alpha_zero_and_k_zero():
+    p = synth.uniform_problem(33, 44, 10, seed=6, beta=0.25)
+    full, C = guarded(p.m, p.n, p.C)
+    A = torch.full((p.m, p.k), float("nan"), device="cuda")
+    B = torch.full((p.k, p.n), float("nan"), device="cuda")
+    torch_api.gemm(A, B, C, 0.0, 0.25, dtype=G3_F32)
+    assert np.array_equal(C.cpu().numpy(), (np.float32(0.25) * p.C))
+    full2, C2 = guarded(p.m, p.n, p.C)
+    torch_api.gemm(torch.empty(p.m, 0, device="cuda"), torch.empty(0, p.n, device="cuda"), C2, 1.0, 0.25,
+                   dtype=G3_F32)
+    assert np.array_equal(C2.cpu().numpy(), (np.float32(0.25) * p.C))
+
+
+def test_deterministic():
+    p = synth.uniform_problem(300, 300, 777, seed=7, beta=0.5)
+    a = run(p)
+    b = run(p)
+    assert np.array_equal(a, b)
