@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--simt-steps", type=int, default=3)
+    ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -208,7 +209,8 @@ def main():
     flops = 2.0 * n * n * n
 
     def step(dtype, out):
-        torch_api.gemm(A, B, out, 1.0, 0.5, dtype=dtype, stream=stream)
+        cfg = args.config if dtype == G3_F32_3XBF16 else -1
+        torch_api.gemm(A, B, out, 1.0, 0.5, dtype=dtype, stream=stream, config=cfg)
 
     # --- correctness on sampled rows of the full-size problem (same launch config)
     import oracle
@@ -307,7 +309,8 @@ def main():
     achieved = tensor_flops / (per_launch_ms * 1e-3) / 1e12
     peak = float(peaks["bf16_tflops"])
     st = _lib.g3_plan_query(n, n, n, G3_F32_3XBF16)
-    member = _lib.g3_family_describe(st[1]) if st[0] == 0 and st[1] >= 0 else "?"
+    cfg_used = args.config if args.config >= 0 else st[1]
+    member = _lib.g3_family_describe(cfg_used) if st[0] == 0 and cfg_used >= 0 else "?"
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     simt_tflops = flops / (simt_ms * 1e-3) / 1e12
     sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
@@ -327,7 +330,7 @@ def main():
         "speedup_vs_simt": simt_ms / (ms_max / args.steps),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "tc_gemm_kernel<256,2,TC_3XBF16>",
+                     "kernel": f"tc_gemm_kernel ({member})",
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
                      "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", peak)),
                      "per_launch_ms": per_launch_ms, "launches_timed": kern_n,

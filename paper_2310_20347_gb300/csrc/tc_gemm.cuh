@@ -89,7 +89,16 @@ struct TcConfig {
   static constexpr uint32_t kABytes = BM_T * 128;                      // BM_T rows x 128 B
   static constexpr uint32_t kPlaneBytes = T::kBtBytes + kABytes;       // one plane of a stage
   static constexpr uint32_t kStageBytes = T::kPlanes * kPlaneBytes;
-  static constexpr uint32_t kTmemCols = 2 * BM_T;                      // two accumulators
+  // The tensor core adds each MMA's products to its FP32 accumulator with
+  // truncation, so the FP32-accurate mode keeps the hi*hi products and the
+  // hi*lo + lo*hi corrections in separate accumulators (one third of the
+  // truncating updates each for the large term) and adds them, rounded to
+  // nearest, in the epilogue.  Accumulator sets are double-buffered across
+  // output tiles when TMEM (512 columns) has room.
+  static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16) ? 2 : 1;
+  static constexpr uint32_t kSetCols = kAccPerTile * BM_T;
+  static constexpr uint32_t kNumBufs = (2 * kSetCols <= 512) ? 2 : 1;
+  static constexpr uint32_t kTmemCols = kNumBufs * kSetCols;
   static constexpr uint32_t kBarBytes = 256;
   static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kBarBytes;
   static constexpr int kThreads = 192;
@@ -212,10 +221,11 @@ __global__ void __launch_bounds__(192, 1)
         decode_tile(t, p, tm, tn, s);
         const int kb0 = s * p.kb_per_split;
         const int kb1 = min(p.num_kb, kb0 + p.kb_per_split);
-        const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+        const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
         if (!wait_parity(&tmem_empty[acc], aph ^ 1u, wd, WD_MMA_TMEM_EMPTY)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + acc * BM_T;
+        const uint32_t d_tmem = tmem_base + acc * Cfg::kSetCols;   // main accumulator
+        const uint32_t d_corr = d_tmem + BM_T;                       // 3xBF16 corrections
         uint32_t accumulate = 0;
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
@@ -235,10 +245,11 @@ __global__ void __launch_bounds__(192, 1)
               const uint32_t lo = Cfg::kPlaneBytes;
               const uint64_t bt_lo = smem_desc_sw128(st + lo + bt_off, T::kBtLBO, 1024);
               const uint64_t a_lo = smem_desc_sw128(st + lo + a_off, 16, 1024);
-              // small terms first: Bhi*Alo, Blo*Ahi, then Bhi*Ahi (Blo*Alo dropped)
-              mma_f16(d_tmem, bt_hi, a_lo, idesc, accumulate);
-              mma_f16(d_tmem, bt_lo, a_hi, idesc, 1u);
-              mma_f16(d_tmem, bt_hi, a_hi, idesc, 1u);
+              // corrections Bhi*Alo + Blo*Ahi in their own accumulator, then the
+              // main term Bhi*Ahi; Blo*Alo is dropped
+              mma_f16(d_corr, bt_hi, a_lo, idesc, accumulate);
+              mma_f16(d_corr, bt_lo, a_hi, idesc, 1u);
+              mma_f16(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else if (MODE == TC_FP8) {
               mma_f8(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else {
@@ -271,7 +282,7 @@ __global__ void __launch_bounds__(192, 1)
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
       int tm, tn, s;
       decode_tile(t, p, tm, tn, s);
-      const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+      const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
       bool ok = wait_parity(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
@@ -281,11 +292,19 @@ __global__ void __launch_bounds__(192, 1)
       const bool jok = j < p.n;
       const int rows_here = min(BM_T, p.m - m0);
       const int nchunks = (rows_here + 31) >> 5;
-      const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * BM_T;
+      const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * Cfg::kSetCols;
       for (int c = 0; c < nchunks; ++c) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(tbase + c * 32, r);
-        tmem_ld_wait();
+        if (MODE == TC_3XBF16) {
+          uint32_t rc[32];
+          tmem_ld_32x32b_x32(tbase + BM_T + c * 32, rc);
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(__fadd_rn(__uint_as_float(r[i]), __uint_as_float(rc[i])));
+        } else {
+          tmem_ld_wait();
+        }
         if (c == nchunks - 1) {
           tc_fence_before();
           __syncwarp();

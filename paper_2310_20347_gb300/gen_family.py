@@ -57,7 +57,7 @@ def enumerate_family():
     members = []
     for mode in MODES:
         for bm in BMS:
-            if 2 * bm > TMEM_COLUMNS:
+            if (2 if mode == "3xbf16" else 1) * bm > TMEM_COLUMNS:
                 continue
             fits = [s for s in range(2, 9) if smem_bytes(mode, bm, s) <= SMEM_LIMIT]
             if not fits:
@@ -65,9 +65,11 @@ def enumerate_family():
             chosen = [max(fits)]
             if max(fits) - 1 in fits and max(fits) > 3:
                 chosen.append(max(fits) - 1)
+            acc_cols = (2 if mode == "3xbf16" else 1) * bm     # main (+ correction) accumulators
+            bufs = 2 if 2 * acc_cols <= TMEM_COLUMNS else 1       # double-buffered across tiles?
             for st in chosen:
                 members.append({"mode": mode, "bm": bm, "stages": st,
-                                "smem": smem_bytes(mode, bm, st)})
+                                "smem": smem_bytes(mode, bm, st), "tmem_bufs": bufs})
     for i, m in enumerate(members):
         m["index"] = i
     return members

@@ -150,6 +150,14 @@ def test_3xbf16_square_gate():
     print(f"3xbf16 1024^3 kernel {e_k:.3e} gate {e_g:.3e}")
 
 
+@pytest.mark.parametrize("config", [-1] + members("3xbf16")[:2])
+def test_3xbf16_deep_k_gate(config):
+    # k = 16384 as in the largest square: the tensor core truncates each FP32
+    # accumulation, so depth is where the accuracy of the mode is decided
+    e_k, e_g = x3_check(synth.uniform_problem(200, 300, 16384, seed=18, beta=0.5), gate=2e-6, config=config)
+    print(f"3xbf16 k=16384 config {config}: kernel {e_k:.3e} gate {e_g:.3e}")
+
+
 def test_3xbf16_split_k():
     x3_check(synth.uniform_problem(64, 100, 4096, seed=12, beta=0.5), gate=2e-6, split_k=5)
 
@@ -180,7 +188,12 @@ def fp8_check(p, config=-1):
     e_k = rel_err(got, oracle.gemm(Ad, Bd, p.C, p.alpha, p.beta), oracle.absprod(Ad, Bd, p.alpha), bc)
     e_g = rel_err(got, oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), oracle.absprod(p.A, p.B, p.alpha), bc)
     assert e_k <= 1e-4, ("kernel", e_k)
-    assert e_g <= 6e-2, ("gate", e_g)
+    if p.k >= 64:
+        assert e_g <= 6e-2, ("gate", e_g)
+    else:
+        # a handful of products: one factor pair's E4M3 rounding (each at most
+        # 2^-4 relative for normal values) is not averaged out
+        assert e_g <= 2 * 2.0 ** -4 + 2.0 ** -8, ("format bound", e_g)
     return e_k, e_g
 
 
