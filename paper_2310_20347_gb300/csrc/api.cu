@@ -170,7 +170,9 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
       if (pl.member >= 0 && g_family[pl.member].bm == f.bm) continue;   // first (deepest) variant per bm
       const long long tiles = ((m + f.bm - 1) / f.bm) * (long long)pl.tiles_n;
       const long long waves = (tiles + sms - 1) / sms;
-      const double cost = (double)waves * f.bm / tile_efficiency(f.bm);
+      // a single accumulator set serialises every tile's epilogue with the
+      // next tile's main loop (measured: 71% vs 90% of peak at 16384^3)
+      const double cost = (double)waves * f.bm / tile_efficiency(f.bm) * (f.bufs < 2 ? 1.3 : 1.0);
       if (cost < best * 0.999) {
         best = cost;
         pl.member = i;
@@ -620,7 +622,8 @@ int g3_family_describe(int index, char* buf, size_t len) {
   }
   const FamilyEntry& f = g_family[index];
   static const char* names[] = {"bf16", "3xbf16", "fp8"};
-  std::snprintf(buf, len, "mode=%s bm=%d bn=128 stages=%d smem=%d", names[f.mode], f.bm, f.stages, f.smem);
+  std::snprintf(buf, len, "mode=%s bm=%d bn=128 stages=%d smem=%d bufs=%d", names[f.mode], f.bm, f.stages, f.smem,
+                f.bufs);
   return G3_OK;
 }
 

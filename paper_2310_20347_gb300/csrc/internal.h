@@ -18,6 +18,7 @@ struct FamilyEntry {
   int bm;       // output rows per tile (= MMA N)
   int stages;   // shared-memory ring depth
   int smem;     // dynamic shared memory bytes
+  int bufs;     // TMEM accumulator sets (2: the epilogue overlaps the next tile)
   TcLaunchFn launch;
 };
 

@@ -20,7 +20,8 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int grid, cuda
 template <int IDX, int MODE, int BM, int ST>
 void add_member(FamilyEntry* t) {
   if constexpr (MODE == G3_TU_MODE) {
-    t[IDX] = FamilyEntry{IDX, MODE, BM, ST, (int)TcConfig<BM, ST, MODE>::kSmemBytes, &launch_tc<BM, ST, MODE>};
+    using Cfg = TcConfig<BM, ST, MODE>;
+    t[IDX] = FamilyEntry{IDX, MODE, BM, ST, (int)Cfg::kSmemBytes, (int)Cfg::kNumBufs, &launch_tc<BM, ST, MODE>};
   }
 }
 
