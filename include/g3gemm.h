@@ -218,6 +218,34 @@ G3_API int g3_kernel_time_ms(double* total_ms, int* launches, int reset);
  * g3_get_last_device_status() then returns G3_ERR_TIMEOUT.                   */
 G3_API int g3_debug_withhold_next(int64_t timeout_ms);
 
+/* --- Allocation-free FP32-accurate GEMM -------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory themselves or through the library:
+ * applications whose framework owns all device memory and hands it out from
+ * its own pool, processes held to a fixed memory budget, and code that must
+ * not risk the device-wide synchronisation a cudaMalloc or cudaFree can cause.
+ *
+ * Computes the same C := beta*C + alpha*A*B as g3_gemm(..., G3_F32_3XBF16)
+ * (float32 A, B, C on the device, same layout rules, same argument errors),
+ * without split-K, on `cuda_stream` (NULL = the current stream).  The hi/lo
+ * bfloat16 copies of A and B are kept in a 64 MiB array built into the library
+ * instead of allocated workspace; the call issues no cudaMalloc, cudaFree or
+ * other allocating routine.  Limit: 4 * (m * ceil8(k) + k * ceil8(n)) bytes
+ * plus alignment must fit in 64 MiB (e.g. m = n = k = 2800); larger problems
+ * return G3_ERR_UNSUPPORTED before anything is launched.
+ *
+ * - The first call on a device looks up that device's copy of the array; make
+ *   that first call before any stream capture.
+ * - Every call, on every stream, uses the same array, and the array keeps the
+ *   previous call's contents.  Nothing in it has to start at zero: each call
+ *   writes every byte it later reads.  Two calls whose work overlaps on the
+ *   GPU (e.g. on two streams without ordering between them) race on the
+ *   array and corrupt each other's results.
+ * - Every GPU that loads the library holds the 64 MiB until the process exits. */
+G3_API int g3_gemm_3xbf16_noalloc(int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
+                                  const float* B, int64_t ldb, double beta, float* C, int64_t ldc,
+                                  void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

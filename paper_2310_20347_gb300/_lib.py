@@ -28,7 +28,7 @@ EXPORTED = (
     "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
     "g3_plan_query", "g3_launch_count", "g3_kernel_timing", "g3_kernel_time_ms",
-    "g3_debug_withhold_next",
+    "g3_debug_withhold_next", "g3_gemm_3xbf16_noalloc",
 )
 
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
             "g3_kernel_timing": ([i32], i32),
             "g3_kernel_time_ms": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
             "g3_debug_withhold_next": ([i64], i32),
+            "g3_gemm_3xbf16_noalloc": ([i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -209,3 +210,9 @@ def g3_kernel_time_ms(reset: bool = True):
 
 def g3_debug_withhold_next(timeout_ms: int) -> int:
     return load().g3_debug_withhold_next(timeout_ms)
+
+
+def g3_gemm_3xbf16_noalloc(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None) -> int:
+    """FP32-accurate GEMM whose scratch is a fixed array inside the library:
+    for callers that may not allocate device memory (see include/g3gemm.h)."""
+    return load().g3_gemm_3xbf16_noalloc(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream)

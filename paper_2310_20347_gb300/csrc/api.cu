@@ -688,3 +688,66 @@ int g3_kernel_time_ms(double* total_ms, int* launches, int reset) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP32-accurate GEMM.
+//
+// The hi/lo bfloat16 copies of A and B that the 3xBF16 mode needs live in this
+// fixed array of the library's device image instead of in workspace obtained
+// from cudaMalloc.  The array exists on every device that loads the library,
+// for the lifetime of the process.  Its device address is looked up once per
+// device (cudaGetSymbolAddress, with that device current) on the first call
+// there; host code only ever passes that looked-up address to the kernels.
+static constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g3_noalloc_scratch[kNoAllocScratchBytes];
+static void* g3_noalloc_addr[64] = {};
+
+extern "C" int g3_gemm_3xbf16_noalloc(int64_t m, int64_t n, int64_t k, double alpha, const float* A, int64_t lda,
+                                      const float* B, int64_t ldb, double beta, float* C, int64_t ldc,
+                                      void* stream) {
+  g3_gemm_args a;
+  g3_gemm_args_init(&a);
+  a.m = m; a.n = n; a.k = k;
+  a.alpha = alpha; a.beta = beta;
+  a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = ldc;
+  a.dtype = G3_F32_3XBF16;
+  a.split_k = 1;   // no split-K partials: the scratch holds the operand planes only
+  int st = validate(a);
+  if (st != G3_OK) return st;
+  if (m == 0 || n == 0) return G3_OK;
+  std::lock_guard<std::mutex> lock(g_mu);
+  family_init();
+  if (k > 0 && alpha != 0.0) {
+    // the planes' size depends on m, n, k only, not on the tile the planner picks
+    const Plan pl = make_plan(m, n, k, G3_F32_3XBF16, 152, -1, 1, 0);
+    const size_t need = make_layout(a, pl).total;
+    if (need > kNoAllocScratchBytes) {
+      if (std::getenv("G3_LOG"))
+        std::fprintf(stderr, "g3gemm: g3_gemm_3xbf16_noalloc needs %zu bytes of scratch, the maximum is %zu\n",
+                     need, kNoAllocScratchBytes);
+      return G3_ERR_UNSUPPORTED;
+    }
+  }
+  DevState* d = nullptr;
+  if ((st = ensure_device(&d)) != G3_OK) return st;
+  int dev = -1;
+  G3_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return G3_ERR_NOT_INIT;
+  if (!g3_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g3_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return G3_ERR_CUDA;
+    }
+    g3_noalloc_addr[dev] = p;
+  }
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  if (k == 0 || alpha == 0.0) {
+    G3_CHECK_CUDA(launch_scale_c(C, false, (int)m, (int)n, ldc, (float)beta, s));
+    return G3_OK;
+  }
+  a.workspace = g3_noalloc_addr[dev];
+  a.workspace_bytes = kNoAllocScratchBytes;
+  return run_tc(*d, a, s);
+}
