@@ -177,6 +177,300 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _kernel_ms(lib, fn, reps, flush):
+    """Mean device time of the library's main kernel over `reps` calls of fn,
+    with an L2 flush (a write larger than L2) before every call."""
+    import torch
+    lib.g3_kernel_timing(True)
+    lib.g3_kernel_time_ms(reset=True)
+    for _ in range(reps):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    ms, n = lib.g3_kernel_time_ms(reset=True)
+    lib.g3_kernel_timing(False)
+    return ms / max(n, 1)
+
+
+def _call_ms(fn, reps, flush):
+    """Mean device time of whole calls (all their launches), L2 flushed between."""
+    import torch
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = _events()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def _line(args, metric_value, unit, config, extra):
+    line = {"metric": METRIC, "value": metric_value, "unit": unit, "n_gpus": 1, "steps": args.reps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic", "config": config}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_workload(args):
+    """The non-headline configurations, one JSON line each."""
+    import torch
+
+    import oracle
+    import paper_2310_20347_gb300 as pkg
+    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP8_E4M3, G3_INT8, _lib, synth,
+                                        torch_api)
+    torch.cuda.set_device(0)
+    pkg.load()
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    bf16_peak = float(peaks["bf16_tflops"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    dev = "cuda"
+
+    def sample_err(got_rows, rows, A, B, C, alpha, beta, quantA=None, quantB=None):
+        A64, B64 = A.astype(np.float64), B.astype(np.float64)
+        ref = oracle.gemm(A64, B64, C, alpha, beta, rows=rows)
+        D = oracle.absprod(A64, B64, alpha, rows=rows)
+        if C is not None and beta != 0.0:
+            D = D + np.abs(beta * C[rows].astype(np.float64))
+        e = {"gate": float(np.max(np.abs(got_rows - ref) / np.maximum(D, 1e-300)))}
+        if quantA is not None:
+            Aq, Bq = quantA.astype(np.float64), quantB.astype(np.float64)
+            refq = oracle.gemm(Aq, Bq, C, alpha, beta, rows=rows)
+            Dq = oracle.absprod(Aq, Bq, alpha, rows=rows)
+            e["kernel"] = float(np.max(np.abs(got_rows - refq) / np.maximum(Dq, 1e-300)))
+        return e
+
+    if args.workload == "sweep":
+        out = []
+        for n in synth.SQUARE_SWEEP:
+            p = synth.uniform_problem(n, n, n, seed=0, alpha=1.0, beta=0.5)
+            A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+            C0 = torch.from_numpy(p.C).to(dev)
+            C = C0.clone()
+            rows = np.array([0, n // 2, n - 1])
+            res = {"n": n}
+            for name, dt in (("3xbf16", G3_F32_3XBF16), ("simt", G3_F32)):
+                C.copy_(C0)
+                torch_api.gemm(A, B, C, 1.0, 0.5, dtype=dt)
+                torch.cuda.synchronize()
+                got = C[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
+                err = sample_err(got, rows, p.A, p.B, p.C, 1.0, 0.5)["gate"]
+                reps = max(2, min(args.reps, 3 if (dt == G3_F32 and n >= 8192) else args.reps))
+                for _ in range(2):
+                    torch_api.gemm(A, B, C, 1.0, 0.5, dtype=dt)
+                ms = _call_ms(lambda: torch_api.gemm(A, B, C, 1.0, 0.5, dtype=dt), reps, flush)
+                res[name] = {"ms": ms, "tflops": 2.0 * n ** 3 / ms / 1e9, "rel_err": err}
+            res["speedup"] = res["simt"]["ms"] / res["3xbf16"]["ms"]
+            out.append(res)
+            del A, B, C, C0
+            torch.cuda.empty_cache()
+        _line(args, out[-1]["3xbf16"]["tflops"], "TFLOPS",
+              {"workload": "square FP32 sweep m=n=k in 1024..16384, alpha=1, beta=0.5, uniform [-1,1], "
+                           "3xBF16 vs SIMT (whole calls incl. the split pre-pass), L2 flushed between calls"},
+              {"dtype": "f32", "sweep": out})
+        return
+
+    if args.workload in ("im2col", "im2col-fp8", "im2col-int8"):
+        kind = {"im2col": "bf16", "im2col-fp8": "fp8", "im2col-int8": "int8"}[args.workload]
+        shapes = [(f"L{l}", m, n, k) for (l, m, n, k) in synth.im2col_shapes(16)]
+        shapes += [(f"b1:{m}x{n}x{k}", m, n, k) for (m, n, k) in synth.IM2COL_BATCH1_EXAMPLES]
+        per, tot_ms, tot_bytes, tot_flops, worst = [], 0.0, 0.0, 0.0, {}
+        for li, (name, m, n, k) in enumerate(shapes):
+            seed = li + 1
+            if kind == "int8":
+                p = synth.int8_problem(m, n, k, seed=seed)
+                A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+                C = torch.empty(m, n, dtype=torch.int32, device=dev)
+                fn = lambda: torch_api.gemm(A, B, C, 1, 0, dtype=G3_INT8)
+                esz, csz = 1, 4
+            else:
+                p = synth.normal_problem(m, n, k, seed=seed)
+                A32, B32 = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+                C = torch.empty(m, n, dtype=torch.float32, device=dev)
+                if kind == "bf16":
+                    A, B = torch_api.convert_bf16(A32), torch_api.convert_bf16(B32)
+                    fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_BF16)
+                    esz = 2
+                else:
+                    (A, sa), (B, sb) = torch_api.quantize_fp8(A32), torch_api.quantize_fp8(B32)
+                    fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP8_E4M3, scale_a=sa, scale_b=sb)
+                    esz = 1
+                del A32, B32
+                csz = 4
+            fn()
+            torch.cuda.synchronize()
+            rows = np.array([0, m // 2, m - 1])
+            got = C[torch.from_numpy(rows).to(dev)].cpu().numpy()
+            if kind == "int8":
+                ref = oracle.gemm_i8(p.A, p.B, rows=rows)
+                err = {"exact": bool(np.array_equal(got.astype(np.int64), ref))}
+            elif kind == "bf16":
+                err = sample_err(got.astype(np.float64), rows, p.A, p.B, None, 1.0, 0.0,
+                                 oracle.round_bf16(p.A), oracle.round_bf16(p.B))
+            else:
+                oqa, osa = oracle.fp8_quantize(p.A)
+                oqb, osb = oracle.fp8_quantize(p.B)
+                err = sample_err(got.astype(np.float64), rows, p.A, p.B, None, 1.0, 0.0,
+                                 oracle.e4m3_decode(oqa).astype(np.float64) * osa,
+                                 oracle.e4m3_decode(oqb).astype(np.float64) * osb)
+            for _ in range(args.warmup):
+                fn()
+            ms = _call_ms(fn, args.reps, flush)
+            kms = _kernel_ms(_lib, fn, args.reps, flush)
+            nbytes = esz * (m * k + k * n) + csz * m * n
+            flops = 2.0 * m * n * k
+            st, cfg, sk, rs = _lib.g3_plan_query(m, n, k, {"bf16": G3_BF16, "fp8": G3_FP8_E4M3,
+                                                           "int8": G3_INT8}[kind])
+            per.append({"shape": name, "m": m, "n": n, "k": k, "ms": ms, "kernel_ms": kms,
+                        "tflops": flops / ms / 1e9, "gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / hbm,
+                        "member": _lib.g3_family_describe(cfg) if cfg >= 0 else None, "split_k": sk, "err": err})
+            if name.startswith("L"):
+                tot_ms += ms
+                tot_bytes += nbytes
+                tot_flops += flops
+            for kk, v in err.items():
+                worst[kk] = (worst.get(kk, 0.0) if kk != "exact" else True)
+                worst[kk] = (worst[kk] and v) if kk == "exact" else max(worst[kk], v)
+            del A, B, C
+            torch.cuda.empty_cache()
+        gbs = tot_bytes / tot_ms / 1e6
+        _line(args, tot_flops / tot_ms / 1e9, "TFLOPS",
+              {"workload": f"20 ResNet50 v1.5 im2col GEMMs (Table 1 transposed, batch 16) + 3 batch-1 layers, "
+                           f"{kind} inputs, {'int32' if kind == 'int8' else 'fp32'} C, alpha=1, beta=0; "
+                           f"whole calls, L2 flushed between calls",
+               "l2": "flushed (256 MiB write) before every call"},
+              {"dtype": kind, "total_ms_20_layers": tot_ms, "worst_err": worst,
+               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                            "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                            "algorithmic": f"{'1' if kind != 'bf16' else '2'} B per A/B element + 4 B per C "
+                                           f"element, summed over the 20 layers"},
+               "per_shape": per})
+        return
+
+    if args.workload in ("int8", "fp8"):
+        n = 8192
+        if args.workload == "int8":
+            p = synth.int8_problem(n, n, n, seed=0)
+            A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+            C = torch.empty(n, n, dtype=torch.int32, device=dev)
+            fn = lambda: torch_api.gemm(A, B, C, 1, 0, dtype=G3_INT8)
+        else:
+            p = synth.normal_problem(n, n, n, seed=0)
+            A32, B32 = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+            (A, sa), (B, sb) = torch_api.quantize_fp8(A32), torch_api.quantize_fp8(B32)
+            C = torch.empty(n, n, dtype=torch.float32, device=dev)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP8_E4M3, scale_a=sa, scale_b=sb)
+        fn()
+        torch.cuda.synchronize()
+        rows = np.array([0, n // 2, n - 1])
+        got = C[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        if args.workload == "int8":
+            err = {"exact": bool(np.array_equal(got.astype(np.int64), oracle.gemm_i8(p.A, p.B, rows=rows)))}
+        else:
+            err = sample_err(got.astype(np.float64), rows, p.A, p.B, None, 1.0, 0.0)
+        for _ in range(args.warmup):
+            fn()
+        ms = _call_ms(fn, args.reps, flush)
+        kms = _kernel_ms(_lib, fn, args.reps, flush)
+        flops = 2.0 * n ** 3
+        tensor_peak = bf16_peak * (2.0 if args.workload == "fp8" else 1.0)
+        _line(args, flops / ms / 1e9, "TOPS" if args.workload == "int8" else "TFLOPS",
+              {"workload": f"{args.workload} GEMM m=n=k={n}, alpha=1, beta=0",
+               "path": ("exact: int8 -> bf16 pre-pass, k-chunks of 1024 on the BF16 tensor path, int32 "
+                        "split-K reduce (tcgen05 kind::i8 does not exist on sm_103a)")
+               if args.workload == "int8" else "tcgen05 kind::f8f6f4 E4M3, per-tensor scales"},
+              {"dtype": args.workload, "ms": ms, "kernel_ms": kms, "err": err,
+               "roofline": {"bound": "tensor", "achieved": flops / kms / 1e9, "peak": tensor_peak,
+                            "unit": "TFLOP/s", "frac": flops / kms / 1e9 / tensor_peak, "traffic": None,
+                            "peak_source": f"{peak_src} bf16 burst" + (" x 2 (fp8 nominal ratio)"
+                                                                         if args.workload == "fp8" else ""),
+                            "algorithmic": "2 n^3 per call (INT8: of the main kernel's bf16 work)"}})
+        return
+
+    if args.workload in ("grouped", "grouped-3xbf16"):
+        dt = G3_BF16 if args.workload == "grouped" else G3_F32_3XBF16
+        shapes = synth.grouped_shapes(1000, seed=0)
+        probs = []
+        flops = 0.0
+        rng = np.random.default_rng(0)
+        for gi, (m, n, k) in enumerate(shapes):
+            lda, ldb = -(-k // 8) * 8, -(-n // 8) * 8      # 16-byte rows for TMA
+            if dt == G3_BF16:
+                A = torch.zeros(m, lda, dtype=torch.bfloat16, device=dev)[:, :k]
+                B = torch.zeros(k, ldb, dtype=torch.bfloat16, device=dev)[:, :n]
+            else:
+                A = torch.zeros(m, lda, dtype=torch.float32, device=dev)[:, :k]
+                B = torch.zeros(k, ldb, dtype=torch.float32, device=dev)[:, :n]
+            A.copy_(torch.from_numpy((rng.standard_normal((m, k)) / np.sqrt(k)).astype(np.float32)))
+            B.copy_(torch.from_numpy(rng.standard_normal((k, n)).astype(np.float32)))
+            C = torch.empty(m, n, device=dev)
+            probs.append((A, B, C, 1.0, 0.0))
+            flops += 2.0 * m * n * k
+        plan = torch_api.GroupedPlan(probs, dt)
+        plan.execute()
+        torch.cuda.synchronize()
+        errs = []
+        for gi in range(0, 1000, 50):
+            A, B, C, _, _ = probs[gi]
+            a, b = A.float().cpu().numpy(), B.float().cpu().numpy()
+            rows = np.arange(min(4, a.shape[0]))
+            errs.append(sample_err(C.cpu().numpy()[rows].astype(np.float64), rows, a, b, None, 1.0, 0.0)["gate"])
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                plan.execute(stream=s)
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            g.replay()
+        grouped_ms = _call_ms(g.replay, args.reps, flush)
+        kms = _kernel_ms(_lib, plan.execute, args.reps, flush)
+
+        def per_call():
+            for (A, B, C, a, b) in probs:
+                torch_api.gemm(A, B, C, a, b, dtype=dt)
+
+        per_call()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps_eager = 3
+        for _ in range(reps_eager):
+            per_call()
+        torch.cuda.synchronize()
+        eager_ms = (time.perf_counter() - t0) * 1e3 / reps_eager
+        s2 = torch.cuda.Stream()
+        s2.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s2):
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2, stream=s2):
+                per_call()
+        torch.cuda.synchronize()
+        g2.replay()
+        graph_calls_ms = _call_ms(g2.replay, max(3, args.reps // 4), flush)
+        _line(args, flops / grouped_ms / 1e9, "TFLOPS",
+              {"workload": f"1000 GEMMs, m,n,k log-uniform in [16,1024] (seed 0), "
+                           f"{'bf16' if dt == G3_BF16 else '3xbf16 (fp32 in/out)'}, fp32 C, beta=0",
+               "l2": "flushed before every replay"},
+              {"dtype": "bf16" if dt == G3_BF16 else "bf16x3->f32", "total_gflop": flops / 1e9,
+               "grouped_graph_ms": grouped_ms, "grouped_kernel_ms": kms,
+               "per_call_eager_wall_ms": eager_ms, "per_call_graph_ms": graph_calls_ms,
+               "speedup_vs_eager": eager_ms / grouped_ms, "speedup_vs_graph_of_calls": graph_calls_ms / grouped_ms,
+               "max_rel_err_sampled": max(errs)})
+        plan.close()
+        return
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,10 +482,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
+    ap.add_argument("--workload", default="square",
+                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8",
+                             "grouped", "grouped-3xbf16"],
+                    help="square (default) is the headline step; the others measure the remaining "
+                         "configurations and print one JSON line each")
+    ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "square":
+        return run_workload(args)
 
     import torch
 

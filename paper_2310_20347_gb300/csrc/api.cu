@@ -479,6 +479,40 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Services of this file for the other translation units (see internal.h).
+std::mutex& api_mutex() { return g_mu; }
+
+int current_device_info(DeviceInfo* out) {
+  DevState* d = nullptr;
+  const int st = ensure_device(&d);
+  if (st != G3_OK) return st;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  out->device = dev;
+  out->sms = d->sms;
+  out->status = d->status;
+  return G3_OK;
+}
+
+int encode_tensor_2d(CUtensorMap* map, const void* base, int esize, uint64_t inner, uint64_t outer, uint64_t ld,
+                     uint32_t box_inner, uint32_t box_outer) {
+  return encode_2d(map, base, esize, inner, outer, ld, box_inner, box_outer);
+}
+
+unsigned long long watchdog_timeout_ns() { return watchdog_ns(); }
+
+bool kernel_timing_enabled() { return g_timing; }
+
+void kernel_timing_push(cudaEvent_t e0, cudaEvent_t e1) { g_events.emplace_back(e0, e1); }
+
+bool take_withhold(unsigned long long* timeout_ns) {
+  if (!g_withhold_next) return false;
+  g_withhold_next = false;
+  *timeout_ns = g_withhold_timeout_ns;
+  return true;
+}
+
 }  // namespace g3
 
 using namespace g3;
@@ -575,14 +609,6 @@ int g3_quantize_fp8(const float* x, int64_t rows, int64_t cols, int64_t ldx, uin
                                      scale, s));
   return G3_OK;
 }
-
-int g3_grouped_plan_create(int, const g3_gemm_desc*, int, g3_grouped_plan** plan) {
-  if (plan) *plan = nullptr;
-  return G3_ERR_UNSUPPORTED;
-}
-int g3_grouped_plan_execute(g3_grouped_plan*, void*) { return G3_ERR_UNSUPPORTED; }
-int g3_grouped_plan_destroy(g3_grouped_plan*) { return G3_OK; }
-int g3_gemm_grouped(int, const g3_gemm_desc*, int, void*) { return G3_ERR_UNSUPPORTED; }
 
 int g3_get_last_device_status(int* code) {
   std::lock_guard<std::mutex> lock(g_mu);

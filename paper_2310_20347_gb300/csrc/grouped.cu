@@ -1,0 +1,359 @@
+// grouped.cu -- many independent GEMMs of uneven shapes in one persistent launch.
+//
+// A plan (g3_grouped_plan_create) does all host work once: validation, the
+// per-problem choice of tile height by size bucket (the per-shape selection of
+// the paper's Section 8.4, applied problem by problem), the global tile list
+// ordered by decreasing k-depth (heaviest tiles first, so that the static
+// stride of the persistent CTAs balances), four TMA descriptors per problem in
+// a device table, and the preparation jobs (3xBF16 hi/lo split, re-packing of
+// unaligned BF16 operands, C := beta*C for problems without products).
+// Executing the plan is at most two launches -- one job kernel over all
+// preparation jobs and one tc_grouped_kernel over all tiles -- with no host
+// synchronisation and no allocation.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "family_gen.inc"
+#include "g3gemm.h"
+#include "internal.h"
+#include "bf16.cuh"
+
+namespace g3 {
+namespace {
+
+enum PrepKind : int { PREP_SPLIT = 0, PREP_COPY16 = 1, PREP_SCALE_C = 2 };
+
+// One preparation job of a grouped plan.
+struct PrepJob {
+  const void* src;
+  long long ld_src;   // elements
+  void* hi;           // PREP_SPLIT: hi plane; PREP_COPY16: destination
+  void* lo;           // PREP_SPLIT: lo plane
+  long long ld_dst;   // elements
+  int rows, cols;
+  int kind;
+  float beta;         // PREP_SCALE_C
+};
+
+// blockIdx.y strides over jobs, the x-dimension over each job's elements.
+__global__ void grouped_prep_kernel(const PrepJob* __restrict__ jobs, int njobs) {
+  for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
+    const PrepJob J = jobs[jb];
+    const long long total = (long long)J.rows * J.cols;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+      const long long r = e / J.cols, c = e - r * J.cols;
+      if (J.kind == PREP_SPLIT) {
+        const float v = static_cast<const float*>(J.src)[r * J.ld_src + c];
+        const uint16_t h = bf16_bits(v);
+        static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = h;
+        static_cast<uint16_t*>(J.lo)[r * J.ld_dst + c] = bf16_bits(v - bf16_value(h));
+      } else if (J.kind == PREP_COPY16) {
+        static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = static_cast<const uint16_t*>(J.src)[r * J.ld_src + c];
+      } else {
+        float* p = static_cast<float*>(const_cast<void*>(J.src)) + r * J.ld_src + c;
+        *p = (J.beta == 0.f) ? 0.f : J.beta * *p;
+      }
+    }
+  }
+}
+
+GroupedEntry g_grouped[G3_GROUPED_SIZE];
+bool g_grouped_ready = false;
+
+void grouped_init() {
+  if (g_grouped_ready) return;
+  std::memset(g_grouped, 0, sizeof(g_grouped));
+  register_grouped_bf16(g_grouped);
+  register_grouped_3xbf16(g_grouped);
+  register_grouped_fp8(g_grouped);
+  g_grouped_ready = true;
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+bool aligned16(const void* p, int64_t ld, int es) {
+  return reinterpret_cast<uintptr_t>(p) % 16 == 0 && (ld * es) % 16 == 0;
+}
+
+}  // namespace
+}  // namespace g3
+
+using namespace g3;
+
+struct g3_grouped_plan {
+  int device = -1;
+  int dtype = 0;
+  int count = 0;
+  int entry = -1;        // index into the grouped kernel table
+  int total_tiles = 0;
+  int njobs = 0;
+  int sms = 0;
+  void* dmem = nullptr;  // one allocation: maps | problems | tile list | jobs | operand planes
+  GroupedParams params{};
+  PrepJob* d_jobs = nullptr;
+};
+
+extern "C" {
+
+int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** out) {
+  if (!out) return G3_ERR_ARG;
+  *out = nullptr;
+  if (count < 0) return -101;
+  if (count > 0 && !descs) return -102;
+  if (dtype != G3_BF16 && dtype != G3_F32_3XBF16) return G3_ERR_UNSUPPORTED;
+  for (int i = 0; i < count; ++i) {
+    const g3_gemm_desc& d = descs[i];
+    const int code = i < 900 ? -(100 + i) : G3_ERR_ARG;
+    if (d.m < 0 || d.n < 0 || d.k < 0) return code;
+    if (d.m > INT32_MAX || d.n > INT32_MAX || d.k > INT32_MAX) return G3_ERR_UNSUPPORTED;
+    if (d.lda < std::max<int64_t>(1, d.k) || d.ldb < std::max<int64_t>(1, d.n) ||
+        d.ldc < std::max<int64_t>(1, d.n))
+      return code;
+    if (d.m > 0 && d.n > 0) {
+      if (!d.C) return code;
+      if (d.k > 0 && d.alpha != 0.0 && (!d.A || !d.B)) return code;
+    }
+  }
+  std::lock_guard<std::mutex> lock(api_mutex());
+  DeviceInfo dev;
+  int st = current_device_info(&dev);
+  if (st != G3_OK) return st;
+  grouped_init();
+  const int mode = (dtype == G3_BF16) ? TC_BF16 : TC_3XBF16;
+  int entry = -1;
+  for (int i = 0; i < G3_GROUPED_SIZE; ++i)
+    if (g_grouped[i].launch && g_grouped[i].mode == mode) entry = i;
+  if (entry < 0) return G3_ERR_UNSUPPORTED;
+  const GroupedEntry& ge = g_grouped[entry];
+
+  // ---- per-problem tiling, jobs and plane sizes (host)
+  std::vector<GroupDesc> groups(count);
+  std::vector<PrepJob> jobs;
+  struct Operands { size_t a_off = 0, a_lo_off = 0, b_off = 0, b_lo_off = 0; int64_t lda = 0, ldb = 0;
+                    bool pack_a = false, pack_b = false; bool active = false; };
+  std::vector<Operands> ops(count);
+  size_t planes = 0;
+  auto take = [&](size_t bytes) { size_t o = planes; planes = align256(planes + bytes); return o; };
+  long long total_tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    const g3_gemm_desc& d = descs[i];
+    GroupDesc& g = groups[i];
+    std::memset(&g, 0, sizeof(g));
+    g.m = (int)d.m; g.n = (int)d.n; g.k = (int)d.k;
+    g.alpha = (float)d.alpha; g.beta = (float)d.beta;
+    g.C = static_cast<float*>(d.C);
+    g.ldc = d.ldc;
+    g.bm = (d.m <= 64) ? 64 : std::min(128, ge.bm_max);   // size bucket
+    if (d.m == 0 || d.n == 0) continue;
+    if (d.k == 0 || d.alpha == 0.0) {
+      PrepJob J{};
+      J.src = d.C; J.ld_src = d.ldc; J.rows = g.m; J.cols = g.n; J.kind = PREP_SCALE_C; J.beta = (float)d.beta;
+      jobs.push_back(J);
+      continue;
+    }
+    Operands& o = ops[i];
+    o.active = true;
+    g.tiles_m = (g.m + g.bm - 1) / g.bm;
+    g.tiles_n = (g.n + 127) / 128;
+    g.num_kb = (g.k + 63) / 64;
+    total_tiles += (long long)g.tiles_m * g.tiles_n;
+    if (dtype == G3_F32_3XBF16) {
+      o.lda = round_up(d.k, 8);
+      o.ldb = round_up(d.n, 8);
+      o.a_off = take((size_t)d.m * o.lda * 2);
+      o.a_lo_off = take((size_t)d.m * o.lda * 2);
+      o.b_off = take((size_t)d.k * o.ldb * 2);
+      o.b_lo_off = take((size_t)d.k * o.ldb * 2);
+    } else {
+      o.pack_a = !aligned16(d.A, d.lda, 2);
+      o.pack_b = !aligned16(d.B, d.ldb, 2);
+      o.lda = o.pack_a ? round_up(d.k, 8) : d.lda;
+      o.ldb = o.pack_b ? round_up(d.n, 8) : d.ldb;
+      if (o.pack_a) o.a_off = take((size_t)d.m * o.lda * 2);
+      if (o.pack_b) o.b_off = take((size_t)d.k * o.ldb * 2);
+    }
+  }
+  if (total_tiles > INT32_MAX) return G3_ERR_UNSUPPORTED;
+
+  // ---- device memory: maps | problems | tile list | jobs | planes
+  const size_t maps_bytes = align256(sizeof(CUtensorMap) * 4 * (size_t)std::max(count, 1));
+  const size_t groups_bytes = align256(sizeof(GroupDesc) * (size_t)std::max(count, 1));
+  const size_t tiles_bytes = align256(sizeof(int2) * (size_t)std::max<long long>(total_tiles, 1));
+  const size_t njobs_max = jobs.size() + 2 * (size_t)count;
+  const size_t jobs_bytes = align256(sizeof(PrepJob) * std::max<size_t>(njobs_max, 1));
+  const size_t header = maps_bytes + groups_bytes + tiles_bytes + jobs_bytes;
+  g3_grouped_plan* plan = new g3_grouped_plan();
+  if (cudaMalloc(&plan->dmem, header + planes) != cudaSuccess) {
+    cudaGetLastError();
+    delete plan;
+    return G3_ERR_NOMEM;
+  }
+  uint8_t* base = static_cast<uint8_t*>(plan->dmem);
+  CUtensorMap* d_maps = reinterpret_cast<CUtensorMap*>(base);
+  GroupDesc* d_groups = reinterpret_cast<GroupDesc*>(base + maps_bytes);
+  int2* d_tiles = reinterpret_cast<int2*>(base + maps_bytes + groups_bytes);
+  PrepJob* d_jobs = reinterpret_cast<PrepJob*>(base + maps_bytes + groups_bytes + tiles_bytes);
+  uint8_t* d_planes = base + header;
+
+  std::vector<CUtensorMap> maps(4 * (size_t)std::max(count, 1));
+  std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+  for (int i = 0; i < count && st == G3_OK; ++i) {
+    if (!ops[i].active) continue;
+    const g3_gemm_desc& d = descs[i];
+    const Operands& o = ops[i];
+    const GroupDesc& g = groups[i];
+    const void *a = d.A, *b = d.B, *a_lo = nullptr, *b_lo = nullptr;
+    if (dtype == G3_F32_3XBF16) {
+      a = d_planes + o.a_off; a_lo = d_planes + o.a_lo_off;
+      b = d_planes + o.b_off; b_lo = d_planes + o.b_lo_off;
+      PrepJob ja{d.A, d.lda, (void*)a, (void*)a_lo, o.lda, g.m, g.k, PREP_SPLIT, 0.f};
+      PrepJob jb{d.B, d.ldb, (void*)b, (void*)b_lo, o.ldb, g.k, g.n, PREP_SPLIT, 0.f};
+      jobs.push_back(ja);
+      jobs.push_back(jb);
+    } else {
+      if (o.pack_a) {
+        a = d_planes + o.a_off;
+        jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, o.lda, g.m, g.k, PREP_COPY16, 0.f});
+      }
+      if (o.pack_b) {
+        b = d_planes + o.b_off;
+        jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, o.ldb, g.k, g.n, PREP_COPY16, 0.f});
+      }
+    }
+    CUtensorMap* m4 = &maps[4 * (size_t)i];
+    st = encode_tensor_2d(&m4[0], a, 2, g.k, g.m, o.lda, 64, g.bm);
+    if (st == G3_OK) st = encode_tensor_2d(&m4[1], b, 2, g.n, g.k, o.ldb, 64, 64);
+    if (st == G3_OK && dtype == G3_F32_3XBF16) {
+      st = encode_tensor_2d(&m4[2], a_lo, 2, g.k, g.m, o.lda, 64, g.bm);
+      if (st == G3_OK) st = encode_tensor_2d(&m4[3], b_lo, 2, g.n, g.k, o.ldb, 64, 64);
+    } else {
+      m4[2] = m4[0];
+      m4[3] = m4[1];
+    }
+  }
+  if (st != G3_OK) {
+    cudaFree(plan->dmem);
+    delete plan;
+    return st;
+  }
+
+  // global tile list, heaviest (deepest k) problems first; ties keep problem order
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return groups[x].num_kb * groups[x].bm > groups[y].num_kb * groups[y].bm; });
+  std::vector<int2> tiles;
+  tiles.reserve((size_t)total_tiles);
+  for (int i : order) {
+    if (!ops[i].active) continue;
+    const int nt = groups[i].tiles_m * groups[i].tiles_n;
+    for (int t = 0; t < nt; ++t) tiles.push_back(make_int2(i, t));
+  }
+
+  bool ok = true;
+  ok = ok && cudaMemcpy(d_maps, maps.data(), sizeof(CUtensorMap) * 4 * (size_t)count, cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpy(d_groups, groups.data(), sizeof(GroupDesc) * (size_t)count, cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
+  if (!tiles.empty())
+    ok = ok && cudaMemcpy(d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!jobs.empty())
+    ok = ok && cudaMemcpy(d_jobs, jobs.data(), sizeof(PrepJob) * jobs.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(plan->dmem);
+    delete plan;
+    return G3_ERR_CUDA;
+  }
+  plan->device = dev.device;
+  plan->dtype = dtype;
+  plan->count = count;
+  plan->entry = entry;
+  plan->total_tiles = (int)total_tiles;
+  plan->njobs = (int)jobs.size();
+  plan->sms = dev.sms;
+  plan->d_jobs = d_jobs;
+  plan->params.groups = d_groups;
+  plan->params.maps = d_maps;
+  plan->params.tile_info = d_tiles;
+  plan->params.total_tiles = (int)total_tiles;
+  plan->params.timeout_ns = watchdog_timeout_ns();
+  plan->params.status = dev.status;
+  plan->params.debug_withhold = -1;
+  *out = plan;
+  return G3_OK;
+}
+
+int g3_grouped_plan_execute(g3_grouped_plan* plan, void* stream) {
+  if (!plan) return -101;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) {
+    cudaGetLastError();
+    return G3_ERR_ARG;
+  }
+  if (plan->njobs > 0) {
+    const dim3 grid(16, (unsigned)std::min(plan->njobs, 65535));
+    grouped_prep_kernel<<<grid, 256, 0, s>>>(plan->d_jobs, plan->njobs);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return G3_ERR_CUDA;
+  }
+  if (plan->total_tiles == 0) return G3_OK;
+  GroupedParams p = plan->params;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(api_mutex());
+    unsigned long long t = 0;
+    if (take_withhold(&t)) {
+      p.debug_withhold = 0;
+      p.timeout_ns = t;
+    }
+    if (kernel_timing_enabled()) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+    }
+  }
+  if (e0) cudaEventRecord(e0, s);
+  const int grid = std::min(plan->total_tiles, plan->sms);
+  const cudaError_t e = g_grouped[plan->entry].launch(p, grid, s);
+  if (e1) {
+    cudaEventRecord(e1, s);
+    std::lock_guard<std::mutex> lock(api_mutex());
+    kernel_timing_push(e0, e1);
+  }
+  if (e != cudaSuccess) {
+    if (std::getenv("G3_LOG")) std::fprintf(stderr, "g3gemm: grouped launch: %s\n", cudaGetErrorString(e));
+    return G3_ERR_CUDA;
+  }
+  return G3_OK;
+}
+
+int g3_grouped_plan_destroy(g3_grouped_plan* plan) {
+  if (!plan) return G3_OK;
+  if (plan->dmem) {
+    cudaFree(plan->dmem);   // synchronises with work still using the plan
+    cudaGetLastError();
+  }
+  delete plan;
+  return G3_OK;
+}
+
+int g3_gemm_grouped(int count, const g3_gemm_desc* descs, int dtype, void* stream) {
+  g3_grouped_plan* plan = nullptr;
+  int st = g3_grouped_plan_create(count, descs, dtype, &plan);
+  if (st != G3_OK) return st;
+  st = g3_grouped_plan_execute(plan, stream);
+  if (st == G3_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    st = G3_ERR_CUDA;
+  }
+  g3_grouped_plan_destroy(plan);
+  return st;
+}
+
+}  // extern "C"

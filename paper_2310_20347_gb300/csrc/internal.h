@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <mutex>
 
 #include "simt_sgemm.cuh"
 #include "tc_gemm.cuh"
@@ -26,6 +27,22 @@ void register_family_bf16(FamilyEntry* table);
 void register_family_3xbf16(FamilyEntry* table);
 void register_family_fp8(FamilyEntry* table);
 
+using GroupedLaunchFn = cudaError_t (*)(const GroupedParams& p, int grid, cudaStream_t s);
+
+// One persistent grouped kernel (tiles of at most bm_max rows).
+struct GroupedEntry {
+  int index;
+  int mode;
+  int bm_max;
+  int stages;
+  int smem;
+  GroupedLaunchFn launch;
+};
+
+void register_grouped_bf16(GroupedEntry* table);
+void register_grouped_3xbf16(GroupedEntry* table);
+void register_grouped_fp8(GroupedEntry* table);
+
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.
 cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s);
@@ -45,5 +62,20 @@ cudaError_t launch_splitk_reduce(const float* P, int splits, int rows, int cols,
 
 // Number of kernel launches the library has issued (all translation units).
 void count_launch(int n = 1);
+
+// api.cu services.  Callers of the functions below hold api_mutex().
+struct DeviceInfo {
+  int device;
+  int sms;
+  int* status;   // device status word of the watchdog
+};
+std::mutex& api_mutex();
+int current_device_info(DeviceInfo* out);
+int encode_tensor_2d(CUtensorMap* map, const void* base, int esize, uint64_t inner, uint64_t outer, uint64_t ld,
+                     uint32_t box_inner, uint32_t box_outer);
+unsigned long long watchdog_timeout_ns();
+bool kernel_timing_enabled();
+void kernel_timing_push(cudaEvent_t e0, cudaEvent_t e1);
+bool take_withhold(unsigned long long* timeout_ns);   // one-shot failure-detection test hook
 
 }  // namespace g3

@@ -17,14 +17,9 @@
 #include <cuda_fp8.h>
 #include <cstdint>
 
-namespace g3 {
+#include "bf16.cuh"
 
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-__device__ __forceinline__ float bf16_value(uint16_t b) {
-  return __bfloat162float(__ushort_as_bfloat16(b));
-}
+namespace g3 {
 
 // hi = bf16(x), lo = bf16(x - hi); x - hi is exact in FP32.
 __global__ void split_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,

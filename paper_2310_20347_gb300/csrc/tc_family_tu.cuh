@@ -25,10 +25,32 @@ void add_member(FamilyEntry* t) {
   }
 }
 
+template <int BM, int ST, int MODE>
+cudaError_t launch_grouped(const GroupedParams& p, int grid, cudaStream_t s) {
+  using Cfg = TcConfig<BM, ST, MODE>;
+  auto kern = tc_grouped_kernel<BM, ST, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, Cfg::kThreads, Cfg::kSmemBytes, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int IDX, int MODE, int BM, int ST>
+void add_grouped(GroupedEntry* t) {
+  if constexpr (MODE == G3_TU_MODE) {
+    t[IDX] = GroupedEntry{IDX, MODE, BM, ST, (int)TcConfig<BM, ST, MODE>::kSmemBytes, &launch_grouped<BM, ST, MODE>};
+  }
+}
+
 }  // namespace
 
 #define G3_ADD_MEMBER(idx, mode, bm, st) add_member<idx, mode, bm, st>(table);
 void G3_TU_REGISTER(FamilyEntry* table) { G3_FAMILY_LIST(G3_ADD_MEMBER) }
 #undef G3_ADD_MEMBER
+
+#define G3_ADD_GROUPED(idx, mode, bm, st) add_grouped<idx, mode, bm, st>(table);
+void G3_TU_REGISTER_GROUPED(GroupedEntry* table) { G3_GROUPED_LIST(G3_ADD_GROUPED) }
+#undef G3_ADD_GROUPED
 
 }  // namespace g3

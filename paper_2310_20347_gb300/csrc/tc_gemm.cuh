@@ -14,9 +14,9 @@
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator, alpha/beta, stores
 //
 // Orientation.  The MMA computes D = Bt * At, i.e. the transpose of the C tile:
-// TMEM lane = column j of C (128 per tile), TMEM column = row i of C (BM_T per
+// TMEM lane = column j of C (128 per tile), TMEM column = row i of C (bm per
 // tile).  The MMA's A operand is the k x 128 slice of B (stored n-contiguous, so
-// "MN-major"), its B operand the BM_T x k slice of A (k-contiguous, "K-major").
+// "MN-major"), its B operand the bm x k slice of A (k-contiguous, "K-major").
 // Each epilogue thread then owns one column of C and a warp's store of one row
 // is 32 consecutive floats: every global store is a full 128-byte line.
 //
@@ -25,7 +25,12 @@
 // `raster` m-tiles walked m-fastest keeps that band's A panels and the current
 // B panels in L2); L2 (pc) -> the k-block loop, optionally split across CTAs
 // (split-K, the analogue of the C-in-cache variants of Section 7); L4/L5 (jr, ir)
-// -> the 128 x BM_T tile of one MMA; L6 (pr) -> the k-steps of the MMA.
+// -> the 128 x bm tile of one MMA; L6 (pr) -> the k-steps of the MMA.
+//
+// Which tiles a CTA walks comes from a scheduler policy: SingleSched for one
+// problem (TcParams, tensor maps as kernel parameters), GroupedSched for many
+// independent problems in one launch (a device table of problems, four tensor
+// maps per problem in global memory, and per problem its own tile height bm).
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -64,6 +69,27 @@ struct TcParams {
   unsigned long long timeout_ns;
   int* status;
   int debug_withhold;     // test hook: producer iteration whose stage never fills (-1: none)
+};
+
+// One problem of a grouped launch (device table entry).
+struct GroupDesc {
+  int m, n, k;
+  int tiles_m, tiles_n, num_kb;
+  int bm;                 // rows per tile for this problem (MMA N), <= the kernel's BM_T
+  int pad;
+  float alpha, beta;
+  float* C;
+  long long ldc;
+};
+
+struct GroupedParams {
+  const GroupDesc* groups;
+  const CUtensorMap* maps;   // 4 per problem: A, B, A lo plane, B lo plane
+  const int2* tile_info;     // per global tile: (problem, tile index within the problem)
+  int total_tiles;
+  unsigned long long timeout_ns;
+  int* status;
+  int debug_withhold;
 };
 
 template <int MODE>
@@ -107,23 +133,76 @@ struct TcConfig {
   static_assert(8 * (2 * STAGES + 5) + 8 <= (int)kBarBytes, "barrier area");
 };
 
-__device__ __forceinline__ void decode_tile(int t, const TcParams& p, int& tm, int& tn, int& s) {
-  const int per_split = p.tiles_m * p.tiles_n;
-  s = t / per_split;
-  const int r = t - s * per_split;
-  const int G = p.raster;
-  const int band = r / (G * p.tiles_n);
-  const int in_band = r - band * G * p.tiles_n;
-  const int rows = min(G, p.tiles_m - band * G);
-  tm = band * G + in_band % rows;
-  tn = in_band / rows;
-}
+// One output tile: rows m0 .. m0+bm-1, columns n0 .. n0+127 of problem g, k-blocks kb0 .. kb1-1.
+struct TileJob {
+  int m0, n0, kb0, kb1, bm, split, g;
+};
 
-template <int BM_T, int STAGES, int MODE>
-__global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
-                   const TcParams p) {
+// Where and how a tile's result is written.
+struct EpiJob {
+  void* C;
+  long long ldc;
+  int m, n;
+  float alpha, beta;
+  int out_mode;
+  float* partial;   // OUT_PARTIAL: this split's m x n plane (leading dimension n)
+};
+
+template <int BM_T>
+struct SingleSched {
+  const TcParams* p;
+  const CUtensorMap* maps[4];   // A, B, A lo plane, B lo plane (kernel parameters)
+
+  __device__ __forceinline__ int total() const { return p->tiles_m * p->tiles_n * p->splits; }
+
+  __device__ __forceinline__ TileJob tile(int t) const {
+    const int per_split = p->tiles_m * p->tiles_n;
+    const int s = t / per_split;
+    const int r = t - s * per_split;
+    const int G = p->raster;
+    const int band = r / (G * p->tiles_n);
+    const int in_band = r - band * G * p->tiles_n;
+    const int rows = min(G, p->tiles_m - band * G);
+    const int tm = band * G + in_band % rows;
+    const int tn = in_band / rows;
+    const int kb0 = s * p->kb_per_split;
+    return TileJob{tm * BM_T, tn * 128, kb0, min(p->num_kb, kb0 + p->kb_per_split), BM_T, s, 0};
+  }
+
+  __device__ __forceinline__ const CUtensorMap* map(const TileJob&, int which) const { return maps[which]; }
+
+  __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
+    return EpiJob{p->C, p->ldc, p->m, p->n, p->alpha, p->beta, p->out_mode,
+                  p->partial ? p->partial + (long long)j.split * p->m * p->n : nullptr};
+  }
+};
+
+struct GroupedSched {
+  const GroupedParams* gp;
+
+  __device__ __forceinline__ int total() const { return gp->total_tiles; }
+
+  __device__ __forceinline__ TileJob tile(int t) const {
+    const int2 ti = __ldg(gp->tile_info + t);
+    const int g = ti.x;
+    const GroupDesc* d = gp->groups + g;
+    const int tm = ti.y % d->tiles_m, tn = ti.y / d->tiles_m;
+    return TileJob{tm * d->bm, tn * 128, 0, d->num_kb, d->bm, 0, g};
+  }
+
+  __device__ __forceinline__ const CUtensorMap* map(const TileJob& j, int which) const {
+    return gp->maps + 4 * j.g + which;
+  }
+
+  __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
+    const GroupDesc* d = gp->groups + j.g;
+    return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr};
+  }
+};
+
+template <int BM_T, int STAGES, int MODE, class Sched>
+__device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long timeout_ns, int* status,
+                                             int debug_withhold, const float* scale_a, const float* scale_b) {
   using T = TcTraits<MODE>;
   using Cfg = TcConfig<BM_T, STAGES, MODE>;
   extern __shared__ uint8_t smem_raw[];
@@ -152,12 +231,6 @@ __global__ void __launch_bounds__(192, 1)
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
-    if (MODE == TC_3XBF16) {
-      tma_prefetch_desc(&tmA_lo);
-      tma_prefetch_desc(&tmB_lo);
-    }
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, Cfg::kTmemCols);
@@ -168,8 +241,8 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  Watchdog wd{p.timeout_ns, p.status, abort_flag};
-  const int total_tiles = p.tiles_m * p.tiles_n * p.splits;
+  Watchdog wd{timeout_ns, status, abort_flag};
+  const int total_tiles = S.total();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -177,57 +250,51 @@ __global__ void __launch_bounds__(192, 1)
       uint32_t it = 0;
       bool ok = true;
       for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
-        int tm, tn, s;
-        decode_tile(t, p, tm, tn, s);
-        const int kb0 = s * p.kb_per_split;
-        const int kb1 = min(p.num_kb, kb0 + p.kb_per_split);
-        const int m0 = tm * BM_T, n0 = tn * 128;
-        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+        const TileJob j = S.tile(t);
+        const uint32_t stage_bytes = T::kPlanes * (T::kBtBytes + (uint32_t)j.bm * 128u);
+        for (int kb = j.kb0; kb < j.kb1; ++kb, ++it) {
           const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
           if (!wait_parity(&empty[stage], ph ^ 1u, wd, WD_PRODUCER_EMPTY)) { ok = false; break; }
-          if ((int)it == p.debug_withhold) continue;   // failure-detection test: never arrive
-          mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+          if ((int)it == debug_withhold) continue;   // failure-detection test: never arrive
+          mbar_arrive_expect_tx(&full[stage], stage_bytes);
           uint8_t* st = smem + stage * Cfg::kStageBytes;
           const int k0 = kb * T::kBK;
 #pragma unroll
           for (int pl = 0; pl < T::kPlanes; ++pl) {
             uint8_t* bt = st + pl * Cfg::kPlaneBytes;
             uint8_t* at = bt + T::kBtBytes;
-            const CUtensorMap* mb = (pl == 0) ? &tmB : &tmB_lo;
-            const CUtensorMap* ma = (pl == 0) ? &tmA : &tmA_lo;
+            const CUtensorMap* mb = S.map(j, pl == 0 ? 1 : 3);
+            const CUtensorMap* ma = S.map(j, pl == 0 ? 0 : 2);
 #pragma unroll
             for (int h = 0; h < T::kNBoxes; ++h)
-              tma_load_2d(bt + h * (T::kBK * 128), mb, n0 + h * T::kBoxN, k0, &full[stage]);
-            tma_load_2d(at, ma, k0, m0, &full[stage]);
+              tma_load_2d(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, &full[stage]);
+            tma_load_2d(at, ma, k0, j.m0, &full[stage]);
           }
         }
       }
       // Let every load already issued land before the CTA can retire.
       const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
-      for (uint32_t j = first; j < it; ++j) {
+      for (uint32_t q = first; q < it; ++q) {
         uint64_t t0 = globaltimer_ns();
-        while (!mbar_try_wait(&full[j % STAGES], (j / STAGES) & 1u))
-          if (globaltimer_ns() - t0 > p.timeout_ns) { atomicCAS(p.status, 0, WD_DRAIN); break; }
+        while (!mbar_try_wait(&full[q % STAGES], (q / STAGES) & 1u))
+          if (globaltimer_ns() - t0 > timeout_ns) { atomicCAS(status, 0, WD_DRAIN); break; }
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/true, /*b_mn=*/false, 128, BM_T);
       uint32_t it = 0, lt = 0;
       bool ok = true;
       for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++lt) {
-        int tm, tn, s;
-        decode_tile(t, p, tm, tn, s);
-        const int kb0 = s * p.kb_per_split;
-        const int kb1 = min(p.num_kb, kb0 + p.kb_per_split);
+        const TileJob j = S.tile(t);
+        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/true, /*b_mn=*/false, 128, j.bm);
         const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
         if (!wait_parity(&tmem_empty[acc], aph ^ 1u, wd, WD_MMA_TMEM_EMPTY)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * Cfg::kSetCols;   // main accumulator
         const uint32_t d_corr = d_tmem + BM_T;                       // 3xBF16 corrections
         uint32_t accumulate = 0;
-        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+        for (int kb = j.kb0; kb < j.kb1; ++kb, ++it) {
           const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
           if (!wait_parity(&full[stage], ph, wd, WD_MMA_FULL)) { ok = false; break; }
           tc_fence_after();
@@ -266,31 +333,31 @@ __global__ void __launch_bounds__(192, 1)
       mma_commit(drain);
       uint64_t t0 = globaltimer_ns();
       while (!mbar_try_wait(drain, 0))
-        if (globaltimer_ns() - t0 > p.timeout_ns) { atomicCAS(p.status, 0, WD_DRAIN); break; }
+        if (globaltimer_ns() - t0 > timeout_ns) { atomicCAS(status, 0, WD_DRAIN); break; }
     }
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;                  // TMEM lane quarter this warp may access
-    float alpha = p.alpha;
+    float scale = 1.0f;
     if (MODE == TC_FP8) {
-      const float sa = p.scale_a ? *p.scale_a : 1.0f;
-      const float sb = p.scale_b ? *p.scale_b : 1.0f;
-      alpha = alpha * (sa * sb);
+      const float sa = scale_a ? *scale_a : 1.0f;
+      const float sb = scale_b ? *scale_b : 1.0f;
+      scale = sa * sb;
     }
-    const float beta = p.beta;
     uint32_t lt = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
-      int tm, tn, s;
-      decode_tile(t, p, tm, tn, s);
+      const TileJob j = S.tile(t);
+      const EpiJob e = S.epi(j);
+      const float alpha = e.alpha * scale;
+      const float beta = e.beta;
       const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
       bool ok = wait_parity(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
-      const int m0 = tm * BM_T;
-      const int j = tn * 128 + q * 32 + lane;              // column of C owned by this thread
-      const bool jok = j < p.n;
-      const int rows_here = min(BM_T, p.m - m0);
+      const int col = j.n0 + q * 32 + lane;               // column of C owned by this thread
+      const bool cok = col < e.n;
+      const int rows_here = min(j.bm, e.m - j.m0);
       const int nchunks = (rows_here + 31) >> 5;
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * Cfg::kSetCols;
       for (int c = 0; c < nchunks; ++c) {
@@ -310,34 +377,34 @@ __global__ void __launch_bounds__(192, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(&tmem_empty[acc]);
         }
-        const int i0 = m0 + c * 32;
-        const int iend = min(32, p.m - i0);
-        if (jok) {
-          if (p.out_mode == OUT_F32) {
-            float* cp = static_cast<float*>(p.C) + (long long)i0 * p.ldc + j;
+        const int i0 = j.m0 + c * 32;
+        const int iend = min(32, e.m - i0);
+        if (cok) {
+          if (e.out_mode == OUT_F32) {
+            float* cp = static_cast<float*>(e.C) + (long long)i0 * e.ldc + col;
             if (beta != 0.0f) {
 #pragma unroll
               for (int i = 0; i < 32; ++i)
-                if (i < iend) cp[i * p.ldc] = fmaf(alpha, __uint_as_float(r[i]), beta * cp[i * p.ldc]);
+                if (i < iend) cp[i * e.ldc] = fmaf(alpha, __uint_as_float(r[i]), beta * cp[i * e.ldc]);
             } else {
 #pragma unroll
               for (int i = 0; i < 32; ++i)
-                if (i < iend) cp[i * p.ldc] = alpha * __uint_as_float(r[i]);
+                if (i < iend) cp[i * e.ldc] = alpha * __uint_as_float(r[i]);
             }
-          } else if (p.out_mode == OUT_I32) {
-            int* cp = static_cast<int*>(p.C) + (long long)i0 * p.ldc + j;
+          } else if (e.out_mode == OUT_I32) {
+            int* cp = static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
               if (i < iend) {
                 const int v = __float2int_rn(__uint_as_float(r[i]));
-                cp[i * p.ldc] = (beta != 0.0f) ? (cp[i * p.ldc] + v) : v;
+                cp[i * e.ldc] = (beta != 0.0f) ? (cp[i * e.ldc] + v) : v;
               }
             }
           } else {
-            float* pp = p.partial + (long long)s * p.m * p.n + (long long)i0 * p.n + j;
+            float* pp = e.partial + (long long)i0 * e.n + col;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (i < iend) pp[(long long)i * p.n] = __uint_as_float(r[i]);
+              if (i < iend) pp[(long long)i * e.n] = __uint_as_float(r[i]);
           }
         }
       }
@@ -350,6 +417,32 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_after();
     tmem_dealloc(tmem_base, Cfg::kTmemCols);
   }
+}
+
+template <int BM_T, int STAGES, int MODE>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
+                   const __grid_constant__ TcParams p) {
+  if (threadIdx.x == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+    if (MODE == TC_3XBF16) {
+      tma_prefetch_desc(&tmA_lo);
+      tma_prefetch_desc(&tmB_lo);
+    }
+  }
+  const SingleSched<BM_T> S{&p, {&tmA, &tmB, &tmA_lo, &tmB_lo}};
+  tc_gemm_body<BM_T, STAGES, MODE>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
+}
+
+// Many independent problems in one persistent launch: every CTA walks the
+// global tile index of all problems; each tile finds its problem in
+// gp.tile_info and uses that problem's tensor maps, tile height and epilogue.
+template <int BM_T, int STAGES, int MODE>
+__global__ void __launch_bounds__(192, 1) tc_grouped_kernel(const __grid_constant__ GroupedParams gp) {
+  const GroupedSched S{&gp};
+  tc_gemm_body<BM_T, STAGES, MODE>(S, gp.timeout_ns, gp.status, gp.debug_withhold, nullptr, nullptr);
 }
 
 }  // namespace g3

@@ -75,8 +75,26 @@ def enumerate_family():
     return members
 
 
+# Grouped launches: problems of at most 1024 x 1024 take tiles of 64 or 128
+# rows (chosen per problem by the planner's size bucket), so the kernel's
+# buffers are sized for bm_max = 128; one member per mode with the deepest ring.
+GROUPED_MODES = ("bf16", "3xbf16")
+GROUPED_BM_MAX = 128
+
+
+def enumerate_grouped():
+    out = []
+    for mode in GROUPED_MODES:
+        fits = [s for s in range(2, 9) if smem_bytes(mode, GROUPED_BM_MAX, s) <= SMEM_LIMIT]
+        st = max(fits)
+        out.append({"index": len(out), "mode": mode, "bm_max": GROUPED_BM_MAX, "stages": st,
+                    "smem": smem_bytes(mode, GROUPED_BM_MAX, st)})
+    return out
+
+
 def write(out_dir: str) -> list:
     members = enumerate_family()
+    grouped = enumerate_grouped()
     lines = ["// Generated by gen_family.py -- do not edit.",
              "// X(index, mode, bm, stages)",
              "#define G3_FAMILY_LIST(X) \\"]
@@ -84,6 +102,13 @@ def write(out_dir: str) -> list:
         lines.append(f"  X({m['index']}, {MODE_ENUM[m['mode']]}, {m['bm']}, {m['stages']}) \\")
     lines.append("")
     lines.append(f"#define G3_FAMILY_SIZE {len(members)}")
+    lines.append("")
+    lines.append("// X(index, mode, bm_max, stages): persistent grouped kernels")
+    lines.append("#define G3_GROUPED_LIST(X) \\")
+    for g in grouped:
+        lines.append(f"  X({g['index']}, {MODE_ENUM[g['mode']]}, {g['bm_max']}, {g['stages']}) \\")
+    lines.append("")
+    lines.append(f"#define G3_GROUPED_SIZE {len(grouped)}")
     text = "\n".join(lines) + "\n"
     inc = os.path.join(out_dir, "csrc", "family_gen.inc")
     old = open(inc).read() if os.path.exists(inc) else None
@@ -91,7 +116,7 @@ def write(out_dir: str) -> list:
         with open(inc, "w") as f:
             f.write(text)
     js = os.path.join(out_dir, "family.json")
-    jtext = json.dumps(members, indent=1) + "\n"
+    jtext = json.dumps({"members": members, "grouped": grouped}, indent=1) + "\n"
     old = open(js).read() if os.path.exists(js) else None
     if old != jtext:
         with open(js, "w") as f:

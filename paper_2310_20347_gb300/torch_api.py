@@ -92,3 +92,42 @@ def quantize_fp8(x: torch.Tensor, stream=None):
 def device_status():
     st, code = _lib.g3_get_last_device_status()
     return st, code
+
+
+class GroupedPlan:
+    """A g3_grouped_plan over (A, B, C, alpha, beta) tuples of torch tensors.
+    The tensors must stay alive while the plan exists."""
+
+    def __init__(self, problems, dtype):
+        in_t = _ELEM[dtype][0]
+        descs = []
+        self._keep = []
+        for (A, B, C, alpha, beta) in problems:
+            m, k = A.shape
+            n = B.shape[1]
+            if A.dtype != in_t or B.dtype != in_t or C.dtype != torch.float32:
+                raise TypeError("operand dtypes do not match the plan's dtype")
+            d = _lib.g3_gemm_desc()
+            d.m, d.n, d.k = m, n, k
+            d.lda, d.ldb, d.ldc = _ld(A, "A"), _ld(B, "B"), _ld(C, "C")
+            d.alpha, d.beta = float(alpha), float(beta)
+            d.A, d.B, d.C = _ptr(A), _ptr(B), _ptr(C)
+            descs.append(d)
+            self._keep.append((A, B, C))
+        st, plan = _lib.g3_grouped_plan_create(descs, dtype)
+        check(st, "g3_grouped_plan_create")
+        self.plan = plan
+
+    def execute(self, stream=None):
+        check(_lib.g3_grouped_plan_execute(self.plan, _stream(stream)), "g3_grouped_plan_execute")
+
+    def close(self):
+        if self.plan is not None:
+            _lib.g3_grouped_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -68,7 +68,7 @@ def test_family_matches_generator(lib):
     members = gen_family.enumerate_family()
     assert lib.g3_family_size() == len(members)
     with open(os.path.join(ROOT, "paper_2310_20347_gb300", "family.json")) as f:
-        assert json.load(f) == members
+        assert json.load(f) == {"members": members, "grouped": gen_family.enumerate_grouped()}
     for m in members:
         d = lib.g3_family_describe(m["index"])
         assert f"mode={m['mode']} bm={m['bm']} " in d and f"stages={m['stages']}" in d

@@ -1,0 +1,162 @@
+"""Parity of the persistent grouped launch (many uneven GEMMs, one kernel)
+with the oracle, problem by problem, plus CUDA-graph capture, determinism,
+guard bands, degenerate problems and the watchdog."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import SENTINEL, rel_err
+from paper_2310_20347_gb300 import G3_BF16, G3_F32_3XBF16, _lib, synth, torch_api
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(count, seed, lo=1, hi=300, dtype=G3_BF16, unaligned_every=5):
+    """Problems with log-uniform sizes; every `unaligned_every`-th one gets
+    leading dimensions that are not 16-byte multiples; C sits in a guard band."""
+    shapes = synth.grouped_shapes(count, seed=seed, lo=lo, hi=hi)
+    probs, host = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        p = synth.uniform_problem(m, n, k, seed=seed * 1000 + i, alpha=1.0 if i % 3 else -0.5,
+                                  beta=0.0 if i % 2 else 0.5)
+        pad = 3 if (unaligned_every and i % unaligned_every == 0) else 0
+        A32 = torch.zeros(m, k + pad, device="cuda")[:, :k]
+        A32.copy_(torch.from_numpy(p.A))
+        B32 = torch.zeros(k, n + pad, device="cuda")[:, :n]
+        B32.copy_(torch.from_numpy(p.B))
+        if dtype == G3_BF16:
+            Ab = torch.zeros(m, k + pad, dtype=torch.bfloat16, device="cuda")[:, :k]
+            Ab.copy_(torch_api.convert_bf16(A32.contiguous()))
+            Bb = torch.zeros(k, n + pad, dtype=torch.bfloat16, device="cuda")[:, :n]
+            Bb.copy_(torch_api.convert_bf16(B32.contiguous()))
+            A, B = Ab, Bb
+        else:
+            A, B = A32, B32
+        full = torch.full((m + 2, n + 7), SENTINEL, device="cuda")
+        C = full[1:1 + m, 3:3 + n]
+        if p.C is not None:
+            C.copy_(torch.from_numpy(p.C))
+        probs.append((A, B, C, p.alpha, p.beta))
+        host.append((p, full))
+    return probs, host
+
+
+def check_batch(probs, host, dtype):
+    worst_k = worst_g = 0.0
+    for (A, B, C, alpha, beta), (p, full) in zip(probs, host):
+        f = full.cpu().numpy()
+        mask = np.ones(f.shape, bool)
+        mask[1:1 + p.m, 3:3 + p.n] = False
+        assert np.all(f[mask] == np.float32(SENTINEL)), "guard band overwritten"
+        got = C.cpu().numpy()
+        bc = None if p.C is None else p.beta * p.C.astype(np.float64)
+        if dtype == G3_BF16:
+            Aq, Bq = oracle.round_bf16(p.A), oracle.round_bf16(p.B)
+            ref_k = oracle.gemm(Aq, Bq, p.C, p.alpha, p.beta)
+            D_k = oracle.absprod(Aq, Bq, p.alpha)
+            gate = 8e-3
+        else:
+            ref_k = oracle.gemm_3xbf16(p.A, p.B, p.C, p.alpha, p.beta)
+            D_k = oracle.absprod(p.A, p.B, p.alpha)
+            gate = 1.2e-4       # the 3-product split's own bound at any k (3*2^-16)
+        e_k = rel_err(got, ref_k, D_k, bc)
+        e_g = rel_err(got, oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), oracle.absprod(p.A, p.B, p.alpha), bc)
+        assert e_k <= 1e-5, (p.m, p.n, p.k, "kernel", e_k)
+        assert e_g <= gate, (p.m, p.n, p.k, "gate", e_g)
+        worst_k, worst_g = max(worst_k, e_k), max(worst_g, e_g)
+    return worst_k, worst_g
+
+
+@pytest.mark.parametrize("dtype", [G3_BF16, G3_F32_3XBF16])
+def test_grouped_parity(dtype):
+    probs, host = make_batch(60, seed=1, dtype=dtype)
+    plan = torch_api.GroupedPlan(probs, dtype)
+    plan.execute()
+    torch.cuda.synchronize()
+    ek, eg = check_batch(probs, host, dtype)
+    print(f"grouped dtype {dtype}: kernel {ek:.3e} gate {eg:.3e}")
+    plan.close()
+
+
+def test_grouped_large_shapes_and_tiles():
+    # sizes up to 1024 as in the 1000-problem workload: several tiles per problem
+    probs, host = make_batch(12, seed=2, lo=100, hi=1024, dtype=G3_BF16, unaligned_every=0)
+    plan = torch_api.GroupedPlan(probs, G3_BF16)
+    plan.execute()
+    torch.cuda.synchronize()
+    check_batch(probs, host, G3_BF16)
+
+
+def test_grouped_degenerate_problems():
+    dev = "cuda"
+    A = torch.zeros(5, 7, dtype=torch.bfloat16, device=dev)
+    B = torch.zeros(7, 9, dtype=torch.bfloat16, device=dev)
+    C0 = torch.full((5, 9), 2.0, device=dev)
+    C1 = torch.full((5, 9), 2.0, device=dev)
+    C2 = torch.full((0, 9), 2.0, device=dev)
+    Ak = torch.zeros(5, 0, dtype=torch.bfloat16, device=dev)
+    Bk = torch.zeros(0, 9, dtype=torch.bfloat16, device=dev)
+    probs = [(Ak, Bk, C0, 1.0, 0.5),             # k = 0: C := beta*C
+             (A, B, C1, 0.0, 3.0),               # alpha = 0: C := beta*C
+             (torch.zeros(0, 7, dtype=torch.bfloat16, device=dev), B, C2, 1.0, 0.0)]   # m = 0
+    plan = torch_api.GroupedPlan(probs, G3_BF16)
+    plan.execute()
+    torch.cuda.synchronize()
+    assert torch.all(C0 == 1.0) and torch.all(C1 == 6.0)
+    plan.close()
+
+
+def test_grouped_graph_capture_and_determinism():
+    probs, host = make_batch(40, seed=3, dtype=G3_F32_3XBF16)
+    # beta = 0 everywhere so that replays are idempotent
+    probs = [(A, B, C, a, 0.0) for (A, B, C, a, b) in probs]
+    for (p, _full) in host:
+        p.beta = 0.0
+    plan = torch_api.GroupedPlan(probs, G3_F32_3XBF16)
+    plan.execute()
+    torch.cuda.synchronize()
+    first = [C.clone() for (_, _, C, _, _) in probs]
+    for (_, _, C, _, _) in probs:
+        C.zero_()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.execute(stream=s)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for f, (_, _, C, _, _) in zip(first, probs):
+        assert torch.equal(f, C)
+    check_batch(probs, host, G3_F32_3XBF16)
+
+
+def test_grouped_argument_errors():
+    good = _lib.g3_gemm_desc()
+    good.m = good.n = good.k = 4
+    good.lda = good.ldb = good.ldc = 4
+    good.A = good.B = good.C = 16
+    bad = _lib.g3_gemm_desc()
+    bad.m, bad.n, bad.k = 4, 4, 8
+    bad.lda, bad.ldb, bad.ldc = 7, 4, 4
+    bad.A = bad.B = bad.C = 16
+    st, plan = _lib.g3_grouped_plan_create([good, good, bad], G3_BF16)
+    assert st == -102
+    st, plan = _lib.g3_grouped_plan_create([good], _lib.G3_FP8_E4M3)
+    assert st == _lib.G3_ERR_UNSUPPORTED
+
+
+def test_grouped_watchdog():
+    probs, host = make_batch(10, seed=4, lo=64, hi=256, dtype=G3_BF16, unaligned_every=0)
+    plan = torch_api.GroupedPlan(probs, G3_BF16)
+    assert _lib.g3_debug_withhold_next(200) == 0
+    plan.execute()
+    st, code = torch_api.device_status()
+    assert st == _lib.G3_ERR_TIMEOUT and code != 0
+    for (A, B, C, a, b), (p, full) in zip(probs, host):
+        if p.C is not None:
+            C.copy_(torch.from_numpy(p.C))
+    plan.execute()
+    torch.cuda.synchronize()
+    check_batch(probs, host, G3_BF16)
+    assert torch_api.device_status()[0] == 0
