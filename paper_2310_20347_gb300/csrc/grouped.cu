@@ -39,14 +39,15 @@ struct PrepJob {
   float beta;         // PREP_SCALE_C
 };
 
-// blockIdx.y strides over jobs, the x-dimension over each job's elements.
+// blockIdx.y strides over jobs, the x-dimension over each job's elements
+// (a grouped problem is at most 2^31 elements, so 32-bit index arithmetic).
 __global__ void grouped_prep_kernel(const PrepJob* __restrict__ jobs, int njobs) {
   for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
     const PrepJob J = jobs[jb];
-    const long long total = (long long)J.rows * J.cols;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-      const long long r = e / J.cols, c = e - r * J.cols;
+    const unsigned total = (unsigned)J.rows * (unsigned)J.cols;
+    const unsigned cols = (unsigned)J.cols;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+      const unsigned r = e / cols, c = e - r * cols;
       if (J.kind == PREP_SPLIT) {
         const float v = static_cast<const float*>(J.src)[r * J.ld_src + c];
         const uint16_t h = bf16_bits(v);
@@ -111,6 +112,8 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     const int code = i < 900 ? -(100 + i) : G3_ERR_ARG;
     if (d.m < 0 || d.n < 0 || d.k < 0) return code;
     if (d.m > INT32_MAX || d.n > INT32_MAX || d.k > INT32_MAX) return G3_ERR_UNSUPPORTED;
+    // every operand and C of one problem must fit 32-bit element indexing
+    if (d.m * d.k > INT32_MAX || d.k * d.n > INT32_MAX || d.m * d.n > INT32_MAX) return G3_ERR_UNSUPPORTED;
     if (d.lda < std::max<int64_t>(1, d.k) || d.ldb < std::max<int64_t>(1, d.n) ||
         d.ldc < std::max<int64_t>(1, d.n))
       return code;

@@ -119,18 +119,21 @@ struct TcConfig {
   // truncation, so the FP32-accurate mode keeps the hi*hi products and the
   // hi*lo + lo*hi corrections in separate accumulators (one third of the
   // truncating updates each for the large term) and adds them, rounded to
-  // nearest, in the epilogue.  Accumulator sets are double-buffered across
-  // output tiles when TMEM (512 columns) has room.
+  // nearest, in the epilogue.  Accumulator sets are multi-buffered across
+  // output tiles as far as TMEM (512 columns) allows, up to kMaxBufs, so that
+  // the MMA can run several short tiles ahead of the epilogue.
   static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16) ? 2 : 1;
   static constexpr uint32_t kSetCols = kAccPerTile * BM_T;
-  static constexpr uint32_t kNumBufs = (2 * kSetCols <= 512) ? 2 : 1;
+  static constexpr uint32_t kMaxBufs = 4;
+  static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
   static constexpr uint32_t kTmemCols = kNumBufs * kSetCols;
   static constexpr uint32_t kBarBytes = 256;
   static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kBarBytes;
   static constexpr int kThreads = 192;
   static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
-  static_assert(8 * (2 * STAGES + 5) + 8 <= (int)kBarBytes, "barrier area");
+  static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32 && kTmemCols <= 512, "TMEM allocation");
+  static_assert(8 * (2 * STAGES + 2 * kMaxBufs + 1) + 8 <= (int)kBarBytes, "barrier area");
 };
 
 // One output tile: rows m0 .. m0+bm-1, columns n0 .. n0+127 of problem g, k-blocks kb0 .. kb1-1.
@@ -211,8 +214,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::kStageBytes);
   uint64_t* empty = full + STAGES;
   uint64_t* tmem_full = empty + STAGES;
-  uint64_t* tmem_empty = tmem_full + 2;
-  uint64_t* drain = tmem_empty + 2;
+  uint64_t* tmem_empty = tmem_full + Cfg::kMaxBufs;
+  uint64_t* drain = tmem_empty + Cfg::kMaxBufs;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -224,7 +227,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < (int)Cfg::kNumBufs; ++a) {
       mbar_init(&tmem_full[a], 1);
       mbar_init(&tmem_empty[a], 4);
     }
@@ -360,23 +363,14 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       const int rows_here = min(j.bm, e.m - j.m0);
       const int nchunks = (rows_here + 31) >> 5;
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * Cfg::kSetCols;
-      for (int c = 0; c < nchunks; ++c) {
-        uint32_t r[32];
-        tmem_ld_32x32b_x32(tbase + c * 32, r);
-        if (MODE == TC_3XBF16) {
-          uint32_t rc[32];
-          tmem_ld_32x32b_x32(tbase + BM_T + c * 32, rc);
-          tmem_ld_wait();
-#pragma unroll
-          for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(__fadd_rn(__uint_as_float(r[i]), __uint_as_float(rc[i])));
-        } else {
-          tmem_ld_wait();
-        }
-        if (c == nchunks - 1) {
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&tmem_empty[acc]);
-        }
+      // Hand the accumulator set back to the MMA issuer once its last TMEM load completed.
+      auto release = [&]() {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tmem_empty[acc]);
+      };
+      // Rows i0 .. i0+31 of this thread's column: alpha/beta and the stores.
+      auto store_chunk = [&](const uint32_t (&r)[32], int c) {
         const int i0 = j.m0 + c * 32;
         const int iend = min(32, e.m - i0);
         if (cok) {
@@ -405,6 +399,42 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 #pragma unroll
             for (int i = 0; i < 32; ++i)
               if (i < iend) pp[(long long)i * e.n] = __uint_as_float(r[i]);
+          }
+        }
+      };
+      if (MODE == TC_3XBF16) {
+        for (int c = 0; c < nchunks; ++c) {
+          uint32_t r[32], rc[32];
+          tmem_ld_32x32b_x32(tbase + c * 32, r);
+          tmem_ld_32x32b_x32(tbase + BM_T + c * 32, rc);
+          tmem_ld_wait();
+          if (c == nchunks - 1) release();
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            r[i] = __float_as_uint(__fadd_rn(__uint_as_float(r[i]), __uint_as_float(rc[i])));
+          store_chunk(r, c);
+        }
+      } else {
+        // Software pipeline: the TMEM load of chunk c+1 is in flight while
+        // chunk c is scaled and stored.
+        uint32_t ra[32], rb[32];
+        tmem_ld_32x32b_x32(tbase, ra);
+        tmem_ld_wait();
+        if (nchunks == 1) release();
+        for (int c = 0; c < nchunks; c += 2) {
+          const bool has_b = c + 1 < nchunks;
+          if (has_b) tmem_ld_32x32b_x32(tbase + (c + 1) * 32, rb);
+          store_chunk(ra, c);
+          if (has_b) {
+            tmem_ld_wait();
+            if (c + 1 == nchunks - 1) release();
+            const bool has_a = c + 2 < nchunks;
+            if (has_a) tmem_ld_32x32b_x32(tbase + (c + 2) * 32, ra);
+            store_chunk(rb, c + 1);
+            if (has_a) {
+              tmem_ld_wait();
+              if (c + 2 == nchunks - 1) release();
+            }
           }
         }
       }
