@@ -200,6 +200,24 @@ G3_API int g3_family_describe(int index, char* buf, size_t len);
  * split count, raster band); -1 in *config for the FP32 SIMT kernel.        */
 G3_API int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* split_k, int* raster);
 
+/* --- Autotuner: the per-shape search of the paper's Section 8.4 -------------
+ * g3_autotune times every member of the generated family that applies to
+ * `dtype`, each with split-K in {1, 2, 3, 4, 6, 8, 12, 16} (bounded by the
+ * k-blocks), on scratch operands of shape m x n x k it allocates and frees,
+ * and records the fastest (member, split) for the shape's size bucket: dtype
+ * and ceil(log2) of each of m, n, k.  Later g3_gemm calls in that bucket use
+ * the record instead of the planner's model.  Synchronous; allocates.
+ * Outputs (any may be NULL): the member index, the split count, its time in
+ * ms.  G3_F32 has a single kernel: *best_config = -1.
+ * g3_tune_cache_save / load write and read the records as text ("dtype
+ * log2(m) log2(n) log2(k) member split ms" per line); the environment variable
+ * G3_TUNE_CACHE names a file loaded on first planning.  clear forgets all.   */
+G3_API int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, int* best_split,
+                       double* best_ms);
+G3_API int g3_tune_cache_save(const char* path);
+G3_API int g3_tune_cache_load(const char* path);
+G3_API int g3_tune_cache_clear(void);
+
 /* Kernel launches issued by the library since the process started.         */
 G3_API uint64_t g3_launch_count(void);
 

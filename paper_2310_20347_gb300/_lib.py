@@ -29,6 +29,7 @@ EXPORTED = (
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
     "g3_plan_query", "g3_launch_count", "g3_kernel_timing", "g3_kernel_time_ms",
     "g3_debug_withhold_next", "g3_gemm_3xbf16_noalloc",
+    "g3_autotune", "g3_tune_cache_save", "g3_tune_cache_load", "g3_tune_cache_clear",
 )
 
 
@@ -95,6 +96,11 @@ def load(path: str = LIB_PATH):
             "g3_kernel_time_ms": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
             "g3_debug_withhold_next": ([i64], i32),
             "g3_gemm_3xbf16_noalloc": ([i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp], i32),
+            "g3_autotune": ([i64, i64, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                             ctypes.POINTER(dbl)], i32),
+            "g3_tune_cache_save": ([ctypes.c_char_p], i32),
+            "g3_tune_cache_load": ([ctypes.c_char_p], i32),
+            "g3_tune_cache_clear": ([], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -206,6 +212,24 @@ def g3_kernel_time_ms(reset: bool = True):
     ms, n = ctypes.c_double(0.0), ctypes.c_int(0)
     load().g3_kernel_time_ms(ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0)
     return ms.value, n.value
+
+
+def g3_autotune(m, n, k, dtype):
+    c, s, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    st = load().g3_autotune(m, n, k, dtype, ctypes.byref(c), ctypes.byref(s), ctypes.byref(ms))
+    return st, c.value, s.value, ms.value
+
+
+def g3_tune_cache_save(path: str) -> int:
+    return load().g3_tune_cache_save(path.encode())
+
+
+def g3_tune_cache_load(path: str) -> int:
+    return load().g3_tune_cache_load(path.encode())
+
+
+def g3_tune_cache_clear() -> int:
+    return load().g3_tune_cache_clear()
 
 
 def g3_debug_withhold_next(timeout_ms: int) -> int:

@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "g3gemm.h"
@@ -152,9 +154,68 @@ struct Plan {
 // grows as N shrinks; values from the operand bytes each MMA reads).
 double tile_efficiency(int bm) { return bm >= 256 ? 1.0 : (bm >= 128 ? 0.8 : 0.55); }
 
+// ---------------------------------------------------------------- tuning cache
+// Results of g3_autotune, keyed by dtype and the power-of-two bucket of each of
+// m, n, k (the smallest b with 2^b >= x); the planner prefers them to its model.
+struct TuneKey {
+  int dtype, bm, bn, bk;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dtype, bm, bn, bk) < std::tie(o.dtype, o.bm, o.bn, o.bk);
+  }
+};
+struct TuneVal {
+  int member, split;
+  double ms;
+};
+std::map<TuneKey, TuneVal> g_tune;
+bool g_tune_env_loaded = false;
+
+int size_bucket(int64_t x) {
+  int b = 0;
+  while ((int64_t(1) << b) < x && b < 62) ++b;
+  return b;
+}
+TuneKey tune_key(int64_t m, int64_t n, int64_t k, int dtype) {
+  return TuneKey{dtype, size_bucket(m), size_bucket(n), size_bucket(k)};
+}
+
+int tune_load_locked(const char* path) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return -101;
+  char line[256];
+  int loaded = 0;
+  while (std::fgets(line, sizeof line, f)) {
+    TuneKey key;
+    TuneVal val;
+    if (line[0] == '#') continue;
+    if (std::sscanf(line, "%d %d %d %d %d %d %lf", &key.dtype, &key.bm, &key.bn, &key.bk, &val.member, &val.split,
+                    &val.ms) == 7 &&
+        val.member >= 0 && val.member < G3_FAMILY_SIZE && val.split >= 1) {
+      g_tune[key] = val;
+      ++loaded;
+    }
+  }
+  std::fclose(f);
+  return loaded;
+}
+
+void tune_env_once() {
+  if (g_tune_env_loaded) return;
+  g_tune_env_loaded = true;
+  if (const char* p = std::getenv("G3_TUNE_CACHE")) tune_load_locked(p);
+}
+
 Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_member, int force_split,
                int force_raster) {
   Plan pl;
+  if (force_member < 0 && force_split <= 0) {
+    tune_env_once();
+    auto it = g_tune.find(tune_key(m, n, k, dtype));
+    if (it != g_tune.end()) {
+      force_member = it->second.member;
+      force_split = it->second.split;
+    }
+  }
   const int mode = tc_mode_of(dtype);
   const int bk = (mode == TC_FP8) ? 128 : 64;
   pl.num_kb = (int)((k + bk - 1) / bk);
@@ -710,6 +771,131 @@ int g3_kernel_time_ms(double* total_ms, int* launches, int reset) {
     }
     g_events.clear();
   }
+  return G3_OK;
+}
+
+int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, int* best_split, double* best_ms) {
+  if (m <= 0) return -101;
+  if (n <= 0) return -102;
+  if (k <= 0) return -103;
+  if (dtype < G3_F32 || dtype > G3_INT8) return -104;
+  if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || (dtype == G3_INT8 && k > 131072)) return G3_ERR_UNSUPPORTED;
+  if (dtype == G3_F32) {   // one kernel: nothing to choose
+    if (best_config) *best_config = -1;
+    if (best_split) *best_split = 1;
+    if (best_ms) *best_ms = 0.0;
+    return G3_OK;
+  }
+  int sms = 152;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    DevState* d = nullptr;
+    const int st = ensure_device(&d);
+    if (st != G3_OK) return st;
+    sms = d->sms;
+  }
+  const int es_in = (dtype == G3_BF16) ? 2 : (dtype == G3_F32_3XBF16 ? 4 : 1);
+  const int64_t lda = round_up(k, 16), ldb = round_up(n, 16);
+  void *A = nullptr, *B = nullptr, *C = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(C);
+    cudaGetLastError();
+  };
+  if (cudaMalloc(&A, (size_t)m * lda * es_in) != cudaSuccess || cudaMalloc(&B, (size_t)k * ldb * es_in) != cudaSuccess ||
+      cudaMalloc(&C, (size_t)m * n * 4) != cudaSuccess) {
+    cleanup();
+    return G3_ERR_NOMEM;
+  }
+  // small non-zero operands (0x3C in every byte): representative tensor-core power
+  cudaMemset(A, 0x3C, (size_t)m * lda * es_in);
+  cudaMemset(B, 0x3C, (size_t)k * ldb * es_in);
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    return G3_ERR_CUDA;
+  }
+  const int mode = tc_mode_of(dtype);
+  const int bk = (mode == TC_FP8) ? 128 : 64;
+  const int num_kb = (int)((k + bk - 1) / bk);
+  int best_member = -1, best_sk = 1;
+  double best = 1e30;
+  for (int i = 0; i < G3_FAMILY_SIZE; ++i) {
+    if (!g_family[i].launch || g_family[i].mode != mode) continue;
+    for (int sk : {1, 2, 3, 4, 6, 8, 12, 16}) {
+      if (sk > num_kb) break;
+      if (dtype == G3_INT8 && (num_kb + sk - 1) / sk > 16 && sk < (num_kb + 15) / 16) continue;
+      g3_gemm_args a;
+      g3_gemm_args_init(&a);
+      a.m = m; a.n = n; a.k = k;
+      a.alpha = 1.0; a.beta = 0.0;
+      a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = n;
+      a.dtype = dtype;
+      a.config = i;
+      a.split_k = sk;
+      if (gemm_impl(a, s) != G3_OK) continue;   // warm-up (and workspace growth)
+      double t_min = 1e30;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        const int st = gemm_impl(a, s);
+        cudaEventRecord(e1, s);
+        if (st != G3_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+          t_min = 1e30;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t_min = std::min(t_min, (double)ms);
+      }
+      if (t_min < best) {
+        best = t_min;
+        best_member = i;
+        best_sk = sk;
+      }
+    }
+  }
+  cleanup();
+  if (best_member < 0) return G3_ERR_UNSUPPORTED;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_tune[tune_key(m, n, k, dtype)] = TuneVal{best_member, best_sk, best};
+  }
+  (void)sms;
+  if (best_config) *best_config = best_member;
+  if (best_split) *best_split = best_sk;
+  if (best_ms) *best_ms = best;
+  return G3_OK;
+}
+
+int g3_tune_cache_save(const char* path) {
+  if (!path) return -101;
+  std::lock_guard<std::mutex> lock(g_mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return -101;
+  std::fprintf(f, "# g3gemm tuning cache: dtype log2(m) log2(n) log2(k) member split ms\n");
+  for (const auto& kv : g_tune)
+    std::fprintf(f, "%d %d %d %d %d %d %.6f\n", kv.first.dtype, kv.first.bm, kv.first.bn, kv.first.bk,
+                 kv.second.member, kv.second.split, kv.second.ms);
+  std::fclose(f);
+  return G3_OK;
+}
+
+int g3_tune_cache_load(const char* path) {
+  if (!path) return -101;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int n = tune_load_locked(path);
+  return n < 0 ? n : G3_OK;
+}
+
+int g3_tune_cache_clear(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_tune.clear();
   return G3_OK;
 }
 

@@ -93,3 +93,27 @@ def test_planner_choices(lib):
     assert sk == 8
     st, cfg, sk, rs = L.g3_plan_query(128, 128, 100, L.G3_F32)
     assert cfg == -1
+
+
+def test_tuning_cache_overrides_planner(lib, tmp_path):
+    from paper_2310_20347_gb300 import gen_family
+    fam = gen_family.enumerate_family()
+    L = lib
+    assert L.g3_tune_cache_clear() == 0
+    st, cfg0, sk0, _ = L.g3_plan_query(1000, 3000, 700, L.G3_BF16)
+    other = next(f["index"] for f in fam if f["mode"] == "bf16" and f["index"] != cfg0)
+    # bucket of (1000, 3000, 700) = (10, 12, 10); dtype G3_BF16 = 2
+    path = tmp_path / "tune.txt"
+    path.write_text(f"# test\n2 10 12 10 {other} 3 0.5\n")
+    assert L.g3_tune_cache_load(str(path)) == 0
+    st, cfg, sk, _ = L.g3_plan_query(1000, 3000, 700, L.G3_BF16)
+    assert (cfg, sk) == (other, 3)
+    # another shape of the same bucket follows the record; another bucket does not
+    assert L.g3_plan_query(600, 2100, 513, L.G3_BF16)[1:3] == (other, 3)
+    assert L.g3_plan_query(1000, 3000, 1500, L.G3_BF16)[1:3] == (cfg0, sk0)
+    out = tmp_path / "saved.txt"
+    assert L.g3_tune_cache_save(str(out)) == 0
+    assert f"2 10 12 10 {other} 3" in out.read_text()
+    assert L.g3_tune_cache_clear() == 0
+    assert L.g3_plan_query(1000, 3000, 700, L.G3_BF16)[1:3] == (cfg0, sk0)
+    assert L.g3_tune_cache_load(str(tmp_path / "missing.txt")) == -101
