@@ -58,6 +58,7 @@ void family_init() {
   register_family_bf16(g_family);
   register_family_3xbf16(g_family);
   register_family_fp8(g_family);
+  register_family_int8emu(g_family);
   g_family_ready = true;
 }
 
@@ -123,6 +124,21 @@ int encode_2d(CUtensorMap* map, const void* base, int esize, uint64_t inner, uin
   return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
 }
 
+// C (m rows x n columns of 4-byte elements, leading dimension ldc) for TMA
+// stores of 32-row x 128-column boxes, no swizzle (row-major staging tile).
+int encode_c_2d(CUtensorMap* map, void* base, bool is_int, uint64_t n, uint64_t m, uint64_t ldc) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return G3_ERR_CUDA;
+  cuuint64_t dims[2] = {n, m};
+  cuuint64_t strides[1] = {ldc * 4};
+  cuuint32_t box[2] = {128, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
+}
+
 bool tma_ok(const void* p, int64_t ld, int esize) {
   return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((ld * esize) % 16 == 0);
 }
@@ -136,7 +152,7 @@ int tc_mode_of(int dtype) {
     case G3_BF16: return TC_BF16;
     case G3_F32_3XBF16: return TC_3XBF16;
     case G3_FP8_E4M3: return TC_FP8;
-    case G3_INT8: return TC_BF16;   // exact emulation: int8 values are exact in bfloat16
+    case G3_INT8: return TC_I8EMU;  // exact emulation: int8 values are exact in bfloat16
     default: return -1;
   }
 }
@@ -251,10 +267,8 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     splits = (int)std::min<long long>(sms / tiles, std::min(pl.num_kb / 4, 16));
     splits = std::max(splits, 1);
   }
-  if (dtype == G3_INT8) splits = std::max(splits, (pl.num_kb + 15) / 16);   // k-chunks of <= 1024
   splits = std::min(splits, pl.num_kb);
   pl.kb_per_split = (pl.num_kb + splits - 1) / splits;
-  if (dtype == G3_INT8) pl.kb_per_split = std::min(pl.kb_per_split, 16);
   pl.splits = (pl.num_kb + pl.kb_per_split - 1) / pl.kb_per_split;
   pl.raster = force_raster > 0 ? force_raster : 8;
   pl.raster = std::max(1, std::min(pl.raster, pl.tiles_m));
@@ -458,7 +472,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   // TMA descriptors: A as (k inner, m rows) in boxes of BK x bm; B as (n inner,
   // k rows) in boxes of (128 bytes of n) x BK.
   const uint32_t bk = 128 / es, boxn = 128 / es;
-  CUtensorMap maps[4];
+  CUtensorMap maps[5];
   std::memset(maps, 0, sizeof(maps));
   if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
   if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
@@ -490,6 +504,8 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   p.timeout_ns = watchdog_ns();
   p.status = d.status;
   p.debug_withhold = -1;
+  // INT8: at most 16 k-blocks (1024 products, |sum| <= 2^24) per FP32 accumulator
+  p.kchunk = (a.dtype == G3_INT8) ? 16 : 0;
   if (g_withhold_next) {
     p.debug_withhold = 0;
     p.timeout_ns = g_withhold_timeout_ns;
@@ -501,6 +517,11 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
     p.partial = reinterpret_cast<float*>(ws + L.partial);
   } else {
     p.out_mode = is_int ? OUT_I32 : OUT_F32;
+    // C without a read of its old values goes out through TMA stores when its
+    // rows are 16-byte aligned (boxes of 32 rows x 128 columns, clipped to C)
+    if (a.beta == 0.0 && reinterpret_cast<uintptr_t>(a.C) % 16 == 0 && (a.ldc * 4) % 16 == 0 &&
+        encode_c_2d(&maps[4], a.C, is_int, n, m, a.ldc) == G3_OK)
+      p.c_tma = 1;
   }
   const long long total_tiles = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
   const int grid = (int)std::min<long long>(total_tiles, d.sms);
@@ -708,7 +729,7 @@ int g3_family_describe(int index, char* buf, size_t len) {
     family_init();
   }
   const FamilyEntry& f = g_family[index];
-  static const char* names[] = {"bf16", "3xbf16", "fp8"};
+  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu"};
   std::snprintf(buf, len, "mode=%s bm=%d bn=128 stages=%d smem=%d bufs=%d", names[f.mode], f.bm, f.stages, f.smem,
                 f.bufs);
   return G3_OK;
@@ -830,7 +851,6 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
     if (!g_family[i].launch || g_family[i].mode != mode) continue;
     for (int sk : {1, 2, 3, 4, 6, 8, 12, 16}) {
       if (sk > num_kb) break;
-      if (dtype == G3_INT8 && (num_kb + sk - 1) / sk > 16 && sk < (num_kb + 15) / 16) continue;
       g3_gemm_args a;
       g3_gemm_args_init(&a);
       a.m = m; a.n = n; a.k = k;

@@ -72,6 +72,7 @@ void grouped_init() {
   register_grouped_bf16(g_grouped);
   register_grouped_3xbf16(g_grouped);
   register_grouped_fp8(g_grouped);
+  register_grouped_int8emu(g_grouped);
   g_grouped_ready = true;
 }
 

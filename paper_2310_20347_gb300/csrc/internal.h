@@ -10,6 +10,7 @@
 
 namespace g3 {
 
+// maps: A, B, A lo plane, B lo plane, C (the last used only when p.c_tma)
 using TcLaunchFn = cudaError_t (*)(const CUtensorMap* maps, const TcParams& p, int grid, cudaStream_t s);
 
 // One member of the generated tensor-core kernel family.
@@ -26,6 +27,7 @@ struct FamilyEntry {
 void register_family_bf16(FamilyEntry* table);
 void register_family_3xbf16(FamilyEntry* table);
 void register_family_fp8(FamilyEntry* table);
+void register_family_int8emu(FamilyEntry* table);
 
 using GroupedLaunchFn = cudaError_t (*)(const GroupedParams& p, int grid, cudaStream_t s);
 
@@ -42,6 +44,7 @@ struct GroupedEntry {
 void register_grouped_bf16(GroupedEntry* table);
 void register_grouped_3xbf16(GroupedEntry* table);
 void register_grouped_fp8(GroupedEntry* table);
+void register_grouped_int8emu(GroupedEntry* table);
 
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.

@@ -132,8 +132,8 @@ __global__ void scale_c_kernel(TC* __restrict__ C, int rows, int cols, long long
 }
 
 // Deterministic split-K reduction: partial sums are added in split order 0..S-1.
-// INT: partials hold integer values exactly (|x| <= 2^24); they are converted
-// and summed in int32, then C (beta in {0, 1}) is added.
+// INT: the partial planes hold int32 values (the exact-integer kernel writes
+// them as such); they are summed in int32, then C (beta in {0, 1}) is added.
 template <bool INT>
 __global__ void splitk_reduce_kernel(const float* __restrict__ P, int splits, int rows, int cols, float alpha,
                                      float beta, void* C, long long ldc) {
@@ -143,7 +143,8 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ P, int splits, in
       const long long off = (long long)r * cols + c;
       if (INT) {
         int s32 = 0;
-        for (int s = 0; s < splits; ++s) s32 += __float2int_rn(P[s * plane + off]);
+        const int* Pi = reinterpret_cast<const int*>(P);
+        for (int s = 0; s < splits; ++s) s32 += Pi[s * plane + off];
         int* cp = static_cast<int*>(C) + r * ldc + c;
         *cp = (beta != 0.f) ? (*cp + s32) : s32;
       } else {

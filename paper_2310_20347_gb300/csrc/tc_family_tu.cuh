@@ -12,7 +12,7 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int grid, cuda
   auto kern = tc_gemm_kernel<BM, ST, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, Cfg::kThreads, Cfg::kSmemBytes, s>>>(maps[0], maps[1], maps[2], maps[3], p);
+  kern<<<grid, Cfg::kThreads, Cfg::kSmemBytes, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], p);
   count_launch();
   return cudaGetLastError();
 }

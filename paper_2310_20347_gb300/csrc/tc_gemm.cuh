@@ -40,7 +40,11 @@
 
 namespace g3 {
 
-enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2 };
+// TC_I8EMU: int8 GEMM computed exactly on the BF16 tensor path (int8 values are
+// exact in bfloat16); k is accumulated in chunks of at most 1024 products per
+// TMEM accumulator, which keeps every FP32 partial sum an exact integer, and
+// the epilogue adds the chunks in int32.
+enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3 };
 enum OutMode : int { OUT_F32 = 0, OUT_I32 = 1, OUT_PARTIAL = 2 };
 
 // Watchdog status codes (written to the device status word; see g3gemm.h).
@@ -69,6 +73,8 @@ struct TcParams {
   unsigned long long timeout_ns;
   int* status;
   int debug_withhold;     // test hook: producer iteration whose stage never fills (-1: none)
+  int kchunk;             // k-blocks per accumulation chunk (0: the whole k range of a tile)
+  int c_tma;              // 1: C (beta == 0) is written through TMA stores with the tmC map
 };
 
 // One problem of a grouped launch (device table entry).
@@ -127,8 +133,10 @@ struct TcConfig {
   static constexpr uint32_t kMaxBufs = 4;
   static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
   static constexpr uint32_t kTmemCols = kNumBufs * kSetCols;
+  // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128 columns x 4 bytes.
+  static constexpr uint32_t kCStageBytes = 2 * 32 * 128 * 4;
   static constexpr uint32_t kBarBytes = 256;
-  static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kBarBytes;
+  static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kCStageBytes + kBarBytes;
   static constexpr int kThreads = 192;
   static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
@@ -139,6 +147,7 @@ struct TcConfig {
 // One output tile: rows m0 .. m0+bm-1, columns n0 .. n0+127 of problem g, k-blocks kb0 .. kb1-1.
 struct TileJob {
   int m0, n0, kb0, kb1, bm, split, g;
+  int kchunk;   // k-blocks per accumulation chunk, 0 = one chunk
 };
 
 // Where and how a tile's result is written.
@@ -148,13 +157,15 @@ struct EpiJob {
   int m, n;
   float alpha, beta;
   int out_mode;
-  float* partial;   // OUT_PARTIAL: this split's m x n plane (leading dimension n)
+  float* partial;             // OUT_PARTIAL: this split's m x n plane (leading dimension n)
+  const CUtensorMap* cmap;    // non-null: store C (beta == 0) by TMA through this map
 };
 
 template <int BM_T>
 struct SingleSched {
   const TcParams* p;
   const CUtensorMap* maps[4];   // A, B, A lo plane, B lo plane (kernel parameters)
+  const CUtensorMap* cmap;      // C for TMA stores, or null
 
   __device__ __forceinline__ int total() const { return p->tiles_m * p->tiles_n * p->splits; }
 
@@ -169,14 +180,14 @@ struct SingleSched {
     const int tm = band * G + in_band % rows;
     const int tn = in_band / rows;
     const int kb0 = s * p->kb_per_split;
-    return TileJob{tm * BM_T, tn * 128, kb0, min(p->num_kb, kb0 + p->kb_per_split), BM_T, s, 0};
+    return TileJob{tm * BM_T, tn * 128, kb0, min(p->num_kb, kb0 + p->kb_per_split), BM_T, s, 0, p->kchunk};
   }
 
   __device__ __forceinline__ const CUtensorMap* map(const TileJob&, int which) const { return maps[which]; }
 
   __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
     return EpiJob{p->C, p->ldc, p->m, p->n, p->alpha, p->beta, p->out_mode,
-                  p->partial ? p->partial + (long long)j.split * p->m * p->n : nullptr};
+                  p->partial ? p->partial + (long long)j.split * p->m * p->n : nullptr, cmap};
   }
 };
 
@@ -190,7 +201,7 @@ struct GroupedSched {
     const int g = ti.x;
     const GroupDesc* d = gp->groups + g;
     const int tm = ti.y % d->tiles_m, tn = ti.y / d->tiles_m;
-    return TileJob{tm * d->bm, tn * 128, 0, d->num_kb, d->bm, 0, g};
+    return TileJob{tm * d->bm, tn * 128, 0, d->num_kb, d->bm, 0, g, 0};
   }
 
   __device__ __forceinline__ const CUtensorMap* map(const TileJob& j, int which) const {
@@ -199,7 +210,7 @@ struct GroupedSched {
 
   __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
     const GroupDesc* d = gp->groups + j.g;
-    return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr};
+    return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr, nullptr};
   }
 };
 
@@ -208,10 +219,13 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
                                              int debug_withhold, const float* scale_a, const float* scale_b) {
   using T = TcTraits<MODE>;
   using Cfg = TcConfig<BM_T, STAGES, MODE>;
+  constexpr bool kIntChunked = (MODE == TC_I8EMU);
+  static_assert(!kIntChunked || BM_T <= 128, "int32 running sums live in registers: bm <= 128");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::kStageBytes);
+  float* cstage = reinterpret_cast<float*>(smem + STAGES * Cfg::kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::kStageBytes + Cfg::kCStageBytes);
   uint64_t* empty = full + STAGES;
   uint64_t* tmem_full = empty + STAGES;
   uint64_t* tmem_empty = tmem_full + Cfg::kMaxBufs;
@@ -286,18 +300,21 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t it = 0, lt = 0;
+      uint32_t it = 0, lt = 0;   // lt counts accumulation chunks (one per tile unless k is chunked)
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++lt) {
+      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
         const TileJob j = S.tile(t);
         const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/true, /*b_mn=*/false, 128, j.bm);
+        const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
+        for (int c0 = j.kb0; ok && c0 < j.kb1; c0 += span, ++lt) {
+        const int c1 = min(j.kb1, c0 + span);
         const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
         if (!wait_parity(&tmem_empty[acc], aph ^ 1u, wd, WD_MMA_TMEM_EMPTY)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * Cfg::kSetCols;   // main accumulator
         const uint32_t d_corr = d_tmem + BM_T;                       // 3xBF16 corrections
         uint32_t accumulate = 0;
-        for (int kb = j.kb0; kb < j.kb1; ++kb, ++it) {
+        for (int kb = c0; kb < c1; ++kb, ++it) {
           const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
           if (!wait_parity(&full[stage], ph, wd, WD_MMA_FULL)) { ok = false; break; }
           tc_fence_after();
@@ -331,6 +348,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
         }
         if (!ok) break;
         mma_commit(&tmem_full[acc]);   // accumulator ready for the epilogue
+        }
       }
       // Make sure no MMA is in flight before TMEM is released.
       mma_commit(drain);
@@ -347,21 +365,53 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       const float sb = scale_b ? *scale_b : 1.0f;
       scale = sa * sb;
     }
-    uint32_t lt = 0;
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
+    uint32_t lt = 0;   // accumulation chunks consumed, in the MMA issuer's order
+    uint32_t schunk = 0;   // 32-row chunks staged for TMA stores (selects the staging buffer)
+    bool alive = true;
+    for (int t = blockIdx.x; alive && t < total_tiles; t += gridDim.x) {
       const TileJob j = S.tile(t);
       const EpiJob e = S.epi(j);
       const float alpha = e.alpha * scale;
       const float beta = e.beta;
-      const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
-      bool ok = wait_parity(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      tc_fence_after();
       const int col = j.n0 + q * 32 + lane;               // column of C owned by this thread
       const bool cok = col < e.n;
       const int rows_here = min(j.bm, e.m - j.m0);
       const int nchunks = (rows_here + 31) >> 5;
+      const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
+      const int nkc = (j.kb1 - j.kb0 + span - 1) / span;
+      // Outputs that do not read C leave through shared memory and TMA stores
+      // (whole 32 x 128 boxes, clipped to C by the tensor map).
+      const bool use_tma = e.cmap != nullptr && beta == 0.0f && (e.out_mode == OUT_F32 || e.out_mode == OUT_I32);
+      // stage_begin: a free staging buffer (the store issued from it two chunks
+      // ago has read it); this thread's column of the 32 rows goes to
+      // buf[i * 128 + q * 32 + lane]; stage_end: hand the box to the TMA unit.
+      auto stage_begin = [&]() -> float* {
+        if (threadIdx.x == 64) bulk_wait_group_read<1>();
+        named_barrier_sync(1, 128);
+        return cstage + (schunk & 1u) * (32 * 128) + q * 32 + lane;
+      };
+      auto stage_end = [&](int c) {
+        fence_proxy_async_smem();
+        named_barrier_sync(1, 128);
+        if (threadIdx.x == 64) {
+          tma_store_2d(e.cmap, j.n0, j.m0 + c * 32, cstage + (schunk & 1u) * (32 * 128));
+          bulk_commit_group();
+        }
+        ++schunk;
+      };
+      // exact-integer mode: int32 running sums of this thread's column, one per row
+      int isum[kIntChunked ? BM_T : 1];
+#pragma unroll
+      for (int i = 0; i < (kIntChunked ? BM_T : 1); ++i) isum[i] = 0;
+      for (int kc = 0; kc < nkc; ++kc, ++lt) {
+      const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
+      bool ok = wait_parity(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        alive = false;
+        break;
+      }
+      tc_fence_after();
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * Cfg::kSetCols;
       // Hand the accumulator set back to the MMA issuer once its last TMEM load completed.
       auto release = [&]() {
@@ -369,8 +419,59 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
         __syncwarp();
         if (lane == 0) mbar_arrive(&tmem_empty[acc]);
       };
+      if constexpr (kIntChunked) {
+        // Each chunk holds an integer-valued FP32 sum of at most 1024 products
+        // of magnitude <= 2^14, hence exact; convert and add in int32.
+#pragma unroll
+        for (int rc = 0; rc < BM_T / 32; ++rc) {
+          if (rc < nchunks) {
+            uint32_t r[32];
+            tmem_ld_32x32b_x32(tbase + rc * 32, r);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) isum[rc * 32 + i] += __float2int_rn(__uint_as_float(r[i]));
+          }
+        }
+        release();
+        if (kc == nkc - 1 && use_tma) {
+#pragma unroll
+          for (int rc = 0; rc < BM_T / 32; ++rc) {
+            if (rc < nchunks) {
+              float* buf = stage_begin();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) buf[i * 128] = __int_as_float(isum[rc * 32 + i]);
+              stage_end(rc);
+            }
+          }
+        } else if (kc == nkc - 1 && cok) {
+          if (e.out_mode == OUT_PARTIAL) {
+            int* pp = reinterpret_cast<int*>(e.partial) + (long long)j.m0 * e.n + col;
+#pragma unroll
+            for (int i = 0; i < BM_T; ++i)
+              if (i < rows_here) pp[(long long)i * e.n] = isum[i];
+          } else {
+            int* cp = static_cast<int*>(e.C) + (long long)j.m0 * e.ldc + col;
+#pragma unroll
+            for (int i = 0; i < BM_T; ++i)
+              if (i < rows_here) cp[i * e.ldc] = (beta != 0.0f) ? cp[i * e.ldc] + isum[i] : isum[i];
+          }
+        }
+        continue;
+      }
       // Rows i0 .. i0+31 of this thread's column: alpha/beta and the stores.
       auto store_chunk = [&](const uint32_t (&r)[32], int c) {
+        if (use_tma) {
+          float* buf = stage_begin();
+          if (e.out_mode == OUT_I32) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) buf[i * 128] = __int_as_float(__float2int_rn(__uint_as_float(r[i])));
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) buf[i * 128] = alpha * __uint_as_float(r[i]);
+          }
+          stage_end(c);
+          return;
+        }
         const int i0 = j.m0 + c * 32;
         const int iend = min(32, e.m - i0);
         if (cok) {
@@ -438,7 +539,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           }
         }
       }
+      }   // accumulation chunks
     }
+    if (threadIdx.x == 64) bulk_wait_group_all();   // every TMA store of C has completed
   }
 
   tc_fence_before();
@@ -453,7 +556,7 @@ template <int BM_T, int STAGES, int MODE>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
-                   const __grid_constant__ TcParams p) {
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ TcParams p) {
   if (threadIdx.x == 0) {
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
@@ -461,8 +564,9 @@ __global__ void __launch_bounds__(192, 1)
       tma_prefetch_desc(&tmA_lo);
       tma_prefetch_desc(&tmB_lo);
     }
+    if (p.c_tma) tma_prefetch_desc(&tmC);
   }
-  const SingleSched<BM_T> S{&p, {&tmA, &tmB, &tmA_lo, &tmB_lo}};
+  const SingleSched<BM_T> S{&p, {&tmA, &tmB, &tmA_lo, &tmB_lo}, p.c_tma ? &tmC : nullptr};
   tc_gemm_body<BM_T, STAGES, MODE>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
 }
 

@@ -37,9 +37,12 @@ MODES = {            # name: (planes, element bytes)
     "bf16": (1, 2),
     "3xbf16": (2, 2),
     "fp8": (1, 1),
+    "int8emu": (1, 2),   # exact int8 on the BF16 path, k accumulated in chunks of <= 1024
 }
-MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8"}
+MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8", "int8emu": "TC_I8EMU"}
 BMS = (256, 128, 64)
+# int8emu keeps one int32 running sum per row of its column in registers
+MAX_BM = {"int8emu": 128}
 
 
 def stage_bytes(mode: str, bm: int) -> int:
@@ -49,15 +52,18 @@ def stage_bytes(mode: str, bm: int) -> int:
     return planes * (bt + a)
 
 
+C_STAGE_BYTES = 2 * 32 * 128 * 4   # epilogue staging of C for TMA stores (two 32 x 128 fp32 boxes)
+
+
 def smem_bytes(mode: str, bm: int, stages: int) -> int:
-    return ALIGN_SLACK + stages * stage_bytes(mode, bm) + BAR_BYTES
+    return ALIGN_SLACK + stages * stage_bytes(mode, bm) + C_STAGE_BYTES + BAR_BYTES
 
 
 def enumerate_family():
     members = []
     for mode in MODES:
         for bm in BMS:
-            if (2 if mode == "3xbf16" else 1) * bm > TMEM_COLUMNS:
+            if (2 if mode == "3xbf16" else 1) * bm > TMEM_COLUMNS or bm > MAX_BM.get(mode, 256):
                 continue
             fits = [s for s in range(2, 9) if smem_bytes(mode, bm, s) <= SMEM_LIMIT]
             if not fits:
@@ -66,7 +72,7 @@ def enumerate_family():
             if max(fits) - 1 in fits and max(fits) > 3:
                 chosen.append(max(fits) - 1)
             acc_cols = (2 if mode == "3xbf16" else 1) * bm     # main (+ correction) accumulators
-            bufs = 2 if 2 * acc_cols <= TMEM_COLUMNS else 1       # double-buffered across tiles?
+            bufs = min(4, TMEM_COLUMNS // acc_cols)               # accumulator sets across tiles
             for st in chosen:
                 members.append({"mode": mode, "bm": bm, "stages": st,
                                 "smem": smem_bytes(mode, bm, st), "tmem_bufs": bufs})
