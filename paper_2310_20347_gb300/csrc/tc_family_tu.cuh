@@ -6,15 +6,34 @@
 namespace g3 {
 namespace {
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel of the stream drains; it waits (griddepcontrol.wait)
+// before touching global memory.
+inline cudaLaunchConfig_t pdl_config(int grid, int threads, size_t smem, cudaStream_t s,
+                                     cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
 template <int BM, int ST, int MODE>
 cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int grid, cudaStream_t s) {
   using Cfg = TcConfig<BM, ST, MODE>;
   auto kern = tc_gemm_kernel<BM, ST, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, Cfg::kThreads, Cfg::kSmemBytes, s>>>(maps[0], maps[1], maps[2], maps[3], maps[4], p);
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = pdl_config(grid, Cfg::kThreads, Cfg::kSmemBytes, s, attr);
+  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], p);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int IDX, int MODE, int BM, int ST>
@@ -31,9 +50,11 @@ cudaError_t launch_grouped(const GroupedParams& p, int grid, cudaStream_t s) {
   auto kern = tc_grouped_kernel<BM, ST, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, Cfg::kThreads, Cfg::kSmemBytes, s>>>(p);
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = pdl_config(grid, Cfg::kThreads, Cfg::kSmemBytes, s, attr);
+  e = cudaLaunchKernelEx(&cfg, kern, p);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int IDX, int MODE, int BM, int ST>

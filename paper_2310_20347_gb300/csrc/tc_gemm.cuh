@@ -257,6 +257,11 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // Programmatic dependent launch: the set-up above overlaps the tail of the
+  // previous kernel in the stream; wait for that kernel (and its memory) before
+  // any global access, and let the next kernel start its own set-up.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   Watchdog wd{timeout_ns, status, abort_flag};
   const int total_tiles = S.total();
