@@ -30,6 +30,13 @@ cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s) {
 
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* lo,
                               long long ldy, cudaStream_t s) {
+  const bool vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && ldx % 4 == 0 && reinterpret_cast<uintptr_t>(hi) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(lo) % 16 == 0 && ldy % 8 == 0;
+  if (vec) {
+    split_bf16_vec8_kernel<<<rows_grid(rows, cols, 8), 256, 0, s>>>(x, rows, cols, ldx, hi, lo, ldy);
+    count_launch();
+    return cudaGetLastError();
+  }
   split_bf16_kernel<<<rows_grid(rows, cols, 4), 256, 0, s>>>(x, rows, cols, ldx, hi, lo, ldy);
   count_launch();
   return cudaGetLastError();

@@ -133,6 +133,18 @@ def test_3xbf16_split_matches_oracle():
     assert np.array_equal(lo.float().cpu().numpy().view(np.uint32), olo.view(np.uint32))
 
 
+@pytest.mark.parametrize("rows,cols,ldx", [(37, 1037, 1040), (5, 2048, 2048), (3, 7, 8), (64, 1000, 1003)])
+def test_3xbf16_split_vectorised_and_tail(rows, cols, ldx):
+    # 16-byte-aligned rows take the 8-wide path, the last cols % 8 the scalar tail
+    r = np.random.default_rng(19)
+    full = (r.standard_normal((rows, ldx)) * 10.0 ** r.integers(-20, 20, (rows, ldx))).astype(np.float32)
+    x = torch.from_numpy(full).cuda()[:, :cols]
+    hi, lo = torch_api.split_bf16(x)
+    ohi, olo = oracle.split_bf16(full[:, :cols])
+    assert np.array_equal(hi.float().cpu().numpy().view(np.uint32), ohi.view(np.uint32))
+    assert np.array_equal(lo.float().cpu().numpy().view(np.uint32), olo.view(np.uint32))
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_3xbf16_shapes(shape):
     m, n, k = shape
