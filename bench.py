@@ -424,18 +424,19 @@ def run_workload(args):
             A, B = torch_api.convert_bf16(torch.from_numpy(p.A).to(dev)), torch_api.convert_bf16(
                 torch.from_numpy(p.B).to(dev))
             C = torch.empty(n, n, dtype=torch.float32, device=dev)
-            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_BF16)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_BF16, config=args.config)
         elif args.workload == "int8":
             p = synth.int8_problem(n, n, n, seed=0)
             A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
             C = torch.empty(n, n, dtype=torch.int32, device=dev)
-            fn = lambda: torch_api.gemm(A, B, C, 1, 0, dtype=G3_INT8)
+            fn = lambda: torch_api.gemm(A, B, C, 1, 0, dtype=G3_INT8, config=args.config)
         else:
             p = synth.normal_problem(n, n, n, seed=0)
             A32, B32 = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
             (A, sa), (B, sb) = torch_api.quantize_fp8(A32), torch_api.quantize_fp8(B32)
             C = torch.empty(n, n, dtype=torch.float32, device=dev)
-            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP8_E4M3, scale_a=sa, scale_b=sb)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP8_E4M3, scale_a=sa, scale_b=sb,
+                                        config=args.config)
         fn()
         torch.cuda.synchronize()
         rows = np.array([0, n // 2, n - 1])

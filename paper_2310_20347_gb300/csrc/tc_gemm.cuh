@@ -133,11 +133,17 @@ struct TcConfig {
   static constexpr uint32_t kMaxBufs = 4;
   static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
   static constexpr uint32_t kTmemCols = kNumBufs * kSetCols;
+  // Epilogue warps: one per TMEM lane quarter, each thread owning all bm rows
+  // of its column.  (An exact-integer variant with bm = 256 and eight epilogue
+  // warps of 128 rows each measured slower than bm = 128: its large unrolled
+  // epilogue starved the MMA-issuing thread of instruction fetch.)
+  static constexpr int kEpiWarps = 4;
+  static constexpr int kEpiRows = BM_T;   // rows of the tile per epilogue thread
   // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128 columns x 4 bytes.
   static constexpr uint32_t kCStageBytes = 2 * 32 * 128 * 4;
   static constexpr uint32_t kBarBytes = 256;
   static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kCStageBytes + kBarBytes;
-  static constexpr int kThreads = 192;
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;
   static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
   static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32 && kTmemCols <= 512, "TMEM allocation");
@@ -220,7 +226,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   using T = TcTraits<MODE>;
   using Cfg = TcConfig<BM_T, STAGES, MODE>;
   constexpr bool kIntChunked = (MODE == TC_I8EMU);
-  static_assert(!kIntChunked || BM_T <= 128, "int32 running sums live in registers: bm <= 128");
+  static_assert(!kIntChunked || Cfg::kEpiRows <= 128, "int32 running sums live in registers: <= 128 rows");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -243,7 +249,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
     }
     for (int a = 0; a < (int)Cfg::kNumBufs; ++a) {
       mbar_init(&tmem_full[a], 1);
-      mbar_init(&tmem_empty[a], 4);
+      mbar_init(&tmem_empty[a], Cfg::kEpiWarps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -387,6 +393,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       // Outputs that do not read C leave through shared memory and TMA stores
       // (whole 32 x 128 boxes, clipped to C by the tensor map).
       const bool use_tma = e.cmap != nullptr && beta == 0.0f && (e.out_mode == OUT_F32 || e.out_mode == OUT_I32);
+      const int r0 = 0;   // first tile row of this thread's running sums
       // stage_begin: a free staging buffer (the store issued from it two chunks
       // ago has read it); this thread's column of the 32 rows goes to
       // buf[i * 128 + q * 32 + lane]; stage_end: hand the box to the TMA unit.
@@ -404,10 +411,14 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
         }
         ++schunk;
       };
-      // exact-integer mode: int32 running sums of this thread's column, one per row
-      int isum[kIntChunked ? BM_T : 1];
+      // exact-integer mode: int32 running sums of this thread's column, one per
+      // row r0 .. r0 + kEpiRows - 1 of the tile
+      constexpr int kSums = kIntChunked ? Cfg::kEpiRows : 1;
+      int isum[kSums];
 #pragma unroll
-      for (int i = 0; i < (kIntChunked ? BM_T : 1); ++i) isum[i] = 0;
+      for (int i = 0; i < kSums; ++i) isum[i] = 0;
+      const int rows_mine = min(Cfg::kEpiRows, rows_here - r0);            // may be <= 0
+      const int nchunks_mine = rows_mine > 0 ? (rows_mine + 31) >> 5 : 0;
       for (int kc = 0; kc < nkc; ++kc, ++lt) {
       const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
       bool ok = wait_parity(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
@@ -428,19 +439,19 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
         // Each chunk holds an integer-valued FP32 sum of at most 1024 products
         // of magnitude <= 2^14, hence exact; convert and add in int32.
 #pragma unroll
-        for (int rc = 0; rc < BM_T / 32; ++rc) {
-          if (rc < nchunks) {
-            uint32_t r[32];
-            tmem_ld_32x32b_x32(tbase + rc * 32, r);
+        for (int rc = 0; rc < Cfg::kEpiRows / 16; ++rc) {
+          if (rc < 2 * nchunks_mine) {
+            uint32_t r[16];
+            tmem_ld_32x32b_x16(tbase + r0 + rc * 16, r);
             tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) isum[rc * 32 + i] += __float2int_rn(__uint_as_float(r[i]));
+            for (int i = 0; i < 16; ++i) isum[rc * 16 + i] += __float2int_rn(__uint_as_float(r[i]));
           }
         }
         release();
         if (kc == nkc - 1 && use_tma) {
 #pragma unroll
-          for (int rc = 0; rc < BM_T / 32; ++rc) {
+          for (int rc = 0; rc < Cfg::kEpiRows / 32; ++rc) {
             if (rc < nchunks) {
               float* buf = stage_begin();
 #pragma unroll
@@ -449,20 +460,20 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             }
           }
         } else if (kc == nkc - 1 && cok) {
+          const int i0 = j.m0 + r0;
           if (e.out_mode == OUT_PARTIAL) {
-            int* pp = reinterpret_cast<int*>(e.partial) + (long long)j.m0 * e.n + col;
+            int* pp = reinterpret_cast<int*>(e.partial) + (long long)i0 * e.n + col;
 #pragma unroll
-            for (int i = 0; i < BM_T; ++i)
-              if (i < rows_here) pp[(long long)i * e.n] = isum[i];
+            for (int i = 0; i < Cfg::kEpiRows; ++i)
+              if (i < rows_mine) pp[(long long)i * e.n] = isum[i];
           } else {
-            int* cp = static_cast<int*>(e.C) + (long long)j.m0 * e.ldc + col;
+            int* cp = static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
 #pragma unroll
-            for (int i = 0; i < BM_T; ++i)
-              if (i < rows_here) cp[i * e.ldc] = (beta != 0.0f) ? cp[i * e.ldc] + isum[i] : isum[i];
+            for (int i = 0; i < Cfg::kEpiRows; ++i)
+              if (i < rows_mine) cp[i * e.ldc] = (beta != 0.0f) ? cp[i * e.ldc] + isum[i] : isum[i];
           }
         }
-        continue;
-      }
+      } else {
       // Rows i0 .. i0+31 of this thread's column: alpha/beta and the stores.
       auto store_chunk = [&](const uint32_t (&r)[32], int c) {
         if (use_tma) {
@@ -544,6 +555,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           }
         }
       }
+      }   // float / 3xBF16 epilogue
       }   // accumulation chunks
     }
     if (threadIdx.x == 64) bulk_wait_group_all();   // every TMA store of C has completed
@@ -558,7 +570,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 }
 
 template <int BM_T, int STAGES, int MODE>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ TcParams p) {
@@ -579,7 +591,8 @@ __global__ void __launch_bounds__(192, 1)
 // global tile index of all problems; each tile finds its problem in
 // gp.tile_info and uses that problem's tensor maps, tile height and epilogue.
 template <int BM_T, int STAGES, int MODE>
-__global__ void __launch_bounds__(192, 1) tc_grouped_kernel(const __grid_constant__ GroupedParams gp) {
+__global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE>::kThreads, 1)
+    tc_grouped_kernel(const __grid_constant__ GroupedParams gp) {
   const GroupedSched S{&gp};
   tc_gemm_body<BM_T, STAGES, MODE>(S, gp.timeout_ns, gp.status, gp.debug_withhold, nullptr, nullptr);
 }

@@ -90,7 +90,7 @@ def test_planner_choices(lib):
     assert sk > 1
     # INT8 runs on the exact-integer members (k chunked inside the kernel): no split needed
     st, cfg, sk, rs = L.g3_plan_query(8192, 8192, 8192, L.G3_INT8)
-    assert fam[cfg]["mode"] == "int8emu" and fam[cfg]["bm"] <= 128 and sk == 1
+    assert fam[cfg]["mode"] == "int8emu" and fam[cfg]["bm"] == 128 and sk == 1
     st, cfg, sk, rs = L.g3_plan_query(128, 128, 100, L.G3_F32)
     assert cfg == -1
 

@@ -239,6 +239,18 @@ def test_int8_bit_exact(shape, beta):
     assert np.array_equal(got.astype(np.int64), oracle.gemm_i8(p.A, p.B, p.C, 1, beta))
 
 
+@pytest.mark.parametrize("config", members("int8emu"))
+def test_int8_every_member(config):
+    # ragged m (several 256-row tiles and a tail), k across two 1024 chunks + a tail
+    p = synth.int8_problem(600, 300, 2200, seed=20, beta=1)
+    A, B = dev(p.A), dev(p.B)
+    full, C = guarded(p.m, p.n, p.C, dtype=torch.int32)
+    torch_api.gemm(A, B, C, 1, 1, dtype=G3_INT8, config=config)
+    torch.cuda.synchronize()
+    check_guard(full, p.m, p.n)
+    assert np.array_equal(C.cpu().numpy().astype(np.int64), oracle.gemm_i8(p.A, p.B, p.C, 1, 1))
+
+
 def test_int8_worst_case_magnitude():
     # all -128 at k = 8192: every entry is 8192 * 2^14 = 2^27 exactly
     A = np.full((40, 8192), -128, np.int8)
