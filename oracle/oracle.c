@@ -222,6 +222,70 @@ void oracle_split_bf16(float x, float* hi, float* lo) {
     *lo = oracle_round_bf16(d);
 }
 
+void oracle_split3_bf16(float x, float* hi, float* mid, float* lo) {
+    float h = oracle_round_bf16(x);
+    float d = x - h;              /* exact: h is x rounded to 8 significant bits */
+    float m = oracle_round_bf16(d);
+    float e = d - m;              /* exact: m is d rounded to 8 significant bits */
+    *hi = h;
+    *mid = m;
+    *lo = oracle_round_bf16(e);
+}
+
+/* The 6-product method: 1) split both operands in three, 2) form the six
+ * kept products per term, 3) sum over p.  Products are exact in binary64.    */
+void oracle_gemm_rows_6xbf16_f64(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
+                                 double alpha, const float* A, int64_t lda,
+                                 const float* B, int64_t ldb, double beta,
+                                 const double* C_in, int64_t ldc_in,
+                                 double* C_out, int64_t ldc_out, int nthreads) {
+    if (nrows <= 0 || n <= 0) return;
+    int nt = threads_for(nthreads);
+    size_t kn = (size_t)(k > 0 ? k : 1) * (size_t)n;
+    double* Bh = (double*)malloc(sizeof(double) * kn);
+    double* Bm = (double*)malloc(sizeof(double) * kn);
+    double* Bl = (double*)malloc(sizeof(double) * kn);
+    for (int64_t p = 0; p < k; ++p)
+        for (int64_t j = 0; j < n; ++j) {
+            float h, m, l;
+            oracle_split3_bf16(B[p * ldb + j], &h, &m, &l);
+            Bh[p * n + j] = h;
+            Bm[p * n + j] = m;
+            Bl[p * n + j] = l;
+        }
+#pragma omp parallel num_threads(nt)
+    {
+        double* acc = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t r = 0; r < nrows; ++r) {
+            int64_t i = row_index(rows, r);
+            for (int64_t j = 0; j < n; ++j) acc[j] = 0.0;
+            if (alpha != 0.0) {
+                for (int64_t p = 0; p < k; ++p) {
+                    float h, m, l;
+                    oracle_split3_bf16(A[i * lda + p], &h, &m, &l);
+                    double ah = h, am = m, al = l;
+                    const double* bh = Bh + p * n;
+                    const double* bm = Bm + p * n;
+                    const double* bl = Bl + p * n;
+                    for (int64_t j = 0; j < n; ++j)
+                        acc[j] += ah * bh[j] + ah * bm[j] + am * bh[j] + ah * bl[j] + al * bh[j] + am * bm[j];
+                }
+            }
+            double* crow = C_out + r * ldc_out;
+            for (int64_t j = 0; j < n; ++j) {
+                double ab = (alpha != 0.0) ? alpha * acc[j] : 0.0;
+                double bc = (beta != 0.0) ? beta * C_in[i * ldc_in + j] : 0.0;
+                crow[j] = bc + ab;
+            }
+        }
+        free(acc);
+    }
+    free(Bh);
+    free(Bm);
+    free(Bl);
+}
+
 /* The compensated 3-product split, in the order the method takes it:
  * 1) split both operands, 2) form the three products per term, 3) sum over p.
  * Each product of two bfloat16 values is exact in binary64, so S differs from

@@ -93,6 +93,20 @@ void oracle_gemm_rows_3xbf16_f64(int64_t nrows, const int64_t* rows, int64_t n, 
                                  const double* C_in, int64_t ldc_in,
                                  double* C_out, int64_t ldc_out, int nthreads);
 
+/* Three-part split: hi = bf16(x), mid = bf16(x - hi), lo = bf16((x - hi) - mid),
+ * every difference exact in binary32, so that x = hi + mid + lo for normal x. */
+void oracle_split3_bf16(float x, float* hi, float* mid, float* lo);
+
+/* The 6-product method on the three-part split, step by step, in binary64:
+ * S = sum_p (Ah*Bh + Ah*Bm + Am*Bh + Ah*Bl + Al*Bh + Am*Bm); the products
+ * Am*Bl, Al*Bm and Al*Bl (relative size <= 2^-23) are dropped;
+ * C_out = beta*C_in + alpha*S.                                               */
+void oracle_gemm_rows_6xbf16_f64(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
+                                 double alpha, const float* A, int64_t lda,
+                                 const float* B, int64_t ldb, double beta,
+                                 const double* C_in, int64_t ldc_in,
+                                 double* C_out, int64_t ldc_out, int nthreads);
+
 /* Number of OpenMP threads a call with nthreads <= 0 would use. */
 int oracle_max_threads(void);
 

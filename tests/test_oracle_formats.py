@@ -122,6 +122,40 @@ def test_3xbf16_exact_on_bf16_inputs(oracle):
                           oracle.gemm(p.A, p.B, p.C, 0.5, 2.0))
 
 
+def test_split3_is_exact_and_bf16(oracle):
+    r = np.random.default_rng(5)
+    x = np.concatenate([r.uniform(-1, 1, 20000), r.standard_normal(20000) * 1e5]).astype(np.float32)
+    h, m, l = oracle.split3_bf16(x)
+    for plane in (h, m, l):
+        assert np.all((plane.view(np.uint32) & 0xFFFF) == 0)
+    # hi + mid + lo reproduces every normal binary32 value exactly
+    assert np.array_equal(h.astype(np.float64) + m.astype(np.float64) + l.astype(np.float64),
+                          x.astype(np.float64))
+    assert np.all(np.abs(m) <= np.abs(x) * 2.0 ** -8) and np.all(np.abs(l) <= np.abs(x) * 2.0 ** -16)
+
+
+def test_6xbf16_closed_form(oracle):
+    # a = 1 + 2^-9 + 2^-17 splits as (1, 2^-9, 2^-17); b = 1 + 2^-10 + 2^-18 as
+    # (1, 2^-10, 2^-18).  ab adds mid*lo + lo*mid = 2^-26 and lo*lo = 2^-35 to
+    # the six kept products 1 + 2^-9 + 2^-10 + 2^-17 + 2^-18 + 2^-19.
+    a = np.array([[1 + 2.0 ** -9 + 2.0 ** -17]], np.float32)
+    b = np.array([[1 + 2.0 ** -10 + 2.0 ** -18]], np.float32)
+    got = oracle.gemm_6xbf16(a, b)[0, 0]
+    assert got == 1 + 2.0 ** -9 + 2.0 ** -10 + 2.0 ** -17 + 2.0 ** -18 + 2.0 ** -19
+    assert oracle.gemm(a, b)[0, 0] - got == 2.0 ** -26 + 2.0 ** -35
+
+
+def test_6xbf16_within_bound_at_every_k(oracle):
+    # dropped products: |mid*lo| + |lo*mid| + |lo*lo| <= (2^-23 + 2^-32)|a||b|
+    bound = 2.0 ** -23 + 2.0 ** -32
+    for k in (1, 3, 16, 200):
+        p = synth.uniform_problem(30, 40, k, seed=k)
+        exact = oracle.gemm(p.A, p.B)
+        approx = oracle.gemm_6xbf16(p.A, p.B)
+        D = oracle.absprod(p.A, p.B)
+        assert np.max(np.abs(approx - exact) / D) <= bound
+
+
 def test_3xbf16_within_split_bound(oracle):
     # |ab - (ah bh + ah bl + al bh)| <= (2^-16 + 2^-16 + 2^-16 + 2^-32)|a||b|.
     bound = 3 * 2.0 ** -16 + 2.0 ** -32
