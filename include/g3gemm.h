@@ -144,6 +144,12 @@ G3_API int g3_convert_bf16(const float* x, int64_t rows, int64_t cols, int64_t l
 G3_API int g3_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo, int64_t ldy,
                   void* cuda_stream);
 
+/* hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid): the three-part
+ * split the FP32-accurate mode uses for k <= 512 (both differences are exact
+ * in FP32).  Errors as g3_split_bf16; -106 / -107: mid / lo is null.        */
+G3_API int g3_split3_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* mid, void* lo,
+                          int64_t ldy, void* cuda_stream);
+
 /* Per-tensor E4M3 quantisation: scale = amax|x| / 448 (1 when x == 0),
  * q = e4m3_satfinite(x / scale) with the quotient rounded in float32.
  * `scale` is a device float written by the call; q has leading dimension ldq. */

@@ -24,7 +24,7 @@ G3_OK, G3_ERR_ARG, G3_ERR_UNSUPPORTED, G3_ERR_CUDA, G3_ERR_NOMEM, G3_ERR_TIMEOUT
 # Every symbol include/g3gemm.h declares (checked against the header by the tests).
 EXPORTED = (
     "g3_gemm", "g3_set_stream", "g3_gemm_args_init", "g3_gemm_ex", "g3_gemm_workspace_size",
-    "g3_convert_bf16", "g3_split_bf16", "g3_quantize_fp8",
+    "g3_convert_bf16", "g3_split_bf16", "g3_split3_bf16", "g3_quantize_fp8",
     "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
     "g3_plan_query", "g3_launch_count", "g3_kernel_timing", "g3_kernel_time_ms",
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
             "g3_gemm_workspace_size": ([ctypes.POINTER(g3_gemm_args), ctypes.POINTER(sz)], i32),
             "g3_convert_bf16": ([vp, i64, i64, i64, vp, i64, vp], i32),
             "g3_split_bf16": ([vp, i64, i64, i64, vp, vp, i64, vp], i32),
+            "g3_split3_bf16": ([vp, i64, i64, i64, vp, vp, vp, i64, vp], i32),
             "g3_quantize_fp8": ([vp, i64, i64, i64, vp, i64, vp, vp], i32),
             "g3_grouped_plan_create": ([i32, ctypes.POINTER(g3_gemm_desc), i32, ctypes.POINTER(vp)], i32),
             "g3_grouped_plan_execute": ([vp, vp], i32),
@@ -148,6 +149,10 @@ def g3_convert_bf16(x, rows, cols, ldx, y, ldy, stream=None) -> int:
 
 def g3_split_bf16(x, rows, cols, ldx, hi, lo, ldy, stream=None) -> int:
     return load().g3_split_bf16(x, rows, cols, ldx, hi, lo, ldy, stream)
+
+
+def g3_split3_bf16(x, rows, cols, ldx, hi, mid, lo, ldy, stream=None) -> int:
+    return load().g3_split3_bf16(x, rows, cols, ldx, hi, mid, lo, ldy, stream)
 
 
 def g3_quantize_fp8(x, rows, cols, ldx, q, ldq, scale, stream=None) -> int:

@@ -59,6 +59,7 @@ void family_init() {
   register_family_3xbf16(g_family);
   register_family_fp8(g_family);
   register_family_int8emu(g_family);
+  register_family_6xbf16(g_family);
   g_family_ready = true;
 }
 
@@ -147,10 +148,15 @@ int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // ---------------------------------------------------------------- planner
-int tc_mode_of(int dtype) {
+// FP32-accurate GEMMs with k <= 512 take the three-part split (6 products):
+// at small k the two-part split's dropped terms exceed 2e-6 of sum |a||b|.
+// 512 is a power of two, so one tuning-cache k bucket never mixes the modes.
+constexpr int64_t kSixProductMaxK = 512;
+
+int tc_mode_of(int dtype, int64_t k) {
   switch (dtype) {
     case G3_BF16: return TC_BF16;
-    case G3_F32_3XBF16: return TC_3XBF16;
+    case G3_F32_3XBF16: return k <= kSixProductMaxK ? TC_6XBF16 : TC_3XBF16;
     case G3_FP8_E4M3: return TC_FP8;
     case G3_INT8: return TC_I8EMU;  // exact emulation: int8 values are exact in bfloat16
     default: return -1;
@@ -232,7 +238,7 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
       force_split = it->second.split;
     }
   }
-  const int mode = tc_mode_of(dtype);
+  const int mode = tc_mode_of(dtype, k);
   const int bk = (mode == TC_FP8) ? 128 : 64;
   pl.num_kb = (int)((k + bk - 1) / bk);
   pl.tiles_n = (int)((n + 127) / 128);
@@ -280,6 +286,7 @@ struct Layout {
   bool pack_a = false, pack_b = false;
   int64_t lda_p = 0, ldb_p = 0;   // leading dimensions of re-packed / converted operands
   size_t a_hi = 0, a_lo = 0, b_hi = 0, b_lo = 0, partial = 0, amax = 0;
+  size_t a_mid = 0, b_mid = 0;    // middle planes of the three-part split
   size_t total = 0;
 };
 
@@ -300,6 +307,10 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl) {
       L.a_lo = take((size_t)m * L.lda_p * 2);
       L.b_hi = take((size_t)k * L.ldb_p * 2);
       L.b_lo = take((size_t)k * L.ldb_p * 2);
+      if (tc_mode_of(a.dtype, k) == TC_6XBF16) {
+        L.a_mid = take((size_t)m * L.lda_p * 2);
+        L.b_mid = take((size_t)k * L.ldb_p * 2);
+      }
       break;
     case G3_INT8:
       L.pack_a = L.pack_b = true;
@@ -437,11 +448,19 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
 
   const int64_t m = a.m, n = a.n, k = a.k;
   const int es = (a.dtype == G3_FP8_E4M3) ? 1 : 2;
-  const void *A_hi = a.A, *A_lo = nullptr, *B_hi = a.B, *B_lo = nullptr;
+  const void *A_hi = a.A, *A_lo = nullptr, *B_hi = a.B, *B_lo = nullptr, *A_mid = nullptr, *B_mid = nullptr;
   int64_t lda = a.lda, ldb = a.ldb;
 
   // a1: operand preparation
-  if (a.dtype == G3_F32_3XBF16) {
+  if (fam.mode == TC_6XBF16) {
+    uint16_t *ah = (uint16_t*)(ws + L.a_hi), *am = (uint16_t*)(ws + L.a_mid), *al = (uint16_t*)(ws + L.a_lo);
+    uint16_t *bh = (uint16_t*)(ws + L.b_hi), *bm = (uint16_t*)(ws + L.b_mid), *bl = (uint16_t*)(ws + L.b_lo);
+    G3_CHECK_CUDA(launch_split3_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, am, al, L.lda_p, s));
+    G3_CHECK_CUDA(launch_split3_bf16((const float*)a.B, (int)k, (int)n, a.ldb, bh, bm, bl, L.ldb_p, s));
+    A_hi = ah; A_mid = am; A_lo = al; B_hi = bh; B_mid = bm; B_lo = bl;
+    lda = L.lda_p;
+    ldb = L.ldb_p;
+  } else if (a.dtype == G3_F32_3XBF16) {
     uint16_t *ah = (uint16_t*)(ws + L.a_hi), *al = (uint16_t*)(ws + L.a_lo);
     uint16_t *bh = (uint16_t*)(ws + L.b_hi), *bl = (uint16_t*)(ws + L.b_lo);
     G3_CHECK_CUDA(launch_split_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p, s));
@@ -472,16 +491,24 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   // TMA descriptors: A as (k inner, m rows) in boxes of BK x bm; B as (n inner,
   // k rows) in boxes of (128 bytes of n) x BK.
   const uint32_t bk = 128 / es, boxn = 128 / es;
-  CUtensorMap maps[5];
+  // Maps 2p, 2p+1 are A, B of plane p: plane 0 = hi (or the only plane),
+  // plane 1 = lo (two-part split) or mid (three-part split), plane 2 = lo
+  // (three-part split).  Unused planes repeat plane 0 (the kernel never loads
+  // them).  Map 6 is C's store map.
+  CUtensorMap maps[7];
   std::memset(maps, 0, sizeof(maps));
   if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
   if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
-  if (a.dtype == G3_F32_3XBF16) {
+  maps[2] = maps[4] = maps[0];
+  maps[3] = maps[5] = maps[1];
+  if (fam.mode == TC_6XBF16) {
+    if ((st = encode_2d(&maps[2], A_mid, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[3], B_mid, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[4], A_lo, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[5], B_lo, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
+  } else if (a.dtype == G3_F32_3XBF16) {
     if ((st = encode_2d(&maps[2], A_lo, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
     if ((st = encode_2d(&maps[3], B_lo, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
-  } else {
-    maps[2] = maps[0];
-    maps[3] = maps[1];
   }
 
   TcParams p;
@@ -520,7 +547,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
     // C without a read of its old values goes out through TMA stores when its
     // rows are 16-byte aligned (boxes of 32 rows x 128 columns, clipped to C)
     if (a.beta == 0.0 && reinterpret_cast<uintptr_t>(a.C) % 16 == 0 && (a.ldc * 4) % 16 == 0 &&
-        encode_c_2d(&maps[4], a.C, is_int, n, m, a.ldc) == G3_OK)
+        encode_c_2d(&maps[6], a.C, is_int, n, m, a.ldc) == G3_OK)
       p.c_tma = 1;
   }
   const long long total_tiles = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
@@ -644,13 +671,15 @@ int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
   return G3_OK;
 }
 
-static int prep_check(const void* x, int64_t rows, int64_t cols, int64_t ldx, const void* y, int64_t ldy) {
+// Arguments x, rows, cols, ldx, y are positions 1-5; ldy_pos is ldy's position.
+static int prep_check(const void* x, int64_t rows, int64_t cols, int64_t ldx, const void* y, int64_t ldy,
+                      int ldy_pos = 6) {
   if (rows < 0) return -102;
   if (cols < 0) return -103;
   if (ldx < std::max<int64_t>(1, cols)) return -104;
   if (rows > INT32_MAX || cols > INT32_MAX) return G3_ERR_UNSUPPORTED;
   if (rows > 0 && cols > 0 && (!x || !y)) return x ? -105 : -101;
-  if (ldy < std::max<int64_t>(1, cols)) return -106;
+  if (ldy < std::max<int64_t>(1, cols)) return -(100 + ldy_pos);
   return G3_OK;
 }
 
@@ -664,13 +693,26 @@ int g3_convert_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, voi
 
 int g3_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo, int64_t ldy,
                   void* stream) {
-  int st = prep_check(x, rows, cols, ldx, hi, ldy);
+  int st = prep_check(x, rows, cols, ldx, hi, ldy, 7);
   if (st != G3_OK) return st;
   if (rows > 0 && cols > 0 && !lo) return -106;
   if (rows == 0 || cols == 0) return G3_OK;
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
   G3_CHECK_CUDA(launch_split_bf16(x, (int)rows, (int)cols, ldx, static_cast<uint16_t*>(hi),
                                   static_cast<uint16_t*>(lo), ldy, s));
+  return G3_OK;
+}
+
+int g3_split3_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* mid, void* lo,
+                   int64_t ldy, void* stream) {
+  int st = prep_check(x, rows, cols, ldx, hi, ldy, 8);
+  if (st != G3_OK) return st;
+  if (rows > 0 && cols > 0 && !mid) return -106;
+  if (rows > 0 && cols > 0 && !lo) return -107;
+  if (rows == 0 || cols == 0) return G3_OK;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  G3_CHECK_CUDA(launch_split3_bf16(x, (int)rows, (int)cols, ldx, static_cast<uint16_t*>(hi),
+                                   static_cast<uint16_t*>(mid), static_cast<uint16_t*>(lo), ldy, s));
   return G3_OK;
 }
 
@@ -729,7 +771,7 @@ int g3_family_describe(int index, char* buf, size_t len) {
     family_init();
   }
   const FamilyEntry& f = g_family[index];
-  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu"};
+  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16"};
   std::snprintf(buf, len, "mode=%s bm=%d bn=128 stages=%d smem=%d bufs=%d", names[f.mode], f.bm, f.stages, f.smem,
                 f.bufs);
   return G3_OK;
@@ -842,7 +884,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
     cleanup();
     return G3_ERR_CUDA;
   }
-  const int mode = tc_mode_of(dtype);
+  const int mode = tc_mode_of(dtype, k);
   const int bk = (mode == TC_FP8) ? 128 : 64;
   const int num_kb = (int)((k + bk - 1) / bk);
   int best_member = -1, best_sk = 1;

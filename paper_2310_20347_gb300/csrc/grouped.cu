@@ -4,9 +4,10 @@
 // per-problem choice of tile height by size bucket (the per-shape selection of
 // the paper's Section 8.4, applied problem by problem), the global tile list
 // ordered by decreasing k-depth (heaviest tiles first, so that the static
-// stride of the persistent CTAs balances), four TMA descriptors per problem in
-// a device table, and the preparation jobs (3xBF16 hi/lo split, re-packing of
-// unaligned BF16 operands, C := beta*C for problems without products).
+// stride of the persistent CTAs balances), six TMA descriptors per problem in
+// a device table, and the preparation jobs (FP32 hi/lo or hi/mid/lo split,
+// re-packing of unaligned BF16 operands, C := beta*C for problems without
+// products).
 // Executing the plan is at most two launches -- one job kernel over all
 // preparation jobs and one tc_grouped_kernel over all tiles -- with no host
 // synchronisation and no allocation.
@@ -25,14 +26,15 @@
 namespace g3 {
 namespace {
 
-enum PrepKind : int { PREP_SPLIT = 0, PREP_COPY16 = 1, PREP_SCALE_C = 2 };
+enum PrepKind : int { PREP_SPLIT = 0, PREP_COPY16 = 1, PREP_SCALE_C = 2, PREP_SPLIT3 = 3 };
 
 // One preparation job of a grouped plan.
 struct PrepJob {
   const void* src;
   long long ld_src;   // elements
-  void* hi;           // PREP_SPLIT: hi plane; PREP_COPY16: destination
-  void* lo;           // PREP_SPLIT: lo plane
+  void* hi;           // PREP_SPLIT(3): hi plane; PREP_COPY16: destination
+  void* lo;           // PREP_SPLIT(3): lo plane
+  void* mid;          // PREP_SPLIT3: mid plane
   long long ld_dst;   // elements
   int rows, cols;
   int kind;
@@ -53,6 +55,14 @@ __global__ void grouped_prep_kernel(const PrepJob* __restrict__ jobs, int njobs)
         const uint16_t h = bf16_bits(v);
         static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = h;
         static_cast<uint16_t*>(J.lo)[r * J.ld_dst + c] = bf16_bits(v - bf16_value(h));
+      } else if (J.kind == PREP_SPLIT3) {
+        const float v = static_cast<const float*>(J.src)[r * J.ld_src + c];
+        const uint16_t h = bf16_bits(v);
+        const float dv = v - bf16_value(h);
+        const uint16_t md = bf16_bits(dv);
+        static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = h;
+        static_cast<uint16_t*>(J.mid)[r * J.ld_dst + c] = md;
+        static_cast<uint16_t*>(J.lo)[r * J.ld_dst + c] = bf16_bits(dv - bf16_value(md));
       } else if (J.kind == PREP_COPY16) {
         static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = static_cast<const uint16_t*>(J.src)[r * J.ld_src + c];
       } else {
@@ -73,6 +83,7 @@ void grouped_init() {
   register_grouped_3xbf16(g_grouped);
   register_grouped_fp8(g_grouped);
   register_grouped_int8emu(g_grouped);
+  register_grouped_6xbf16(g_grouped);
   g_grouped_ready = true;
 }
 
@@ -128,7 +139,15 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   int st = current_device_info(&dev);
   if (st != G3_OK) return st;
   grouped_init();
-  const int mode = (dtype == G3_BF16) ? TC_BF16 : TC_3XBF16;
+  // FP32-accurate plans take the three-part split (6 products) for every
+  // problem as soon as one of them has k <= 512, where the two-part split's
+  // dropped terms exceed 2e-6 of sum |a||b|.
+  bool small_k = false;
+  for (int i = 0; i < count; ++i)
+    if (descs[i].m > 0 && descs[i].n > 0 && descs[i].k > 0 && descs[i].alpha != 0.0 && descs[i].k <= 512)
+      small_k = true;
+  const int mode = (dtype == G3_BF16) ? TC_BF16 : (small_k ? TC_6XBF16 : TC_3XBF16);
+  const bool split3 = mode == TC_6XBF16;
   int entry = -1;
   for (int i = 0; i < G3_GROUPED_SIZE; ++i)
     if (g_grouped[i].launch && g_grouped[i].mode == mode) entry = i;
@@ -138,7 +157,8 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   // ---- per-problem tiling, jobs and plane sizes (host)
   std::vector<GroupDesc> groups(count);
   std::vector<PrepJob> jobs;
-  struct Operands { size_t a_off = 0, a_lo_off = 0, b_off = 0, b_lo_off = 0; int64_t lda = 0, ldb = 0;
+  struct Operands { size_t a_off = 0, a_lo_off = 0, b_off = 0, b_lo_off = 0, a_mid_off = 0, b_mid_off = 0;
+                    int64_t lda = 0, ldb = 0;
                     bool pack_a = false, pack_b = false; bool active = false; };
   std::vector<Operands> ops(count);
   size_t planes = 0;
@@ -173,6 +193,10 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
       o.a_lo_off = take((size_t)d.m * o.lda * 2);
       o.b_off = take((size_t)d.k * o.ldb * 2);
       o.b_lo_off = take((size_t)d.k * o.ldb * 2);
+      if (split3) {
+        o.a_mid_off = take((size_t)d.m * o.lda * 2);
+        o.b_mid_off = take((size_t)d.k * o.ldb * 2);
+      }
     } else {
       o.pack_a = !aligned16(d.A, d.lda, 2);
       o.pack_b = !aligned16(d.B, d.ldb, 2);
@@ -185,7 +209,7 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   if (total_tiles > INT32_MAX) return G3_ERR_UNSUPPORTED;
 
   // ---- device memory: maps | problems | tile list | jobs | planes
-  const size_t maps_bytes = align256(sizeof(CUtensorMap) * 4 * (size_t)std::max(count, 1));
+  const size_t maps_bytes = align256(sizeof(CUtensorMap) * kMapsPerProblem * (size_t)std::max(count, 1));
   const size_t groups_bytes = align256(sizeof(GroupDesc) * (size_t)std::max(count, 1));
   const size_t tiles_bytes = align256(sizeof(int2) * (size_t)std::max<long long>(total_tiles, 1));
   const size_t njobs_max = jobs.size() + 2 * (size_t)count;
@@ -204,40 +228,50 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   PrepJob* d_jobs = reinterpret_cast<PrepJob*>(base + maps_bytes + groups_bytes + tiles_bytes);
   uint8_t* d_planes = base + header;
 
-  std::vector<CUtensorMap> maps(4 * (size_t)std::max(count, 1));
+  std::vector<CUtensorMap> maps(kMapsPerProblem * (size_t)std::max(count, 1));
   std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
   for (int i = 0; i < count && st == G3_OK; ++i) {
     if (!ops[i].active) continue;
     const g3_gemm_desc& d = descs[i];
     const Operands& o = ops[i];
     const GroupDesc& g = groups[i];
-    const void *a = d.A, *b = d.B, *a_lo = nullptr, *b_lo = nullptr;
+    const void *a = d.A, *b = d.B, *a_lo = nullptr, *b_lo = nullptr, *a_mid = nullptr, *b_mid = nullptr;
     if (dtype == G3_F32_3XBF16) {
       a = d_planes + o.a_off; a_lo = d_planes + o.a_lo_off;
       b = d_planes + o.b_off; b_lo = d_planes + o.b_lo_off;
-      PrepJob ja{d.A, d.lda, (void*)a, (void*)a_lo, o.lda, g.m, g.k, PREP_SPLIT, 0.f};
-      PrepJob jb{d.B, d.ldb, (void*)b, (void*)b_lo, o.ldb, g.k, g.n, PREP_SPLIT, 0.f};
-      jobs.push_back(ja);
-      jobs.push_back(jb);
+      const int kind = split3 ? PREP_SPLIT3 : PREP_SPLIT;
+      if (split3) {
+        a_mid = d_planes + o.a_mid_off;
+        b_mid = d_planes + o.b_mid_off;
+      }
+      jobs.push_back(PrepJob{d.A, d.lda, (void*)a, (void*)a_lo, (void*)a_mid, o.lda, g.m, g.k, kind, 0.f});
+      jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, (void*)b_lo, (void*)b_mid, o.ldb, g.k, g.n, kind, 0.f});
     } else {
       if (o.pack_a) {
         a = d_planes + o.a_off;
-        jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, o.lda, g.m, g.k, PREP_COPY16, 0.f});
+        jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, nullptr, o.lda, g.m, g.k, PREP_COPY16, 0.f});
       }
       if (o.pack_b) {
         b = d_planes + o.b_off;
-        jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, o.ldb, g.k, g.n, PREP_COPY16, 0.f});
+        jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, nullptr, o.ldb, g.k, g.n, PREP_COPY16, 0.f});
       }
     }
-    CUtensorMap* m4 = &maps[4 * (size_t)i];
-    st = encode_tensor_2d(&m4[0], a, 2, g.k, g.m, o.lda, 64, g.bm);
-    if (st == G3_OK) st = encode_tensor_2d(&m4[1], b, 2, g.n, g.k, o.ldb, 64, 64);
+    // maps 2p, 2p+1 = A, B of plane p: hi; then lo (two-part) or mid, lo
+    // (three-part); unused planes repeat plane 0
+    CUtensorMap* mp = &maps[kMapsPerProblem * (size_t)i];
+    st = encode_tensor_2d(&mp[0], a, 2, g.k, g.m, o.lda, 64, g.bm);
+    if (st == G3_OK) st = encode_tensor_2d(&mp[1], b, 2, g.n, g.k, o.ldb, 64, 64);
+    mp[2] = mp[4] = mp[0];
+    mp[3] = mp[5] = mp[1];
+    const void* p1a = split3 ? a_mid : a_lo;
+    const void* p1b = split3 ? b_mid : b_lo;
     if (st == G3_OK && dtype == G3_F32_3XBF16) {
-      st = encode_tensor_2d(&m4[2], a_lo, 2, g.k, g.m, o.lda, 64, g.bm);
-      if (st == G3_OK) st = encode_tensor_2d(&m4[3], b_lo, 2, g.n, g.k, o.ldb, 64, 64);
-    } else {
-      m4[2] = m4[0];
-      m4[3] = m4[1];
+      st = encode_tensor_2d(&mp[2], p1a, 2, g.k, g.m, o.lda, 64, g.bm);
+      if (st == G3_OK) st = encode_tensor_2d(&mp[3], p1b, 2, g.n, g.k, o.ldb, 64, 64);
+    }
+    if (st == G3_OK && split3) {
+      st = encode_tensor_2d(&mp[4], a_lo, 2, g.k, g.m, o.lda, 64, g.bm);
+      if (st == G3_OK) st = encode_tensor_2d(&mp[5], b_lo, 2, g.n, g.k, o.ldb, 64, 64);
     }
   }
   if (st != G3_OK) {
@@ -260,7 +294,8 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   }
 
   bool ok = true;
-  ok = ok && cudaMemcpy(d_maps, maps.data(), sizeof(CUtensorMap) * 4 * (size_t)count, cudaMemcpyHostToDevice) ==
+  ok = ok && cudaMemcpy(d_maps, maps.data(), sizeof(CUtensorMap) * kMapsPerProblem * (size_t)count,
+                        cudaMemcpyHostToDevice) ==
                  cudaSuccess;
   ok = ok && cudaMemcpy(d_groups, groups.data(), sizeof(GroupDesc) * (size_t)count, cudaMemcpyHostToDevice) ==
                  cudaSuccess;

@@ -10,7 +10,7 @@
 
 namespace g3 {
 
-// maps: A, B, A lo plane, B lo plane, C (the last used only when p.c_tma)
+// maps: A, B of operand planes 0, 1, 2, then C (used only when p.c_tma)
 using TcLaunchFn = cudaError_t (*)(const CUtensorMap* maps, const TcParams& p, int grid, cudaStream_t s);
 
 // One member of the generated tensor-core kernel family.
@@ -28,6 +28,7 @@ void register_family_bf16(FamilyEntry* table);
 void register_family_3xbf16(FamilyEntry* table);
 void register_family_fp8(FamilyEntry* table);
 void register_family_int8emu(FamilyEntry* table);
+void register_family_6xbf16(FamilyEntry* table);
 
 using GroupedLaunchFn = cudaError_t (*)(const GroupedParams& p, int grid, cudaStream_t s);
 
@@ -45,12 +46,15 @@ void register_grouped_bf16(GroupedEntry* table);
 void register_grouped_3xbf16(GroupedEntry* table);
 void register_grouped_fp8(GroupedEntry* table);
 void register_grouped_int8emu(GroupedEntry* table);
+void register_grouped_6xbf16(GroupedEntry* table);
 
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.
 cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s);
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* lo,
                               long long ldy, cudaStream_t s);
+cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,
+                               uint16_t* lo, long long ldy, cudaStream_t s);
 cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s);
 cudaError_t launch_int8_to_bf16(const int8_t* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,

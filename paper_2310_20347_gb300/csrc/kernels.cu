@@ -42,6 +42,13 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx,
   return cudaGetLastError();
 }
 
+cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,
+                               uint16_t* lo, long long ldy, cudaStream_t s) {
+  split3_bf16_kernel<<<rows_grid(rows, cols, 1), 256, 0, s>>>(x, rows, cols, ldx, hi, mid, lo, ldy);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s) {
   convert_bf16_kernel<<<rows_grid(rows, cols, 4), 256, 0, s>>>(x, rows, cols, ldx, y, ldy);

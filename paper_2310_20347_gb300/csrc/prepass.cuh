@@ -83,6 +83,30 @@ __global__ void split_bf16_vec8_kernel(const float* __restrict__ x, int rows, in
   }
 }
 
+// Three-part split for the small-k FP32-accurate mode: hi = bf16(x),
+// mid = bf16(x - hi), lo = bf16((x - hi) - mid); both differences are exact.
+__device__ __forceinline__ void split3(float v, uint16_t& h, uint16_t& m, uint16_t& l) {
+  h = bf16_bits(v);
+  const float d = v - bf16_value(h);
+  m = bf16_bits(d);
+  l = bf16_bits(d - bf16_value(m));
+}
+
+__global__ void split3_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                   uint16_t* __restrict__ hi, uint16_t* __restrict__ mid, uint16_t* __restrict__ lo,
+                                   long long ldy) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = x + r * ldx;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+      uint16_t h, m, l;
+      split3(xr[c], h, m, l);
+      hi[r * ldy + c] = h;
+      mid[r * ldy + c] = m;
+      lo[r * ldy + c] = l;
+    }
+  }
+}
+
 __global__ void convert_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
                                     uint16_t* __restrict__ y, long long ldy) {
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {

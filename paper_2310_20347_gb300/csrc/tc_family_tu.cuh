@@ -31,7 +31,7 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int grid, cuda
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = pdl_config(grid, Cfg::kThreads, Cfg::kSmemBytes, s, attr);
-  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], p);
+  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], p);
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -44,7 +44,9 @@ namespace g3 {
 // exact in bfloat16); k is accumulated in chunks of at most 1024 products per
 // TMEM accumulator, which keeps every FP32 partial sum an exact integer, and
 // the epilogue adds the chunks in int32.
-enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3 };
+// TC_6XBF16: the FP32-accurate mode for small k: operands split in three
+// bfloat16 parts (hi + mid + lo), six products per k-step.
+enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3, TC_6XBF16 = 4 };
 enum OutMode : int { OUT_F32 = 0, OUT_I32 = 1, OUT_PARTIAL = 2 };
 
 // Watchdog status codes (written to the device status word; see g3gemm.h).
@@ -88,9 +90,13 @@ struct GroupDesc {
   long long ldc;
 };
 
+// Tensor maps of one problem: A and B of each operand plane (hi, then the
+// lower parts of the split modes), then C.
+constexpr int kMapsPerProblem = 6;
+
 struct GroupedParams {
   const GroupDesc* groups;
-  const CUtensorMap* maps;   // 4 per problem: A, B, A lo plane, B lo plane
+  const CUtensorMap* maps;   // kMapsPerProblem per problem: A/B of plane 0, 1, 2
   const int2* tile_info;     // per global tile: (problem, tile index within the problem)
   int total_tiles;
   unsigned long long timeout_ns;
@@ -100,7 +106,7 @@ struct GroupedParams {
 
 template <int MODE>
 struct TcTraits {
-  static constexpr int kPlanes = (MODE == TC_3XBF16) ? 2 : 1;   // hi/lo operand planes
+  static constexpr int kPlanes = (MODE == TC_3XBF16) ? 2 : (MODE == TC_6XBF16 ? 3 : 1);   // operand planes
   static constexpr int kElem = (MODE == TC_FP8) ? 1 : 2;        // bytes per element
   static constexpr int kBK = 128 / kElem;                        // k per block: one 128-B row
   static constexpr int kKStep = 32 / kElem;                      // k per MMA instruction
@@ -128,7 +134,7 @@ struct TcConfig {
   // nearest, in the epilogue.  Accumulator sets are multi-buffered across
   // output tiles as far as TMEM (512 columns) allows, up to kMaxBufs, so that
   // the MMA can run several short tiles ahead of the epilogue.
-  static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16) ? 2 : 1;
+  static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16 || MODE == TC_6XBF16) ? 2 : 1;
   static constexpr uint32_t kSetCols = kAccPerTile * BM_T;
   static constexpr uint32_t kMaxBufs = 4;
   static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
@@ -170,7 +176,7 @@ struct EpiJob {
 template <int BM_T>
 struct SingleSched {
   const TcParams* p;
-  const CUtensorMap* maps[4];   // A, B, A lo plane, B lo plane (kernel parameters)
+  const CUtensorMap* maps[kMapsPerProblem];   // A, B of planes 0..2 (kernel parameters)
   const CUtensorMap* cmap;      // C for TMA stores, or null
 
   __device__ __forceinline__ int total() const { return p->tiles_m * p->tiles_n * p->splits; }
@@ -211,7 +217,7 @@ struct GroupedSched {
   }
 
   __device__ __forceinline__ const CUtensorMap* map(const TileJob& j, int which) const {
-    return gp->maps + 4 * j.g + which;
+    return gp->maps + kMapsPerProblem * j.g + which;
   }
 
   __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
@@ -291,8 +297,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           for (int pl = 0; pl < T::kPlanes; ++pl) {
             uint8_t* bt = st + pl * Cfg::kPlaneBytes;
             uint8_t* at = bt + T::kBtBytes;
-            const CUtensorMap* mb = S.map(j, pl == 0 ? 1 : 3);
-            const CUtensorMap* ma = S.map(j, pl == 0 ? 0 : 2);
+            const CUtensorMap* mb = S.map(j, 2 * pl + 1);
+            const CUtensorMap* ma = S.map(j, 2 * pl);
 #pragma unroll
             for (int h = 0; h < T::kNBoxes; ++h)
               tma_load_2d(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, &full[stage]);
@@ -347,6 +353,20 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
               // main term Bhi*Ahi; Blo*Alo is dropped
               mma_f16(d_corr, bt_hi, a_lo, idesc, accumulate);
               mma_f16(d_corr, bt_lo, a_hi, idesc, 1u);
+              mma_f16(d_tmem, bt_hi, a_hi, idesc, accumulate);
+            } else if (MODE == TC_6XBF16) {
+              const uint32_t p1 = Cfg::kPlaneBytes, p2 = 2 * Cfg::kPlaneBytes;
+              const uint64_t bt_mid = smem_desc_sw128(st + p1 + bt_off, T::kBtLBO, 1024);
+              const uint64_t a_mid = smem_desc_sw128(st + p1 + a_off, 16, 1024);
+              const uint64_t bt_lo = smem_desc_sw128(st + p2 + bt_off, T::kBtLBO, 1024);
+              const uint64_t a_lo = smem_desc_sw128(st + p2 + a_off, 16, 1024);
+              // corrections hi*mid + mid*hi + hi*lo + lo*hi + mid*mid, then hi*hi;
+              // mid*lo, lo*mid and lo*lo (<= 2^-23 relative) are dropped
+              mma_f16(d_corr, bt_hi, a_mid, idesc, accumulate);
+              mma_f16(d_corr, bt_mid, a_hi, idesc, 1u);
+              mma_f16(d_corr, bt_hi, a_lo, idesc, 1u);
+              mma_f16(d_corr, bt_lo, a_hi, idesc, 1u);
+              mma_f16(d_corr, bt_mid, a_mid, idesc, 1u);
               mma_f16(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else if (MODE == TC_FP8) {
               mma_f8(d_tmem, bt_hi, a_hi, idesc, accumulate);
@@ -519,7 +539,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           }
         }
       };
-      if (MODE == TC_3XBF16) {
+      if (MODE == TC_3XBF16 || MODE == TC_6XBF16) {
         for (int c = 0; c < nchunks; ++c) {
           uint32_t r[32], rc[32];
           tmem_ld_32x32b_x32(tbase + c * 32, r);
@@ -572,18 +592,23 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 template <int BM_T, int STAGES, int MODE>
 __global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo,
+                   const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
+                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ TcParams p) {
   if (threadIdx.x == 0) {
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
-    if (MODE == TC_3XBF16) {
-      tma_prefetch_desc(&tmA_lo);
-      tma_prefetch_desc(&tmB_lo);
+    if (TcTraits<MODE>::kPlanes > 1) {
+      tma_prefetch_desc(&tmA1);
+      tma_prefetch_desc(&tmB1);
+    }
+    if (TcTraits<MODE>::kPlanes > 2) {
+      tma_prefetch_desc(&tmA2);
+      tma_prefetch_desc(&tmB2);
     }
     if (p.c_tma) tma_prefetch_desc(&tmC);
   }
-  const SingleSched<BM_T> S{&p, {&tmA, &tmB, &tmA_lo, &tmB_lo}, p.c_tma ? &tmC : nullptr};
+  const SingleSched<BM_T> S{&p, {&tmA, &tmB, &tmA1, &tmB1, &tmA2, &tmB2}, p.c_tma ? &tmC : nullptr};
   tc_gemm_body<BM_T, STAGES, MODE>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
 }
 

@@ -6,7 +6,7 @@ search that keeps the best member per problem shape (Section 8.4).  This
 script plays the generator's role for the GPU kernels: it enumerates the
 parameter space
 
-    mode     bf16 | 3xbf16 | fp8      operand format of the MMA
+    mode     bf16 | 3xbf16 | 6xbf16 | fp8 | int8emu   operand format of the MMA
     bm       64 | 128 | 256           output rows per tile = MMA N (tile is bm x 128)
     stages   2 .. 8                   depth of the shared-memory k-block ring
 
@@ -38,8 +38,11 @@ MODES = {            # name: (planes, element bytes)
     "3xbf16": (2, 2),
     "fp8": (1, 1),
     "int8emu": (1, 2),   # exact int8 on the BF16 path, k accumulated in chunks of <= 1024
+    "6xbf16": (3, 2),    # FP32-accurate, three-part split, 6 products: used for small k
 }
-MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8", "int8emu": "TC_I8EMU"}
+MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8", "int8emu": "TC_I8EMU",
+             "6xbf16": "TC_6XBF16"}
+SPLIT_MODES = ("3xbf16", "6xbf16")   # two accumulators per tile (main + corrections)
 BMS = (256, 128, 64)
 # int8emu keeps one int32 running sum per row of its column in registers
 MAX_BM = {"int8emu": 128}
@@ -63,7 +66,7 @@ def enumerate_family():
     members = []
     for mode in MODES:
         for bm in BMS:
-            if (2 if mode == "3xbf16" else 1) * bm > TMEM_COLUMNS or bm > MAX_BM.get(mode, 256):
+            if (2 if mode in SPLIT_MODES else 1) * bm > TMEM_COLUMNS or bm > MAX_BM.get(mode, 256):
                 continue
             fits = [s for s in range(2, 9) if smem_bytes(mode, bm, s) <= SMEM_LIMIT]
             if not fits:
@@ -71,7 +74,7 @@ def enumerate_family():
             chosen = [max(fits)]
             if max(fits) - 1 in fits and max(fits) > 3:
                 chosen.append(max(fits) - 1)
-            acc_cols = (2 if mode == "3xbf16" else 1) * bm     # main (+ correction) accumulators
+            acc_cols = (2 if mode in SPLIT_MODES else 1) * bm  # main (+ correction) accumulators
             bufs = min(4, TMEM_COLUMNS // acc_cols)               # accumulator sets across tiles
             for st in chosen:
                 members.append({"mode": mode, "bm": bm, "stages": st,
@@ -84,7 +87,7 @@ def enumerate_family():
 # Grouped launches: problems of at most 1024 x 1024 take tiles of 64 or 128
 # rows (chosen per problem by the planner's size bucket), so the kernel's
 # buffers are sized for bm_max = 128; one member per mode with the deepest ring.
-GROUPED_MODES = ("bf16", "3xbf16")
+GROUPED_MODES = ("bf16", "3xbf16", "6xbf16")
 GROUPED_BM_MAX = 128
 
 

@@ -80,6 +80,16 @@ def split_bf16(x: torch.Tensor, stream=None):
     return hi, lo
 
 
+def split3_bf16(x: torch.Tensor, stream=None):
+    """(hi, mid, lo) bfloat16 planes of the three-part split, shaped like x."""
+    hi = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    mid = torch.empty_like(hi)
+    lo = torch.empty_like(hi)
+    check(_lib.g3_split3_bf16(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), hi.data_ptr(), mid.data_ptr(),
+                              lo.data_ptr(), max(x.shape[1], 1), _stream(stream)), "g3_split3_bf16")
+    return hi, mid, lo
+
+
 def quantize_fp8(x: torch.Tensor, stream=None):
     """(codes uint8 like x, scale float32 tensor of one element)."""
     q = torch.empty(x.shape, dtype=torch.uint8, device=x.device)

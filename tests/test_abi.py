@@ -52,6 +52,16 @@ def test_argument_errors(lib):
     assert L.g3_gemm(4, 4, 8, 1.0, None, 8, p, 4, 0.0, p, 4, 0) == -105
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, None, 4, 0.0, p, 4, 0) == -107
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, None, 4, 0) == -110
+    # operand preparation: the same positional codes
+    assert L.g3_convert_bf16(p, 4, 8, 8, p, 7) == -106
+    assert L.g3_split_bf16(p, 4, 8, 8, p, p, 7) == -107
+    assert L.g3_split_bf16(p, 4, 8, 8, p, None, 8) == -106
+    assert L.g3_split3_bf16(p, 4, 8, 7, p, p, p, 8) == -104
+    assert L.g3_split3_bf16(p, 4, 8, 8, None, p, p, 8) == -105
+    assert L.g3_split3_bf16(p, 4, 8, 8, p, None, p, 8) == -106
+    assert L.g3_split3_bf16(p, 4, 8, 8, p, p, None, 8) == -107
+    assert L.g3_split3_bf16(p, 4, 8, 8, p, p, p, 7) == -108
+    assert L.g3_split3_bf16(p, 0, 8, 8, None, None, None, 8) == 0
     # INT8 accepts only alpha == 1 and beta in {0, 1}
     assert L.g3_gemm(4, 4, 8, 2.0, p, 8, p, 4, 0.0, p, 4, 4) == L.G3_ERR_UNSUPPORTED
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.5, p, 4, 4) == L.G3_ERR_UNSUPPORTED
@@ -91,6 +101,10 @@ def test_planner_choices(lib):
     # INT8 runs on the exact-integer members (k chunked inside the kernel): no split needed
     st, cfg, sk, rs = L.g3_plan_query(8192, 8192, 8192, L.G3_INT8)
     assert fam[cfg]["mode"] == "int8emu" and fam[cfg]["bm"] == 128 and sk == 1
+    # FP32-accurate at k <= 512: the three-part split (6 products); above: two-part
+    for k, mode in ((16, "6xbf16"), (512, "6xbf16"), (513, "3xbf16"), (4096, "3xbf16")):
+        st, cfg, sk, rs = L.g3_plan_query(2048, 2048, k, L.G3_F32_3XBF16)
+        assert st == 0 and fam[cfg]["mode"] == mode, (k, fam[cfg])
     st, cfg, sk, rs = L.g3_plan_query(128, 128, 100, L.G3_F32)
     assert cfg == -1
 

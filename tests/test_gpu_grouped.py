@@ -43,6 +43,9 @@ def make_batch(count, seed, lo=1, hi=300, dtype=G3_BF16, unaligned_every=5):
 
 
 def check_batch(probs, host, dtype):
+    # an FP32-accurate plan takes the three-part split for all of its problems
+    # as soon as one problem with products has k <= 512
+    split3 = any(p.m > 0 and p.n > 0 and 0 < p.k <= 512 and p.alpha != 0 for p, _ in host)
     worst_k = worst_g = 0.0
     for (A, B, C, alpha, beta), (p, full) in zip(probs, host):
         f = full.cpu().numpy()
@@ -57,9 +60,10 @@ def check_batch(probs, host, dtype):
             D_k = oracle.absprod(Aq, Bq, p.alpha)
             gate = 8e-3
         else:
-            ref_k = oracle.gemm_3xbf16(p.A, p.B, p.C, p.alpha, p.beta)
+            method = oracle.gemm_6xbf16 if split3 else oracle.gemm_3xbf16
+            ref_k = method(p.A, p.B, p.C, p.alpha, p.beta)
             D_k = oracle.absprod(p.A, p.B, p.alpha)
-            gate = 1.2e-4       # the 3-product split's own bound at any k (3*2^-16)
+            gate = 2e-6
         e_k = rel_err(got, ref_k, D_k, bc)
         e_g = rel_err(got, oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), oracle.absprod(p.A, p.B, p.alpha), bc)
         assert e_k <= 1e-5, (p.m, p.n, p.k, "kernel", e_k)
@@ -76,6 +80,18 @@ def test_grouped_parity(dtype):
     torch.cuda.synchronize()
     ek, eg = check_batch(probs, host, dtype)
     print(f"grouped dtype {dtype}: kernel {ek:.3e} gate {eg:.3e}")
+    plan.close()
+
+
+def test_grouped_fp32_deep_k_takes_two_part_split():
+    # every k > 512: the plan runs the 3-product kernel, still within 2e-6
+    probs, host = make_batch(8, seed=4, lo=600, hi=1024, dtype=G3_F32_3XBF16, unaligned_every=3)
+    assert all(p.k > 512 for p, _ in host)
+    plan = torch_api.GroupedPlan(probs, G3_F32_3XBF16)
+    plan.execute()
+    torch.cuda.synchronize()
+    ek, eg = check_batch(probs, host, G3_F32_3XBF16)
+    print(f"grouped fp32 deep k: kernel {ek:.3e} gate {eg:.3e}")
     plan.close()
 
 
