@@ -53,7 +53,12 @@ extern "C" {
  *   G3_F32         A, B, C float32; FP32 FFMA on the CUDA cores.
  *   G3_F32_3XBF16  A, B, C float32; each operand split into hi + lo bfloat16
  *                  parts, C += Ahi*Bhi + Ahi*Blo + Alo*Bhi on the tensor cores
- *                  with FP32 accumulation (the lo*lo term is dropped).
+ *                  with FP32 accumulation (the lo*lo term is dropped).  For
+ *                  k <= 512 the split has three parts (hi + mid + lo) and six
+ *                  products (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid):
+ *                  at small k the two-part split's own error is above 2e-6
+ *                  of sum |a||b|.  A grouped call takes the three-part split
+ *                  for all its problems when one of them has k <= 512.
  *   G3_BF16        A, B bfloat16 (raw 16-bit patterns); C float32.
  *   G3_FP8_E4M3    A, B OCP E4M3 bytes with per-tensor scales (g3_gemm_ex);
  *                  C float32 = alpha*scale_a*scale_b*(Aq Bq) + beta*C.
