@@ -418,7 +418,7 @@ def run_workload(args):
         return
 
     if args.workload in ("int8", "fp8", "bf16"):
-        n = 8192
+        n = args.dsize
         if args.workload == "bf16":
             p = synth.normal_problem(n, n, n, seed=0)
             A, B = torch_api.convert_bf16(torch.from_numpy(p.A).to(dev)), torch_api.convert_bf16(
@@ -557,6 +557,7 @@ def main():
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")
+    ap.add_argument("--dsize", type=int, default=8192, help="int8 / fp8 / bf16 workloads: m = n = k")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--only", default="", help="im2col workloads: comma-separated layer names (e.g. L1,L12)")
     ap.add_argument("--tune", action="store_true", help="im2col workloads: autotune every shape first")

@@ -196,14 +196,18 @@ G3_API int g3_gemm_grouped(int count, const g3_gemm_desc* descs, int dtype, void
 
 /* Synchronise the device, return G3_ERR_TIMEOUT if any kernel since the last
  * call reported an expired wait (G3_OK otherwise) and clear the word.  The
- * raw device code is stored in *code when code != NULL.                      */
+ * raw device code is stored in *code when code != NULL: 0x101-0x105 name the
+ * wait that expired (producer, MMA stage, MMA accumulator, epilogue, drain);
+ * 0x106: the two CTAs of a CTA-pair member were given different TMEM
+ * addresses, and the kernel did no work.                                     */
 G3_API int g3_get_last_device_status(int* code);
 
 G3_API const char* g3_status_string(int status);
 
 /* Number of members of the generated tensor-core kernel family, and a
- * one-line description ("mode=bf16 bm=256 stages=4 smem=197888") of member
- * `index` written to buf (NUL-terminated, truncated to len).               */
+ * one-line description ("mode=bf16 bm=256 bn=128 stages=4 smem=197888 bufs=2
+ * cg=1"; cg = 2: a CTA-pair member with 256-column tiles) of member `index`
+ * written to buf (NUL-terminated, truncated to len).                        */
 G3_API int g3_family_size(void);
 G3_API int g3_family_describe(int index, char* buf, size_t len);
 

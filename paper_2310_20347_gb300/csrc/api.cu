@@ -172,9 +172,21 @@ struct Plan {
   int raster = 8;
 };
 
-// Relative throughput of one SM with an MMA of N = bm (smem bandwidth per flop
-// grows as N shrinks; values from the operand bytes each MMA reads).
-double tile_efficiency(int bm) { return bm >= 256 ? 1.0 : (bm >= 128 ? 0.8 : 0.55); }
+// Relative throughput of a member.  Measured on GB300 (BF16 8192^3 and the
+// FP32-accurate 16384^3), one k-block of a tile costs about
+//   max(MMA time, L / stages)
+// clocks: the MMA time is 73 clocks per MMA of 128 x 128 x 16 (x 2 with N = 256),
+// times the products per k-step; L (about 3000 clocks for one CTA, 4000 for a
+// CTA pair, whose stages complete only when both CTAs' loads have landed) is
+// the load latency that the shared-memory ring must cover.  N = 128 members of
+// one product therefore stay near 0.6 of peak at any ring depth, N = 256 reach
+// 0.86 (one CTA) and 0.96 (pair), and the 3-product members are MMA-bound.
+double tile_efficiency(const FamilyEntry& f) {
+  const int products = f.mode == TC_3XBF16 ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
+  const double mma = 4.0 * products * 73.0 * f.bm / 128.0;
+  const double lat = (f.cg > 1 ? 4000.0 : 3000.0) / f.stages;
+  return std::min(0.97, mma / std::max(mma, lat));
+}
 
 // ---------------------------------------------------------------- tuning cache
 // Results of g3_autotune, keyed by dtype and the power-of-two bucket of each of
@@ -241,7 +253,6 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   const int mode = tc_mode_of(dtype, k);
   const int bk = (mode == TC_FP8) ? 128 : 64;
   pl.num_kb = (int)((k + bk - 1) / bk);
-  pl.tiles_n = (int)((n + 127) / 128);
   if (force_member >= 0 && force_member < G3_FAMILY_SIZE && g_family[force_member].mode == mode &&
       g_family[force_member].launch) {
     pl.member = force_member;
@@ -250,12 +261,16 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     for (int i = 0; i < G3_FAMILY_SIZE; ++i) {
       const FamilyEntry& f = g_family[i];
       if (!f.launch || f.mode != mode) continue;
-      if (pl.member >= 0 && g_family[pl.member].bm == f.bm) continue;   // first (deepest) variant per bm
-      const long long tiles = ((m + f.bm - 1) / f.bm) * (long long)pl.tiles_n;
-      const long long waves = (tiles + sms - 1) / sms;
+      // first (deepest) variant per (bm, cg)
+      if (pl.member >= 0 && g_family[pl.member].bm == f.bm && g_family[pl.member].cg == f.cg) continue;
+      const long long tiles = ((m + f.bm - 1) / f.bm) * ((n + 128LL * f.cg - 1) / (128LL * f.cg));
+      const long long slots = std::max(1, sms / f.cg);   // tiles in flight at once
+      const long long waves = (tiles + slots - 1) / slots;
       // a single accumulator set serialises every tile's epilogue with the
       // next tile's main loop (measured: 71% vs 90% of peak at 16384^3)
-      const double cost = (double)waves * f.bm / tile_efficiency(f.bm) * (f.bufs < 2 ? 1.3 : 1.0);
+      // (pairs: 2% for the cluster set-up, so that ties go to the single CTA)
+      const double cost = (double)waves * f.bm / tile_efficiency(f) * (f.bufs < 2 ? 1.3 : 1.0) *
+                          (f.cg > 1 ? 1.02 : 1.0);
       if (cost < best * 0.999) {
         best = cost;
         pl.member = i;
@@ -264,13 +279,15 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   }
   if (pl.member < 0) return pl;
   const int bm = g_family[pl.member].bm;
+  const int cg = g_family[pl.member].cg;
+  pl.tiles_n = (int)((n + 128LL * cg - 1) / (128LL * cg));
   pl.tiles_m = (int)((m + bm - 1) / bm);
   const long long tiles = (long long)pl.tiles_m * pl.tiles_n;
   int splits = 1;
   if (force_split > 0) {
     splits = force_split;
-  } else if (tiles * 2 <= sms && pl.num_kb >= 8) {
-    splits = (int)std::min<long long>(sms / tiles, std::min(pl.num_kb / 4, 16));
+  } else if (tiles * 2 <= sms / cg && pl.num_kb >= 8) {
+    splits = (int)std::min<long long>(sms / cg / tiles, std::min(pl.num_kb / 4, 16));
     splits = std::max(splits, 1);
   }
   splits = std::min(splits, pl.num_kb);
@@ -497,17 +514,18 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   // them).  Map 6 is C's store map.
   CUtensorMap maps[7];
   std::memset(maps, 0, sizeof(maps));
-  if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+  const uint32_t arows = fam.bm / fam.cg;   // rows of A one CTA stages (half the tile in a pair)
+  if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, arows)) != G3_OK) return st;
   if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
   maps[2] = maps[4] = maps[0];
   maps[3] = maps[5] = maps[1];
   if (fam.mode == TC_6XBF16) {
-    if ((st = encode_2d(&maps[2], A_mid, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[2], A_mid, es, k, m, lda, bk, arows)) != G3_OK) return st;
     if ((st = encode_2d(&maps[3], B_mid, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
-    if ((st = encode_2d(&maps[4], A_lo, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[4], A_lo, es, k, m, lda, bk, arows)) != G3_OK) return st;
     if ((st = encode_2d(&maps[5], B_lo, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
   } else if (a.dtype == G3_F32_3XBF16) {
-    if ((st = encode_2d(&maps[2], A_lo, es, k, m, lda, bk, fam.bm)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[2], A_lo, es, k, m, lda, bk, arows)) != G3_OK) return st;
     if ((st = encode_2d(&maps[3], B_lo, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
   }
 
@@ -550,11 +568,10 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
         encode_c_2d(&maps[6], a.C, is_int, n, m, a.ldc) == G3_OK)
       p.c_tma = 1;
   }
-  const long long total_tiles = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
-  const int grid = (int)std::min<long long>(total_tiles, d.sms);
+
   {
     TimedRegion tr(s);
-    G3_CHECK_CUDA(fam.launch(maps, p, grid, s));
+    G3_CHECK_CUDA(fam.launch(maps, p, d.sms, s));
   }
   if (pl.splits > 1) {
     float alpha = (float)a.alpha;
@@ -772,8 +789,8 @@ int g3_family_describe(int index, char* buf, size_t len) {
   }
   const FamilyEntry& f = g_family[index];
   static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16"};
-  std::snprintf(buf, len, "mode=%s bm=%d bn=128 stages=%d smem=%d bufs=%d", names[f.mode], f.bm, f.stages, f.smem,
-                f.bufs);
+  std::snprintf(buf, len, "mode=%s bm=%d bn=%d stages=%d smem=%d bufs=%d cg=%d", names[f.mode], f.bm, 128 * f.cg,
+                f.stages, f.smem, f.bufs, f.cg);
   return G3_OK;
 }
 

@@ -10,8 +10,9 @@
 
 namespace g3 {
 
-// maps: A, B of operand planes 0, 1, 2, then C (used only when p.c_tma)
-using TcLaunchFn = cudaError_t (*)(const CUtensorMap* maps, const TcParams& p, int grid, cudaStream_t s);
+// maps: A, B of operand planes 0, 1, 2, then C (used only when p.c_tma); the
+// launcher sizes the persistent grid from the tile count and `sms`.
+using TcLaunchFn = cudaError_t (*)(const CUtensorMap* maps, const TcParams& p, int sms, cudaStream_t s);
 
 // One member of the generated tensor-core kernel family.
 struct FamilyEntry {
@@ -21,6 +22,7 @@ struct FamilyEntry {
   int stages;   // shared-memory ring depth
   int smem;     // dynamic shared memory bytes
   int bufs;     // TMEM accumulator sets (2: the epilogue overlaps the next tile)
+  int cg;       // CTAs per MMA: 1, or 2 (a CTA pair; tiles are 256 columns wide)
   TcLaunchFn launch;
 };
 

@@ -29,8 +29,18 @@
 //
 // Which tiles a CTA walks comes from a scheduler policy: SingleSched for one
 // problem (TcParams, tensor maps as kernel parameters), GroupedSched for many
-// independent problems in one launch (a device table of problems, four tensor
+// independent problems in one launch (a device table of problems, six tensor
 // maps per problem in global memory, and per problem its own tile height bm).
+//
+// CTA pairs (CG = 2, a cluster of two CTAs on neighbouring SMs).  One MMA of
+// M = 256 spans both SMs: the tile is 256 columns of C x bm rows; each CTA
+// stages its own 128 columns of B and HALF of the bm rows of A, so a CTA moves
+// 16 KB + bm*64 B per k-block instead of 16 KB + bm*128 B for the same MMA
+// work -- shared-memory fill bandwidth per SM, not the tensor core, is what
+// limits the single-CTA members.  The leader (cluster rank 0) issues every MMA
+// and waits for both CTAs' TMA bytes on its own barriers; its commits arrive on
+// the barriers of both CTAs; each CTA's epilogue drains its own TMEM (its 128
+// columns of C) and reports to the leader.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -56,6 +66,7 @@ enum : int {
   WD_MMA_TMEM_EMPTY = 0x103,
   WD_EPI_TMEM_FULL = 0x104,
   WD_DRAIN = 0x105,
+  WD_PAIR_TMEM = 0x106,   // the two CTAs of a pair did not receive the same TMEM address
 };
 
 struct TcParams {
@@ -121,10 +132,10 @@ struct TcTraits {
   static constexpr uint32_t kBtLBO = (kNBoxes > 1) ? kBK * 128 : 1024;
 };
 
-template <int BM_T, int STAGES, int MODE>
+template <int BM_T, int STAGES, int MODE, int CG = 1>
 struct TcConfig {
   using T = TcTraits<MODE>;
-  static constexpr uint32_t kABytes = BM_T * 128;                      // BM_T rows x 128 B
+  static constexpr uint32_t kABytes = BM_T * 128 / CG;                 // this CTA's rows of A x 128 B
   static constexpr uint32_t kPlaneBytes = T::kBtBytes + kABytes;       // one plane of a stage
   static constexpr uint32_t kStageBytes = T::kPlanes * kPlaneBytes;
   // The tensor core adds each MMA's products to its FP32 accumulator with
@@ -140,17 +151,20 @@ struct TcConfig {
   static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
   static constexpr uint32_t kTmemCols = kNumBufs * kSetCols;
   // Epilogue warps: one per TMEM lane quarter, each thread owning all bm rows
-  // of its column.  (An exact-integer variant with bm = 256 and eight epilogue
-  // warps of 128 rows each measured slower than bm = 128: its large unrolled
-  // epilogue starved the MMA-issuing thread of instruction fetch.)
+  // of its column.  (Exact-integer variants with eight epilogue warps measured
+  // slower: with bm = 256 its large unrolled epilogue starved the MMA-issuing
+  // thread of instruction fetch; with bm = 128, 64 rows each, the 168-register
+  // cap of ten warps made it spill.)
   static constexpr int kEpiWarps = 4;
-  static constexpr int kEpiRows = BM_T;   // rows of the tile per epilogue thread
+  static constexpr int kEpiRows = BM_T / (kEpiWarps / 4);   // rows of the tile per epilogue thread
   // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128 columns x 4 bytes.
   static constexpr uint32_t kCStageBytes = 2 * 32 * 128 * 4;
   static constexpr uint32_t kBarBytes = 256;
   static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kCStageBytes + kBarBytes;
   static constexpr int kThreads = 64 + 32 * kEpiWarps;
   static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
+  static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair");
+  static_assert(kNumBufs >= 1, "TMEM budget");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
   static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32 && kTmemCols <= 512, "TMEM allocation");
   static_assert(8 * (2 * STAGES + 2 * kMaxBufs + 1) + 8 <= (int)kBarBytes, "barrier area");
@@ -173,11 +187,12 @@ struct EpiJob {
   const CUtensorMap* cmap;    // non-null: store C (beta == 0) by TMA through this map
 };
 
-template <int BM_T>
+template <int BM_T, int CG = 1>
 struct SingleSched {
   const TcParams* p;
   const CUtensorMap* maps[kMapsPerProblem];   // A, B of planes 0..2 (kernel parameters)
   const CUtensorMap* cmap;      // C for TMA stores, or null
+  int n_off;                    // 128 * (rank in the CTA pair): this CTA's columns of a pair tile
 
   __device__ __forceinline__ int total() const { return p->tiles_m * p->tiles_n * p->splits; }
 
@@ -192,7 +207,8 @@ struct SingleSched {
     const int tm = band * G + in_band % rows;
     const int tn = in_band / rows;
     const int kb0 = s * p->kb_per_split;
-    return TileJob{tm * BM_T, tn * 128, kb0, min(p->num_kb, kb0 + p->kb_per_split), BM_T, s, 0, p->kchunk};
+    return TileJob{tm * BM_T, tn * (128 * CG) + n_off, kb0, min(p->num_kb, kb0 + p->kb_per_split), BM_T, s, 0,
+                   p->kchunk};
   }
 
   __device__ __forceinline__ const CUtensorMap* map(const TileJob&, int which) const { return maps[which]; }
@@ -226,11 +242,19 @@ struct GroupedSched {
   }
 };
 
-template <int BM_T, int STAGES, int MODE, class Sched>
+// Shared::cluster address of a barrier of the pair's leader (CTA pairs), or
+// the local barrier's address.
+template <bool kPair>
+__device__ __forceinline__ uint32_t mapa_or_local(uint64_t* bar) {
+  return kPair ? mapa_shared(smem_u32(bar), 0) : smem_u32(bar);
+}
+
+template <int BM_T, int STAGES, int MODE, int CG, class Sched>
 __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long timeout_ns, int* status,
                                              int debug_withhold, const float* scale_a, const float* scale_b) {
   using T = TcTraits<MODE>;
-  using Cfg = TcConfig<BM_T, STAGES, MODE>;
+  using Cfg = TcConfig<BM_T, STAGES, MODE, CG>;
+  constexpr bool kPair = (CG == 2);
   constexpr bool kIntChunked = (MODE == TC_I8EMU);
   static_assert(!kIntChunked || Cfg::kEpiRows <= 128, "int32 running sums live in registers: <= 128 rows");
   extern __shared__ uint8_t smem_raw[];
@@ -247,6 +271,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const uint32_t rank = kPair ? cluster_ctarank() : 0u;   // 0: the pair's leader (or a lone CTA)
+  const bool leader = rank == 0;
+  const int first_tile = blockIdx.x / CG;                 // tiles are walked per cluster
+  const int tile_stride = gridDim.x / CG;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -255,20 +283,28 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
     }
     for (int a = 0; a < (int)Cfg::kNumBufs; ++a) {
       mbar_init(&tmem_full[a], 1);
-      mbar_init(&tmem_empty[a], Cfg::kEpiWarps);
+      mbar_init(&tmem_empty[a], CG * Cfg::kEpiWarps);   // the epilogue warps of every CTA of the pair
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, Cfg::kTmemCols);
-    tmem_relinquish();
+    tmem_alloc<CG>(tmem_slot, Cfg::kTmemCols);
+    tmem_relinquish<CG>();
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (kPair) cluster_sync();   // the peer's barriers are initialised before any remote arrive
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  bool pair_ok = true;
+  if constexpr (kPair) {
+    // the pair's MMAs write the same TMEM address in both CTAs
+    const uint32_t peer_base = ld_shared_cluster_u32(mapa_shared(smem_u32(tmem_slot), rank ^ 1u));
+    pair_ok = peer_base == tmem_base;
+    if (!pair_ok && threadIdx.x == 0) atomicCAS(status, 0, WD_PAIR_TMEM);
+  }
   // Programmatic dependent launch: the set-up above overlaps the tail of the
   // previous kernel in the stream; wait for that kernel (and its memory) before
   // any global access, and let the next kernel start its own set-up.
@@ -276,21 +312,24 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   Watchdog wd{timeout_ns, status, abort_flag};
-  const int total_tiles = S.total();
+  const int total_tiles = pair_ok ? S.total() : 0;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
+      for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
         const TileJob j = S.tile(t);
-        const uint32_t stage_bytes = T::kPlanes * (T::kBtBytes + (uint32_t)j.bm * 128u);
+        // bytes this CTA stages per k-block; a pair's leader counts both CTAs'
+        const uint32_t stage_bytes = T::kPlanes * (T::kBtBytes + (uint32_t)j.bm * 128u / CG);
+        const int a_row = j.m0 + (int)rank * (j.bm / CG);
         for (int kb = j.kb0; kb < j.kb1; ++kb, ++it) {
           const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
-          if (!wait_parity(&empty[stage], ph ^ 1u, wd, WD_PRODUCER_EMPTY)) { ok = false; break; }
+          if (!wait_parity<kPair>(&empty[stage], ph ^ 1u, wd, WD_PRODUCER_EMPTY)) { ok = false; break; }
           if ((int)it == debug_withhold) continue;   // failure-detection test: never arrive
-          mbar_arrive_expect_tx(&full[stage], stage_bytes);
+          if (leader) mbar_arrive_expect_tx(&full[stage], CG * stage_bytes);
+          const uint32_t full_c = mapa_or_local<kPair>(&full[stage]);
           uint8_t* st = smem + stage * Cfg::kStageBytes;
           const int k0 = kb * T::kBK;
 #pragma unroll
@@ -299,41 +338,56 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             uint8_t* at = bt + T::kBtBytes;
             const CUtensorMap* mb = S.map(j, 2 * pl + 1);
             const CUtensorMap* ma = S.map(j, 2 * pl);
+            if constexpr (kPair) {
 #pragma unroll
-            for (int h = 0; h < T::kNBoxes; ++h)
-              tma_load_2d(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, &full[stage]);
-            tma_load_2d(at, ma, k0, j.m0, &full[stage]);
+              for (int h = 0; h < T::kNBoxes; ++h)
+                tma_load_2d_pair(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, full_c);
+              tma_load_2d_pair(at, ma, k0, a_row, full_c);
+            } else {
+#pragma unroll
+              for (int h = 0; h < T::kNBoxes; ++h)
+                tma_load_2d(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, &full[stage]);
+              tma_load_2d(at, ma, k0, a_row, &full[stage]);
+            }
           }
         }
       }
-      // Let every load already issued land before the CTA can retire.
-      const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+      // Let every load already issued land before the CTA can retire (a pair's
+      // loads all complete on the leader's barriers; the closing cluster
+      // barrier orders the other CTA after them).
+      const uint32_t first = !leader ? it : (it > (uint32_t)STAGES ? it - STAGES : 0u);
       for (uint32_t q = first; q < it; ++q) {
         uint64_t t0 = globaltimer_ns();
-        while (!mbar_try_wait(&full[q % STAGES], (q / STAGES) & 1u))
+        while (!(kPair ? mbar_try_wait_cluster(&full[q % STAGES], (q / STAGES) & 1u)
+                       : mbar_try_wait(&full[q % STAGES], (q / STAGES) & 1u)))
           if (globaltimer_ns() - t0 > timeout_ns) { atomicCAS(status, 0, WD_DRAIN); break; }
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       uint32_t it = 0, lt = 0;   // lt counts accumulation chunks (one per tile unless k is chunked)
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
+      // commits of a pair arrive on the barrier of both CTAs
+      auto commit = [&](uint64_t* bar) {
+        if constexpr (kPair) mma_commit_pair(bar, 0x3);
+        else mma_commit(bar);
+      };
+      for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
         const TileJob j = S.tile(t);
-        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/true, /*b_mn=*/false, 128, j.bm);
+        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/true, /*b_mn=*/false, 128 * CG, j.bm);
         const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
         for (int c0 = j.kb0; ok && c0 < j.kb1; c0 += span, ++lt) {
         const int c1 = min(j.kb1, c0 + span);
         const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
-        if (!wait_parity(&tmem_empty[acc], aph ^ 1u, wd, WD_MMA_TMEM_EMPTY)) { ok = false; break; }
+        if (!wait_parity<kPair>(&tmem_empty[acc], aph ^ 1u, wd, WD_MMA_TMEM_EMPTY)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * Cfg::kSetCols;   // main accumulator
         const uint32_t d_corr = d_tmem + BM_T;                       // 3xBF16 corrections
         uint32_t accumulate = 0;
         for (int kb = c0; kb < c1; ++kb, ++it) {
           const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
-          if (!wait_parity(&full[stage], ph, wd, WD_MMA_FULL)) { ok = false; break; }
+          if (!wait_parity<kPair>(&full[stage], ph, wd, WD_MMA_FULL)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + stage * Cfg::kStageBytes);
 #pragma unroll
@@ -351,9 +405,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
               const uint64_t a_lo = smem_desc_sw128(st + lo + a_off, 16, 1024);
               // corrections Bhi*Alo + Blo*Ahi in their own accumulator, then the
               // main term Bhi*Ahi; Blo*Alo is dropped
-              mma_f16(d_corr, bt_hi, a_lo, idesc, accumulate);
-              mma_f16(d_corr, bt_lo, a_hi, idesc, 1u);
-              mma_f16(d_tmem, bt_hi, a_hi, idesc, accumulate);
+              mma_f16<CG>(d_corr, bt_hi, a_lo, idesc, accumulate);
+              mma_f16<CG>(d_corr, bt_lo, a_hi, idesc, 1u);
+              mma_f16<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else if (MODE == TC_6XBF16) {
               const uint32_t p1 = Cfg::kPlaneBytes, p2 = 2 * Cfg::kPlaneBytes;
               const uint64_t bt_mid = smem_desc_sw128(st + p1 + bt_off, T::kBtLBO, 1024);
@@ -362,27 +416,27 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
               const uint64_t a_lo = smem_desc_sw128(st + p2 + a_off, 16, 1024);
               // corrections hi*mid + mid*hi + hi*lo + lo*hi + mid*mid, then hi*hi;
               // mid*lo, lo*mid and lo*lo (<= 2^-23 relative) are dropped
-              mma_f16(d_corr, bt_hi, a_mid, idesc, accumulate);
-              mma_f16(d_corr, bt_mid, a_hi, idesc, 1u);
-              mma_f16(d_corr, bt_hi, a_lo, idesc, 1u);
-              mma_f16(d_corr, bt_lo, a_hi, idesc, 1u);
-              mma_f16(d_corr, bt_mid, a_mid, idesc, 1u);
-              mma_f16(d_tmem, bt_hi, a_hi, idesc, accumulate);
+              mma_f16<CG>(d_corr, bt_hi, a_mid, idesc, accumulate);
+              mma_f16<CG>(d_corr, bt_mid, a_hi, idesc, 1u);
+              mma_f16<CG>(d_corr, bt_hi, a_lo, idesc, 1u);
+              mma_f16<CG>(d_corr, bt_lo, a_hi, idesc, 1u);
+              mma_f16<CG>(d_corr, bt_mid, a_mid, idesc, 1u);
+              mma_f16<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else if (MODE == TC_FP8) {
-              mma_f8(d_tmem, bt_hi, a_hi, idesc, accumulate);
+              mma_f8<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else {
-              mma_f16(d_tmem, bt_hi, a_hi, idesc, accumulate);
+              mma_f16<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             }
             accumulate = 1u;
           }
-          mma_commit(&empty[stage]);   // frees the stage when these MMAs finish
+          commit(&empty[stage]);   // frees the stage when these MMAs finish
         }
         if (!ok) break;
-        mma_commit(&tmem_full[acc]);   // accumulator ready for the epilogue
+        commit(&tmem_full[acc]);   // accumulator ready for the epilogue
         }
       }
       // Make sure no MMA is in flight before TMEM is released.
-      mma_commit(drain);
+      mma_commit<CG>(drain);
       uint64_t t0 = globaltimer_ns();
       while (!mbar_try_wait(drain, 0))
         if (globaltimer_ns() - t0 > timeout_ns) { atomicCAS(status, 0, WD_DRAIN); break; }
@@ -399,7 +453,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
     uint32_t lt = 0;   // accumulation chunks consumed, in the MMA issuer's order
     uint32_t schunk = 0;   // 32-row chunks staged for TMA stores (selects the staging buffer)
     bool alive = true;
-    for (int t = blockIdx.x; alive && t < total_tiles; t += gridDim.x) {
+    for (int t = first_tile; alive && t < total_tiles; t += tile_stride) {
       const TileJob j = S.tile(t);
       const EpiJob e = S.epi(j);
       const float alpha = e.alpha * scale;
@@ -412,8 +466,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       const int nkc = (j.kb1 - j.kb0 + span - 1) / span;
       // Outputs that do not read C leave through shared memory and TMA stores
       // (whole 32 x 128 boxes, clipped to C by the tensor map).
-      const bool use_tma = e.cmap != nullptr && beta == 0.0f && (e.out_mode == OUT_F32 || e.out_mode == OUT_I32);
-      const int r0 = 0;   // first tile row of this thread's running sums
+      // (staging assumes the four epilogue warps cover the same rows)
+      const bool use_tma = e.cmap != nullptr && beta == 0.0f && (e.out_mode == OUT_F32 || e.out_mode == OUT_I32) &&
+                           Cfg::kEpiWarps == 4;
+      const int r0 = ((warp - 2) >> 2) * Cfg::kEpiRows;   // first tile row of this thread's rows
       // stage_begin: a free staging buffer (the store issued from it two chunks
       // ago has read it); this thread's column of the 32 rows goes to
       // buf[i * 128 + q * 32 + lane]; stage_end: hand the box to the TMA unit.
@@ -441,7 +497,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       const int nchunks_mine = rows_mine > 0 ? (rows_mine + 31) >> 5 : 0;
       for (int kc = 0; kc < nkc; ++kc, ++lt) {
       const uint32_t acc = lt % Cfg::kNumBufs, aph = (lt / Cfg::kNumBufs) & 1u;
-      bool ok = wait_parity(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
+      bool ok = wait_parity<kPair>(&tmem_full[acc], aph, wd, WD_EPI_TMEM_FULL);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         alive = false;
@@ -453,19 +509,37 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       auto release = [&]() {
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tmem_empty[acc]);
+        if (lane == 0) {
+          if constexpr (kPair) mbar_arrive_cluster(mapa_shared(smem_u32(&tmem_empty[acc]), 0));
+          else mbar_arrive(&tmem_empty[acc]);
+        }
       };
       if constexpr (kIntChunked) {
         // Each chunk holds an integer-valued FP32 sum of at most 1024 products
         // of magnitude <= 2^14, hence exact; convert and add in int32.
+        // 16-row blocks, software-pipelined: block b+1 loads while b is added.
+        constexpr int kBlocks = Cfg::kEpiRows / 16;   // even
+        const int nb = 2 * nchunks_mine;
+        uint32_t ra[16], rb[16];
+        if (nb > 0) {
+          tmem_ld_32x32b_x16(tbase + r0, ra);
+          tmem_ld_wait();
+        }
 #pragma unroll
-        for (int rc = 0; rc < Cfg::kEpiRows / 16; ++rc) {
-          if (rc < 2 * nchunks_mine) {
-            uint32_t r[16];
-            tmem_ld_32x32b_x16(tbase + r0 + rc * 16, r);
-            tmem_ld_wait();
+        for (int rc = 0; rc < kBlocks; rc += 2) {
+          if (rc < nb) {
+            const bool has_b = rc + 1 < nb;
+            if (has_b) tmem_ld_32x32b_x16(tbase + r0 + (rc + 1) * 16, rb);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) isum[rc * 16 + i] += __float2int_rn(__uint_as_float(r[i]));
+            for (int i = 0; i < 16; ++i) isum[rc * 16 + i] += __float2int_rn(__uint_as_float(ra[i]));
+            if (has_b) {
+              tmem_ld_wait();
+              const bool has_a = rc + 2 < nb;
+              if (has_a) tmem_ld_32x32b_x16(tbase + r0 + (rc + 2) * 16, ra);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) isum[(rc + 1) * 16 + i] += __float2int_rn(__uint_as_float(rb[i]));
+              if (has_a) tmem_ld_wait();
+            }
           }
         }
         release();
@@ -480,17 +554,19 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             }
           }
         } else if (kc == nkc - 1 && cok) {
+          // One row after the other through a running pointer (the compiler
+          // would otherwise keep an address per row live across the tile).
           const int i0 = j.m0 + r0;
-          if (e.out_mode == OUT_PARTIAL) {
-            int* pp = reinterpret_cast<int*>(e.partial) + (long long)i0 * e.n + col;
+          const bool partial = e.out_mode == OUT_PARTIAL;
+          const long long ld = partial ? (long long)e.n : e.ldc;
+          int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.n + col
+                            : static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
+          const bool add_c = !partial && beta != 0.0f;
 #pragma unroll
-            for (int i = 0; i < Cfg::kEpiRows; ++i)
-              if (i < rows_mine) pp[(long long)i * e.n] = isum[i];
-          } else {
-            int* cp = static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
-#pragma unroll
-            for (int i = 0; i < Cfg::kEpiRows; ++i)
-              if (i < rows_mine) cp[i * e.ldc] = (beta != 0.0f) ? cp[i * e.ldc] + isum[i] : isum[i];
+          for (int i = 0; i < Cfg::kEpiRows; ++i) {
+            if (i < rows_mine) *cp = add_c ? *cp + isum[i] : isum[i];
+            cp += ld;
+            asm volatile("" ::: "memory");
           }
         }
       } else {
@@ -583,14 +659,17 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   tc_fence_before();
   __syncthreads();
+  // a pair's leader has drained its MMAs (which write both CTAs' TMEM and read
+  // both CTAs' shared memory) and both epilogues are done before either frees
+  if constexpr (kPair) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    tmem_dealloc<CG>(tmem_base, Cfg::kTmemCols);
   }
 }
 
-template <int BM_T, int STAGES, int MODE>
-__global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE>::kThreads, 1)
+template <int BM_T, int STAGES, int MODE, int CG>
+__global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE, CG>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
@@ -608,8 +687,9 @@ __global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE>::kThreads, 1)
     }
     if (p.c_tma) tma_prefetch_desc(&tmC);
   }
-  const SingleSched<BM_T> S{&p, {&tmA, &tmB, &tmA1, &tmB1, &tmA2, &tmB2}, p.c_tma ? &tmC : nullptr};
-  tc_gemm_body<BM_T, STAGES, MODE>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
+  const int n_off = (CG == 2) ? 128 * (int)cluster_ctarank() : 0;
+  const SingleSched<BM_T, CG> S{&p, {&tmA, &tmB, &tmA1, &tmB1, &tmA2, &tmB2}, p.c_tma ? &tmC : nullptr, n_off};
+  tc_gemm_body<BM_T, STAGES, MODE, CG>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
 }
 
 // Many independent problems in one persistent launch: every CTA walks the
@@ -619,7 +699,7 @@ template <int BM_T, int STAGES, int MODE>
 __global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE>::kThreads, 1)
     tc_grouped_kernel(const __grid_constant__ GroupedParams gp) {
   const GroupedSched S{&gp};
-  tc_gemm_body<BM_T, STAGES, MODE>(S, gp.timeout_ns, gp.status, gp.debug_withhold, nullptr, nullptr);
+  tc_gemm_body<BM_T, STAGES, MODE, 1>(S, gp.timeout_ns, gp.status, gp.debug_withhold, nullptr, nullptr);
 }
 
 }  // namespace g3

@@ -7,11 +7,14 @@ script plays the generator's role for the GPU kernels: it enumerates the
 parameter space
 
     mode     bf16 | 3xbf16 | 6xbf16 | fp8 | int8emu   operand format of the MMA
-    bm       64 | 128 | 256           output rows per tile = MMA N (tile is bm x 128)
+    bm       64 | 128 | 256           output rows per tile = MMA N
+    cg       1 | 2                    CTAs per MMA: one SM (tile bm x 128), or a
+                                      CTA pair on two SMs (tile bm x 256, each CTA
+                                      staging half of A's rows: the cluster shape)
     stages   2 .. 8                   depth of the shared-memory k-block ring
 
 filters it with the hardware's analytical limits -- the shared-memory budget
-of one CTA and the 512 TMEM columns of an SM, the GPU counterpart of the cache
+of one CTA and the TMEM columns of an SM, the GPU counterpart of the cache
 model that fixes (mc, nc, kc) in Section 8.2 -- keeps the deepest pipeline that
 fits plus one shallower variant, and writes
 
@@ -46,39 +49,47 @@ SPLIT_MODES = ("3xbf16", "6xbf16")   # two accumulators per tile (main + correct
 BMS = (256, 128, 64)
 # int8emu keeps one int32 running sum per row of its column in registers
 MAX_BM = {"int8emu": 128}
+# CTA-pair members: tile heights worth pairing (a pair of bm = 64 tiles would
+# stage 32-row halves of A, no better than a single bm = 128 CTA)
+PAIR_BMS = (256, 128)
+# TMEM columns one CTA of a pair allocates (the pair allocates collectively:
+# both CTAs receive the same address, which the kernel checks)
+PAIR_TMEM_COLUMNS = 512
 
 
-def stage_bytes(mode: str, bm: int) -> int:
+def stage_bytes(mode: str, bm: int, cg: int = 1) -> int:
     planes, _elem = MODES[mode]
     bt = 128 * 128           # 128 columns of B x 128 bytes of k
-    a = bm * 128             # bm rows of A x 128 bytes of k
+    a = bm * 128 // cg       # this CTA's rows of A x 128 bytes of k
     return planes * (bt + a)
 
 
 C_STAGE_BYTES = 2 * 32 * 128 * 4   # epilogue staging of C for TMA stores (two 32 x 128 fp32 boxes)
 
 
-def smem_bytes(mode: str, bm: int, stages: int) -> int:
-    return ALIGN_SLACK + stages * stage_bytes(mode, bm) + C_STAGE_BYTES + BAR_BYTES
+def smem_bytes(mode: str, bm: int, stages: int, cg: int = 1) -> int:
+    return ALIGN_SLACK + stages * stage_bytes(mode, bm, cg) + C_STAGE_BYTES + BAR_BYTES
 
 
 def enumerate_family():
     members = []
-    for mode in MODES:
-        for bm in BMS:
-            if (2 if mode in SPLIT_MODES else 1) * bm > TMEM_COLUMNS or bm > MAX_BM.get(mode, 256):
-                continue
-            fits = [s for s in range(2, 9) if smem_bytes(mode, bm, s) <= SMEM_LIMIT]
-            if not fits:
-                continue
-            chosen = [max(fits)]
-            if max(fits) - 1 in fits and max(fits) > 3:
-                chosen.append(max(fits) - 1)
-            acc_cols = (2 if mode in SPLIT_MODES else 1) * bm  # main (+ correction) accumulators
-            bufs = min(4, TMEM_COLUMNS // acc_cols)               # accumulator sets across tiles
-            for st in chosen:
-                members.append({"mode": mode, "bm": bm, "stages": st,
-                                "smem": smem_bytes(mode, bm, st), "tmem_bufs": bufs})
+    for cg in (1, 2):
+        tmem = TMEM_COLUMNS if cg == 1 else PAIR_TMEM_COLUMNS
+        for mode in MODES:
+            for bm in (BMS if cg == 1 else PAIR_BMS):
+                acc_cols = (2 if mode in SPLIT_MODES else 1) * bm  # main (+ correction) accumulators
+                if acc_cols > tmem or bm > MAX_BM.get(mode, 256):
+                    continue
+                fits = [s for s in range(2, 9) if smem_bytes(mode, bm, s, cg) <= SMEM_LIMIT]
+                if not fits:
+                    continue
+                chosen = [max(fits)]
+                if max(fits) - 1 in fits and max(fits) > 3:
+                    chosen.append(max(fits) - 1)
+                bufs = min(4, tmem // acc_cols)                     # accumulator sets across tiles
+                for st in chosen:
+                    members.append({"mode": mode, "bm": bm, "stages": st, "cg": cg,
+                                    "smem": smem_bytes(mode, bm, st, cg), "tmem_bufs": bufs})
     for i, m in enumerate(members):
         m["index"] = i
     return members
@@ -105,10 +116,10 @@ def write(out_dir: str) -> list:
     members = enumerate_family()
     grouped = enumerate_grouped()
     lines = ["// Generated by gen_family.py -- do not edit.",
-             "// X(index, mode, bm, stages)",
+             "// X(index, mode, bm, stages, cg)",
              "#define G3_FAMILY_LIST(X) \\"]
     for m in members:
-        lines.append(f"  X({m['index']}, {MODE_ENUM[m['mode']]}, {m['bm']}, {m['stages']}) \\")
+        lines.append(f"  X({m['index']}, {MODE_ENUM[m['mode']]}, {m['bm']}, {m['stages']}, {m['cg']}) \\")
     lines.append("")
     lines.append(f"#define G3_FAMILY_SIZE {len(members)}")
     lines.append("")

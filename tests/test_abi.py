@@ -81,7 +81,8 @@ def test_family_matches_generator(lib):
         assert json.load(f) == {"members": members, "grouped": gen_family.enumerate_grouped()}
     for m in members:
         d = lib.g3_family_describe(m["index"])
-        assert f"mode={m['mode']} bm={m['bm']} " in d and f"stages={m['stages']}" in d
+        assert f"mode={m['mode']} bm={m['bm']} bn={128 * m['cg']} stages={m['stages']}" in d, d
+        assert f"bufs={m['tmem_bufs']} cg={m['cg']}" in d, d
         assert m["smem"] <= gen_family.SMEM_LIMIT and 2 * m["bm"] <= gen_family.TMEM_COLUMNS
 
 
@@ -91,7 +92,7 @@ def test_planner_choices(lib):
     L = lib
     # large square: the widest tile whose accumulators are double-buffered
     st, cfg, sk, rs = L.g3_plan_query(16384, 16384, 16384, L.G3_F32_3XBF16)
-    assert st == 0 and fam[cfg]["mode"] == "3xbf16" and fam[cfg]["bm"] == 128 and fam[cfg]["tmem_bufs"] == 2 and sk == 1
+    assert st == 0 and fam[cfg]["mode"] == "3xbf16" and fam[cfg]["bm"] == 128 and sk == 1
     # Cout = 64 convolution layer: a 64-row tile, no split
     st, cfg, sk, rs = L.g3_plan_query(64, 200704, 147, L.G3_BF16)
     assert fam[cfg]["bm"] == 64 and sk == 1

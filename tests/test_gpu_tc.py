@@ -27,8 +27,12 @@ SHAPES = [(300, 520, 700), (129, 257, 65), (1, 1, 1), (17, 33, 5), (64, 1000, 14
           (256, 128, 64), (513, 300, 129)]
 
 
-def members(mode):
-    return [f["index"] for f in FAMILY if f["mode"] == mode]
+def members(mode, cg=None):
+    return [f["index"] for f in FAMILY if f["mode"] == mode and (cg is None or f["cg"] == cg)]
+
+
+def first_member(mode, bm, cg):
+    return next(f["index"] for f in FAMILY if f["mode"] == mode and f["bm"] == bm and f["cg"] == cg)
 
 
 # ---------------------------------------------------------------- BF16
@@ -69,6 +73,29 @@ def test_bf16_shapes(shape):
 @pytest.mark.parametrize("config", members("bf16"))
 def test_bf16_every_member(config):
     bf16_check(synth.uniform_problem(300, 520, 700, seed=2, alpha=1.25, beta=-0.5), config=config)
+
+
+# CTA pairs: 256-column tiles, each CTA staging half of A's rows.  Shapes put
+# the second CTA's columns or rows partly or wholly outside C, and cover C
+# written through TMA stores (beta = 0) and read-modify-write (beta != 0).
+PAIR_SHAPES = [(300, 520, 700), (129, 257, 65), (40, 300, 200), (600, 129, 1000), (1, 1, 1), (256, 256, 64)]
+
+
+@pytest.mark.parametrize("shape", PAIR_SHAPES)
+@pytest.mark.parametrize("config", members("bf16", cg=2))
+def test_bf16_pair_ragged(config, shape):
+    m, n, k = shape
+    for beta in (0.0, 0.5):
+        bf16_check(synth.uniform_problem(m, n, k, seed=30, alpha=1.5, beta=beta), config=config)
+
+
+@pytest.mark.parametrize("config", members("bf16", cg=2)[:1] + members("3xbf16", cg=2)[:1])
+def test_pair_split_k(config):
+    p = synth.uniform_problem(200, 300, 3000, seed=31, alpha=0.5, beta=1.0)
+    if FAMILY[config]["mode"] == "bf16":
+        bf16_check(p, config=config, split_k=3)
+    else:
+        x3_check(p, config=config, split_k=3)
 
 
 @pytest.mark.parametrize("split", [2, 3, 7])
@@ -309,7 +336,7 @@ def test_watchdog_reports_timeout_without_hanging():
     Ab, Bb = torch_api.convert_bf16(dev(p.A)), torch_api.convert_bf16(dev(p.B))
     C = torch.zeros(p.m, p.n, device="cuda")
     assert _lib.g3_debug_withhold_next(200) == 0
-    torch_api.gemm(Ab, Bb, C, 1.0, 0.0, dtype=G3_BF16)
+    torch_api.gemm(Ab, Bb, C, 1.0, 0.0, dtype=G3_BF16, config=first_member("bf16", 128, 1))
     st, code = torch_api.device_status()
     assert st == _lib.G3_ERR_TIMEOUT and code != 0
     # the context is still usable and the next call is correct
