@@ -177,6 +177,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Sources that decide the headline kernel's DRAM traffic (its code, launch and
+# tensor maps).  A DRAM-traffic record taken with ncu is reported as the
+# roofline's "traffic" only while these files hash to the recorded value.
+TRAFFIC_SOURCES = ("csrc/tc_gemm.cuh", "csrc/ptx.cuh", "csrc/tc_family_tu.cuh", "csrc/tc_family_3xbf16.cu",
+                   "csrc/api.cu")
+TRAFFIC_RECORD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                              "tc_gemm_3xbf16_16384_dram.md")
+
+
+def kernel_sources_hash():
+    import hashlib
+    pkg = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2310_20347_gb300")
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(pkg, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(member, n):
+    """DRAM bytes per launch from the ncu record, or (None, why)."""
+    try:
+        text = open(TRAFFIC_RECORD).read()
+    except OSError:
+        return None, "no ncu record"
+    rec = {}
+    for line in text.splitlines():
+        if ":" in line and line.split(":", 1)[0].strip() in ("member", "size", "sources_sha256",
+                                                             "dram_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("member") != member or rec.get("size") != str(n):
+        return None, "ncu record is for another member or size"
+    if rec.get("sources_sha256") != kernel_sources_hash():
+        return None, "kernel sources changed since the ncu record"
+    return float(rec["dram_bytes_per_launch"]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+
+
 def _events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -558,11 +596,16 @@ def main():
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--dsize", type=int, default=8192, help="int8 / fp8 / bf16 workloads: m = n = k")
+    ap.add_argument("--print-kernel-hash", action="store_true",
+                    help="print the hash of the headline kernel's sources (for the DRAM-traffic record) and exit")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--only", default="", help="im2col workloads: comma-separated layer names (e.g. L1,L12)")
     ap.add_argument("--tune", action="store_true", help="im2col workloads: autotune every shape first")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.print_kernel_hash:
+        print(kernel_sources_hash())
+        return
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "square":
@@ -686,6 +729,7 @@ def main():
     st = _lib.g3_plan_query(n, n, n, G3_F32_3XBF16)
     cfg_used = args.config if args.config >= 0 else st[1]
     member = _lib.g3_family_describe(cfg_used) if st[0] == 0 and cfg_used >= 0 else "?"
+    traffic, traffic_src = recorded_traffic(member, n)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     simt_tflops = flops / (simt_ms * 1e-3) / 1e12
     sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
@@ -704,7 +748,7 @@ def main():
                  "frac": simt_tflops / simt_peak},
         "speedup_vs_simt": simt_ms / (ms_max / args.steps),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "kernel": f"tc_gemm_kernel ({member})",
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
                      "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", peak)),
