@@ -90,6 +90,20 @@ typedef enum {
 G3_API int g3_gemm(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B,
             int64_t ldb, double beta, void* C, int64_t ldc, int dtype);
 
+/* g3_gemm with A, B and C in HOST memory (row-major, leading dimensions in
+ * elements; C is read when beta != 0 and overwritten with the result).  The
+ * call copies B to the device, then streams row blocks of A (and C) up while
+ * earlier blocks compute and finished blocks of C come back, on two
+ * library-owned copy streams ordered against `cuda_stream` (NULL = the
+ * current stream).  It returns before the work is done: the host buffers must
+ * stay valid and untouched until `cuda_stream` has completed.  Page-locked
+ * host memory is needed for the copies to overlap.  The device copies live in
+ * one library buffer per device, grown on first use of a size: calls on
+ * different streams must not overlap.  FP8 runs with unit scales.  Errors as
+ * g3_gemm; G3_ERR_NOMEM when the device copies do not fit.                   */
+G3_API int g3_gemm_host(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B,
+                        int64_t ldb, double beta, void* C, int64_t ldc, int dtype, void* cuda_stream);
+
 /* Set the stream later calls without an explicit stream use (a cudaStream_t;
  * NULL = legacy default stream).  The setting is per process.             */
 G3_API int g3_set_stream(void* cuda_stream);

@@ -24,12 +24,19 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
+constexpr int kHostMaxBlocks = 8;   // row blocks of a g3_gemm_host pipeline
+
 struct DevState {
   bool init = false;
   int sms = 0;
   int* status = nullptr;   // device address of g_device_status
   void* ws = nullptr;      // library-owned workspace
   size_t ws_bytes = 0;
+  // g3_gemm_host: device copies of A, B, C and the copy streams / events
+  void* hbuf = nullptr;
+  size_t hbuf_bytes = 0;
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t ev[2 * kHostMaxBlocks + 3] = {};
 };
 
 std::mutex g_mu;
@@ -643,6 +650,100 @@ bool take_withhold(unsigned long long* timeout_ns) {
 
 using namespace g3;
 
+// C := beta*C + alpha*A*B with A, B, C in host memory, as a pipeline on three
+// streams: B goes up first (every row block of C needs all of it); then each
+// row block of A (and of C when beta != 0) goes up on `up` while the previous
+// block is computed on the caller's stream, and each finished block of C
+// comes back on `down` while later blocks compute.  Device copies live in a
+// library buffer; the caller's stream waits for the last download.
+static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
+  int st = validate(a);
+  if (st != G3_OK) return st;
+  if (a.m == 0 || a.n == 0) return G3_OK;
+  const int64_t m = a.m, n = a.n, k = a.k;
+  const int es = (a.dtype == G3_F32 || a.dtype == G3_F32_3XBF16) ? 4 : (a.dtype == G3_BF16 ? 2 : 1);
+  const int64_t lda_d = round_up(std::max<int64_t>(k, 1), 16), ldb_d = round_up(n, 16), ldc_d = round_up(n, 16);
+  const size_t a_bytes = align256((size_t)m * lda_d * es), b_bytes = align256((size_t)std::max<int64_t>(k, 1) * ldb_d * es);
+  const size_t c_bytes = align256((size_t)m * ldc_d * 4);
+  const bool products = k > 0 && a.alpha != 0.0;
+  const bool read_c = a.beta != 0.0;
+  const int nb = (m >= 2048 && products) ? 4 : 1;
+  const int64_t rb = round_up((m + nb - 1) / nb, 256);
+  uint8_t* base = nullptr;
+  cudaEvent_t* ev = nullptr;
+  cudaStream_t up = nullptr, down = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    DevState* d = nullptr;
+    if ((st = ensure_device(&d)) != G3_OK) return st;
+    if (!d->up) {
+      if (cudaStreamCreateWithFlags(&d->up, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&d->down, cudaStreamNonBlocking) != cudaSuccess)
+        return G3_ERR_CUDA;
+      for (auto& e : d->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return G3_ERR_CUDA;
+    }
+    const size_t need = a_bytes + b_bytes + c_bytes;
+    if (d->hbuf_bytes < need) {
+      if (d->hbuf) {
+        cudaDeviceSynchronize();
+        cudaFree(d->hbuf);
+        d->hbuf = nullptr;
+        d->hbuf_bytes = 0;
+      }
+      if (cudaMalloc(&d->hbuf, need) != cudaSuccess) {
+        cudaGetLastError();
+        return G3_ERR_NOMEM;
+      }
+      d->hbuf_bytes = need;
+    }
+    base = static_cast<uint8_t*>(d->hbuf);
+    ev = d->ev;
+    up = d->up;
+    down = d->down;
+  }
+  uint8_t* dA = base;
+  uint8_t* dB = base + a_bytes;
+  uint8_t* dC = base + a_bytes + b_bytes;
+  // the device copies may still be in use by an earlier call on this stream
+  G3_CHECK_CUDA(cudaEventRecord(ev[0], s));
+  G3_CHECK_CUDA(cudaStreamWaitEvent(up, ev[0], 0));
+  if (products)
+    G3_CHECK_CUDA(cudaMemcpy2DAsync(dB, ldb_d * es, a.B, a.ldb * es, n * es, k, cudaMemcpyHostToDevice, up));
+  for (int b = 0; b < nb; ++b) {
+    const int64_t r0 = b * rb, r1 = std::min(m, r0 + rb);
+    if (r0 >= r1) break;
+    const int64_t rows = r1 - r0;
+    if (products)
+      G3_CHECK_CUDA(cudaMemcpy2DAsync(dA + (size_t)r0 * lda_d * es, lda_d * es,
+                                      static_cast<const uint8_t*>(a.A) + (size_t)r0 * a.lda * es, a.lda * es, k * es,
+                                      rows, cudaMemcpyHostToDevice, up));
+    if (read_c)
+      G3_CHECK_CUDA(cudaMemcpy2DAsync(dC + (size_t)r0 * ldc_d * 4, ldc_d * 4,
+                                      static_cast<const uint8_t*>(a.C) + (size_t)r0 * a.ldc * 4, a.ldc * 4, n * 4,
+                                      rows, cudaMemcpyHostToDevice, up));
+    G3_CHECK_CUDA(cudaEventRecord(ev[1 + b], up));
+    G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev[1 + b], 0));
+    g3_gemm_args blk = a;
+    blk.m = rows;
+    blk.A = dA + (size_t)r0 * lda_d * es;
+    blk.lda = lda_d;
+    blk.B = dB;
+    blk.ldb = ldb_d;
+    blk.C = dC + (size_t)r0 * ldc_d * 4;
+    blk.ldc = ldc_d;
+    if ((st = gemm_impl(blk, s)) != G3_OK) return st;
+    G3_CHECK_CUDA(cudaEventRecord(ev[1 + kHostMaxBlocks + b], s));
+    G3_CHECK_CUDA(cudaStreamWaitEvent(down, ev[1 + kHostMaxBlocks + b], 0));
+    G3_CHECK_CUDA(cudaMemcpy2DAsync(static_cast<uint8_t*>(a.C) + (size_t)r0 * a.ldc * 4, a.ldc * 4,
+                                    dC + (size_t)r0 * ldc_d * 4, ldc_d * 4, n * 4, rows, cudaMemcpyDeviceToHost,
+                                    down));
+  }
+  G3_CHECK_CUDA(cudaEventRecord(ev[2 * kHostMaxBlocks + 1], down));
+  G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev[2 * kHostMaxBlocks + 1], 0));
+  return G3_OK;
+}
+
 extern "C" {
 
 void g3_gemm_args_init(g3_gemm_args* a) {
@@ -665,6 +766,17 @@ int g3_gemm(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_
 int g3_set_stream(void* stream) {
   g_stream = static_cast<cudaStream_t>(stream);
   return G3_OK;
+}
+
+int g3_gemm_host(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B,
+                 int64_t ldb, double beta, void* C, int64_t ldc, int dtype, void* stream) {
+  g3_gemm_args a;
+  g3_gemm_args_init(&a);
+  a.m = m; a.n = n; a.k = k;
+  a.alpha = alpha; a.beta = beta;
+  a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = ldc;
+  a.dtype = dtype;
+  return gemm_host_impl(a, stream ? static_cast<cudaStream_t>(stream) : g_stream);
 }
 
 int g3_gemm_ex(const g3_gemm_args* args, void* stream) {

@@ -65,6 +65,24 @@ def gemm(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, stream=None, **kw):
     return C
 
 
+def gemm_host(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, stream=None):
+    """C := beta*C + alpha*A@B with CPU tensors (pin them for overlap) through
+    g3_gemm_host; asynchronous on `stream` -- synchronise it before reading C."""
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or tuple(C.shape) != (m, n):
+        raise ValueError(f"shape mismatch: A {tuple(A.shape)} B {tuple(B.shape)} C {tuple(C.shape)}")
+    in_t, out_t = _ELEM[dtype]
+    for t, want, name in ((A, in_t, "A"), (B, in_t, "B"), (C, out_t, "C")):
+        if t.dtype != want:
+            raise TypeError(f"{name} must be {want} for dtype {dtype}, got {t.dtype}")
+        if t.is_cuda:
+            raise ValueError(f"{name} must be a CPU tensor")
+    check(_lib.g3_gemm_host(m, n, k, float(alpha), A.data_ptr(), _ld(A, "A"), B.data_ptr(), _ld(B, "B"),
+                            float(beta), C.data_ptr(), _ld(C, "C"), dtype, _stream(stream)), "g3_gemm_host")
+    return C
+
+
 def convert_bf16(x: torch.Tensor, stream=None) -> torch.Tensor:
     y = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
     check(_lib.g3_convert_bf16(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), y.data_ptr(),

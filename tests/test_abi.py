@@ -52,6 +52,11 @@ def test_argument_errors(lib):
     assert L.g3_gemm(4, 4, 8, 1.0, None, 8, p, 4, 0.0, p, 4, 0) == -105
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, None, 4, 0.0, p, 4, 0) == -107
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, None, 4, 0) == -110
+    # host-buffer entry point: the same validation, nothing touches a device
+    assert L.g3_gemm_host(-1, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, 0, None) == -101
+    assert L.g3_gemm_host(4, 4, 8, 1.0, p, 7, p, 4, 0.0, p, 4, 0, None) == -106
+    assert L.g3_gemm_host(4, 4, 8, 1.0, p, 8, p, 4, 0.0, None, 4, 0, None) == -110
+    assert L.g3_gemm_host(0, 4, 8, 1.0, None, 8, None, 4, 0.0, None, 4, 0, None) == 0
     # operand preparation: the same positional codes
     assert L.g3_convert_bf16(p, 4, 8, 8, p, 7) == -106
     assert L.g3_split_bf16(p, 4, 8, 8, p, p, 7) == -107

@@ -1,0 +1,69 @@
+"""g3_gemm_host: A, B, C in page-locked host memory, copies pipelined with the
+row blocks of the computation.  Checked against the oracle with each dtype's
+tolerance (bit-exact for INT8), single- and multi-block, strided host rows."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import rel_err
+from paper_2310_20347_gb300 import G3_BF16, G3_F32, G3_F32_3XBF16, G3_INT8, synth, torch_api
+
+pytestmark = pytest.mark.gpu
+
+
+def pinned(x, pad=0):
+    """A page-locked host tensor holding x, optionally with `pad` extra columns per row."""
+    full = torch.zeros(x.shape[0], x.shape[1] + pad, dtype=x.dtype).pin_memory()
+    full[:, : x.shape[1]] = x
+    return full[:, : x.shape[1]]
+
+
+@pytest.mark.parametrize("m,n,k,dtype,pad", [(300, 200, 150, G3_F32, 0), (2500, 300, 700, G3_F32_3XBF16, 3),
+                                             (2049, 130, 64, G3_F32_3XBF16, 0), (700, 520, 300, G3_F32, 5)])
+def test_host_fp32(m, n, k, dtype, pad):
+    p = synth.uniform_problem(m, n, k, seed=40, alpha=1.25, beta=0.5)
+    hA, hB, hC = pinned(torch.from_numpy(p.A), pad), pinned(torch.from_numpy(p.B), pad), pinned(torch.from_numpy(p.C), pad)
+    s = torch.cuda.current_stream()
+    torch_api.gemm_host(hA, hB, hC, p.alpha, p.beta, dtype=dtype, stream=s)
+    s.synchronize()
+    D = oracle.absprod(p.A, p.B, p.alpha)
+    e = rel_err(hC.numpy(), oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), D, p.beta * p.C.astype(np.float64))
+    assert e <= 2e-6, e
+
+
+def test_host_bf16_beta_zero_multiblock():
+    p = synth.normal_problem(3000, 260, 520, seed=41)
+    Ab = torch.from_numpy(oracle.round_bf16(p.A)).to(torch.bfloat16)
+    Bb = torch.from_numpy(oracle.round_bf16(p.B)).to(torch.bfloat16)
+    hA, hB = pinned(Ab), pinned(Bb)
+    hC = pinned(torch.full((p.m, p.n), float("nan")))
+    torch_api.gemm_host(hA, hB, hC, 1.0, 0.0, dtype=G3_BF16)
+    torch.cuda.current_stream().synchronize()
+    Aq, Bq = oracle.round_bf16(p.A), oracle.round_bf16(p.B)
+    e = rel_err(hC.numpy(), oracle.gemm(Aq, Bq, None, 1.0, 0.0), oracle.absprod(Aq, Bq, 1.0))
+    assert e <= 1e-5, e
+
+
+@pytest.mark.parametrize("m,beta", [(600, 1), (2600, 0)])
+def test_host_int8_bit_exact(m, beta):
+    p = synth.int8_problem(m, 300, 1100, seed=42, beta=beta)
+    hA, hB = pinned(torch.from_numpy(p.A)), pinned(torch.from_numpy(p.B))
+    hC = pinned(torch.from_numpy(p.C) if p.C is not None else torch.zeros(m, 300, dtype=torch.int32))
+    torch_api.gemm_host(hA, hB, hC, 1, beta, dtype=G3_INT8)
+    torch.cuda.current_stream().synchronize()
+    assert np.array_equal(hC.numpy().astype(np.int64), oracle.gemm_i8(p.A, p.B, p.C, 1, beta))
+
+
+def test_host_back_to_back_calls_reuse_the_device_copies():
+    # two calls queued without a host synchronisation in between
+    p = synth.uniform_problem(2100, 140, 260, seed=43, beta=0.0)
+    q = synth.uniform_problem(1800, 140, 260, seed=44, beta=0.0)
+    hA, hB, hC = pinned(torch.from_numpy(p.A)), pinned(torch.from_numpy(p.B)), pinned(torch.zeros(p.m, p.n))
+    gA, gB, gC = pinned(torch.from_numpy(q.A)), pinned(torch.from_numpy(q.B)), pinned(torch.zeros(q.m, q.n))
+    torch_api.gemm_host(hA, hB, hC, 1.0, 0.0, dtype=G3_F32_3XBF16)
+    torch_api.gemm_host(gA, gB, gC, 1.0, 0.0, dtype=G3_F32_3XBF16)
+    torch.cuda.current_stream().synchronize()
+    for prob, out in ((p, hC), (q, gC)):
+        e = rel_err(out.numpy(), oracle.gemm(prob.A, prob.B, None, 1.0, 0.0), oracle.absprod(prob.A, prob.B, 1.0))
+        assert e <= 2e-6, e
