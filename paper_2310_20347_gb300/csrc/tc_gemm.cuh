@@ -148,14 +148,21 @@ struct TcConfig {
   static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16 || MODE == TC_6XBF16) ? 2 : 1;
   static constexpr uint32_t kSetCols = kAccPerTile * BM_T;
   static constexpr uint32_t kMaxBufs = 4;
-  static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
-  static constexpr uint32_t kTmemCols = kNumBufs * kSetCols;
+  // The exact-integer mode with bm = 256 keeps its int32 running sums in TMEM
+  // (columns 256-511, beside one chunk accumulator) instead of registers.
+  static constexpr bool kTmemSums = (MODE == TC_I8EMU && BM_T == 256);
+  static constexpr uint32_t kSumCol = 256;
+  static constexpr uint32_t kNumBufs =
+      kTmemSums ? 1 : ((512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs);
+  static constexpr uint32_t kTmemCols = kTmemSums ? 512 : kNumBufs * kSetCols;
   // Epilogue warps: one per TMEM lane quarter, each thread owning all bm rows
   // of its column.  (Exact-integer variants with eight epilogue warps measured
   // slower: with bm = 256 its large unrolled epilogue starved the MMA-issuing
   // thread of instruction fetch; with bm = 128, 64 rows each, the 168-register
   // cap of ten warps made it spill.)
-  static constexpr int kEpiWarps = 4;
+  // The TMEM-sum member drains its accumulator every 1024 products while the
+  // MMA waits; eight warps (two per lane quarter, 128 rows each) halve that.
+  static constexpr int kEpiWarps = kTmemSums ? 8 : 4;
   static constexpr int kEpiRows = BM_T / (kEpiWarps / 4);   // rows of the tile per epilogue thread
   // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128 columns x 4 bytes.
   static constexpr uint32_t kCStageBytes = 2 * 32 * 128 * 4;
@@ -256,7 +263,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   using Cfg = TcConfig<BM_T, STAGES, MODE, CG>;
   constexpr bool kPair = (CG == 2);
   constexpr bool kIntChunked = (MODE == TC_I8EMU);
-  static_assert(!kIntChunked || Cfg::kEpiRows <= 128, "int32 running sums live in registers: <= 128 rows");
+  static_assert(!kIntChunked || Cfg::kTmemSums || Cfg::kEpiRows <= 128,
+                "int32 running sums in registers: <= 128 rows");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -489,7 +497,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       };
       // exact-integer mode: int32 running sums of this thread's column, one per
       // row r0 .. r0 + kEpiRows - 1 of the tile
-      constexpr int kSums = kIntChunked ? Cfg::kEpiRows : 1;
+      constexpr int kSums = (kIntChunked && !Cfg::kTmemSums) ? Cfg::kEpiRows : 1;
       int isum[kSums];
 #pragma unroll
       for (int i = 0; i < kSums; ++i) isum[i] = 0;
@@ -514,7 +522,48 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           else mbar_arrive(&tmem_empty[acc]);
         }
       };
-      if constexpr (kIntChunked) {
+      if constexpr (Cfg::kTmemSums) {
+        // Exact integers, running sums in TMEM: per 32-row block, load the
+        // chunk's FP32 sums (exact integers, <= 1024 products of |x| <= 2^14)
+        // and the int32 running sums, add in int32, and either put the sums
+        // back (tcgen05.st) or, after the last chunk, write them to C.
+        // This warp's rows are r0 .. r0 + kEpiRows - 1 of the tile.
+        const uint32_t tsum = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + Cfg::kSumCol + r0;
+        const uint32_t tacc = tbase + r0;
+        const bool first = kc == 0, last = kc == nkc - 1;
+        if (nchunks_mine == 0) release();   // no rows here (short tile): hand back at once
+        for (int rc = 0; rc < nchunks_mine; ++rc) {
+          uint32_t ra[32], rs[32];
+          tmem_ld_32x32b_x32(tacc + rc * 32, ra);
+          if (!first) tmem_ld_32x32b_x32(tsum + rc * 32, rs);
+          tmem_ld_wait();
+          if (rc == nchunks_mine - 1) release();
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            rs[i] = static_cast<uint32_t>((first ? 0 : static_cast<int>(rs[i])) +
+                                          __float2int_rn(__uint_as_float(ra[i])));
+          if (!last) {
+            tmem_st_32x32b_x32(tsum + rc * 32, rs);
+          } else if (use_tma) {
+            float* buf = stage_begin();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) buf[i * 128] = __uint_as_float(rs[i]);
+            stage_end(rc);
+          } else if (cok) {
+            const int i0 = j.m0 + r0 + rc * 32;
+            const int iend = min(32, e.m - i0);
+            const bool partial = e.out_mode == OUT_PARTIAL;
+            const long long ld = partial ? (long long)e.n : e.ldc;
+            int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.n + col
+                              : static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
+            const bool add_c = !partial && beta != 0.0f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < iend) cp[i * ld] = add_c ? cp[i * ld] + static_cast<int>(rs[i]) : static_cast<int>(rs[i]);
+          }
+        }
+        if (!last) tmem_st_wait();
+      } else if constexpr (kIntChunked) {
         // Each chunk holds an integer-valued FP32 sum of at most 1024 products
         // of magnitude <= 2^14, hence exact; convert and add in int32.
         // 16-row blocks, software-pipelined: block b+1 loads while b is added.

@@ -104,9 +104,10 @@ def test_planner_choices(lib):
     # few output tiles, deep k: split-K
     st, cfg, sk, rs = L.g3_plan_query(512, 49, 4608, L.G3_BF16)
     assert sk > 1
-    # INT8 runs on the exact-integer members (k chunked inside the kernel): no split needed
+    # INT8 runs on the exact-integer members (k chunked inside the kernel): the
+    # bm = 256 CTA pair with its int32 running sums in TMEM, no split needed
     st, cfg, sk, rs = L.g3_plan_query(8192, 8192, 8192, L.G3_INT8)
-    assert fam[cfg]["mode"] == "int8emu" and fam[cfg]["bm"] == 128 and sk == 1
+    assert fam[cfg]["mode"] == "int8emu" and fam[cfg]["bm"] == 256 and fam[cfg]["cg"] == 2 and sk == 1
     # FP32-accurate at k <= 512: the three-part split (6 products); above: two-part
     for k, mode in ((16, "6xbf16"), (512, "6xbf16"), (513, "3xbf16"), (4096, "3xbf16")):
         st, cfg, sk, rs = L.g3_plan_query(2048, 2048, k, L.G3_F32_3XBF16)

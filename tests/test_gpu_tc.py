@@ -316,6 +316,23 @@ def test_int8_every_member(config):
     assert np.array_equal(C.cpu().numpy().astype(np.int64), oracle.gemm_i8(p.A, p.B, p.C, 1, 1))
 
 
+@pytest.mark.parametrize("shape,beta,split", [((600, 300, 2200), 0, 0), ((257, 520, 3000), 1, 0),
+                                              ((300, 129, 4100), 0, 3), ((1, 1, 1), 0, 0), ((513, 260, 1024), 1, 2)])
+@pytest.mark.parametrize("config", [f["index"] for f in FAMILY if f["mode"] == "int8emu" and f["bm"] == 256])
+def test_int8_tmem_sums(config, shape, beta, split):
+    # bm = 256 members keep the int32 running sums in TMEM: chunks of 1024
+    # products, ragged rows and columns, C by TMA stores (beta = 0) or added in
+    # place (beta = 1), and int32 split-K partials
+    m, n, k = shape
+    p = synth.int8_problem(m, n, k, seed=25, beta=beta)
+    A, B = dev(p.A), dev(p.B)
+    full, C = guarded(m, n, p.C, dtype=torch.int32)
+    torch_api.gemm(A, B, C, 1, beta, dtype=G3_INT8, config=config, split_k=split)
+    torch.cuda.synchronize()
+    check_guard(full, m, n)
+    assert np.array_equal(C.cpu().numpy().astype(np.int64), oracle.gemm_i8(p.A, p.B, p.C, 1, beta))
+
+
 def test_int8_worst_case_magnitude():
     # all -128 at k = 8192: every entry is 8192 * 2^14 = 2^27 exactly
     A = np.full((40, 8192), -128, np.int8)
@@ -329,6 +346,22 @@ def test_int8_worst_case_magnitude():
 
 
 # ---------------------------------------------------------------- failure detection
+def test_watchdog_pair_member_reports_timeout_without_hanging():
+    # a CTA pair: the leader's MMA wait runs out first; the other CTA's waits
+    # run out on their own bounded timers and both meet at the closing barrier
+    assert torch_api.device_status()[0] == 0
+    p = synth.uniform_problem(512, 512, 1024, seed=24)
+    Ab, Bb = torch_api.convert_bf16(dev(p.A)), torch_api.convert_bf16(dev(p.B))
+    C = torch.zeros(p.m, p.n, device="cuda")
+    cfg = first_member("bf16", 256, 2)
+    assert _lib.g3_debug_withhold_next(200) == 0
+    torch_api.gemm(Ab, Bb, C, 1.0, 0.0, dtype=G3_BF16, config=cfg)
+    st, code = torch_api.device_status()
+    assert st == _lib.G3_ERR_TIMEOUT and code != 0
+    bf16_check(p, config=cfg)
+    assert torch_api.device_status()[0] == 0
+
+
 def test_watchdog_reports_timeout_without_hanging():
     st, code = torch_api.device_status()
     assert st == 0
