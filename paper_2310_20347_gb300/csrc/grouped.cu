@@ -35,40 +35,84 @@ struct PrepJob {
   void* hi;           // PREP_SPLIT(3): hi plane; PREP_COPY16: destination
   void* lo;           // PREP_SPLIT(3): lo plane
   void* mid;          // PREP_SPLIT3: mid plane
-  long long ld_dst;   // elements
+  long long ld_dst;   // elements; destination rows start on 16-byte boundaries
   int rows, cols;
   int kind;
   float beta;         // PREP_SCALE_C
+  int vec;            // float source rows 16-byte aligned: 16-byte loads
 };
 
-// blockIdx.y strides over jobs, the x-dimension over each job's elements
-// (a grouped problem is at most 2^31 elements, so 32-bit index arithmetic).
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) {
+  return static_cast<uint32_t>(a) | (static_cast<uint32_t>(b) << 16);
+}
+__device__ __forceinline__ void store8(uint16_t* dst, const uint16_t (&v)[8], int cnt) {
+  if (cnt == 8) {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+  } else {
+    for (int i = 0; i < cnt; ++i) dst[i] = v[i];
+  }
+}
+
+// blockIdx.y strides over jobs, the x-dimension over each job's units of 8
+// consecutive elements of a row (a grouped problem is at most 2^31 elements,
+// so 32-bit index arithmetic); planes are written with 16-byte stores.
 __global__ void grouped_prep_kernel(const PrepJob* __restrict__ jobs, int njobs) {
   for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
     const PrepJob J = jobs[jb];
-    const unsigned total = (unsigned)J.rows * (unsigned)J.cols;
-    const unsigned cols = (unsigned)J.cols;
-    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-      const unsigned r = e / cols, c = e - r * cols;
-      if (J.kind == PREP_SPLIT) {
-        const float v = static_cast<const float*>(J.src)[r * J.ld_src + c];
-        const uint16_t h = bf16_bits(v);
-        static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = h;
-        static_cast<uint16_t*>(J.lo)[r * J.ld_dst + c] = bf16_bits(v - bf16_value(h));
-      } else if (J.kind == PREP_SPLIT3) {
-        const float v = static_cast<const float*>(J.src)[r * J.ld_src + c];
-        const uint16_t h = bf16_bits(v);
-        const float dv = v - bf16_value(h);
-        const uint16_t md = bf16_bits(dv);
-        static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = h;
-        static_cast<uint16_t*>(J.mid)[r * J.ld_dst + c] = md;
-        static_cast<uint16_t*>(J.lo)[r * J.ld_dst + c] = bf16_bits(dv - bf16_value(md));
-      } else if (J.kind == PREP_COPY16) {
-        static_cast<uint16_t*>(J.hi)[r * J.ld_dst + c] = static_cast<const uint16_t*>(J.src)[r * J.ld_src + c];
-      } else {
+    if (J.kind == PREP_SCALE_C) {
+      const unsigned total = (unsigned)J.rows * (unsigned)J.cols;
+      const unsigned cols = (unsigned)J.cols;
+      for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const unsigned r = e / cols, c = e - r * cols;
         float* p = static_cast<float*>(const_cast<void*>(J.src)) + r * J.ld_src + c;
         *p = (J.beta == 0.f) ? 0.f : J.beta * *p;
       }
+      continue;
+    }
+    const unsigned upr = ((unsigned)J.cols + 7u) >> 3;   // units per row
+    const unsigned total = (unsigned)J.rows * upr;
+    for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+      const unsigned r = u / upr, c0 = (u - r * upr) << 3;
+      const int cnt = min(8, J.cols - (int)c0);
+      const long long dofs = (long long)r * J.ld_dst + c0;
+      if (J.kind == PREP_COPY16) {
+        const uint16_t* xr = static_cast<const uint16_t*>(J.src) + (long long)r * J.ld_src + c0;
+        uint16_t v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = i < cnt ? xr[i] : 0;
+        store8(static_cast<uint16_t*>(J.hi) + dofs, v, cnt);
+        continue;
+      }
+      const float* xr = static_cast<const float*>(J.src) + (long long)r * J.ld_src + c0;
+      float x[8];
+      if (J.vec && cnt == 8) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(xr));
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(xr) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = i < cnt ? xr[i] : 0.f;
+      }
+      uint16_t h[8], l[8];
+      if (J.kind == PREP_SPLIT3) {
+        uint16_t md[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          h[i] = bf16_bits(x[i]);
+          const float d = x[i] - bf16_value(h[i]);
+          md[i] = bf16_bits(d);
+          l[i] = bf16_bits(d - bf16_value(md[i]));
+        }
+        store8(static_cast<uint16_t*>(J.mid) + dofs, md, cnt);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          h[i] = bf16_bits(x[i]);
+          l[i] = bf16_bits(x[i] - bf16_value(h[i]));
+        }
+      }
+      store8(static_cast<uint16_t*>(J.hi) + dofs, h, cnt);
+      store8(static_cast<uint16_t*>(J.lo) + dofs, l, cnt);
     }
   }
 }
@@ -244,16 +288,17 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
         a_mid = d_planes + o.a_mid_off;
         b_mid = d_planes + o.b_mid_off;
       }
-      jobs.push_back(PrepJob{d.A, d.lda, (void*)a, (void*)a_lo, (void*)a_mid, o.lda, g.m, g.k, kind, 0.f});
-      jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, (void*)b_lo, (void*)b_mid, o.ldb, g.k, g.n, kind, 0.f});
+      const int va = aligned16(d.A, d.lda, 4) ? 1 : 0, vb = aligned16(d.B, d.ldb, 4) ? 1 : 0;
+      jobs.push_back(PrepJob{d.A, d.lda, (void*)a, (void*)a_lo, (void*)a_mid, o.lda, g.m, g.k, kind, 0.f, va});
+      jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, (void*)b_lo, (void*)b_mid, o.ldb, g.k, g.n, kind, 0.f, vb});
     } else {
       if (o.pack_a) {
         a = d_planes + o.a_off;
-        jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, nullptr, o.lda, g.m, g.k, PREP_COPY16, 0.f});
+        jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, nullptr, o.lda, g.m, g.k, PREP_COPY16, 0.f, 0});
       }
       if (o.pack_b) {
         b = d_planes + o.b_off;
-        jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, nullptr, o.ldb, g.k, g.n, PREP_COPY16, 0.f});
+        jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, nullptr, o.ldb, g.k, g.n, PREP_COPY16, 0.f, 0});
       }
     }
     // maps 2p, 2p+1 = A, B of plane p: hi; then lo (two-part) or mid, lo

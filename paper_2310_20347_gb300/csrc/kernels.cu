@@ -58,6 +58,13 @@ cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ld
 
 cudaError_t launch_int8_to_bf16(const int8_t* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s) {
+  const bool vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && ldx % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0 &&
+                   ldy % 8 == 0;
+  if (vec) {
+    int8_to_bf16_vec16_kernel<<<rows_grid(rows, cols, 16), 256, 0, s>>>(x, rows, cols, ldx, y, ldy);
+    count_launch();
+    return cudaGetLastError();
+  }
   int8_to_bf16_kernel<<<rows_grid(rows, cols, 4), 256, 0, s>>>(x, rows, cols, ldx, y, ldy);
   count_launch();
   return cudaGetLastError();
