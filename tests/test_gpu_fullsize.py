@@ -1,0 +1,119 @@
+"""Parity at the full sizes of the measured workloads, in the launch
+configuration the benchmark times (the planner's member and split), checked on
+sampled rows of C that the oracle computes in binary64 (int64 for INT8):
+
+  FP32-accurate 16384^3 (alpha 1, beta 0.5, uniform [-1, 1], seed 0)  gate 2e-6
+  BF16 / FP8 / INT8 8192^3                        8e-3 / 6e-2 / bit-exact
+  the 20 im2col layer shapes (batch 16) in BF16    kernel check 1e-5, gate 8e-3
+  the 1000-problem grouped batches (BF16 and FP32-accurate), every 25th
+  problem checked in full
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2310_20347_gb300 import G3_BF16, G3_F32_3XBF16, G3_FP8_E4M3, G3_INT8, synth, torch_api
+
+pytestmark = pytest.mark.gpu
+
+
+def sampled_err(got_rows, rows, A, B, C, alpha, beta):
+    """max |C - C_ref| / (|alpha| |A||B| + |beta C|) over the sampled rows."""
+    ref = oracle.gemm(A[rows], B, None if C is None else C[rows], alpha, beta)
+    D = oracle.absprod(A[rows], B, alpha)
+    if C is not None and beta != 0.0:
+        D = D + np.abs(beta * C[rows].astype(np.float64))
+    return float(np.max(np.abs(got_rows - ref) / np.maximum(D, 1e-300)))
+
+
+def test_fp32_accurate_16384_cubed():
+    n = 16384
+    p = synth.uniform_problem(n, n, n, seed=0, alpha=1.0, beta=0.5)
+    A, B, C = (torch.from_numpy(x).cuda() for x in (p.A, p.B, p.C))
+    torch_api.gemm(A, B, C, 1.0, 0.5, dtype=G3_F32_3XBF16)
+    rows = np.array([0, 1, 5461, 8192, 12345, n - 1])
+    got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    del A, B, C
+    e = sampled_err(got, rows, p.A, p.B, p.C, 1.0, 0.5)
+    print(f"16384^3 FP32-accurate sampled error {e:.3e}")
+    assert e <= 2e-6
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8", "int8"])
+def test_dtype_8192_cubed(kind):
+    n = 8192
+    rows = np.array([0, 77, n // 2, n - 1])
+    sel = torch.from_numpy(rows).cuda()
+    if kind == "int8":
+        p = synth.int8_problem(n, n, n, seed=0)
+        A, B = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.B).cuda()
+        C = torch.empty(n, n, dtype=torch.int32, device="cuda")
+        torch_api.gemm(A, B, C, 1, 0, dtype=G3_INT8)
+        got = C[sel].cpu().numpy().astype(np.int64)
+        assert np.array_equal(got, oracle.gemm_i8(p.A[rows], p.B))
+        return
+    p = synth.normal_problem(n, n, n, seed=0)
+    A32, B32 = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.B).cuda()
+    C = torch.empty(n, n, device="cuda")
+    if kind == "bf16":
+        A, B = torch_api.convert_bf16(A32), torch_api.convert_bf16(B32)
+        torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_BF16)
+        tol = 8e-3
+    else:
+        (A, sa), (B, sb) = torch_api.quantize_fp8(A32), torch_api.quantize_fp8(B32)
+        torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP8_E4M3, scale_a=sa, scale_b=sb)
+        tol = 6e-2
+    e = sampled_err(C[sel].double().cpu().numpy(), rows, p.A, p.B, None, 1.0, 0.0)
+    print(f"{kind} 8192^3 sampled error {e:.3e}")
+    assert e <= tol
+
+
+def test_im2col_layers_bf16():
+    worst_k = worst_g = 0.0
+    for li, (name, m, n, k) in enumerate(synth.im2col_shapes(16)):
+        p = synth.normal_problem(m, n, k, seed=li + 1)
+        A, B = torch_api.convert_bf16(torch.from_numpy(p.A).cuda()), torch_api.convert_bf16(torch.from_numpy(p.B).cuda())
+        C = torch.empty(m, n, device="cuda")
+        torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_BF16)
+        rows = np.unique(np.array([0, m // 3, m - 1]))
+        got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        Aq, Bq = oracle.round_bf16(p.A), oracle.round_bf16(p.B)
+        e_k = sampled_err(got, rows, Aq, Bq, None, 1.0, 0.0)
+        e_g = sampled_err(got, rows, p.A, p.B, None, 1.0, 0.0)
+        assert e_k <= 1e-5, (name, e_k)
+        assert e_g <= 8e-3, (name, e_g)
+        worst_k, worst_g = max(worst_k, e_k), max(worst_g, e_g)
+    print(f"im2col 20 layers: kernel {worst_k:.3e} gate {worst_g:.3e}")
+
+
+@pytest.mark.parametrize("dtype", [G3_BF16, G3_F32_3XBF16])
+def test_grouped_1000(dtype):
+    shapes = synth.grouped_shapes(1000, seed=0)
+    probs, host = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        p = synth.uniform_problem(m, n, k, seed=i)
+        A32, B32 = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.B).cuda()
+        if dtype == G3_BF16:
+            A, B = torch_api.convert_bf16(A32), torch_api.convert_bf16(B32)
+        else:
+            A, B = A32, B32
+        C = torch.full((m, n), float("nan"), device="cuda")
+        probs.append((A, B, C, 1.0, 0.0))
+        host.append(p)
+    plan = torch_api.GroupedPlan(probs, dtype)
+    plan.execute()
+    torch.cuda.synchronize()
+    worst = 0.0
+    for i in range(0, 1000, 25):
+        p, C = host[i], probs[i][2].double().cpu().numpy()
+        if dtype == G3_BF16:
+            Aq, Bq = oracle.round_bf16(p.A), oracle.round_bf16(p.B)
+            e = float(np.max(np.abs(C - oracle.gemm(Aq, Bq)) / np.maximum(oracle.absprod(Aq, Bq, 1.0), 1e-300)))
+            assert e <= 1e-5, (i, e)
+        else:
+            e = float(np.max(np.abs(C - oracle.gemm(p.A, p.B)) / np.maximum(oracle.absprod(p.A, p.B, 1.0), 1e-300)))
+            assert e <= 2e-6, (i, e)
+        worst = max(worst, e)
+    plan.close()
+    print(f"grouped 1000 dtype {dtype}: worst checked error {worst:.3e}")
