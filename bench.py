@@ -264,7 +264,7 @@ def run_workload(args):
 
     import oracle
     import paper_2310_20347_gb300 as pkg
-    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP8_E4M3, G3_INT8, _lib, synth,
+    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, _lib, synth,
                                         torch_api)
     torch.cuda.set_device(0)
     pkg.load()
@@ -455,9 +455,14 @@ def run_workload(args):
                "per_shape": per})
         return
 
-    if args.workload in ("int8", "fp8", "bf16"):
+    if args.workload in ("int8", "fp8", "bf16", "fp16"):
         n = args.dsize
-        if args.workload == "bf16":
+        if args.workload == "fp16":
+            p = synth.normal_problem(n, n, n, seed=0)
+            A, B = torch.from_numpy(p.A).to(dev).half(), torch.from_numpy(p.B).to(dev).half()
+            C = torch.empty(n, n, dtype=torch.float32, device=dev)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP16, config=args.config)
+        elif args.workload == "bf16":
             p = synth.normal_problem(n, n, n, seed=0)
             A, B = torch_api.convert_bf16(torch.from_numpy(p.A).to(dev)), torch_api.convert_bf16(
                 torch.from_numpy(p.B).to(dev))
@@ -494,7 +499,8 @@ def run_workload(args):
                "path": {"int8": "exact: int8 -> bf16 pre-pass, k-chunks of 1024 on the BF16 tensor path, "
                                 "int32 split-K reduce (tcgen05 kind::i8 does not exist on sm_103a)",
                         "fp8": "tcgen05 kind::f8f6f4 E4M3, per-tensor scales",
-                        "bf16": "tcgen05 kind::f16 BF16, FP32 accumulation"}[args.workload]},
+                        "bf16": "tcgen05 kind::f16 BF16, FP32 accumulation",
+                        "fp16": "tcgen05 kind::f16 FP16, FP32 accumulation"}[args.workload]},
               {"dtype": args.workload, "ms": ms, "kernel_ms": kms, "err": err,
                "roofline": {"bound": "tensor", "achieved": flops / kms / 1e9, "peak": tensor_peak,
                             "unit": "TFLOP/s", "frac": flops / kms / 1e9 / tensor_peak, "traffic": None,
@@ -591,7 +597,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16",
+                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

@@ -63,13 +63,15 @@ extern "C" {
  *   G3_FP8_E4M3    A, B OCP E4M3 bytes with per-tensor scales (g3_gemm_ex);
  *                  C float32 = alpha*scale_a*scale_b*(Aq Bq) + beta*C.
  *   G3_INT8        A, B int8; C int32; alpha must be 1 and beta 0 or 1; exact
- *                  (k <= 131072 so that no int32 overflow is possible). */
+ *                  (k <= 131072 so that no int32 overflow is possible).
+ *   G3_FP16        A, B IEEE binary16 (raw 16-bit patterns); C float32.     */
 typedef enum {
   G3_F32 = 0,
   G3_F32_3XBF16 = 1,
   G3_BF16 = 2,
   G3_FP8_E4M3 = 3,
-  G3_INT8 = 4
+  G3_INT8 = 4,
+  G3_FP16 = 5
 } g3_dtype;
 
 typedef enum {

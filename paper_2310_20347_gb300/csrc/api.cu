@@ -67,6 +67,7 @@ void family_init() {
   register_family_fp8(g_family);
   register_family_int8emu(g_family);
   register_family_6xbf16(g_family);
+  register_family_f16(g_family);
   g_family_ready = true;
 }
 
@@ -163,6 +164,7 @@ constexpr int64_t kSixProductMaxK = 512;
 int tc_mode_of(int dtype, int64_t k) {
   switch (dtype) {
     case G3_BF16: return TC_BF16;
+    case G3_FP16: return TC_F16;
     case G3_F32_3XBF16: return k <= kSixProductMaxK ? TC_6XBF16 : TC_3XBF16;
     case G3_FP8_E4M3: return TC_FP8;
     case G3_INT8: return TC_I8EMU;  // exact emulation: int8 values are exact in bfloat16
@@ -344,8 +346,9 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl) {
       L.b_hi = take((size_t)k * L.ldb_p * 2);
       break;
     case G3_BF16:
+    case G3_FP16:
     case G3_FP8_E4M3: {
-      const int es = a.dtype == G3_BF16 ? 2 : 1;
+      const int es = a.dtype == G3_FP8_E4M3 ? 1 : 2;
       L.pack_a = !tma_ok(a.A, a.lda, es);
       L.pack_b = !tma_ok(a.B, a.ldb, es);
       L.lda_p = L.pack_a ? round_up(k, 16 / es) : a.lda;
@@ -421,7 +424,7 @@ int validate(const g3_gemm_args& a) {
   if (a.m < 0) return -101;
   if (a.n < 0) return -102;
   if (a.k < 0) return -103;
-  if (a.dtype < G3_F32 || a.dtype > G3_INT8) return -112;
+  if (a.dtype < G3_F32 || a.dtype > G3_FP16) return -112;
   if (a.lda < std::max<int64_t>(1, a.k)) return -106;
   if (a.ldb < std::max<int64_t>(1, a.n)) return -108;
   if (a.ldc < std::max<int64_t>(1, a.n)) return -111;
@@ -661,7 +664,8 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   if (st != G3_OK) return st;
   if (a.m == 0 || a.n == 0) return G3_OK;
   const int64_t m = a.m, n = a.n, k = a.k;
-  const int es = (a.dtype == G3_F32 || a.dtype == G3_F32_3XBF16) ? 4 : (a.dtype == G3_BF16 ? 2 : 1);
+  const int es = (a.dtype == G3_F32 || a.dtype == G3_F32_3XBF16) ? 4
+                 : ((a.dtype == G3_BF16 || a.dtype == G3_FP16) ? 2 : 1);
   const int64_t lda_d = round_up(std::max<int64_t>(k, 1), 16), ldb_d = round_up(n, 16), ldc_d = round_up(n, 16);
   const size_t a_bytes = align256((size_t)m * lda_d * es), b_bytes = align256((size_t)std::max<int64_t>(k, 1) * ldb_d * es);
   const size_t c_bytes = align256((size_t)m * ldc_d * 4);
@@ -900,7 +904,7 @@ int g3_family_describe(int index, char* buf, size_t len) {
     family_init();
   }
   const FamilyEntry& f = g_family[index];
-  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16"};
+  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16", "f16"};
   std::snprintf(buf, len, "mode=%s bm=%d bn=%d stages=%d smem=%d bufs=%d cg=%d", names[f.mode], f.bm, 128 * f.cg,
                 f.stages, f.smem, f.bufs, f.cg);
   return G3_OK;
@@ -910,7 +914,7 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   if (m < 0) return -101;
   if (n < 0) return -102;
   if (k < 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_INT8) return -104;
+  if (dtype < G3_F32 || dtype > G3_FP16) return -104;
   if (dtype == G3_F32) {
     if (config) *config = -1;
     if (split_k) *split_k = 1;
@@ -970,7 +974,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   if (m <= 0) return -101;
   if (n <= 0) return -102;
   if (k <= 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_INT8) return -104;
+  if (dtype < G3_F32 || dtype > G3_FP16) return -104;
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || (dtype == G3_INT8 && k > 131072)) return G3_ERR_UNSUPPORTED;
   if (dtype == G3_F32) {   // one kernel: nothing to choose
     if (best_config) *best_config = -1;
@@ -986,7 +990,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
     if (st != G3_OK) return st;
     sms = d->sms;
   }
-  const int es_in = (dtype == G3_BF16) ? 2 : (dtype == G3_F32_3XBF16 ? 4 : 1);
+  const int es_in = (dtype == G3_BF16 || dtype == G3_FP16) ? 2 : (dtype == G3_F32_3XBF16 ? 4 : 1);
   const int64_t lda = round_up(k, 16), ldb = round_up(n, 16);
   void *A = nullptr, *B = nullptr, *C = nullptr;
   cudaStream_t s = nullptr;

@@ -31,6 +31,7 @@ void register_family_3xbf16(FamilyEntry* table);
 void register_family_fp8(FamilyEntry* table);
 void register_family_int8emu(FamilyEntry* table);
 void register_family_6xbf16(FamilyEntry* table);
+void register_family_f16(FamilyEntry* table);
 
 using GroupedLaunchFn = cudaError_t (*)(const GroupedParams& p, int grid, cudaStream_t s);
 
@@ -49,6 +50,7 @@ void register_grouped_3xbf16(GroupedEntry* table);
 void register_grouped_fp8(GroupedEntry* table);
 void register_grouped_int8emu(GroupedEntry* table);
 void register_grouped_6xbf16(GroupedEntry* table);
+void register_grouped_f16(GroupedEntry* table);
 
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.

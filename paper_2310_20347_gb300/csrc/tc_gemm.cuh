@@ -56,7 +56,7 @@ namespace g3 {
 // the epilogue adds the chunks in int32.
 // TC_6XBF16: the FP32-accurate mode for small k: operands split in three
 // bfloat16 parts (hi + mid + lo), six products per k-step.
-enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3, TC_6XBF16 = 4 };
+enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3, TC_6XBF16 = 4, TC_F16 = 5 };
 enum OutMode : int { OUT_F32 = 0, OUT_I32 = 1, OUT_PARTIAL = 2 };
 
 // Watchdog status codes (written to the device status word; see g3gemm.h).
@@ -125,7 +125,8 @@ struct TcTraits {
   static constexpr int kBoxN = 128 / kElem;                      // n per TMA box of B
   static constexpr int kNBoxes = 128 / kBoxN;                    // boxes per 128-wide n tile
   static constexpr uint32_t kBtBytes = 128 * 128;                // 128 n x 128 bytes of k
-  static constexpr uint32_t kAFmt = (MODE == TC_FP8) ? 0u : 1u;  // E4M3 : BF16
+  // operand format code: 0 = E4M3 (kind::f8f6f4) or F16 (kind::f16), 1 = BF16
+  static constexpr uint32_t kAFmt = (MODE == TC_FP8 || MODE == TC_F16) ? 0u : 1u;
   // Leading byte offset of the MN-major Bt operand: the distance between its
   // 128-byte-wide n groups (one TMA box each).  With a single group (FP8) the
   // field is unused; 1024 keeps every address inside the stage either way.

@@ -17,8 +17,8 @@ import torch
 
 import oracle
 from gpu_util import check_guard, dev, guarded, rel_err
-from paper_2310_20347_gb300 import (G3_BF16, G3_F32_3XBF16, G3_FP8_E4M3, G3_INT8, _lib, gen_family, synth,
-                                    torch_api)
+from paper_2310_20347_gb300 import (G3_BF16, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, _lib, gen_family,
+                                    synth, torch_api)
 
 pytestmark = pytest.mark.gpu
 
@@ -243,6 +243,39 @@ def test_3xbf16_integer_inputs_bit_exact():
     p = synth.small_int_problem(250, 330, 1000, seed=13, alpha=1.0, beta=2.0)
     got = x3_run(p)
     assert np.array_equal(got.astype(np.float64), oracle.gemm(p.A, p.B, p.C, 1.0, 2.0))
+
+
+# ---------------------------------------------------------------- FP16
+def f16_check(p, config=-1, split_k=0):
+    A16, B16 = p.A.astype(np.float16), p.B.astype(np.float16)   # IEEE round to nearest even
+    full, C = guarded(p.m, p.n, p.C)
+    torch_api.gemm(torch.from_numpy(A16).cuda(), torch.from_numpy(B16).cuda(), C, p.alpha, p.beta, dtype=G3_FP16,
+                   config=config, split_k=split_k)
+    torch.cuda.synchronize()
+    check_guard(full, p.m, p.n)
+    got = C.cpu().numpy()
+    bc = None if p.C is None else p.beta * p.C.astype(np.float64)
+    Aq, Bq = A16.astype(np.float64), B16.astype(np.float64)
+    e_k = rel_err(got, oracle.gemm(Aq, Bq, p.C, p.alpha, p.beta), oracle.absprod(Aq, Bq, p.alpha), bc)
+    e_g = rel_err(got, oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), oracle.absprod(p.A, p.B, p.alpha), bc)
+    assert e_k <= 1e-5, ("kernel", e_k)
+    assert e_g <= 2e-3, ("gate", e_g)   # two roundings to binary16 (2^-11 each)
+    return e_k, e_g
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp16_shapes(shape):
+    m, n, k = shape
+    f16_check(synth.uniform_problem(m, n, k, seed=26, alpha=0.75, beta=0.5))
+
+
+@pytest.mark.parametrize("config", members("f16"))
+def test_fp16_every_member(config):
+    f16_check(synth.uniform_problem(300, 520, 700, seed=27, alpha=1.0, beta=0.0), config=config)
+
+
+def test_fp16_split_k():
+    f16_check(synth.uniform_problem(96, 200, 3000, seed=28, beta=1.0), split_k=3)
 
 
 # ---------------------------------------------------------------- FP8
