@@ -120,7 +120,14 @@ G3_API int g3_set_stream(void* cuda_stream);
  *                      member of the generated kernel family (g3_family_*).
  *   split_k            0: the planner's choice; >= 1 forces that many splits.
  *   raster             0: the planner's choice; >= 1 the band width (in tiles)
- *                      of the tile walk.                                    */
+ *                      of the tile walk.
+ *   trans_a, trans_b   0: A is m x k (lda >= k), B is k x n (ldb >= n);
+ *                      1: the operand is stored transposed -- A as k x m
+ *                      (lda >= m), B as n x k (ldb >= k) -- and C := beta*C
+ *                      + alpha * op(A) op(B) (BLAS transa/transb).  A
+ *                      transposed operand is first copied into the row-major
+ *                      layout in a library-owned buffer (grown on first use,
+ *                      even when `workspace` is given).                     */
 typedef struct g3_gemm_args {
   int64_t m, n, k;
   double alpha, beta;
@@ -138,6 +145,8 @@ typedef struct g3_gemm_args {
   int config;
   int split_k;
   int raster;
+  int trans_a;
+  int trans_b;
 } g3_gemm_args;
 
 /* Initialise the optional fields of `args` to their defaults (config = -1,

@@ -49,7 +49,8 @@ class g3_gemm_args(ctypes.Structure):
                 ("dtype", ctypes.c_int),
                 ("scale_a", ctypes.c_void_p), ("scale_b", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("config", ctypes.c_int), ("split_k", ctypes.c_int), ("raster", ctypes.c_int)]
+                ("config", ctypes.c_int), ("split_k", ctypes.c_int), ("raster", ctypes.c_int),
+                ("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int)]
 
 
 class g3_gemm_desc(ctypes.Structure):

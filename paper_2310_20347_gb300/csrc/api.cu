@@ -32,6 +32,9 @@ struct DevState {
   int* status = nullptr;   // device address of g_device_status
   void* ws = nullptr;      // library-owned workspace
   size_t ws_bytes = 0;
+  // row-major copies of transposed operands (trans_a / trans_b)
+  void* tbuf = nullptr;
+  size_t tbuf_bytes = 0;
   // g3_gemm_host: device copies of A, B, C and the copy streams / events
   void* hbuf = nullptr;
   size_t hbuf_bytes = 0;
@@ -425,8 +428,10 @@ int validate(const g3_gemm_args& a) {
   if (a.n < 0) return -102;
   if (a.k < 0) return -103;
   if (a.dtype < G3_F32 || a.dtype > G3_FP16) return -112;
-  if (a.lda < std::max<int64_t>(1, a.k)) return -106;
-  if (a.ldb < std::max<int64_t>(1, a.n)) return -108;
+  if (a.trans_a != 0 && a.trans_a != 1) return -119;
+  if (a.trans_b != 0 && a.trans_b != 1) return -120;
+  if (a.lda < std::max<int64_t>(1, a.trans_a ? a.m : a.k)) return -106;
+  if (a.ldb < std::max<int64_t>(1, a.trans_b ? a.k : a.n)) return -108;
   if (a.ldc < std::max<int64_t>(1, a.n)) return -111;
   if (a.m == 0 || a.n == 0) return G3_OK;
   if (!a.C) return -110;
@@ -596,6 +601,47 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   return G3_OK;
 }
 
+int input_esize(int dtype) {
+  if (dtype == G3_F32 || dtype == G3_F32_3XBF16) return 4;
+  return (dtype == G3_BF16 || dtype == G3_FP16) ? 2 : 1;
+}
+
+// Transposed operands: copy them into row-major A (m x k) / B (k x n) in the
+// device's transpose buffer and point the arguments there.
+int untranspose(DevState& d, g3_gemm_args& a, cudaStream_t s) {
+  const int es = input_esize(a.dtype);
+  const int64_t lda_t = round_up(std::max<int64_t>(a.k, 1), 16), ldb_t = round_up(a.n, 16);
+  const size_t a_bytes = a.trans_a ? align256((size_t)a.m * lda_t * es) : 0;
+  const size_t b_bytes = a.trans_b ? align256((size_t)a.k * ldb_t * es) : 0;
+  if (d.tbuf_bytes < a_bytes + b_bytes) {
+    if (d.tbuf) {
+      cudaDeviceSynchronize();
+      cudaFree(d.tbuf);
+      d.tbuf = nullptr;
+      d.tbuf_bytes = 0;
+    }
+    if (cudaMalloc(&d.tbuf, a_bytes + b_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return G3_ERR_NOMEM;
+    }
+    d.tbuf_bytes = a_bytes + b_bytes;
+  }
+  uint8_t* base = static_cast<uint8_t*>(d.tbuf);
+  if (a.trans_a) {   // stored k x m
+    G3_CHECK_CUDA(launch_transpose(a.A, (int)a.k, (int)a.m, a.lda, base, lda_t, es, s));
+    a.A = base;
+    a.lda = lda_t;
+    a.trans_a = 0;
+  }
+  if (a.trans_b) {   // stored n x k
+    G3_CHECK_CUDA(launch_transpose(a.B, (int)a.n, (int)a.k, a.ldb, base + a_bytes, ldb_t, es, s));
+    a.B = base + a_bytes;
+    a.ldb = ldb_t;
+    a.trans_b = 0;
+  }
+  return G3_OK;
+}
+
 int gemm_impl(g3_gemm_args a, cudaStream_t s) {
   int st = validate(a);
   if (st != G3_OK) return st;
@@ -603,6 +649,7 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g_mu);
   DevState* d = nullptr;
   if ((st = ensure_device(&d)) != G3_OK) return st;
+  if ((a.trans_a || a.trans_b) && a.k > 0 && a.alpha != 0.0 && (st = untranspose(*d, a, s)) != G3_OK) return st;
   const bool is_int = a.dtype == G3_INT8;
   if (a.k == 0 || a.alpha == 0.0) {
     if (is_int && a.beta == 1.0) return G3_OK;
@@ -799,6 +846,9 @@ int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
   if ((st = ensure_device(&d)) != G3_OK) return st;
   g3_gemm_args a = *args;
   if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b)) a.split_k = 1;
+  // a transposed operand reaches the kernel as an aligned row-major copy
+  if (a.trans_a) { a.A = d->ws ? d->ws : reinterpret_cast<void*>(uintptr_t(256)); a.lda = round_up(a.k, 16); }
+  if (a.trans_b) { a.B = d->ws ? d->ws : reinterpret_cast<void*>(uintptr_t(256)); a.ldb = round_up(a.n, 16); }
   const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d->sms, a.config, a.split_k, a.raster);
   *bytes = make_layout(a, pl).total;
   return G3_OK;

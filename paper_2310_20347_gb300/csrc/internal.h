@@ -63,6 +63,9 @@ cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ld
                                 cudaStream_t s);
 cudaError_t launch_int8_to_bf16(const int8_t* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s);
+// y (cols x rows) := transpose of x (rows x cols), elements of esize bytes (1, 2 or 4).
+cudaError_t launch_transpose(const void* x, int rows, int cols, long long ldx, void* y, long long ldy, int esize,
+                             cudaStream_t s);
 cudaError_t launch_pack_rows(const void* x, int rows, long long row_bytes, long long ldx_bytes, void* y,
                              long long ldy_bytes, cudaStream_t s);
 cudaError_t launch_quantize_e4m3(const float* x, int rows, int cols, long long ldx, unsigned int* amax_bits,

@@ -70,6 +70,24 @@ cudaError_t launch_int8_to_bf16(const int8_t* x, int rows, int cols, long long l
   return cudaGetLastError();
 }
 
+cudaError_t launch_transpose(const void* x, int rows, int cols, long long ldx, void* y, long long ldy, int esize,
+                             cudaStream_t s) {
+  const long long tiles = (long long)((rows + 31) / 32) * ((cols + 31) / 32);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, 152LL * 16));
+  const dim3 block(32, 8, 1);
+  if (esize == 4)
+    transpose_kernel<uint32_t><<<grid, block, 0, s>>>(static_cast<const uint32_t*>(x), rows, cols, ldx,
+                                                       static_cast<uint32_t*>(y), ldy);
+  else if (esize == 2)
+    transpose_kernel<uint16_t><<<grid, block, 0, s>>>(static_cast<const uint16_t*>(x), rows, cols, ldx,
+                                                       static_cast<uint16_t*>(y), ldy);
+  else
+    transpose_kernel<uint8_t><<<grid, block, 0, s>>>(static_cast<const uint8_t*>(x), rows, cols, ldx,
+                                                      static_cast<uint8_t*>(y), ldy);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack_rows(const void* x, int rows, long long row_bytes, long long ldx_bytes, void* y,
                              long long ldy_bytes, cudaStream_t s) {
   pack_rows_kernel<<<rows_grid(rows, row_bytes, 1), 256, 0, s>>>(static_cast<const uint8_t*>(x), rows, row_bytes,

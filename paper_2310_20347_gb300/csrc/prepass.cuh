@@ -173,6 +173,29 @@ __global__ void pack_rows_kernel(const uint8_t* __restrict__ x, int rows, long l
   }
 }
 
+// y (cols x rows, leading dimension ldy) := transpose of x (rows x cols,
+// leading dimension ldx), elements of type T, through a 32 x 33 shared tile so
+// that both the reads and the writes are coalesced.  Block (32, 8).
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ x, int rows, int cols, long long ldx, T* __restrict__ y,
+                                 long long ldy) {
+  __shared__ T tile[32][33];
+  const int tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+  for (long long t = blockIdx.x; t < (long long)tr * tc; t += gridDim.x) {
+    const int r0 = (int)(t / tc) * 32, c0 = (int)(t % tc) * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int r = r0 + i, c = c0 + threadIdx.x;
+      if (r < rows && c < cols) tile[i][threadIdx.x] = x[(long long)r * ldx + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int c = c0 + i, r = r0 + threadIdx.x;   // output row c, column r
+      if (c < cols && r < rows) y[(long long)c * ldy + r] = tile[threadIdx.x][i];
+    }
+    __syncthreads();
+  }
+}
+
 // amax of |x| as the bit pattern of a non-negative float (monotone as unsigned).
 __global__ void absmax_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
                               unsigned int* __restrict__ amax_bits) {

@@ -33,9 +33,10 @@ def _ptr(t):
 
 
 def gemm_args(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, scale_a=None, scale_b=None, config=-1,
-              split_k=0, raster=0, workspace=None):
-    m, k = A.shape
-    k2, n = B.shape
+              split_k=0, raster=0, workspace=None, trans_a=False, trans_b=False):
+    """trans_a / trans_b: A is given as k x m / B as n x k (op = transpose)."""
+    m, k = (A.shape[1], A.shape[0]) if trans_a else tuple(A.shape)
+    k2, n = (B.shape[1], B.shape[0]) if trans_b else tuple(B.shape)
     if k2 != k or tuple(C.shape) != (m, n):
         raise ValueError(f"shape mismatch: A {tuple(A.shape)} B {tuple(B.shape)} C {tuple(C.shape)}")
     in_t, out_t = _ELEM[dtype]
@@ -55,6 +56,7 @@ def gemm_args(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, scale_a=None, scale_b=
     if workspace is not None:
         a.workspace, a.workspace_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     a.config, a.split_k, a.raster = config, split_k, raster
+    a.trans_a, a.trans_b = int(bool(trans_a)), int(bool(trans_b))
     return a
 
 

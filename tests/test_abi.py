@@ -52,6 +52,15 @@ def test_argument_errors(lib):
     assert L.g3_gemm(4, 4, 8, 1.0, None, 8, p, 4, 0.0, p, 4, 0) == -105
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, None, 4, 0.0, p, 4, 0) == -107
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, None, 4, 0) == -110
+    # transposed operands: lda >= m for A stored k x m, ldb >= k for B stored n x k
+    a = L.g3_gemm_args_init()
+    a.m, a.n, a.k, a.A, a.B, a.C, a.alpha = 6, 4, 8, p, p, p, 1.0
+    a.lda, a.ldb, a.ldc, a.trans_a = 5, 4, 4, 1
+    assert L.g3_gemm_workspace_size(a)[0] == -106
+    a.lda, a.trans_b, a.ldb = 6, 1, 7
+    assert L.g3_gemm_workspace_size(a)[0] == -108
+    a.ldb, a.trans_b = 8, 2
+    assert L.g3_gemm_workspace_size(a)[0] == -120
     # host-buffer entry point: the same validation, nothing touches a device
     assert L.g3_gemm_host(-1, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, 0, None) == -101
     assert L.g3_gemm_host(4, 4, 8, 1.0, p, 7, p, 4, 0.0, p, 4, 0, None) == -106
