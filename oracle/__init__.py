@@ -58,6 +58,9 @@ def _load():
             lib.oracle_round_bf16.argtypes = [ctypes.c_float]
             lib.oracle_round_bf16.restype = ctypes.c_float
             lib.oracle_round_bf16_array.argtypes = [vp, vp, i64]
+            lib.oracle_round_tf32.argtypes = [ctypes.c_float]
+            lib.oracle_round_tf32.restype = ctypes.c_float
+            lib.oracle_round_tf32_array.argtypes = [vp, vp, i64]
             lib.oracle_e4m3_decode.argtypes = [ctypes.c_uint8]
             lib.oracle_e4m3_decode.restype = ctypes.c_float
             lib.oracle_e4m3_encode.argtypes = [ctypes.c_float]
@@ -201,6 +204,14 @@ def round_bf16(x):
     x = _c(x, np.float32)
     y = np.empty_like(x)
     _load().oracle_round_bf16_array(_ptr(x), _ptr(y), x.size)
+    return y
+
+
+def round_tf32(x):
+    """TF32 round-to-nearest-even of float32 values, returned as float32."""
+    x = _c(x, np.float32)
+    y = np.empty_like(x)
+    _load().oracle_round_tf32_array(_ptr(x), _ptr(y), x.size)
     return y
 
 

@@ -160,6 +160,26 @@ void oracle_round_bf16_array(const float* x, float* y, int64_t count) {
     for (int64_t i = 0; i < count; ++i) y[i] = oracle_round_bf16(x[i]);
 }
 
+/* TF32 rounding written from the number grid: q = x / spacing rounded to the
+ * nearest integer (rint: ties to even in the default rounding mode), then
+ * q * spacing; both steps are exact in binary64. */
+float oracle_round_tf32(float x) {
+    if (isnan(x)) return f32_from(0x7FC00000u);
+    if (isinf(x) || x == 0.0f) return x;
+    int e;
+    frexp((double)x, &e);              /* |x| = f * 2^e with f in [0.5, 1) */
+    int E = e - 1;                     /* unbiased exponent of x */
+    if (E < -126) E = -126;            /* subnormals share the smallest spacing */
+    const double spacing = ldexp(1.0, E - 10);
+    const double r = rint((double)x / spacing) * spacing;
+    if (fabs(r) >= ldexp(1.0, 128)) return x > 0 ? f32_from(0x7F800000u) : f32_from(0xFF800000u);
+    return (float)r;
+}
+
+void oracle_round_tf32_array(const float* x, float* y, int64_t count) {
+    for (int64_t i = 0; i < count; ++i) y[i] = oracle_round_tf32(x[i]);
+}
+
 /* OCP 8-bit floating point, E4M3: exponent bias 7, subnormals m * 2^-9,
  * S.1111.111 is NaN (there is no infinity).                                  */
 float oracle_e4m3_decode(uint8_t code) {

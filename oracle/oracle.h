@@ -66,6 +66,14 @@ void oracle_gemm_rows_i8_i64(int64_t nrows, const int64_t* rows, int64_t n, int6
 float oracle_round_bf16(float x);
 void  oracle_round_bf16_array(const float* x, float* y, int64_t count);
 
+/* TF32: binary32's sign and 8-bit exponent with 10 fraction bits.  Round to
+ * nearest, ties to even, on the TF32 grid: spacing 2^(E-10) at a normal x of
+ * unbiased exponent E, 2^-136 among subnormals; beyond the largest finite
+ * TF32 value the result overflows to +-Inf; NaN gives 0x7FC00000.  Returned
+ * as the binary32 value. */
+float oracle_round_tf32(float x);
+void  oracle_round_tf32_array(const float* x, float* y, int64_t count);
+
 /* OCP FP8 E4M3 ("fn"): 1 sign, 4 exponent (bias 7), 3 fraction bits, no
  * infinities, NaN = S.1111.111, largest finite 448.  Decoding is the format
  * definition; encoding picks the nearest finite value with ties to the even

@@ -168,3 +168,54 @@ def test_3xbf16_within_split_bound(oracle):
         assert rel <= bound
         assert rel < 2e-5            # far below bfloat16's own 2^-8
         assert rel > 0               # it is an approximation: lo*lo is dropped
+
+
+# ---------------------------------------------------------------- TF32
+def test_tf32_fixed_points_every_pattern(oracle):
+    # every sign / exponent / 10-bit fraction combination is a TF32 value
+    sign_exp = np.arange(1 << 9, dtype=np.uint32) << 23
+    frac = np.arange(1 << 10, dtype=np.uint32) << 13
+    pats = (sign_exp[:, None] | frac[None, :]).ravel()
+    x = _f32(pats)
+    keep = ~np.isnan(x)
+    assert np.array_equal(oracle.round_tf32(x[keep]).view(np.uint32), pats[keep])
+
+
+def test_tf32_nearest_with_ties_to_even(oracle):
+    # against the grid itself: the result lies on the TF32 grid (low 13 bits
+    # zero), no grid neighbour (one step in the encoding) is nearer, and a tie
+    # picks the neighbour with an even last fraction bit
+    r = np.random.default_rng(1)
+    hi = r.integers(0, 0xFF, 120000, dtype=np.uint32) << 23 | (r.integers(0, 1 << 10, 120000, dtype=np.uint32) << 13)
+    hi |= r.integers(0, 2, 120000, dtype=np.uint32) << 31
+    low = np.concatenate([np.full(30000, 0x1000), np.full(30000, 0x0FFF), np.full(30000, 0x1001),
+                          r.integers(0, 1 << 13, 30000)]).astype(np.uint32)
+    x = _f32(hi | low)
+    y = oracle.round_tf32(x)
+    yb = y.view(np.uint32)
+    fin = np.isfinite(y)
+    assert np.all(yb[fin] & 0x1FFF == 0)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    for step in (0x2000, -0x2000):
+        nb = (yb.astype(np.int64) + step)
+        ok = fin & (nb >= 0) & ((nb & 0x7F800000) != 0x7F800000) & ((nb & 0x7FFFFFFF) <= 0x7F7FE000)
+        ok &= ((nb ^ yb.astype(np.int64)) & 0x80000000) == 0   # same sign
+        nd = nb[ok].astype(np.uint32).view(np.float32).astype(np.float64)
+        d_here, d_nb = np.abs(xd[ok] - yd[ok]), np.abs(xd[ok] - nd)
+        assert np.all(d_here <= d_nb)
+        tie = d_here == d_nb
+        assert np.all((yb[ok][tie] >> 13) & 1 == 0)
+
+
+def test_tf32_closed_forms_and_overflow(oracle):
+    one = 1.0
+    cases = [(one + 2.0 ** -10, one + 2.0 ** -10), (one + 2.0 ** -11, one),
+             (one + 3 * 2.0 ** -11, one + 2.0 ** -9), (one + 2.0 ** -11 + 2.0 ** -20, one + 2.0 ** -10),
+             (-(one + 2.0 ** -11 + 2.0 ** -20), -(one + 2.0 ** -10)), (2049.0, 2048.0), (2051.0, 2052.0)]
+    for x, want in cases:
+        assert oracle.round_tf32(np.array([x], np.float32))[0] == np.float32(want), x
+    big = _f32([0x7F7FE000, 0x7F7FEFFF, 0x7F7FF000, 0xFF7FF000, 0x7F7FFFFF])
+    got = oracle.round_tf32(big).view(np.uint32)
+    assert list(got) == [0x7F7FE000, 0x7F7FE000, 0x7F800000, 0xFF800000, 0x7F800000]
+    sub = _f32([0x00000FFF, 0x00001000, 0x00003000, 0x00001001])   # subnormals: spacing 2^-136
+    assert list(oracle.round_tf32(sub).view(np.uint32)) == [0x0, 0x0, 0x4000, 0x2000]
