@@ -264,7 +264,7 @@ def run_workload(args):
 
     import oracle
     import paper_2310_20347_gb300 as pkg
-    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, _lib, synth,
+    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib, synth,
                                         torch_api)
     torch.cuda.set_device(0)
     pkg.load()
@@ -455,9 +455,14 @@ def run_workload(args):
                "per_shape": per})
         return
 
-    if args.workload in ("int8", "fp8", "bf16", "fp16"):
+    if args.workload in ("int8", "fp8", "bf16", "fp16", "tf32"):
         n = args.dsize
-        if args.workload == "fp16":
+        if args.workload == "tf32":
+            p = synth.normal_problem(n, n, n, seed=0)
+            A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+            C = torch.empty(n, n, dtype=torch.float32, device=dev)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_TF32, config=args.config)
+        elif args.workload == "fp16":
             p = synth.normal_problem(n, n, n, seed=0)
             A, B = torch.from_numpy(p.A).to(dev).half(), torch.from_numpy(p.B).to(dev).half()
             C = torch.empty(n, n, dtype=torch.float32, device=dev)
@@ -493,19 +498,21 @@ def run_workload(args):
         ms = _call_ms(fn, args.reps, flush)
         kms = _kernel_ms(_lib, fn, args.reps, flush)
         flops = 2.0 * n ** 3
-        tensor_peak = bf16_peak * (2.0 if args.workload == "fp8" else 1.0)
+        tensor_peak = bf16_peak * {"fp8": 2.0, "tf32": 0.5}.get(args.workload, 1.0)
         _line(args, flops / ms / 1e9, "TOPS" if args.workload == "int8" else "TFLOPS",
               {"workload": f"{args.workload} GEMM m=n=k={n}, alpha=1, beta=0",
                "path": {"int8": "exact: int8 -> bf16 pre-pass, k-chunks of 1024 on the BF16 tensor path, "
                                 "int32 split-K reduce (tcgen05 kind::i8 does not exist on sm_103a)",
                         "fp8": "tcgen05 kind::f8f6f4 E4M3, per-tensor scales",
                         "bf16": "tcgen05 kind::f16 BF16, FP32 accumulation",
-                        "fp16": "tcgen05 kind::f16 FP16, FP32 accumulation"}[args.workload]},
+                        "fp16": "tcgen05 kind::f16 FP16, FP32 accumulation",
+                        "tf32": "TF32 rounding pre-pass + tcgen05 kind::tf32, FP32 accumulation"}[args.workload]},
               {"dtype": args.workload, "ms": ms, "kernel_ms": kms, "err": err,
                "roofline": {"bound": "tensor", "achieved": flops / kms / 1e9, "peak": tensor_peak,
                             "unit": "TFLOP/s", "frac": flops / kms / 1e9 / tensor_peak, "traffic": None,
-                            "peak_source": f"{peak_src} bf16 burst" + (" x 2 (fp8 nominal ratio)"
-                                                                         if args.workload == "fp8" else ""),
+                            "peak_source": f"{peak_src} bf16 burst" + {
+                                "fp8": " x 2 (fp8 nominal ratio)",
+                                "tf32": " x 0.5 (tf32 nominal ratio)"}.get(args.workload, ""),
                             "algorithmic": "2 n^3 per call (INT8: of the main kernel's bf16 work)"}})
         return
 
@@ -597,7 +604,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16",
+                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

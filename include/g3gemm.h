@@ -64,14 +64,18 @@ extern "C" {
  *                  C float32 = alpha*scale_a*scale_b*(Aq Bq) + beta*C.
  *   G3_INT8        A, B int8; C int32; alpha must be 1 and beta 0 or 1; exact
  *                  (k <= 131072 so that no int32 overflow is possible).
- *   G3_FP16        A, B IEEE binary16 (raw 16-bit patterns); C float32.     */
+ *   G3_FP16        A, B IEEE binary16 (raw 16-bit patterns); C float32.
+ *   G3_TF32        A, B, C float32; A and B rounded to TF32 (10 fraction
+ *                  bits, nearest even) by a pre-pass, products on kind::tf32
+ *                  with FP32 accumulation.                                 */
 typedef enum {
   G3_F32 = 0,
   G3_F32_3XBF16 = 1,
   G3_BF16 = 2,
   G3_FP8_E4M3 = 3,
   G3_INT8 = 4,
-  G3_FP16 = 5
+  G3_FP16 = 5,
+  G3_TF32 = 6
 } g3_dtype;
 
 typedef enum {
@@ -169,6 +173,11 @@ G3_API int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes);
 /* y = bfloat16(x), round to nearest even (raw 16-bit patterns).             */
 G3_API int g3_convert_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* y, int64_t ldy,
                     void* cuda_stream);
+
+/* y = x rounded to TF32 (10 fraction bits, nearest even; overflow to +-Inf,
+ * NaN to 0x7FC00000), stored as float32: the pre-pass of G3_TF32.          */
+G3_API int g3_convert_tf32(const float* x, int64_t rows, int64_t cols, int64_t ldx, float* y, int64_t ldy,
+                           void* cuda_stream);
 
 /* hi = bf16(x), lo = bf16(x - hi): the split of the FP32-accurate mode.     */
 G3_API int g3_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo, int64_t ldy,

@@ -7,7 +7,7 @@ The compute lives in libg3gemm.so (CUDA for sm_103a, C ABI in include/g3gemm.h);
 torch CUDA tensors.  ``synth`` holds the seeded input generators.
 Importing the package loads nothing; the library is loaded on first use.
 """
-from ._lib import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, DTYPES,  # noqa: F401
+from ._lib import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, DTYPES,  # noqa: F401
                    G3Error, load)
 
 

@@ -71,6 +71,7 @@ void family_init() {
   register_family_int8emu(g_family);
   register_family_6xbf16(g_family);
   register_family_f16(g_family);
+  register_family_tf32(g_family);
   g_family_ready = true;
 }
 
@@ -130,7 +131,8 @@ int encode_2d(CUtensorMap* map, const void* base, int esize, uint64_t inner, uin
   cuuint64_t strides[1] = {ld * (uint64_t)esize};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
-  CUtensorMapDataType dt = esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                : (esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
   CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
@@ -168,12 +170,16 @@ int tc_mode_of(int dtype, int64_t k) {
   switch (dtype) {
     case G3_BF16: return TC_BF16;
     case G3_FP16: return TC_F16;
+    case G3_TF32: return TC_TF32;
     case G3_F32_3XBF16: return k <= kSixProductMaxK ? TC_6XBF16 : TC_3XBF16;
     case G3_FP8_E4M3: return TC_FP8;
     case G3_INT8: return TC_I8EMU;  // exact emulation: int8 values are exact in bfloat16
     default: return -1;
   }
 }
+
+// k per k-block: one 128-byte row of the swizzled tile
+int kblock_of(int mode) { return mode == TC_FP8 ? 128 : (mode == TC_TF32 ? 32 : 64); }
 
 struct Plan {
   int member = -1;
@@ -263,7 +269,7 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     }
   }
   const int mode = tc_mode_of(dtype, k);
-  const int bk = (mode == TC_FP8) ? 128 : 64;
+  const int bk = kblock_of(mode);
   pl.num_kb = (int)((k + bk - 1) / bk);
   if (force_member >= 0 && force_member < G3_FAMILY_SIZE && g_family[force_member].mode == mode &&
       g_family[force_member].launch) {
@@ -340,6 +346,13 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl) {
         L.a_mid = take((size_t)m * L.lda_p * 2);
         L.b_mid = take((size_t)k * L.ldb_p * 2);
       }
+      break;
+    case G3_TF32:   // rounded copies, binary32; B transposed (n x k, K-major)
+      L.pack_a = L.pack_b = true;
+      L.lda_p = round_up(k, 4);
+      L.ldb_p = round_up(k, 4);
+      L.a_hi = take((size_t)m * L.lda_p * 4);
+      L.b_hi = take((size_t)n * L.ldb_p * 4);
       break;
     case G3_INT8:
       L.pack_a = L.pack_b = true;
@@ -427,7 +440,7 @@ int validate(const g3_gemm_args& a) {
   if (a.m < 0) return -101;
   if (a.n < 0) return -102;
   if (a.k < 0) return -103;
-  if (a.dtype < G3_F32 || a.dtype > G3_FP16) return -112;
+  if (a.dtype < G3_F32 || a.dtype > G3_TF32) return -112;
   if (a.trans_a != 0 && a.trans_a != 1) return -119;
   if (a.trans_b != 0 && a.trans_b != 1) return -120;
   if (a.lda < std::max<int64_t>(1, a.trans_a ? a.m : a.k)) return -106;
@@ -479,7 +492,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   if (st != G3_OK) return st;
 
   const int64_t m = a.m, n = a.n, k = a.k;
-  const int es = (a.dtype == G3_FP8_E4M3) ? 1 : 2;
+  const int es = (a.dtype == G3_FP8_E4M3) ? 1 : (a.dtype == G3_TF32 ? 4 : 2);
   const void *A_hi = a.A, *A_lo = nullptr, *B_hi = a.B, *B_lo = nullptr, *A_mid = nullptr, *B_mid = nullptr;
   int64_t lda = a.lda, ldb = a.ldb;
 
@@ -498,6 +511,13 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
     G3_CHECK_CUDA(launch_split_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p, s));
     G3_CHECK_CUDA(launch_split_bf16((const float*)a.B, (int)k, (int)n, a.ldb, bh, bl, L.ldb_p, s));
     A_hi = ah; A_lo = al; B_hi = bh; B_lo = bl;
+    lda = L.lda_p;
+    ldb = L.ldb_p;
+  } else if (a.dtype == G3_TF32) {
+    float *ah = (float*)(ws + L.a_hi), *bh = (float*)(ws + L.b_hi);
+    G3_CHECK_CUDA(launch_convert_tf32((const float*)a.A, (int)m, (int)k, a.lda, ah, L.lda_p, s));
+    G3_CHECK_CUDA(launch_convert_tf32_t((const float*)a.B, (int)k, (int)n, a.ldb, bh, L.ldb_p, s));
+    A_hi = ah; B_hi = bh;
     lda = L.lda_p;
     ldb = L.ldb_p;
   } else if (a.dtype == G3_INT8) {
@@ -531,7 +551,11 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   std::memset(maps, 0, sizeof(maps));
   const uint32_t arows = fam.bm / fam.cg;   // rows of A one CTA stages (half the tile in a pair)
   if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, arows)) != G3_OK) return st;
-  if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
+  if (a.dtype == G3_TF32) {   // B stored n x k: boxes of bk (k) x 128 (n rows)
+    if ((st = encode_2d(&maps[1], B_hi, es, k, n, ldb, bk, 128)) != G3_OK) return st;
+  } else if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) {
+    return st;
+  }
   maps[2] = maps[4] = maps[0];
   maps[3] = maps[5] = maps[1];
   if (fam.mode == TC_6XBF16) {
@@ -602,7 +626,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
 }
 
 int input_esize(int dtype) {
-  if (dtype == G3_F32 || dtype == G3_F32_3XBF16) return 4;
+  if (dtype == G3_F32 || dtype == G3_F32_3XBF16 || dtype == G3_TF32) return 4;
   return (dtype == G3_BF16 || dtype == G3_FP16) ? 2 : 1;
 }
 
@@ -711,8 +735,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   if (st != G3_OK) return st;
   if (a.m == 0 || a.n == 0) return G3_OK;
   const int64_t m = a.m, n = a.n, k = a.k;
-  const int es = (a.dtype == G3_F32 || a.dtype == G3_F32_3XBF16) ? 4
-                 : ((a.dtype == G3_BF16 || a.dtype == G3_FP16) ? 2 : 1);
+  const int es = input_esize(a.dtype);
   const int64_t lda_d = round_up(std::max<int64_t>(k, 1), 16), ldb_d = round_up(n, 16), ldc_d = round_up(n, 16);
   const size_t a_bytes = align256((size_t)m * lda_d * es), b_bytes = align256((size_t)std::max<int64_t>(k, 1) * ldb_d * es);
   const size_t c_bytes = align256((size_t)m * ldc_d * 4);
@@ -886,6 +909,14 @@ int g3_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void*
   return G3_OK;
 }
 
+int g3_convert_tf32(const float* x, int64_t rows, int64_t cols, int64_t ldx, float* y, int64_t ldy, void* stream) {
+  int st = prep_check(x, rows, cols, ldx, y, ldy);
+  if (st != G3_OK || rows == 0 || cols == 0) return st;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  G3_CHECK_CUDA(launch_convert_tf32(x, (int)rows, (int)cols, ldx, y, ldy, s));
+  return G3_OK;
+}
+
 int g3_split3_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* mid, void* lo,
                    int64_t ldy, void* stream) {
   int st = prep_check(x, rows, cols, ldx, hi, ldy, 8);
@@ -954,7 +985,7 @@ int g3_family_describe(int index, char* buf, size_t len) {
     family_init();
   }
   const FamilyEntry& f = g_family[index];
-  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16", "f16"};
+  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16", "f16", "tf32"};
   std::snprintf(buf, len, "mode=%s bm=%d bn=%d stages=%d smem=%d bufs=%d cg=%d", names[f.mode], f.bm, 128 * f.cg,
                 f.stages, f.smem, f.bufs, f.cg);
   return G3_OK;
@@ -964,7 +995,7 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   if (m < 0) return -101;
   if (n < 0) return -102;
   if (k < 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_FP16) return -104;
+  if (dtype < G3_F32 || dtype > G3_TF32) return -104;
   if (dtype == G3_F32) {
     if (config) *config = -1;
     if (split_k) *split_k = 1;
@@ -1024,7 +1055,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   if (m <= 0) return -101;
   if (n <= 0) return -102;
   if (k <= 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_FP16) return -104;
+  if (dtype < G3_F32 || dtype > G3_TF32) return -104;
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || (dtype == G3_INT8 && k > 131072)) return G3_ERR_UNSUPPORTED;
   if (dtype == G3_F32) {   // one kernel: nothing to choose
     if (best_config) *best_config = -1;
@@ -1040,7 +1071,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
     if (st != G3_OK) return st;
     sms = d->sms;
   }
-  const int es_in = (dtype == G3_BF16 || dtype == G3_FP16) ? 2 : (dtype == G3_F32_3XBF16 ? 4 : 1);
+  const int es_in = input_esize(dtype);
   const int64_t lda = round_up(k, 16), ldb = round_up(n, 16);
   void *A = nullptr, *B = nullptr, *C = nullptr;
   cudaStream_t s = nullptr;
@@ -1068,7 +1099,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
     return G3_ERR_CUDA;
   }
   const int mode = tc_mode_of(dtype, k);
-  const int bk = (mode == TC_FP8) ? 128 : 64;
+  const int bk = kblock_of(mode);
   const int num_kb = (int)((k + bk - 1) / bk);
   int best_member = -1, best_sk = 1;
   double best = 1e30;

@@ -32,6 +32,7 @@ void register_family_fp8(FamilyEntry* table);
 void register_family_int8emu(FamilyEntry* table);
 void register_family_6xbf16(FamilyEntry* table);
 void register_family_f16(FamilyEntry* table);
+void register_family_tf32(FamilyEntry* table);
 
 using GroupedLaunchFn = cudaError_t (*)(const GroupedParams& p, int grid, cudaStream_t s);
 
@@ -51,6 +52,7 @@ void register_grouped_fp8(GroupedEntry* table);
 void register_grouped_int8emu(GroupedEntry* table);
 void register_grouped_6xbf16(GroupedEntry* table);
 void register_grouped_f16(GroupedEntry* table);
+void register_grouped_tf32(GroupedEntry* table);
 
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.
@@ -59,6 +61,12 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx,
                               long long ldy, cudaStream_t s);
 cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,
                                uint16_t* lo, long long ldy, cudaStream_t s);
+// y = x rounded to TF32 (nearest, ties to even), kept as binary32.
+cudaError_t launch_convert_tf32(const float* x, int rows, int cols, long long ldx, float* y, long long ldy,
+                                cudaStream_t s);
+// y (cols x rows) = transpose of x rounded to TF32: B of the TF32 mode, K-major.
+cudaError_t launch_convert_tf32_t(const float* x, int rows, int cols, long long ldx, float* y, long long ldy,
+                                  cudaStream_t s);
 cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s);
 cudaError_t launch_int8_to_bf16(const int8_t* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,

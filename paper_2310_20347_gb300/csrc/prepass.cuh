@@ -107,6 +107,38 @@ __global__ void split3_bf16_kernel(const float* __restrict__ x, int rows, int co
   }
 }
 
+// TF32 round to nearest even on the encoding: add half an ulp of the 10-bit
+// fraction (plus one when the kept last bit is odd) and clear the 13 dropped
+// bits; a carry into the exponent rounds up to the next binade or to infinity.
+__device__ __forceinline__ float tf32_rne(float v) {
+  uint32_t u = __float_as_uint(v);
+  if ((u & 0x7F800000u) == 0x7F800000u) return __uint_as_float((u & 0x007FFFFFu) ? 0x7FC00000u : u);
+  u += 0x0FFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xFFFFE000u);
+}
+
+// y = tf32(x); 4 elements per thread step with 16-byte accesses when both
+// matrices' rows are 16-byte aligned (vec), else one by one.
+template <bool VEC>
+__global__ void convert_tf32_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                    float* __restrict__ y, long long ldy) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = x + r * ldx;
+    float* yr = y + r * ldy;
+    if (VEC) {
+      const int cols4 = cols >> 2;
+      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols4; c += gridDim.x * blockDim.x) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(xr) + c);
+        reinterpret_cast<float4*>(yr)[c] = make_float4(tf32_rne(a.x), tf32_rne(a.y), tf32_rne(a.z), tf32_rne(a.w));
+      }
+      if (blockIdx.x == 0)
+        for (int c = (cols4 << 2) + threadIdx.x; c < cols; c += blockDim.x) yr[c] = tf32_rne(xr[c]);
+    } else {
+      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) yr[c] = tf32_rne(xr[c]);
+    }
+  }
+}
+
 __global__ void convert_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
                                     uint16_t* __restrict__ y, long long ldy) {
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
@@ -176,7 +208,7 @@ __global__ void pack_rows_kernel(const uint8_t* __restrict__ x, int rows, long l
 // y (cols x rows, leading dimension ldy) := transpose of x (rows x cols,
 // leading dimension ldx), elements of type T, through a 32 x 33 shared tile so
 // that both the reads and the writes are coalesced.  Block (32, 8).
-template <typename T>
+template <typename T, bool ROUND_TF32 = false>
 __global__ void transpose_kernel(const T* __restrict__ x, int rows, int cols, long long ldx, T* __restrict__ y,
                                  long long ldy) {
   __shared__ T tile[32][33];
@@ -185,7 +217,10 @@ __global__ void transpose_kernel(const T* __restrict__ x, int rows, int cols, lo
     const int r0 = (int)(t / tc) * 32, c0 = (int)(t % tc) * 32;
     for (int i = threadIdx.y; i < 32; i += 8) {
       const int r = r0 + i, c = c0 + threadIdx.x;
-      if (r < rows && c < cols) tile[i][threadIdx.x] = x[(long long)r * ldx + c];
+      if (r < rows && c < cols) {
+        if constexpr (ROUND_TF32) tile[i][threadIdx.x] = __float_as_uint(tf32_rne(__uint_as_float(x[(long long)r * ldx + c])));
+        else tile[i][threadIdx.x] = x[(long long)r * ldx + c];
+      }
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += 8) {

@@ -56,7 +56,7 @@ namespace g3 {
 // the epilogue adds the chunks in int32.
 // TC_6XBF16: the FP32-accurate mode for small k: operands split in three
 // bfloat16 parts (hi + mid + lo), six products per k-step.
-enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3, TC_6XBF16 = 4, TC_F16 = 5 };
+enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3, TC_6XBF16 = 4, TC_F16 = 5, TC_TF32 = 6 };
 enum OutMode : int { OUT_F32 = 0, OUT_I32 = 1, OUT_PARTIAL = 2 };
 
 // Watchdog status codes (written to the device status word; see g3gemm.h).
@@ -118,19 +118,24 @@ struct GroupedParams {
 template <int MODE>
 struct TcTraits {
   static constexpr int kPlanes = (MODE == TC_3XBF16) ? 2 : (MODE == TC_6XBF16 ? 3 : 1);   // operand planes
-  static constexpr int kElem = (MODE == TC_FP8) ? 1 : 2;        // bytes per element
+  static constexpr int kElem = (MODE == TC_FP8) ? 1 : (MODE == TC_TF32 ? 4 : 2);   // bytes per element
   static constexpr int kBK = 128 / kElem;                        // k per block: one 128-B row
   static constexpr int kKStep = 32 / kElem;                      // k per MMA instruction
   static constexpr int kKSteps = kBK / kKStep;                   // = 4
   static constexpr int kBoxN = 128 / kElem;                      // n per TMA box of B
   static constexpr int kNBoxes = 128 / kBoxN;                    // boxes per 128-wide n tile
   static constexpr uint32_t kBtBytes = 128 * 128;                // 128 n x 128 bytes of k
-  // operand format code: 0 = E4M3 (kind::f8f6f4) or F16 (kind::f16), 1 = BF16
-  static constexpr uint32_t kAFmt = (MODE == TC_FP8 || MODE == TC_F16) ? 0u : 1u;
+  // operand format code: 0 = E4M3 (kind::f8f6f4) or F16 (kind::f16), 1 = BF16,
+  // 2 = TF32 (kind::tf32)
+  static constexpr uint32_t kAFmt = (MODE == TC_FP8 || MODE == TC_F16) ? 0u : (MODE == TC_TF32 ? 2u : 1u);
   // Leading byte offset of the MN-major Bt operand: the distance between its
   // 128-byte-wide n groups (one TMA box each).  With a single group (FP8) the
   // field is unused; 1024 keeps every address inside the stage either way.
   static constexpr uint32_t kBtLBO = (kNBoxes > 1) ? kBK * 128 : 1024;
+  // TF32 operands must be K-major on the tensor core (measured: an MN-major
+  // TF32 operand reads wrong elements): B arrives transposed (n x k) from the
+  // rounding pre-pass and its tile is staged like A's, 128 n-rows of 128 bytes.
+  static constexpr bool kBtKMajor = (MODE == TC_TF32);
 };
 
 template <int BM_T, int STAGES, int MODE, int CG = 1>
@@ -347,17 +352,21 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             uint8_t* at = bt + T::kBtBytes;
             const CUtensorMap* mb = S.map(j, 2 * pl + 1);
             const CUtensorMap* ma = S.map(j, 2 * pl);
-            if constexpr (kPair) {
+            if constexpr (T::kBtKMajor) {
+              // B stored n x k: one box of 128 n-rows x kBK k
+              if constexpr (kPair) tma_load_2d_pair(bt, mb, k0, j.n0, full_c);
+              else tma_load_2d(bt, mb, k0, j.n0, &full[stage]);
+            } else if constexpr (kPair) {
 #pragma unroll
               for (int h = 0; h < T::kNBoxes; ++h)
                 tma_load_2d_pair(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, full_c);
-              tma_load_2d_pair(at, ma, k0, a_row, full_c);
             } else {
 #pragma unroll
               for (int h = 0; h < T::kNBoxes; ++h)
                 tma_load_2d(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, &full[stage]);
-              tma_load_2d(at, ma, k0, a_row, &full[stage]);
             }
+            if constexpr (kPair) tma_load_2d_pair(at, ma, k0, a_row, full_c);
+            else tma_load_2d(at, ma, k0, a_row, &full[stage]);
           }
         }
       }
@@ -384,7 +393,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       };
       for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
         const TileJob j = S.tile(t);
-        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/true, /*b_mn=*/false, 128 * CG, j.bm);
+        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/!T::kBtKMajor, /*b_mn=*/false, 128 * CG, j.bm);
         const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
         for (int c0 = j.kb0; ok && c0 < j.kb1; c0 += span, ++lt) {
         const int c1 = min(j.kb1, c0 + span);
@@ -404,9 +413,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             // MN-major Bt: a k-step is kKStep whole 128-byte rows (kKStep/8 atoms);
             // LBO = distance between 64-/128-wide n boxes, SBO = 8 rows.
             // K-major A: a k-step is 32 bytes inside the swizzled 128-byte row.
-            const uint32_t bt_off = ks * T::kKStep * 128;
+            const uint32_t bt_off = T::kBtKMajor ? ks * 32 : ks * T::kKStep * 128;
             const uint32_t a_off = T::kBtBytes + ks * 32;
-            const uint64_t bt_hi = smem_desc_sw128(st + bt_off, T::kBtLBO, 1024);
+            const uint64_t bt_hi = T::kBtKMajor ? smem_desc_sw128(st + bt_off, 16, 1024)
+                                                : smem_desc_sw128(st + bt_off, T::kBtLBO, 1024);
             const uint64_t a_hi = smem_desc_sw128(st + a_off, 16, 1024);
             if (MODE == TC_3XBF16) {
               const uint32_t lo = Cfg::kPlaneBytes;
@@ -433,6 +443,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
               mma_f16<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else if (MODE == TC_FP8) {
               mma_f8<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
+            } else if (MODE == TC_TF32) {
+              mma_tf32<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else {
               mma_f16<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             }

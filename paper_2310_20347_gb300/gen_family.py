@@ -6,7 +6,7 @@ search that keeps the best member per problem shape (Section 8.4).  This
 script plays the generator's role for the GPU kernels: it enumerates the
 parameter space
 
-    mode     bf16 | f16 | 3xbf16 | 6xbf16 | fp8 | int8emu   operand format of the MMA
+    mode     bf16 | f16 | tf32 | 3xbf16 | 6xbf16 | fp8 | int8emu   operand format of the MMA
     bm       64 | 128 | 256           output rows per tile = MMA N
     cg       1 | 2                    CTAs per MMA: one SM (tile bm x 128), or a
                                       CTA pair on two SMs (tile bm x 256, each CTA
@@ -43,9 +43,10 @@ MODES = {            # name: (planes, element bytes)
     "int8emu": (1, 2),   # exact int8 on the BF16 path, k accumulated in chunks of <= 1024
     "6xbf16": (3, 2),    # FP32-accurate, three-part split, 6 products: used for small k
     "f16": (1, 2),       # IEEE binary16 operands on kind::f16
+    "tf32": (1, 4),      # TF32 operands (binary32 storage) on kind::tf32
 }
 MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8", "int8emu": "TC_I8EMU",
-             "6xbf16": "TC_6XBF16", "f16": "TC_F16"}
+             "6xbf16": "TC_6XBF16", "f16": "TC_F16", "tf32": "TC_TF32"}
 SPLIT_MODES = ("3xbf16", "6xbf16")   # two accumulators per tile (main + corrections)
 BMS = (256, 128, 64)
 # int8emu keeps one int32 running sum per row of its column in registers, or,

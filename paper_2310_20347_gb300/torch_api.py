@@ -7,11 +7,12 @@ from __future__ import annotations
 import torch
 
 from . import _lib
-from ._lib import G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, check
+from ._lib import G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, check
 
 _ELEM = {G3_F32: (torch.float32, torch.float32), G3_F32_3XBF16: (torch.float32, torch.float32),
          G3_BF16: (torch.bfloat16, torch.float32), G3_FP8_E4M3: (torch.uint8, torch.float32),
-         G3_INT8: (torch.int8, torch.int32), G3_FP16: (torch.float16, torch.float32)}
+         G3_INT8: (torch.int8, torch.int32), G3_FP16: (torch.float16, torch.float32),
+         G3_TF32: (torch.float32, torch.float32)}
 
 
 def _stream(stream):
@@ -89,6 +90,13 @@ def convert_bf16(x: torch.Tensor, stream=None) -> torch.Tensor:
     y = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
     check(_lib.g3_convert_bf16(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), y.data_ptr(),
                                max(x.shape[1], 1), _stream(stream)), "g3_convert_bf16")
+    return y
+
+
+def convert_tf32(x: torch.Tensor, stream=None) -> torch.Tensor:
+    y = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    check(_lib.g3_convert_tf32(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), y.data_ptr(),
+                               max(x.shape[1], 1), _stream(stream)), "g3_convert_tf32")
     return y
 
 

@@ -3,7 +3,7 @@ configuration the benchmark times (the planner's member and split), checked on
 sampled rows of C that the oracle computes in binary64 (int64 for INT8):
 
   FP32-accurate 16384^3 (alpha 1, beta 0.5, uniform [-1, 1], seed 0)  gate 2e-6
-  BF16 / FP16 / FP8 / INT8 8192^3                 8e-3 / 2e-3 / 6e-2 / bit-exact
+  BF16 / FP16 / TF32 / FP8 / INT8 8192^3          8e-3 / 2e-3 / 2e-3 / 6e-2 / bit-exact
   the 20 im2col layer shapes (batch 16) in BF16    kernel check 1e-5, gate 8e-3
   the 1000-problem grouped batches (BF16 and FP32-accurate), every 25th
   problem checked in full
@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2310_20347_gb300 import G3_BF16, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, synth, torch_api
+from paper_2310_20347_gb300 import G3_BF16, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, synth, torch_api
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_fp32_accurate_16384_cubed():
     assert e <= 2e-6
 
 
-@pytest.mark.parametrize("kind", ["bf16", "fp16", "fp8", "int8"])
+@pytest.mark.parametrize("kind", ["bf16", "fp16", "tf32", "fp8", "int8"])
 def test_dtype_8192_cubed(kind):
     n = 8192
     rows = np.array([0, 77, n // 2, n - 1])
@@ -62,6 +62,9 @@ def test_dtype_8192_cubed(kind):
         tol = 8e-3
     elif kind == "fp16":
         torch_api.gemm(A32.half(), B32.half(), C, 1.0, 0.0, dtype=G3_FP16)
+        tol = 2e-3
+    elif kind == "tf32":
+        torch_api.gemm(A32, B32, C, 1.0, 0.0, dtype=G3_TF32)
         tol = 2e-3
     else:
         (A, sa), (B, sb) = torch_api.quantize_fp8(A32), torch_api.quantize_fp8(B32)

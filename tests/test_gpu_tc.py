@@ -17,8 +17,8 @@ import torch
 
 import oracle
 from gpu_util import check_guard, dev, guarded, rel_err
-from paper_2310_20347_gb300 import (G3_BF16, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, _lib, gen_family,
-                                    synth, torch_api)
+from paper_2310_20347_gb300 import (G3_BF16, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib,
+                                    gen_family, synth, torch_api)
 
 pytestmark = pytest.mark.gpu
 
@@ -276,6 +276,53 @@ def test_fp16_every_member(config):
 
 def test_fp16_split_k():
     f16_check(synth.uniform_problem(96, 200, 3000, seed=28, beta=1.0), split_k=3)
+
+
+# ---------------------------------------------------------------- TF32
+def test_tf32_conversion_matches_oracle():
+    r = np.random.default_rng(29)
+    bits = r.integers(0, 1 << 32, 300000, dtype=np.uint64).astype(np.uint32)
+    bits[:4096] = (bits[:4096] & 0xFFFFE000) | 0x1000          # exact ties
+    bits[4096:8192] &= 0x80001FFF                              # subnormals
+    bits[8192:8200] = [0x7F7FF000, 0xFF7FF000, 0x7F800000, 0xFF800000, 0x7FC00000, 0x7F800001, 0, 0x80000000]
+    x = bits.view(np.float32).reshape(300, 1000)
+    got = torch_api.convert_tf32(torch.from_numpy(x.copy()).cuda()).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), oracle.round_tf32(x).view(np.uint32))
+
+
+def tf32_check(p, config=-1, split_k=0):
+    full, C = guarded(p.m, p.n, p.C)
+    torch_api.gemm(dev(p.A), dev(p.B), C, p.alpha, p.beta, dtype=G3_TF32, config=config, split_k=split_k)
+    torch.cuda.synchronize()
+    check_guard(full, p.m, p.n)
+    got = C.cpu().numpy()
+    bc = None if p.C is None else p.beta * p.C.astype(np.float64)
+    Aq, Bq = oracle.round_tf32(p.A), oracle.round_tf32(p.B)
+    e_k = rel_err(got, oracle.gemm(Aq, Bq, p.C, p.alpha, p.beta), oracle.absprod(Aq, Bq, p.alpha), bc)
+    e_g = rel_err(got, oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), oracle.absprod(p.A, p.B, p.alpha), bc)
+    assert e_k <= 1e-5, ("kernel", e_k)
+    assert e_g <= 2e-3, ("gate", e_g)   # two roundings to TF32 (2^-11 each)
+    return e_k, e_g
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tf32_shapes(shape):
+    m, n, k = shape
+    tf32_check(synth.uniform_problem(m, n, k, seed=31, alpha=-0.5, beta=0.5))
+
+
+@pytest.mark.parametrize("config", members("tf32"))
+def test_tf32_every_member(config):
+    tf32_check(synth.uniform_problem(300, 520, 700, seed=32, beta=0.0), config=config)
+
+
+def test_tf32_split_k_and_integers_exact():
+    tf32_check(synth.uniform_problem(96, 200, 3000, seed=33, beta=1.0), split_k=3)
+    p = synth.small_int_problem(200, 150, 600, seed=34, alpha=1.0, beta=1.0)
+    C = dev(p.C)
+    torch_api.gemm(dev(p.A), dev(p.B), C, 1.0, 1.0, dtype=G3_TF32)
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), oracle.gemm(p.A, p.B, p.C, 1.0, 1.0))
 
 
 # ---------------------------------------------------------------- FP8
