@@ -190,21 +190,45 @@ struct Plan {
   int raster = 8;
 };
 
-// Relative throughput of a member.  Measured on GB300 (BF16 8192^3 and the
-// FP32-accurate 16384^3), one k-block of a tile costs about
-//   max(MMA time, L / stages)
-// clocks: the MMA time is 73 clocks per MMA of 128 x 128 x 16 (x 2 with N = 256),
-// times the products per k-step; L (about 3000 clocks for one CTA, 4000 for a
-// CTA pair, whose stages complete only when both CTAs' loads have landed) is
-// the load latency that the shared-memory ring must cover.  N = 128 members of
-// one product therefore stay near 0.6 of peak at any ring depth, N = 256 reach
-// 0.86 (one CTA) and 0.96 (pair), and the 3-product members are MMA-bound.
+// Clocks one k-block of a tile costs a member, measured on GB300: the MMA
+// time (73 clocks per MMA of 128 x 128 x 16, x 2 for N = 256, times the
+// products per k-step), the shared-memory fill (about 64 bytes per clock per
+// SM), or the load latency the ring must cover (about 3000 clocks for one
+// CTA, 4400 for a CTA pair, whose stages complete only when both CTAs' loads
+// have landed) spread over its stages -- whichever is largest; a two-stage
+// ring exposes part of every refill.
+double kblock_clocks(const FamilyEntry& f) {
+  const int products = f.mode == TC_3XBF16 ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
+  const double mma = 4.0 * products * 73.0 * f.bm / 128.0;
+  const double stage_bytes = (double)(f.smem - 1024 - 2 * 32 * 128 * 4 - 256) / f.stages;
+  const double fill = stage_bytes / 64.0;
+  const double lat = (f.cg > 1 ? 4400.0 : 3000.0) / f.stages;
+  double t = std::max(mma, std::max(fill, lat));
+  if (f.stages <= 2) t *= 1.07;
+  return t;
+}
+
+// Fraction of the tensor peak a member sustains in its main loop.
 double tile_efficiency(const FamilyEntry& f) {
   const int products = f.mode == TC_3XBF16 ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
   const double mma = 4.0 * products * 73.0 * f.bm / 128.0;
-  const double lat = (f.cg > 1 ? 4000.0 : 3000.0) / f.stages;
-  return std::min(0.97, mma / std::max(mma, lat));
+  return std::min(0.97, mma / kblock_clocks(f));
 }
+
+// Slow-down of a member whose single accumulator set makes the MMA wait for
+// each tile's epilogue: epilogue time over main-loop time of one tile (the
+// epilogue reads and writes its bm x 128 block of C at about 45 bytes per ns
+// per SM, plus ~2 us of TMEM and barrier latency).  The exact-integer members
+// with sums in TMEM wait at every 1024-product chunk instead (measured 0.74 of
+// the 0.96 their tile reaches without chunks).
+double single_buffer_factor(const FamilyEntry& f, int num_kb) {
+  if (f.bufs >= 2) return 1.0;
+  if (f.mode == TC_I8EMU) return 1.3;
+  const double t_tile_ns = num_kb * kblock_clocks(f) / 1.9;
+  const double t_epi_ns = f.bm * 128.0 * 8.0 / 45.0 + 2000.0;
+  return 1.0 + t_epi_ns / std::max(t_tile_ns, 1.0);
+}
+
 
 // ---------------------------------------------------------------- tuning cache
 // Results of g3_autotune, keyed by dtype and the power-of-two bucket of each of
@@ -284,10 +308,8 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
       const long long tiles = ((m + f.bm - 1) / f.bm) * ((n + 128LL * f.cg - 1) / (128LL * f.cg));
       const long long slots = std::max(1, sms / f.cg);   // tiles in flight at once
       const long long waves = (tiles + slots - 1) / slots;
-      // a single accumulator set serialises every tile's epilogue with the
-      // next tile's main loop (measured: 71% vs 90% of peak at 16384^3)
       // (pairs: 2% for the cluster set-up, so that ties go to the single CTA)
-      const double cost = (double)waves * f.bm / tile_efficiency(f) * (f.bufs < 2 ? 1.3 : 1.0) *
+      const double cost = (double)waves * f.bm / tile_efficiency(f) * single_buffer_factor(f, pl.num_kb) *
                           (f.cg > 1 ? 1.02 : 1.0);
       if (cost < best * 0.999) {
         best = cost;

@@ -570,9 +570,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.n + col
                               : static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
             const bool add_c = !partial && beta != 0.0f;
+            int cv[32];   // the reads of C first: one memory round trip
+#pragma unroll
+            for (int i = 0; i < 32; ++i) cv[i] = (add_c && i < iend) ? cp[i * ld] : 0;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (i < iend) cp[i * ld] = add_c ? cp[i * ld] + static_cast<int>(rs[i]) : static_cast<int>(rs[i]);
+              if (i < iend) cp[i * ld] = cv[i] + static_cast<int>(rs[i]);
           }
         }
         if (!last) tmem_st_wait();
@@ -652,9 +655,13 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           if (e.out_mode == OUT_F32) {
             float* cp = static_cast<float*>(e.C) + (long long)i0 * e.ldc + col;
             if (beta != 0.0f) {
+              // all 32 reads of C first (one memory round trip), then the stores
+              float cv[32];
+#pragma unroll
+              for (int i = 0; i < 32; ++i) cv[i] = (i < iend) ? cp[i * e.ldc] : 0.0f;
 #pragma unroll
               for (int i = 0; i < 32; ++i)
-                if (i < iend) cp[i * e.ldc] = fmaf(alpha, __uint_as_float(r[i]), beta * cp[i * e.ldc]);
+                if (i < iend) cp[i * e.ldc] = fmaf(alpha, __uint_as_float(r[i]), beta * cv[i]);
             } else {
 #pragma unroll
               for (int i = 0; i < 32; ++i)
@@ -662,13 +669,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             }
           } else if (e.out_mode == OUT_I32) {
             int* cp = static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
+            int cv[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              if (i < iend) {
-                const int v = __float2int_rn(__uint_as_float(r[i]));
-                cp[i * e.ldc] = (beta != 0.0f) ? (cp[i * e.ldc] + v) : v;
-              }
-            }
+            for (int i = 0; i < 32; ++i) cv[i] = (beta != 0.0f && i < iend) ? cp[i * e.ldc] : 0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < iend) cp[i * e.ldc] = cv[i] + __float2int_rn(__uint_as_float(r[i]));
           } else {
             float* pp = e.partial + (long long)i0 * e.n + col;
 #pragma unroll

@@ -104,9 +104,13 @@ def test_planner_choices(lib):
     from paper_2310_20347_gb300 import gen_family
     fam = gen_family.enumerate_family()
     L = lib
-    # large square: the widest tile whose accumulators are double-buffered
+    # large square, FP32-accurate: the 256 x 256 CTA-pair tile (its single
+    # accumulator set costs little against 256 k-blocks of main loop)
     st, cfg, sk, rs = L.g3_plan_query(16384, 16384, 16384, L.G3_F32_3XBF16)
-    assert st == 0 and fam[cfg]["mode"] == "3xbf16" and fam[cfg]["bm"] == 128 and sk == 1
+    assert st == 0 and fam[cfg]["mode"] == "3xbf16" and fam[cfg]["bm"] == 256 and fam[cfg]["cg"] == 2 and sk == 1
+    # BF16 8192^3: the 256 x 256 CTA pair with double-buffered accumulators
+    st, cfg, sk, rs = L.g3_plan_query(8192, 8192, 8192, L.G3_BF16)
+    assert fam[cfg]["bm"] == 256 and fam[cfg]["cg"] == 2 and fam[cfg]["tmem_bufs"] == 2
     # Cout = 64 convolution layer: a 64-row tile, no split
     st, cfg, sk, rs = L.g3_plan_query(64, 200704, 147, L.G3_BF16)
     assert fam[cfg]["bm"] == 64 and sk == 1
