@@ -125,7 +125,7 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def cpu_oracle_sample(p, target_s=12.0, max_rows=512):
+def cpu_oracle_sample(p, target_s=12.0, max_rows=4096):
     """Time the binary64 oracle on a bounded sample: whole rows of C."""
     import oracle
     A64 = p.A.astype(np.float64)
