@@ -58,6 +58,7 @@ def _load():
             lib.oracle_round_bf16.argtypes = [ctypes.c_float]
             lib.oracle_round_bf16.restype = ctypes.c_float
             lib.oracle_round_bf16_array.argtypes = [vp, vp, i64]
+            lib.oracle_conv2d_nhwc_f64.argtypes = [i64] * 13 + [dbl, vp, vp, dbl, vp, vp, i32]
             lib.oracle_round_tf32.argtypes = [ctypes.c_float]
             lib.oracle_round_tf32.restype = ctypes.c_float
             lib.oracle_round_tf32_array.argtypes = [vp, vp, i64]
@@ -205,6 +206,27 @@ def round_bf16(x):
     y = np.empty_like(x)
     _load().oracle_round_bf16_array(_ptr(x), _ptr(y), x.size)
     return y
+
+
+def conv_out_size(H, R, stride, pad, dil=1):
+    return (H + 2 * pad - dil * (R - 1) - 1) // stride + 1
+
+
+def conv2d_nhwc(x, w, stride=(1, 1), pad=(0, 0), dil=(1, 1), y=None, alpha=1.0, beta=0.0, nthreads=0):
+    """beta*y + alpha*conv2d(x, w) in binary64 (Section 8.1's convolution layers):
+    x is N x H x W x C, w is R x S x C x K; returns N x P x Q x K."""
+    x = _c(x, np.float64)
+    w = _c(w, np.float64)
+    N, H, W, C = x.shape
+    R, S, C2, K = w.shape
+    assert C == C2
+    P = conv_out_size(H, R, stride[0], pad[0], dil[0])
+    Q = conv_out_size(W, S, stride[1], pad[1], dil[1])
+    yin = _c(y, np.float64) if (y is not None and beta != 0.0) else None
+    out = np.empty((N, P, Q, K), np.float64)
+    _load().oracle_conv2d_nhwc_f64(N, H, W, C, K, R, S, stride[0], stride[1], pad[0], pad[1], dil[0], dil[1],
+                                   float(alpha), _ptr(x), _ptr(w), float(beta), _ptr(yin), _ptr(out), int(nthreads))
+    return out
 
 
 def round_tf32(x):

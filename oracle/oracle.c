@@ -160,6 +160,39 @@ void oracle_round_bf16_array(const float* x, float* y, int64_t count) {
     for (int64_t i = 0; i < count; ++i) y[i] = oracle_round_bf16(x[i]);
 }
 
+void oracle_conv2d_nhwc_f64(int64_t N, int64_t H, int64_t W, int64_t C, int64_t K, int64_t R, int64_t S,
+                            int64_t str_h, int64_t str_w, int64_t pad_h, int64_t pad_w, int64_t dil_h,
+                            int64_t dil_w, double alpha, const double* x, const double* w, double beta,
+                            const double* y_in, double* y_out, int nthreads) {
+    const int64_t P = (H + 2 * pad_h - dil_h * (R - 1) - 1) / str_h + 1;
+    const int64_t Q = (W + 2 * pad_w - dil_w * (S - 1) - 1) / str_w + 1;
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for num_threads(nthreads) collapse(2) schedule(dynamic)
+    for (int64_t n = 0; n < N; ++n) {
+        for (int64_t p = 0; p < P; ++p) {
+            for (int64_t q = 0; q < Q; ++q) {
+                double* out = y_out + ((n * P + p) * Q + q) * K;
+                for (int64_t k = 0; k < K; ++k) out[k] = 0.0;
+                for (int64_t r = 0; r < R; ++r) {
+                    const int64_t h = p * str_h - pad_h + r * dil_h;
+                    if (h < 0 || h >= H) continue;
+                    for (int64_t s = 0; s < S; ++s) {
+                        const int64_t v = q * str_w - pad_w + s * dil_w;
+                        if (v < 0 || v >= W) continue;
+                        const double* xp = x + ((n * H + h) * W + v) * C;
+                        const double* wp = w + (r * S + s) * C * K;
+                        for (int64_t c = 0; c < C; ++c)
+                            for (int64_t k = 0; k < K; ++k) out[k] += xp[c] * wp[c * K + k];
+                    }
+                }
+                const double* yin = y_in ? y_in + ((n * P + p) * Q + q) * K : NULL;
+                for (int64_t k = 0; k < K; ++k)
+                    out[k] = alpha * out[k] + (yin && beta != 0.0 ? beta * yin[k] : 0.0);
+            }
+        }
+    }
+}
+
 /* TF32 rounding written from the number grid: q = x / spacing rounded to the
  * nearest integer (rint: ties to even in the default rounding mode), then
  * q * spacing; both steps are exact in binary64. */

@@ -59,6 +59,20 @@ void oracle_gemm_rows_i8_i64(int64_t nrows, const int64_t* rows, int64_t n, int6
                              const int32_t* C_in, int64_t ldc_in,
                              int64_t* C_out, int64_t ldc_out, int nthreads);
 
+/* --- Convolution --------------------------------------------------------------
+ * y := beta*y + alpha*conv(x, w), the convolution layers the paper casts to
+ * GEMM (Section 8.1, Table 1), by its definition: x is N x H x W x C (NHWC),
+ * w is R x S x C x K, y is N x P x Q x K with P = (H + 2*pad_h - dil_h*(R-1)
+ * - 1) / str_h + 1 (Q likewise) and
+ *   y[n][p][q][k] = sum over r, s, c of x[n][p*str_h - pad_h + r*dil_h]
+ *                                      [q*str_w - pad_w + s*dil_w][c] * w[r][s][c][k],
+ * input positions outside the image contributing zero.  Sums in binary64 in
+ * the order r, s, c.  Threads over (n, p).                                   */
+void oracle_conv2d_nhwc_f64(int64_t N, int64_t H, int64_t W, int64_t C, int64_t K, int64_t R, int64_t S,
+                            int64_t str_h, int64_t str_w, int64_t pad_h, int64_t pad_w, int64_t dil_h,
+                            int64_t dil_w, double alpha, const double* x, const double* w, double beta,
+                            const double* y_in, double* y_out, int nthreads);
+
 /* --- Number formats ---------------------------------------------------------
  * bfloat16: 1 sign, 8 exponent, 7 fraction bits (the top half of a binary32).
  * Round to nearest, ties to even; overflow gives +-Inf; NaN gives the quiet

@@ -31,6 +31,20 @@ RESNET50_TABLE1 = (
     (19, 6272, 2048, 1024), (20, 6272, 512, 2048),
 )
 
+# The convolution behind each Table 1 layer (ResNet-50 v1.5, square inputs):
+# input size H (= W), input channels C, output channels K, filter R x R,
+# stride, padding.  Table 1 fixes m / 128 = Hout^2, n = K and k = C R^2; the
+# input size and stride follow from where the layer sits in the network (the
+# stride-2 3x3 convolutions and 1x1 downsampling projections halve the size).
+RESNET50_CONV = tuple(dict(layer=l, H=h, C=c, K=kk, R=r, stride=st, pad=pd) for (l, h, c, kk, r, st, pd) in (
+    (1, 224, 3, 64, 7, 2, 3), (2, 56, 64, 64, 1, 1, 0), (3, 56, 64, 64, 3, 1, 1),
+    (4, 56, 64, 256, 1, 1, 0), (5, 56, 256, 64, 1, 1, 0), (6, 56, 256, 128, 1, 1, 0),
+    (7, 56, 128, 128, 3, 2, 1), (8, 28, 128, 512, 1, 1, 0), (9, 56, 256, 512, 1, 2, 0),
+    (10, 28, 512, 128, 1, 1, 0), (11, 28, 512, 256, 1, 1, 0), (12, 28, 256, 256, 3, 2, 1),
+    (13, 14, 256, 1024, 1, 1, 0), (14, 28, 512, 1024, 1, 2, 0), (15, 14, 1024, 256, 1, 1, 0),
+    (16, 14, 1024, 512, 1, 1, 0), (17, 14, 512, 512, 3, 2, 1), (18, 7, 512, 2048, 1, 1, 0),
+    (19, 14, 1024, 2048, 1, 2, 0), (20, 7, 2048, 512, 1, 1, 0)))
+
 # Three batch-1 layers used as named examples of the convolution workload.
 IM2COL_BATCH1_EXAMPLES = ((64, 12544, 147), (256, 3136, 576), (2048, 49, 1024))
 
