@@ -235,6 +235,28 @@ def _kernel_ms(lib, fn, reps, flush):
     return ms / max(n, 1)
 
 
+def _rotating_graph_ms(calls, nrep):
+    """Mean device time per call of `calls` (one per rotating operand set, each
+    already run once) issued back to back from a CUDA graph."""
+    import torch
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(gs):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            for i in range(nrep):
+                calls[i % len(calls)]()
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / nrep
+
+
 def _call_ms(fn, reps, flush):
     """Mean device time of whole calls (all their launches), L2 flushed between."""
     import torch
@@ -516,6 +538,70 @@ def run_workload(args):
                             "algorithmic": "2 n^3 per call (INT8: of the main kernel's bf16 work)"}})
         return
 
+    if args.workload == "conv":
+        # the Table 1 layers with C % 64 == 0 as implicit-GEMM convolutions
+        # (NHWC bf16 activations, RSCK weights, NPQK fp32 output), batch 16
+        per, tot_ms, tot_kms, tot_bytes, tot_flops, worst = [], 0.0, 0.0, 0.0, 0.0, 0.0
+        for geo in synth.RESNET50_CONV:
+            if geo["C"] % 64 or (args.only and f"L{geo['layer']}" not in args.only.split(",")):
+                continue
+            H, C, K, R, st, pd = geo["H"], geo["C"], geo["K"], geo["R"], geo["stride"], geo["pad"]
+            rng = np.random.default_rng(geo["layer"])
+            xh = rng.standard_normal((16, H, H, C)).astype(np.float32)
+            wh = (rng.standard_normal((R, R, C, K)) / np.sqrt(R * R * C)).astype(np.float32)
+            x = torch.from_numpy(xh).to(dev).to(torch.bfloat16)
+            w = torch.from_numpy(wh).to(dev).to(torch.bfloat16)
+            P = (H + 2 * pd - R) // st + 1
+            y = torch.empty(16, P, P, K, dtype=torch.float32, device=dev)
+            fn = lambda: torch_api.conv2d(x, w, y, (st, st), (pd, pd))
+            fn()
+            torch.cuda.synchronize()
+            xq, wq = x[:1].float().cpu().numpy(), w.float().cpu().numpy()
+            want = oracle.conv2d_nhwc(xq, wq, (st, st), (pd, pd))[0]
+            D = oracle.conv2d_nhwc(np.abs(xq), np.abs(wq), (st, st), (pd, pd))[0]
+            err = float(np.max(np.abs(y[0].cpu().numpy() - want) / np.maximum(D, 1e-300)))
+            flops = 2.0 * 16 * P * P * K * R * R * C
+            nbytes = 2.0 * (16 * H * H * C + R * R * C * K) + 4.0 * 16 * P * P * K
+            # rotating operand sets (together >= 512 MiB, 4x L2) replayed back to
+            # back from a CUDA graph, as the layers of a captured network run
+            sets = max(1, min(64, -(-(512 << 20) // int(nbytes))))
+            copies = [(x.clone(), w.clone(), torch.empty_like(y)) for _ in range(sets - 1)] + [(x, w, y)]
+            calls = [lambda a=a, b=b, c=c: torch_api.conv2d(a, b, c, (st, st), (pd, pd)) for a, b, c in copies]
+            for c_ in calls:
+                c_()
+            torch.cuda.synchronize()
+            nrep = max(args.reps, 2 * sets)
+            ms = _rotating_graph_ms(calls, nrep)
+            kms = _kernel_ms(_lib, fn, args.reps, flush)
+            cold_ms = _call_ms(fn, 5, flush)
+            del copies, calls
+            cfg = _lib.g3_plan_query(16 * P * P, K, R * R * C, G3_BF16)
+            per.append({"layer": geo["layer"], "N": 16, "H": H, "C": C, "K": K, "R": R, "stride": st, "pad": pd,
+                        "ms": ms, "kernel_ms": kms, "cold_call_ms": cold_ms, "rotating_sets": sets,
+                        "tflops": flops / ms / 1e9, "gbs": nbytes / ms / 1e6,
+                        "hbm_frac": nbytes / ms / 1e6 / hbm, "member": _lib.g3_family_describe(cfg[1]),
+                        "split_k": cfg[2], "err": err})
+            tot_ms += ms
+            tot_kms += kms
+            tot_bytes += nbytes
+            tot_flops += flops
+            worst = max(worst, err)
+            del x, w, y
+        _line(args, tot_flops / tot_ms / 1e9, "TFLOPS",
+              {"workload": "19 ResNet-50 v1.5 convolution layers of Table 1 (C % 64 == 0), batch 16, as "
+                           "implicit GEMMs (TMA im2col loads of NHWC bf16 activations, no im2col matrix), "
+                           "fp32 NHWC output; whole calls back to back, replayed from a CUDA graph (ms); "
+                           "kernel_ms: the GEMM kernel alone (CUDA events, eager, L2 flushed)",
+               "l2": "rotating operand copies, together >= 512 MiB (4x L2), per layer; cold_call_ms: one call "
+                     "after a 256 MiB L2 flush"},
+              {"dtype": "bf16", "total_ms": tot_ms, "total_kernel_ms": tot_kms, "worst_err": worst,
+               "roofline": {"bound": "hbm", "achieved": tot_bytes / tot_ms / 1e6, "peak": hbm, "unit": "GB/s",
+                            "frac": tot_bytes / tot_ms / 1e6 / hbm, "traffic": None,
+                            "peak_source": f"{peak_src} hbm_gbs",
+                            "algorithmic": "activations and weights read once (2 B), output written once (4 B)"},
+               "per_layer": per})
+        return
+
     if args.workload in ("grouped", "grouped-3xbf16"):
         dt = G3_BF16 if args.workload == "grouped" else G3_F32_3XBF16
         shapes = synth.grouped_shapes(1000, seed=0)
@@ -604,7 +690,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32",
+                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "conv",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

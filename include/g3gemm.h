@@ -110,6 +110,21 @@ G3_API int g3_gemm(int64_t m, int64_t n, int64_t k, double alpha, const void* A,
 G3_API int g3_gemm_host(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B,
                         int64_t ldb, double beta, void* C, int64_t ldc, int dtype, void* cuda_stream);
 
+/* Convolution as an implicit GEMM (the convolution layers the paper casts to
+ * GEMM, Section 8.1 / Table 1), without a materialised im2col matrix:
+ *   y[n][p][q][k] := beta*y + alpha * sum over r, s, c of
+ *       x[n][p*stride_h - pad_h + r*dil_h][q*stride_w - pad_w + s*dil_w][c] * w[r][s][c][k]
+ * x: device N x H x W x C (NHWC), w: device R x S x C x K, both BF16 or FP16
+ * (dtype G3_BF16 / G3_FP16, raw 16-bit patterns; x 16-byte aligned); y:
+ * device float32 N x P x Q x K with P = (H + 2 pad_h - dil_h (R-1) - 1) /
+ * stride_h + 1 (Q likewise).  Input positions outside the image count as
+ * zero.  It is the GEMM m = N P Q, n = K, k = R S C with A read through a TMA
+ * im2col tensor map.  Requires C a multiple of 64, strides 1..8, paddings
+ * 0..128; otherwise G3_ERR_UNSUPPORTED.  -101 / -105: bad sizes.          */
+G3_API int g3_conv2d(int64_t N, int64_t H, int64_t W, int64_t C, int64_t K, int64_t R, int64_t S, int64_t stride_h,
+                     int64_t stride_w, int64_t pad_h, int64_t pad_w, int64_t dil_h, int64_t dil_w, double alpha,
+                     const void* x, const void* w, double beta, float* y, int dtype, void* cuda_stream);
+
 /* Set the stream later calls without an explicit stream use (a cudaStream_t;
  * NULL = legacy default stream).  The setting is per process.             */
 G3_API int g3_set_stream(void* cuda_stream);

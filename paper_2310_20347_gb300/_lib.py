@@ -24,7 +24,7 @@ G3_OK, G3_ERR_ARG, G3_ERR_UNSUPPORTED, G3_ERR_CUDA, G3_ERR_NOMEM, G3_ERR_TIMEOUT
 
 # Every symbol include/g3gemm.h declares (checked against the header by the tests).
 EXPORTED = (
-    "g3_gemm", "g3_gemm_host", "g3_set_stream", "g3_gemm_args_init", "g3_gemm_ex", "g3_gemm_workspace_size",
+    "g3_gemm", "g3_gemm_host", "g3_conv2d", "g3_set_stream", "g3_gemm_args_init", "g3_gemm_ex", "g3_gemm_workspace_size",
     "g3_convert_bf16", "g3_convert_tf32", "g3_split_bf16", "g3_split3_bf16", "g3_quantize_fp8",
     "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         sig = {
             "g3_gemm": ([i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32], i32),
             "g3_gemm_host": ([i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp], i32),
+            "g3_conv2d": ([i64] * 13 + [dbl, vp, vp, dbl, vp, i32, vp], i32),
             "g3_set_stream": ([vp], i32),
             "g3_gemm_args_init": ([ctypes.POINTER(g3_gemm_args)], None),
             "g3_gemm_ex": ([ctypes.POINTER(g3_gemm_args), vp], i32),
@@ -125,6 +126,12 @@ def check(status: int, what: str = "") -> int:
 
 def g3_gemm(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, dtype) -> int:
     return load().g3_gemm(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, dtype)
+
+
+def g3_conv2d(N, H, W, C, K, R, S, stride_h, stride_w, pad_h, pad_w, dil_h, dil_w, alpha, x, w, beta, y, dtype,
+              stream=None) -> int:
+    return load().g3_conv2d(N, H, W, C, K, R, S, stride_h, stride_w, pad_h, pad_w, dil_h, dil_w, alpha, x, w, beta,
+                            y, dtype, stream)
 
 
 def g3_gemm_host(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, dtype, stream=None) -> int:

@@ -120,6 +120,51 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+using EncodeIm2colFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const int*, const int*, cuuint32_t, cuuint32_t,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeIm2colFn encode_im2col_fn() {
+  static EncodeIm2colFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeIm2col", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeIm2colFn) nullptr;
+    }
+    return reinterpret_cast<EncodeIm2colFn>(p);
+  }();
+  return fn;
+}
+
+// Geometry of an implicit-GEMM convolution (g3_conv2d).
+struct ConvDesc {
+  int64_t N, H, W, C, K, R, S, sh, sw, ph, pw, dh, dw, P, Q;
+};
+
+// The NHWC activation tensor as a 4-D im2col tensor map (dims C, W, H, N): a
+// load walks `pixels` output positions -- base positions from (-pad) in steps
+// of the stride, inside the box that ends where the last filter tap still
+// overlaps the padded image -- and reads 64 channels of each.
+int encode_im2col(CUtensorMap* map, const void* x, int esize, const ConvDesc& c, uint32_t pixels) {
+  EncodeIm2colFn fn = encode_im2col_fn();
+  if (!fn) return G3_ERR_CUDA;
+  cuuint64_t dims[4] = {(cuuint64_t)c.C, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.N};
+  cuuint64_t strides[3] = {(cuuint64_t)(c.C * esize), (cuuint64_t)(c.W * c.C * esize),
+                           (cuuint64_t)(c.H * c.W * c.C * esize)};
+  int lower[2] = {(int)-c.pw, (int)-c.ph};
+  int upper[2] = {(int)(c.pw - (c.S - 1) * c.dw), (int)(c.ph - (c.R - 1) * c.dh)};
+  cuuint32_t estr[4] = {1, (cuuint32_t)c.sw, (cuuint32_t)c.sh, 1};
+  const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;   // 2-byte elements; the bytes are copied as is
+  CUresult r = fn(map, dt, 4, const_cast<void*>(x), dims, strides, lower, upper, 64, pixels, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
+}
+
 // A row-major matrix of `outer` rows x `inner` elements (leading dimension ld
 // elements) as a 2-D tensor, loaded in boxes of box_inner x box_outer with the
 // 128-byte swizzle; out-of-range elements of a box read as zero.
@@ -504,7 +549,7 @@ int run_simt(const g3_gemm_args& a, cudaStream_t s) {
   return G3_OK;
 }
 
-int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
+int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* conv = nullptr) {
   const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d.sms, a.config, a.split_k, a.raster);
   if (pl.member < 0) return G3_ERR_UNSUPPORTED;
   const FamilyEntry& fam = g_family[pl.member];
@@ -572,7 +617,11 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   CUtensorMap maps[7];
   std::memset(maps, 0, sizeof(maps));
   const uint32_t arows = fam.bm / fam.cg;   // rows of A one CTA stages (half the tile in a pair)
-  if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, arows)) != G3_OK) return st;
+  if (conv) {
+    if ((st = encode_im2col(&maps[0], a.A, es, *conv, arows)) != G3_OK) return st;
+  } else if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, arows)) != G3_OK) {
+    return st;
+  }
   if (a.dtype == G3_TF32) {   // B stored n x k: boxes of bk (k) x 128 (n rows)
     if ((st = encode_2d(&maps[1], B_hi, es, k, n, ldb, bk, 128)) != G3_OK) return st;
   } else if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) {
@@ -612,6 +661,19 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s) {
   p.debug_withhold = -1;
   // INT8: at most 16 k-blocks (1024 products, |sum| <= 2^24) per FP32 accumulator
   p.kchunk = (a.dtype == G3_INT8) ? 16 : 0;
+  if (conv) {
+    p.conv = 1;
+    p.conv_pq = (int)(conv->P * conv->Q);
+    p.conv_q = (int)conv->Q;
+    p.conv_sh = (int)conv->sh;
+    p.conv_sw = (int)conv->sw;
+    p.conv_ph = (int)conv->ph;
+    p.conv_pw = (int)conv->pw;
+    p.conv_dh = (int)conv->dh;
+    p.conv_dw = (int)conv->dw;
+    p.conv_s = (int)conv->S;
+    p.conv_cblocks = (int)(conv->C / 64);
+  }
   if (g_withhold_next) {
     p.debug_withhold = 0;
     p.timeout_ns = g_withhold_timeout_ns;
@@ -840,6 +902,48 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   return G3_OK;
 }
 
+// Implicit-GEMM convolution: the GEMM of m = N*P*Q output pixels, n = K
+// output channels and k = R*S*C taps x channels, with A read from the NHWC
+// activations through an im2col tensor map instead of a materialised matrix.
+static int conv2d_impl(const ConvDesc& c, double alpha, const void* x, const void* w, double beta, float* y,
+                       int dtype, cudaStream_t s) {
+  if (c.N < 1 || c.H < 1 || c.W < 1) return -101;
+  if (c.C < 64 || c.C % 64 != 0) return G3_ERR_UNSUPPORTED;   // 64 channels = one 128-byte k-block row
+  if (c.K < 1) return -105;
+  if (c.R < 1 || c.S < 1 || c.sh < 1 || c.sw < 1 || c.sh > 8 || c.sw > 8 || c.dh < 1 || c.dw < 1)
+    return G3_ERR_UNSUPPORTED;
+  if (c.ph < 0 || c.pw < 0 || c.ph > 128 || c.pw > 128) return G3_ERR_UNSUPPORTED;
+  if ((c.R - 1) * c.dh - c.ph > 128 || (c.S - 1) * c.dw - c.pw > 128 || c.P < 1 || c.Q < 1) return G3_ERR_UNSUPPORTED;
+  if ((c.R - 1) * c.dh > 65535 || (c.S - 1) * c.dw > 65535) return G3_ERR_UNSUPPORTED;
+  if (dtype != G3_BF16 && dtype != G3_FP16) return G3_ERR_UNSUPPORTED;
+  if (!x || !w || !y) return G3_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(x) % 16 != 0) return G3_ERR_UNSUPPORTED;
+  if (c.N * c.P * c.Q > INT32_MAX || c.R * c.S * c.C > INT32_MAX) return G3_ERR_UNSUPPORTED;
+  g3_gemm_args a;
+  g3_gemm_args_init(&a);
+  a.m = c.N * c.P * c.Q;
+  a.n = c.K;
+  a.k = c.R * c.S * c.C;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.A = x;
+  a.lda = a.k;   // not used to address A (the im2col map does); keeps the layout logic from re-packing it
+  a.B = w;
+  a.ldb = c.K;
+  a.C = y;
+  a.ldc = c.K;
+  a.dtype = dtype;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DevState* d = nullptr;
+  int st = ensure_device(&d);
+  if (st != G3_OK) return st;
+  if (alpha == 0.0) {
+    G3_CHECK_CUDA(launch_scale_c(y, false, (int)a.m, (int)a.n, a.ldc, (float)beta, s));
+    return G3_OK;
+  }
+  return run_tc(*d, a, s, &c);
+}
+
 extern "C" {
 
 void g3_gemm_args_init(g3_gemm_args* a) {
@@ -862,6 +966,17 @@ int g3_gemm(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_
 int g3_set_stream(void* stream) {
   g_stream = static_cast<cudaStream_t>(stream);
   return G3_OK;
+}
+
+int g3_conv2d(int64_t N, int64_t H, int64_t W, int64_t C, int64_t K, int64_t R, int64_t S, int64_t stride_h,
+              int64_t stride_w, int64_t pad_h, int64_t pad_w, int64_t dil_h, int64_t dil_w, double alpha,
+              const void* x, const void* w, double beta, float* y, int dtype, void* stream) {
+  ConvDesc c{N, H, W, C, K, R, S, stride_h, stride_w, pad_h, pad_w, dil_h, dil_w, 0, 0};
+  if (c.sh >= 1 && c.sw >= 1) {
+    c.P = (H + 2 * pad_h - dil_h * (R - 1) - 1) / stride_h + 1;
+    c.Q = (W + 2 * pad_w - dil_w * (S - 1) - 1) / stride_w + 1;
+  }
+  return conv2d_impl(c, alpha, x, w, beta, y, dtype, stream ? static_cast<cudaStream_t>(stream) : g_stream);
 }
 
 int g3_gemm_host(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B,

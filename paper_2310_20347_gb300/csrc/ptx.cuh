@@ -142,6 +142,32 @@ __device__ __forceinline__ void tma_load_2d_pair(void* smem_dst, const void* tma
       : "memory");
 }
 
+// Im2col load from an NHWC tensor (4-D map: C, W, H, N): starting at base
+// position (w, h) of image n, the TMA walks the map's pixels-per-column base
+// positions (W fastest, at the map's traversal strides, wrapping to the next
+// row and image inside the map's bounding box) and copies channels c ..
+// c + channels-per-pixel - 1 of the pixel at base + (off_w, off_h) for each;
+// positions outside the image read zeros.
+__device__ __forceinline__ void tma_load_im2col_4d(void* smem_dst, const void* tmap, int32_t c, int32_t w, int32_t h,
+                                                   int32_t n, uint16_t off_w, uint16_t off_h, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.im2col.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6], {%7, %8};" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c), "r"(w), "r"(h), "r"(n), "r"(smem_u32(bar)), "h"(off_w),
+      "h"(off_h)
+      : "memory");
+}
+// The same for one CTA of a pair (bytes counted on the leader's barrier).
+__device__ __forceinline__ void tma_load_im2col_4d_pair(void* smem_dst, const void* tmap, int32_t c, int32_t w,
+                                                        int32_t h, int32_t n, uint16_t off_w, uint16_t off_h,
+                                                        uint32_t bar_caddr) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.im2col.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6], {%7, %8};" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c), "r"(w), "r"(h), "r"(n), "r"(bar_caddr), "h"(off_w), "h"(off_h)
+      : "memory");
+}
+
 // 2-D tiled store of one box from shared memory (bulk-group completion).
 // Elements of the box outside the tensor are not written.
 __device__ __forceinline__ void tma_store_2d(const void* tmap, int32_t x, int32_t y, const void* smem_src) {

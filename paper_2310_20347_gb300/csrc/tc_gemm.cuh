@@ -88,6 +88,14 @@ struct TcParams {
   int debug_withhold;     // test hook: producer iteration whose stage never fills (-1: none)
   int kchunk;             // k-blocks per accumulation chunk (0: the whole k range of a tile)
   int c_tma;              // 1: C (beta == 0) is written through TMA stores with the tmC map
+  // Implicit-GEMM convolution (conv = 1): A is the NHWC activation tensor read
+  // through an im2col tensor map; row i of A is output pixel i = (n, p, q) and
+  // k-block kb is filter tap (r, s) = divmod(kb / cblocks, S), channel block
+  // kb % cblocks of 64 channels.
+  int conv;
+  int conv_pq, conv_q;            // P * Q and Q of the output
+  int conv_sh, conv_sw, conv_ph, conv_pw, conv_dh, conv_dw;
+  int conv_s, conv_cblocks;       // filter width S, C / 64
 };
 
 // One problem of a grouped launch (device table entry).
@@ -230,6 +238,25 @@ struct SingleSched {
     return EpiJob{p->C, p->ldc, p->m, p->n, p->alpha, p->beta, p->out_mode,
                   p->partial ? p->partial + (long long)j.split * p->m * p->n : nullptr, cmap};
   }
+
+  __device__ __forceinline__ bool conv() const { return p->conv != 0; }
+  // im2col coordinates of k-block kb for the A rows starting at output pixel `pix`
+  __device__ __forceinline__ void conv_coords(int pix, int kb, int (&xyzw)[4], uint16_t (&off)[2]) const {
+    const int n = pix / p->conv_pq;
+    const int rem = pix - n * p->conv_pq;
+    const int pp = rem / p->conv_q;
+    const int qq = rem - pp * p->conv_q;
+    const int rs = kb / p->conv_cblocks;
+    const int cb = kb - rs * p->conv_cblocks;
+    const int r = rs / p->conv_s;
+    const int s = rs - r * p->conv_s;
+    xyzw[0] = cb * 64;
+    xyzw[1] = qq * p->conv_sw - p->conv_pw;
+    xyzw[2] = pp * p->conv_sh - p->conv_ph;
+    xyzw[3] = n;
+    off[0] = static_cast<uint16_t>(s * p->conv_dw);
+    off[1] = static_cast<uint16_t>(r * p->conv_dh);
+  }
 };
 
 struct GroupedSched {
@@ -253,6 +280,9 @@ struct GroupedSched {
     const GroupDesc* d = gp->groups + j.g;
     return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr, nullptr};
   }
+
+  __device__ __forceinline__ bool conv() const { return false; }
+  __device__ __forceinline__ void conv_coords(int, int, int (&)[4], uint16_t (&)[2]) const {}
 };
 
 // Shared::cluster address of a barrier of the pair's leader (CTA pairs), or
@@ -365,8 +395,19 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
               for (int h = 0; h < T::kNBoxes; ++h)
                 tma_load_2d(bt + h * (T::kBK * 128), mb, j.n0 + h * T::kBoxN, k0, &full[stage]);
             }
-            if constexpr (kPair) tma_load_2d_pair(at, ma, k0, a_row, full_c);
-            else tma_load_2d(at, ma, k0, a_row, &full[stage]);
+            if (T::kElem == 2 && S.conv()) {   // implicit GEMM: im2col rows of the activations
+              int xyzw[4];
+              uint16_t off[2];
+              S.conv_coords(a_row, kb, xyzw, off);
+              if constexpr (kPair)
+                tma_load_im2col_4d_pair(at, ma, xyzw[0], xyzw[1], xyzw[2], xyzw[3], off[0], off[1], full_c);
+              else
+                tma_load_im2col_4d(at, ma, xyzw[0], xyzw[1], xyzw[2], xyzw[3], off[0], off[1], &full[stage]);
+            } else if constexpr (kPair) {
+              tma_load_2d_pair(at, ma, k0, a_row, full_c);
+            } else {
+              tma_load_2d(at, ma, k0, a_row, &full[stage]);
+            }
           }
         }
       }

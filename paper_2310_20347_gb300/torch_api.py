@@ -93,6 +93,28 @@ def convert_bf16(x: torch.Tensor, stream=None) -> torch.Tensor:
     return y
 
 
+def conv2d(x, w, y=None, stride=(1, 1), pad=(0, 0), dil=(1, 1), alpha=1.0, beta=0.0, stream=None):
+    """Implicit-GEMM convolution through g3_conv2d: x N x H x W x C and w
+    R x S x C x K (both bf16 or both fp16, contiguous, on the GPU); returns y,
+    N x P x Q x K float32 (given, or new when y is None)."""
+    if x.dim() != 4 or w.dim() != 4 or x.dtype != w.dtype or not x.is_contiguous() or not w.is_contiguous():
+        raise ValueError("x must be N x H x W x C and w R x S x C x K, contiguous, same dtype")
+    dt = {torch.bfloat16: G3_BF16, torch.float16: G3_FP16}.get(x.dtype)
+    if dt is None:
+        raise TypeError("conv2d takes bfloat16 or float16 tensors")
+    N, H, W, C = x.shape
+    R, S, C2, K = w.shape
+    if C2 != C:
+        raise ValueError("channel mismatch")
+    P = (H + 2 * pad[0] - dil[0] * (R - 1) - 1) // stride[0] + 1
+    Q = (W + 2 * pad[1] - dil[1] * (S - 1) - 1) // stride[1] + 1
+    if y is None:
+        y = torch.zeros(N, P, Q, K, dtype=torch.float32, device=x.device)
+    check(_lib.g3_conv2d(N, H, W, C, K, R, S, stride[0], stride[1], pad[0], pad[1], dil[0], dil[1], float(alpha),
+                         x.data_ptr(), w.data_ptr(), float(beta), y.data_ptr(), dt, _stream(stream)), "g3_conv2d")
+    return y
+
+
 def convert_tf32(x: torch.Tensor, stream=None) -> torch.Tensor:
     y = torch.empty(x.shape, dtype=torch.float32, device=x.device)
     check(_lib.g3_convert_tf32(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), y.data_ptr(),

@@ -93,6 +93,28 @@ def test_im2col_layers_bf16():
     print(f"im2col 20 layers: kernel {worst_k:.3e} gate {worst_g:.3e}")
 
 
+def test_resnet50_layers_implicit_gemm():
+    # the 19 Table 1 layers with C % 64 == 0 as implicit-GEMM convolutions at
+    # batch 16; image 0 of each output is checked against the direct oracle
+    worst = 0.0
+    for geo in synth.RESNET50_CONV:
+        if geo["C"] % 64:
+            continue
+        r = np.random.default_rng(geo["layer"])
+        H, C, K, R, st, pd = geo["H"], geo["C"], geo["K"], geo["R"], geo["stride"], geo["pad"]
+        x = oracle.round_bf16(r.standard_normal((16, H, H, C)).astype(np.float32))
+        w = oracle.round_bf16((r.standard_normal((R, R, C, K)) / np.sqrt(R * R * C)).astype(np.float32))
+        y = torch_api.conv2d(torch.from_numpy(x).cuda().to(torch.bfloat16), torch.from_numpy(w).cuda().to(torch.bfloat16),
+                             stride=(st, st), pad=(pd, pd))
+        got = y[0].cpu().numpy()
+        want = oracle.conv2d_nhwc(x[:1], w, (st, st), (pd, pd))[0]
+        D = oracle.conv2d_nhwc(np.abs(x[:1]), np.abs(w), (st, st), (pd, pd))[0]
+        e = float(np.max(np.abs(got - want) / np.maximum(D, 1e-300)))
+        assert e <= 1e-5, (geo, e)
+        worst = max(worst, e)
+    print(f"ResNet-50 implicit-GEMM layers: worst error {worst:.3e}")
+
+
 @pytest.mark.parametrize("dtype", [G3_BF16, G3_F32_3XBF16])
 def test_grouped_1000(dtype):
     shapes = synth.grouped_shapes(1000, seed=0)
