@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from gpu_util import rel_err
-from paper_2310_20347_gb300 import G3_BF16, G3_F32, G3_F32_3XBF16, G3_INT8, synth, torch_api
+from paper_2310_20347_gb300 import G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_INT8, G3_TF32, synth, torch_api
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,24 @@ def test_host_bf16_beta_zero_multiblock():
     torch.cuda.current_stream().synchronize()
     Aq, Bq = oracle.round_bf16(p.A), oracle.round_bf16(p.B)
     e = rel_err(hC.numpy(), oracle.gemm(Aq, Bq, None, 1.0, 0.0), oracle.absprod(Aq, Bq, 1.0))
+    assert e <= 1e-5, e
+
+
+@pytest.mark.parametrize("dtype", [G3_FP16, G3_TF32])
+def test_host_fp16_tf32_multiblock(dtype):
+    p = synth.uniform_problem(2300, 200, 330, seed=45, beta=0.5)
+    if dtype == G3_FP16:
+        Aq, Bq = p.A.astype(np.float16), p.B.astype(np.float16)
+        hA, hB = pinned(torch.from_numpy(Aq)), pinned(torch.from_numpy(Bq))
+        Aq, Bq = Aq.astype(np.float64), Bq.astype(np.float64)
+    else:
+        hA, hB = pinned(torch.from_numpy(p.A)), pinned(torch.from_numpy(p.B))
+        Aq, Bq = oracle.round_tf32(p.A), oracle.round_tf32(p.B)
+    hC = pinned(torch.from_numpy(p.C))
+    torch_api.gemm_host(hA, hB, hC, 1.0, 0.5, dtype=dtype)
+    torch.cuda.current_stream().synchronize()
+    e = rel_err(hC.numpy(), oracle.gemm(Aq, Bq, p.C, 1.0, 0.5), oracle.absprod(Aq, Bq, 1.0),
+                0.5 * p.C.astype(np.float64))
     assert e <= 1e-5, e
 
 

@@ -6,8 +6,8 @@ import torch
 
 import oracle
 from gpu_util import check_guard, guarded, rel_err
-from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, synth,
-                                    torch_api)
+from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32,
+                                    synth, torch_api)
 
 pytestmark = pytest.mark.gpu
 COMBOS = [(True, False), (False, True), (True, True)]
@@ -52,6 +52,22 @@ def test_trans_16bit(ta, tb, kind):
     torch_api.gemm(A, B, C, 1.0, 0.0, dtype=dt, trans_a=ta, trans_b=tb)
     torch.cuda.synchronize()
     e = rel_err(C.cpu().numpy(), oracle.gemm(Aq, Bq), oracle.absprod(Aq, Bq, 1.0))
+    assert e <= 1e-5, e
+
+
+@pytest.mark.parametrize("ta,tb", COMBOS)
+def test_trans_tf32(ta, tb):
+    # TF32 stages B K-major: a transposed B is made row-major, then written
+    # transposed again by the rounding pre-pass
+    p = synth.uniform_problem(140, 264, 200, seed=54, beta=0.5)
+    A, B = stored(p.A, ta, 1), stored(p.B, tb, 3)
+    full, C = guarded(p.m, p.n, p.C)
+    torch_api.gemm(A, B, C, 1.0, 0.5, dtype=G3_TF32, trans_a=ta, trans_b=tb)
+    torch.cuda.synchronize()
+    check_guard(full, p.m, p.n)
+    Aq, Bq = oracle.round_tf32(p.A), oracle.round_tf32(p.B)
+    e = rel_err(C.cpu().numpy(), oracle.gemm(Aq, Bq, p.C, 1.0, 0.5), oracle.absprod(Aq, Bq, 1.0),
+                0.5 * p.C.astype(np.float64))
     assert e <= 1e-5, e
 
 
