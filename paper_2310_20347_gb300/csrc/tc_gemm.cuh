@@ -7,11 +7,12 @@
 //               of 128-byte-swizzled shared-memory tiles (the packed buffers Ac, Bc
 //               of the paper's Section 3.1 / Figure "packing": TMA writes them in
 //               exactly the layout the tensor core reads, so packing costs no pass)
-//   warp 1      MMA issuer: one thread issues tcgen05.mma per 16-element (BF16) or
-//               32-element (FP8) k-step; the accumulator micro-tile lives in TMEM
-//               (the "C resident" micro-kernel of Section 4.1 with TMEM in place of
-//               the register file), double-buffered across output tiles
+//   warp 1      MMA issuer: one thread issues tcgen05.mma per 32-byte k-step (16
+//               BF16/FP16, 32 FP8 or 8 TF32 elements); the accumulator micro-tile
+//               lives in TMEM (the "C resident" micro-kernel of Section 4.1 with
+//               TMEM in place of the register file), multi-buffered across tiles
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator, alpha/beta, stores
+//               (warps 2..9 for the exact-integer member with sums in TMEM)
 //
 // Orientation.  The MMA computes D = Bt * At, i.e. the transpose of the C tile:
 // TMEM lane = column j of C (128 per tile), TMEM column = row i of C (bm per
@@ -41,6 +42,11 @@
 // and waits for both CTAs' TMA bytes on its own barriers; its commits arrive on
 // the barriers of both CTAs; each CTA's epilogue drains its own TMEM (its 128
 // columns of C) and reports to the leader.
+//
+// Implicit-GEMM convolution (TcParams::conv): A is an NHWC activation tensor;
+// the producer loads each k-block of A (64 channels of one filter tap for bm
+// output pixels) with a TMA im2col load, so the convolution runs through the
+// same pipeline without a materialised im2col matrix.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -170,12 +176,12 @@ struct TcConfig {
       kTmemSums ? 1 : ((512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs);
   static constexpr uint32_t kTmemCols = kTmemSums ? 512 : kNumBufs * kSetCols;
   // Epilogue warps: one per TMEM lane quarter, each thread owning all bm rows
-  // of its column.  (Exact-integer variants with eight epilogue warps measured
-  // slower: with bm = 256 its large unrolled epilogue starved the MMA-issuing
-  // thread of instruction fetch; with bm = 128, 64 rows each, the 168-register
-  // cap of ten warps made it spill.)
-  // The TMEM-sum member drains its accumulator every 1024 products while the
-  // MMA waits; eight warps (two per lane quarter, 128 rows each) halve that.
+  // of its column -- except the TMEM-sum member, which drains its accumulator
+  // every 1024 products while the MMA waits: eight warps (two per lane
+  // quarter, 128 rows each) halve that drain.  (With the int32 sums in
+  // registers eight warps were slower: at bm = 256 the unrolled epilogue
+  // starved the MMA thread of instruction fetch, and at bm = 128 the
+  // 168-register cap of ten warps made it spill.)
   static constexpr int kEpiWarps = kTmemSums ? 8 : 4;
   static constexpr int kEpiRows = BM_T / (kEpiWarps / 4);   // rows of the tile per epilogue thread
   // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128 columns x 4 bytes.
