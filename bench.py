@@ -181,7 +181,8 @@ def run_reference(args):
 # DRAM-traffic record taken with ncu is reported as the roofline's "traffic"
 # only while these files hash to the recorded value and the member and size
 # match the record.
-TRAFFIC_SOURCES = ("csrc/tc_gemm.cuh", "csrc/ptx.cuh", "csrc/tc_family_tu.cuh", "csrc/tc_family_3xbf16.cu")
+TRAFFIC_SOURCES = ("csrc/tc_gemm.cuh", "csrc/ptx.cuh", "csrc/sched.cuh", "csrc/tc_family_tu.cuh",
+                   "csrc/tc_family_3xbf16.cu")
 TRAFFIC_RECORD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                               "tc_gemm_3xbf16_16384_dram.md")
 
@@ -309,6 +310,55 @@ def run_workload(args):
             Dq = oracle.absprod(Aq, Bq, alpha, rows=rows)
             e["kernel"] = float(np.max(np.abs(got_rows - refq) / np.maximum(Dq, 1e-300)))
         return e
+
+    if args.workload == "streamk":
+        # Stream-K tail (split_k = G3_SPLIT_STREAM_K) against the plain walk on
+        # shapes whose tiles leave the last wave partly idle: whole calls (L2
+        # flushed between them) and the GEMM kernel alone
+        from paper_2310_20347_gb300 import G3_SPLIT_STREAM_K
+        out = []
+        for kind, n in (("3xbf16", 2048), ("bf16", 4096), ("int8", 8192)):
+            g = torch.Generator(device=dev).manual_seed(n)
+            if kind == "3xbf16":
+                A = torch.rand(n, n, device=dev, generator=g) * 2 - 1
+                B = torch.rand(n, n, device=dev, generator=g) * 2 - 1
+                C = torch.rand(n, n, device=dev, generator=g) * 2 - 1
+                dt, alpha, beta = G3_F32_3XBF16, 1.0, 0.5
+            elif kind == "bf16":
+                A = torch.randn(n, n, device=dev, generator=g).bfloat16()
+                B = torch.randn(n, n, device=dev, generator=g).bfloat16()
+                C = torch.empty(n, n, device=dev)
+                dt, alpha, beta = G3_BF16, 1.0, 0.0
+            else:
+                A = torch.randint(-128, 128, (n, n), dtype=torch.int8, device=dev, generator=g)
+                B = torch.randint(-128, 128, (n, n), dtype=torch.int8, device=dev, generator=g)
+                C = torch.empty(n, n, dtype=torch.int32, device=dev)
+                dt, alpha, beta = G3_INT8, 1, 0
+            st, cfg, _, _ = _lib.g3_plan_query(n, n, n, dt)
+            res = {"kind": kind, "n": n, "member": _lib.g3_family_describe(cfg)}
+            for name, sk in (("plain", 1), ("stream_k", G3_SPLIT_STREAM_K)):
+                fn = lambda: torch_api.gemm(A, B, C, alpha, beta, dtype=dt, split_k=sk)
+                for _ in range(args.warmup):
+                    fn()
+                ms = _call_ms(fn, args.reps, flush)
+                _lib.g3_kernel_timing(True)
+                _lib.g3_kernel_time_ms(reset=True)
+                for _ in range(args.reps):
+                    flush.zero_()
+                    fn()
+                torch.cuda.synchronize()
+                kms, kn = _lib.g3_kernel_time_ms(reset=True)
+                _lib.g3_kernel_timing(False)
+                res[name] = {"call_ms": ms, "gemm_kernel_ms": kms / max(kn, 1)}
+            res["call_ratio"] = res["plain"]["call_ms"] / res["stream_k"]["call_ms"]
+            out.append(res)
+            del A, B, C
+            torch.cuda.empty_cache()
+        _line(args, out[0]["call_ratio"], "x",
+              {"workload": "stream-K tail vs plain tile walk: FP32-accurate 2048^3 (beta 0.5), BF16 4096^3, "
+                           "INT8 8192^3; planner's member, L2 flushed between calls"},
+              {"dtype": "mixed", "cases": out})
+        return
 
     if args.workload == "sweep":
         out = []
@@ -690,7 +740,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "conv",
+                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "conv",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

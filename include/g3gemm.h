@@ -78,6 +78,9 @@ typedef enum {
   G3_TF32 = 6
 } g3_dtype;
 
+/* g3_gemm_args.split_k value that asks for a stream-K tail (see there).    */
+#define G3_SPLIT_STREAM_K (-1)
+
 typedef enum {
   G3_OK = 0,
   G3_ERR_ARG = -1,          /* generic invalid argument (positional: -(100+i)) */
@@ -137,7 +140,19 @@ G3_API int g3_set_stream(void* cuda_stream);
  *                      call allocates nothing; too small -> G3_ERR_ARG.
  *   config             -1: the planner's choice; otherwise the index of a
  *                      member of the generated kernel family (g3_family_*).
- *   split_k            0: the planner's choice; >= 1 forces that many splits.
+ *   split_k            0: the planner's choice; >= 1 forces that many splits
+ *                      (k cut into equal ranges, partial planes of m x n
+ *                      reduced by a second kernel); G3_SPLIT_STREAM_K (-1)
+ *                      forces a stream-K tail: the tiles that do not fill the
+ *                      last wave of the persistent grid are cut along k into
+ *                      one equal piece per CTA (segments of bm x bn partial
+ *                      tiles added by a fix-up kernel in a fixed order, so
+ *                      results are deterministic); where the tiles fill whole
+ *                      waves it computes without a split.  The planner
+ *                      takes a stream-K tail only on request (or from an
+ *                      autotuner record): measured on GB300 it seldom pays.
+ *                      FP8 with device scales takes no split-K (a forced
+ *                      split is ignored) but may take the stream-K tail.
  *   raster             0: the planner's choice; >= 1 the band width (in tiles)
  *                      of the tile walk.
  *   trans_a, trans_b   0: A is m x k (lda >= k), B is k x n (ldb >= n);
@@ -261,12 +276,13 @@ G3_API int g3_family_size(void);
 G3_API int g3_family_describe(int index, char* buf, size_t len);
 
 /* Which configuration the planner picks for a problem (index into the family,
- * split count, raster band); -1 in *config for the FP32 SIMT kernel.        */
+ * split count -- G3_SPLIT_STREAM_K when it takes a stream-K tail --, raster
+ * band); -1 in *config for the FP32 SIMT kernel.                           */
 G3_API int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* split_k, int* raster);
 
 /* --- Autotuner: the per-shape search of the paper's Section 8.4 -------------
  * g3_autotune times every member of the generated family that applies to
- * `dtype`, each with split-K in {1, 2, 3, 4, 6, 8, 12, 16} (bounded by the
+ * `dtype`, each with split-K in {1, stream-K, 2, 3, 4, 6, 8, 12, 16} (bounded by the
  * k-blocks), on scratch operands of shape m x n x k it allocates and frees,
  * and records the fastest (member, split) for the shape's size bucket: dtype
  * and ceil(log2) of each of m, n, k.  Later g3_gemm calls in that bucket use

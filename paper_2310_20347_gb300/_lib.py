@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libg3gemm.so")
 
 G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP8_E4M3, G3_INT8, G3_FP16, G3_TF32 = 0, 1, 2, 3, 4, 5, 6
+G3_SPLIT_STREAM_K = -1   # g3_gemm_args.split_k: a stream-K tail
 DTYPES = {"f32": G3_F32, "3xbf16": G3_F32_3XBF16, "bf16": G3_BF16, "fp8": G3_FP8_E4M3, "int8": G3_INT8,
           "fp16": G3_FP16, "tf32": G3_TF32}
 

@@ -233,6 +233,7 @@ struct Plan {
   int num_kb = 1;
   int tiles_m = 1, tiles_n = 1;
   int raster = 8;
+  int sk_streams = 0, sk_dp = 0, sk_tail = 0, sk_segs = 0;   // stream-K tail (sched.cuh); 0 streams = none
 };
 
 // Clocks one k-block of a tile costs a member, measured on GB300: the MMA
@@ -311,7 +312,7 @@ int tune_load_locked(const char* path) {
     if (line[0] == '#') continue;
     if (std::sscanf(line, "%d %d %d %d %d %d %lf", &key.dtype, &key.bm, &key.bn, &key.bk, &val.member, &val.split,
                     &val.ms) == 7 &&
-        val.member >= 0 && val.member < G3_FAMILY_SIZE && val.split >= 1) {
+        val.member >= 0 && val.member < G3_FAMILY_SIZE && (val.split >= 1 || val.split == G3_SPLIT_STREAM_K)) {
       g_tune[key] = val;
       ++loaded;
     }
@@ -327,9 +328,9 @@ void tune_env_once() {
 }
 
 Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_member, int force_split,
-               int force_raster) {
+               int force_raster, bool allow_splitk = true) {
   Plan pl;
-  if (force_member < 0 && force_split <= 0) {
+  if (force_member < 0 && force_split == 0) {
     tune_env_once();
     auto it = g_tune.find(tune_key(m, n, k, dtype));
     if (it != g_tune.end()) {
@@ -371,15 +372,40 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   int splits = 1;
   if (force_split > 0) {
     splits = force_split;
-  } else if (tiles * 2 <= sms / cg && pl.num_kb >= 8) {
+  } else if (force_split == 0 && tiles * 2 <= sms / cg && pl.num_kb >= 8) {
     splits = (int)std::min<long long>(sms / cg / tiles, std::min(pl.num_kb / 4, 16));
     splits = std::max(splits, 1);
   }
+  if (!allow_splitk) splits = 1;
   splits = std::min(splits, pl.num_kb);
   pl.kb_per_split = (pl.num_kb + splits - 1) / splits;
   pl.splits = (pl.num_kb + pl.kb_per_split - 1) / pl.kb_per_split;
   pl.raster = force_raster > 0 ? force_raster : 8;
   pl.raster = std::max(1, std::min(pl.raster, pl.tiles_m));
+  // Stream-K tail (sched.cuh), by request only (split_k = G3_SPLIT_STREAM_K,
+  // or a tuning record of g3_autotune, which times it among the candidates).
+  // The planner does not choose it by itself: measured on GB300 (FP32-accurate
+  // 2048^3, BF16 4096^3, INT8 8192^3) the last, partly idle wave of whole
+  // tiles runs nearly in proportion to its tile count -- fewer busy SMs share
+  // L2 and HBM -- so cutting it into segments saved at most 3% of the GEMM
+  // kernel (and cost 7% with the 256 x 256 pair tiles, whose segments each
+  // write a 128 KB partial per CTA) while the fix-up pass took 12-14 us.
+  const FamilyEntry& f = g_family[pl.member];
+  if (pl.splits == 1 && force_split == G3_SPLIT_STREAM_K && f.slots && f.stream_k) {
+    const int slots = f.slots(sms);
+    if (slots > 0 && slots <= 1024) {
+      const long long waves = tiles / slots, tail = tiles - waves * slots;
+      if (tail > 0) {
+        const StreamK sk{tail * pl.num_kb, slots, pl.num_kb};
+        int segs = 0;
+        for (int c = 0; c < slots; ++c) segs = std::max(segs, sk.segments(c));
+        pl.sk_streams = slots;
+        pl.sk_dp = (int)(waves * slots);
+        pl.sk_tail = (int)tail;
+        pl.sk_segs = segs;
+      }
+    }
+  }
   return pl;
 }
 
@@ -444,6 +470,10 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl) {
       break;
   }
   if (a.dtype != G3_F32 && pl.splits > 1) L.partial = take((size_t)pl.splits * m * n * 4);
+  if (a.dtype != G3_F32 && pl.sk_streams > 0) {
+    const FamilyEntry& f = g_family[pl.member];
+    L.partial = take((size_t)pl.sk_streams * pl.sk_segs * f.bm * 128 * f.cg * 4);
+  }
   L.total = off;
   return L;
 }
@@ -550,7 +580,8 @@ int run_simt(const g3_gemm_args& a, cudaStream_t s) {
 }
 
 int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* conv = nullptr) {
-  const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d.sms, a.config, a.split_k, a.raster);
+  const bool dev_scales = a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b);
+  const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d.sms, a.config, a.split_k, a.raster, !dev_scales);
   if (pl.member < 0) return G3_ERR_UNSUPPORTED;
   const FamilyEntry& fam = g_family[pl.member];
   const Layout L = make_layout(a, pl);
@@ -680,6 +711,11 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
     g_withhold_next = false;
   }
   const bool is_int = a.dtype == G3_INT8;
+  p.sk_streams = pl.sk_streams;
+  p.sk_dp = pl.sk_dp;
+  p.sk_tail = pl.sk_tail;
+  p.sk_segs = pl.sk_segs;
+  if (pl.sk_streams > 0) p.partial = reinterpret_cast<float*>(ws + L.partial);
   if (pl.splits > 1) {
     p.out_mode = OUT_PARTIAL;
     p.partial = reinterpret_cast<float*>(ws + L.partial);
@@ -705,6 +741,30 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
     }
     G3_CHECK_CUDA(launch_splitk_reduce(p.partial, pl.splits, (int)m, (int)n, alpha, (float)a.beta, a.C, a.ldc,
                                        is_int, s));
+  }
+  if (pl.sk_streams > 0) {
+    SkFixup fx;
+    fx.partial = p.partial;
+    fx.streams = pl.sk_streams;
+    fx.segs = pl.sk_segs;
+    fx.dp = pl.sk_dp;
+    fx.tail = pl.sk_tail;
+    fx.num_kb = pl.num_kb;
+    fx.tiles_m = pl.tiles_m;
+    fx.tiles_n = pl.tiles_n;
+    fx.raster = pl.raster;
+    fx.bm = fam.bm;
+    fx.bn = 128 * fam.cg;
+    fx.m = (int)m;
+    fx.n = (int)n;
+    fx.alpha = (float)a.alpha;
+    fx.beta = (float)a.beta;
+    fx.scale_a = p.scale_a;
+    fx.scale_b = p.scale_b;
+    fx.C = a.C;
+    fx.ldc = a.ldc;
+    fx.is_int = is_int;
+    G3_CHECK_CUDA(launch_streamk_fixup(fx, s));
   }
   return G3_OK;
 }
@@ -764,7 +824,9 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s) {
     G3_CHECK_CUDA(launch_scale_c(a.C, is_int, (int)a.m, (int)a.n, a.ldc, (float)a.beta, s));
     return G3_OK;
   }
-  if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b)) a.split_k = 1;   // scales apply in the kernel epilogue
+  // device scales apply in the kernel epilogue or the stream-K fix-up, which
+  // the split-K reduce cannot: no split-K then
+  if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b) && a.split_k > 1) a.split_k = 1;
   if (a.dtype == G3_F32) return run_simt(a, s);
   return run_tc(*d, a, s);
 }
@@ -1005,11 +1067,12 @@ int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
   DevState* d = nullptr;
   if ((st = ensure_device(&d)) != G3_OK) return st;
   g3_gemm_args a = *args;
-  if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b)) a.split_k = 1;
+  const bool dev_scales = a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b);
+  if (dev_scales && a.split_k > 1) a.split_k = 1;
   // a transposed operand reaches the kernel as an aligned row-major copy
   if (a.trans_a) { a.A = d->ws ? d->ws : reinterpret_cast<void*>(uintptr_t(256)); a.lda = round_up(a.k, 16); }
   if (a.trans_b) { a.B = d->ws ? d->ws : reinterpret_cast<void*>(uintptr_t(256)); a.ldb = round_up(a.n, 16); }
-  const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d->sms, a.config, a.split_k, a.raster);
+  const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d->sms, a.config, a.split_k, a.raster, !dev_scales);
   *bytes = make_layout(a, pl).total;
   return G3_OK;
 }
@@ -1144,9 +1207,10 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   int sms = 152;
   family_init();
   if (ensure_device(&d) == G3_OK) sms = d->sms;
-  const Plan pl = make_plan(m, n, std::max<int64_t>(k, 1), dtype, sms, -1, 0, 0);
+  // (FP8 calls are assumed to carry device scales: no split-K)
+  const Plan pl = make_plan(m, n, std::max<int64_t>(k, 1), dtype, sms, -1, 0, 0, dtype != G3_FP8_E4M3);
   if (config) *config = pl.member;
-  if (split_k) *split_k = pl.splits;
+  if (split_k) *split_k = pl.sk_streams > 0 ? G3_SPLIT_STREAM_K : pl.splits;
   if (raster) *raster = pl.raster;
   return G3_OK;
 }
@@ -1242,7 +1306,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   double best = 1e30;
   for (int i = 0; i < G3_FAMILY_SIZE; ++i) {
     if (!g_family[i].launch || g_family[i].mode != mode) continue;
-    for (int sk : {1, 2, 3, 4, 6, 8, 12, 16}) {
+    for (int sk : {1, G3_SPLIT_STREAM_K, 2, 3, 4, 6, 8, 12, 16}) {
       if (sk > num_kb) break;
       g3_gemm_args a;
       g3_gemm_args_init(&a);

@@ -24,6 +24,8 @@ struct FamilyEntry {
   int bufs;     // TMEM accumulator sets (2: the epilogue overlaps the next tile)
   int cg;       // CTAs per MMA: 1, or 2 (a CTA pair; tiles are 256 columns wide)
   TcLaunchFn launch;
+  int (*slots)(int sms);   // CTAs (pairs) that can be resident at once; 0 on error
+  bool stream_k;           // takes a stream-K tail (TcParams::sk_*)
 };
 
 void register_family_bf16(FamilyEntry* table);
@@ -81,6 +83,23 @@ cudaError_t launch_quantize_e4m3(const float* x, int rows, int cols, long long l
 cudaError_t launch_scale_c(void* C, bool is_int, int rows, int cols, long long ldc, float beta, cudaStream_t s);
 cudaError_t launch_splitk_reduce(const float* P, int splits, int rows, int cols, float alpha, float beta, void* C,
                                  long long ldc, bool is_int, cudaStream_t s);
+
+// Stream-K fix-up: for each of the `tail` last tiles of the walk (sched.cuh),
+// the sum of its segments' partial tiles in stream order, then
+// C := alpha * scale_a * scale_b * sum + beta * C (int32: C := sum (+ C)).
+struct SkFixup {
+  const float* partial;   // [streams * segs][bm][bn] FP32 (int32 bits when is_int)
+  int streams, segs, dp, tail, num_kb;
+  int tiles_m, tiles_n, raster, bm, bn;
+  int m, n;
+  float alpha, beta;
+  const float* scale_a;   // device scalars (FP8), or null = 1
+  const float* scale_b;
+  void* C;
+  long long ldc;
+  bool is_int;
+};
+cudaError_t launch_streamk_fixup(const SkFixup& f, cudaStream_t s);
 
 // Number of kernel launches the library has issued (all translation units).
 void count_launch(int n = 1);

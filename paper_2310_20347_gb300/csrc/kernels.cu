@@ -143,4 +143,123 @@ cudaError_t launch_splitk_reduce(const float* P, int splits, int rows, int cols,
   return cudaGetLastError();
 }
 
+// Stream-K fix-up (sched.cuh).  Block (t, y) covers a strip of 256 x 4
+// consecutive elements of tail tile t: each thread adds the four columns it
+// owns over the tile's partial results -- the slots of the streams whose
+// pieces overlap the tile's k-blocks, in stream order (deterministic, as in
+// the split-K reduce) -- and writes C.  One 16-byte vector per thread and slot
+// keeps many independent loads in flight (partial tiles are bm x bn,
+// row-major, bn a multiple of 4).
+constexpr int kFixupMaxStreams = 1024;
+constexpr int kFixupThreads = 256;
+
+template <bool INT>
+__global__ void __launch_bounds__(kFixupThreads) streamk_fixup_kernel(const SkFixup f) {
+  __shared__ int slot_of[kFixupMaxStreams];   // per stream c0 + i: its slot, or -1 (no segment)
+  __shared__ int nslot;
+  const int t = blockIdx.x;
+  const StreamK sk{(long long)f.tail * f.num_kb, f.streams, f.num_kb};
+  const int c0 = sk.stream_of((long long)t * f.num_kb);
+  const int c1 = sk.stream_of((long long)(t + 1) * f.num_kb - 1);
+  if (threadIdx.x == 0) {   // the tile's slots, compacted, in stream order
+    int ns = 0;
+    for (int c = c0; c <= c1; ++c) {
+      const int j = t - sk.first_tile(c);
+      int tt, kb0, kb1;
+      if (j >= 0 && sk.segment(c, j, tt, kb0, kb1)) slot_of[ns++] = c * f.segs + j;
+    }
+    nslot = ns;
+  }
+  int tm, tn;
+  raster_tile(f.dp + t, f.tiles_m, f.tiles_n, f.raster, tm, tn);
+  const int row0 = tm * f.bm, col0 = tn * f.bn;
+  const int rows = min(f.bm, f.m - row0), cols = min(f.bn, f.n - col0);
+  const int vec_per_row = f.bn / 4;
+  const int v = blockIdx.y * kFixupThreads + threadIdx.x;   // this thread's vector of the tile
+  const int r = v / vec_per_row;
+  const int c4 = (v - r * vec_per_row) * 4;
+  // launched as a programmatic dependent of the GEMM: wait for its grid (and
+  // its memory) before reading any partial tile
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __syncthreads();
+  if (r >= rows || c4 >= cols) return;
+  const long long tile_elems = (long long)f.bm * f.bn;
+  const long long off = (long long)r * f.bn + c4;
+  const int ns = nslot;
+  const int nq = min(4, cols - c4);
+  if (INT) {
+    int acc[4] = {0, 0, 0, 0};
+    for (int i0 = 0; i0 < ns; i0 += 4) {
+      int4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u < ns) x[u] = __ldcs(reinterpret_cast<const int4*>(f.partial + slot_of[i0 + u] * tile_elems + off));
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u < ns) {
+          acc[0] += x[u].x;
+          acc[1] += x[u].y;
+          acc[2] += x[u].z;
+          acc[3] += x[u].w;
+        }
+    }
+    int* cp = static_cast<int*>(f.C) + (long long)(row0 + r) * f.ldc + col0 + c4;
+    if (f.beta != 0.f) {
+      int cv[4];
+      for (int q = 0; q < nq; ++q) cv[q] = cp[q];
+      for (int q = 0; q < nq; ++q) cp[q] = cv[q] + acc[q];
+    } else {
+      for (int q = 0; q < nq; ++q) cp[q] = acc[q];
+    }
+  } else {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i0 = 0; i0 < ns; i0 += 4) {
+      float4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u < ns) x[u] = __ldcs(reinterpret_cast<const float4*>(f.partial + slot_of[i0 + u] * tile_elems + off));
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u < ns) {
+          acc[0] += x[u].x;
+          acc[1] += x[u].y;
+          acc[2] += x[u].z;
+          acc[3] += x[u].w;
+        }
+    }
+    float scale = f.alpha;
+    if (f.scale_a) scale *= *f.scale_a;
+    if (f.scale_b) scale *= *f.scale_b;
+    float* cp = static_cast<float*>(f.C) + (long long)(row0 + r) * f.ldc + col0 + c4;
+    if (f.beta != 0.f) {
+      float cv[4];
+      for (int q = 0; q < nq; ++q) cv[q] = cp[q];
+      for (int q = 0; q < nq; ++q) cp[q] = fmaf(scale, acc[q], f.beta * cv[q]);
+    } else {
+      for (int q = 0; q < nq; ++q) cp[q] = scale * acc[q];
+    }
+  }
+}
+
+cudaError_t launch_streamk_fixup(const SkFixup& f, cudaStream_t s) {
+  if (f.tail <= 0) return cudaSuccess;
+  if (f.streams > kFixupMaxStreams || f.bn % 4 != 0) return cudaErrorInvalidValue;
+  // programmatic stream serialisation: the fix-up's launch overlaps the tail
+  // of the GEMM kernel, which signals its dependents early
+  const int vecs = f.bm * (f.bn / 4);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)f.tail, (unsigned)((vecs + kFixupThreads - 1) / kFixupThreads), 1);
+  cfg.blockDim = dim3(kFixupThreads, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = f.is_int ? cudaLaunchKernelEx(&cfg, streamk_fixup_kernel<true>, f)
+                                 : cudaLaunchKernelEx(&cfg, streamk_fixup_kernel<false>, f);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 }  // namespace g3

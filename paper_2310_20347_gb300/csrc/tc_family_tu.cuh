@@ -25,39 +25,59 @@ inline cudaLaunchConfig_t pdl_config(int grid, int threads, size_t smem, cudaStr
   return cfg;
 }
 
-// Persistent grid: one CTA (or CTA pair) per tile up to what can be resident
-// at once -- the SM count, or for pairs the number of two-CTA clusters the GPU
-// can co-schedule with this kernel's shared memory (queried once per member).
+inline void set_cluster(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int cg) {
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = cg;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.numAttrs = 2;
+}
+
+// Tiles a member can have in flight at once (its persistent slots): the SM
+// count, or for pairs the number of two-CTA clusters the GPU can co-schedule
+// with this kernel's shared memory (queried once per member).  0 on error.
+template <int BM, int ST, int MODE, int CG>
+int tc_slots(int sms) {
+  if constexpr (CG == 1) {
+    return sms;
+  } else {
+    using Cfg = TcConfig<BM, ST, MODE, CG>;
+    static int max_clusters = 0;
+    if (max_clusters <= 0) {
+      auto kern = tc_gemm_kernel<BM, ST, MODE, CG>;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes) !=
+          cudaSuccess)
+        return 0;
+      cudaLaunchAttribute attr[2];
+      cudaLaunchConfig_t cfg = pdl_config(CG, Cfg::kThreads, Cfg::kSmemBytes, nullptr, attr);
+      set_cluster(cfg, attr, CG);
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return 0;
+      }
+      max_clusters = std::min(n, sms / CG);
+    }
+    return max_clusters;
+  }
+}
+
+// Persistent grid: one CTA (or CTA pair) per tile up to the member's slots;
+// with a stream-K tail exactly p.sk_streams of them (one per stream).
 template <int BM, int ST, int MODE, int CG>
 cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int sms, cudaStream_t s) {
   using Cfg = TcConfig<BM, ST, MODE, CG>;
   auto kern = tc_gemm_kernel<BM, ST, MODE, CG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
   if (e != cudaSuccess) return e;
-  const long long tiles = (long long)p.tiles_m * p.tiles_n * p.splits;
+  const int slots = tc_slots<BM, ST, MODE, CG>(sms);
+  if (slots <= 0) return cudaErrorInvalidConfiguration;
+  const long long work = (long long)p.tiles_m * p.tiles_n * p.splits;
+  const long long clusters = p.sk_streams > 0 ? p.sk_streams : std::min<long long>(work, slots);
   cudaLaunchAttribute attr[2];
-  if constexpr (CG == 1) {
-    const int grid = (int)std::min<long long>(tiles, sms);
-    const cudaLaunchConfig_t cfg = pdl_config(grid, Cfg::kThreads, Cfg::kSmemBytes, s, attr);
-    e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], p);
-  } else {
-    static int max_clusters = 0;
-    cudaLaunchConfig_t cfg = pdl_config(CG, Cfg::kThreads, Cfg::kSmemBytes, s, attr);
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = CG;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
-    cfg.numAttrs = 2;
-    if (max_clusters <= 0) {
-      int n = 0;
-      e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
-      if (e != cudaSuccess) return e;
-      if (n <= 0) return cudaErrorInvalidConfiguration;
-      max_clusters = std::min(n, sms / CG);
-    }
-    cfg.gridDim = dim3((unsigned)(CG * std::min<long long>(tiles, max_clusters)), 1, 1);
-    e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], p);
-  }
+  cudaLaunchConfig_t cfg = pdl_config((int)(CG * clusters), Cfg::kThreads, Cfg::kSmemBytes, s, attr);
+  if constexpr (CG > 1) set_cluster(cfg, attr, CG);
+  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], p);
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -66,7 +86,8 @@ template <int IDX, int MODE, int BM, int ST, int CG>
 void add_member(FamilyEntry* t) {
   if constexpr (MODE == G3_TU_MODE) {
     using Cfg = TcConfig<BM, ST, MODE, CG>;
-    t[IDX] = FamilyEntry{IDX, MODE, BM, ST, (int)Cfg::kSmemBytes, (int)Cfg::kNumBufs, CG, &launch_tc<BM, ST, MODE, CG>};
+    t[IDX] = FamilyEntry{IDX, MODE, BM, ST, (int)Cfg::kSmemBytes, (int)Cfg::kNumBufs, CG, &launch_tc<BM, ST, MODE, CG>,
+                         &tc_slots<BM, ST, MODE, CG>, TcStreamK<BM, MODE>::value};
   }
 }
 

@@ -53,6 +53,7 @@
 #include <cstdint>
 
 #include "ptx.cuh"
+#include "sched.cuh"
 
 namespace g3 {
 
@@ -87,7 +88,7 @@ struct TcParams {
   const float* scale_b;
   void* C;                // float (OUT_F32) or int32 (OUT_I32)
   long long ldc;
-  float* partial;         // OUT_PARTIAL: [splits][m][n] float
+  float* partial;         // OUT_PARTIAL: [splits][m][n] float; stream-K: [sk_streams * sk_segs] tiles
   int out_mode;
   unsigned long long timeout_ns;
   int* status;
@@ -102,6 +103,11 @@ struct TcParams {
   int conv_pq, conv_q;            // P * Q and Q of the output
   int conv_sh, conv_sw, conv_ph, conv_pw, conv_dh, conv_dw;
   int conv_s, conv_cblocks;       // filter width S, C / 64
+  // Stream-K tail (sk_streams > 0; see sched.cuh): the first sk_dp tiles of the
+  // walk (a multiple of sk_streams) are computed whole, the last sk_tail tiles
+  // in segments whose partial tiles (bm x 128*CG, FP32 or int32) go to
+  // `partial`; the grid must then hold exactly sk_streams CTAs (or pairs).
+  int sk_streams, sk_dp, sk_tail, sk_segs;
 };
 
 // One problem of a grouped launch (device table entry).
@@ -201,6 +207,7 @@ struct TcConfig {
 struct TileJob {
   int m0, n0, kb0, kb1, bm, split, g;
   int kchunk;   // k-blocks per accumulation chunk, 0 = one chunk
+  int sk;       // 1: a stream-K segment (split = its partial slot); kb0 == kb1: nothing to do
 };
 
 // Where and how a tile's result is written.
@@ -210,39 +217,80 @@ struct EpiJob {
   int m, n;
   float alpha, beta;
   int out_mode;
-  float* partial;             // OUT_PARTIAL: this split's m x n plane (leading dimension n)
+  // OUT_PARTIAL: element (i, j) of C's partial result goes to partial[i * ldp + j]
+  // (split-K: this split's m x n plane, ldp = n; stream-K: a bm x 128*CG slot,
+  // addressed through a base shifted back by the tile's origin)
+  float* partial;
   const CUtensorMap* cmap;    // non-null: store C (beta == 0) by TMA through this map
+  long long ldp;
 };
 
-template <int BM_T, int CG = 1>
+// Stream-K work item u (>= 0) of the tail: segment u / streams of stream
+// u % streams as (tile row, tile column, k-blocks [kb0, kb1), slot); kb0 ==
+// kb1 when that stream has no such segment.  Kept out of line: its 64-bit
+// divisions would otherwise add to the register pressure of the epilogue.
+static __device__ __noinline__ int4 stream_k_item(const TcParams* p, int u, int* slot) {
+  const int c = u % p->sk_streams, jseg = u / p->sk_streams;
+  const StreamK sk{(long long)p->sk_tail * p->num_kb, p->sk_streams, p->num_kb};
+  int tt = 0, kb0 = 0, kb1 = 0;
+  if (!sk.segment(c, jseg, tt, kb0, kb1)) return make_int4(0, 0, 0, 0);
+  int tm, tn;
+  raster_tile(p->sk_dp + tt, p->tiles_m, p->tiles_n, p->raster, tm, tn);
+  *slot = c * p->sk_segs + jseg;
+  return make_int4(tm, tn, kb0, kb1);
+}
+
+// Whether a member takes a stream-K tail: all but the exact-integer members
+// whose int32 sums live in registers (128 or 64 per epilogue thread), whose
+// epilogue has no registers to spare for per-tile output descriptors.
+template <int BM_T, int MODE>
+struct TcStreamK {
+  static constexpr bool value = !(MODE == TC_I8EMU && BM_T < 256);
+};
+
+template <int BM_T, int CG = 1, bool kStreamK = true>
 struct SingleSched {
   const TcParams* p;
   const CUtensorMap* maps[kMapsPerProblem];   // A, B of planes 0..2 (kernel parameters)
   const CUtensorMap* cmap;      // C for TMA stores, or null
   int n_off;                    // 128 * (rank in the CTA pair): this CTA's columns of a pair tile
 
-  __device__ __forceinline__ int total() const { return p->tiles_m * p->tiles_n * p->splits; }
+  // Work items: tiles x splits; with a stream-K tail, the sk_dp whole tiles
+  // and then sk_segs segment slots per stream (item sk_dp + j * sk_streams + c
+  // is segment j of stream c, so the persistent CTA c walks exactly its own
+  // stream when the grid holds sk_streams CTAs or pairs).
+  __device__ __forceinline__ int total() const {
+    return kStreamK && p->sk_streams > 0 ? p->sk_dp + p->sk_streams * p->sk_segs
+                                         : p->tiles_m * p->tiles_n * p->splits;
+  }
 
   __device__ __forceinline__ TileJob tile(int t) const {
+    int tm, tn;
+    if (kStreamK && p->sk_streams > 0 && t >= p->sk_dp) {
+      int slot = 0;
+      const int4 w = stream_k_item(p, t - p->sk_dp, &slot);
+      return TileJob{w.x * BM_T, w.y * (128 * CG) + n_off, w.z, w.w, BM_T, slot, 0, p->kchunk, 1};
+    }
     const int per_split = p->tiles_m * p->tiles_n;
     const int s = t / per_split;
-    const int r = t - s * per_split;
-    const int G = p->raster;
-    const int band = r / (G * p->tiles_n);
-    const int in_band = r - band * G * p->tiles_n;
-    const int rows = min(G, p->tiles_m - band * G);
-    const int tm = band * G + in_band % rows;
-    const int tn = in_band / rows;
+    raster_tile(t - s * per_split, p->tiles_m, p->tiles_n, p->raster, tm, tn);
     const int kb0 = s * p->kb_per_split;
     return TileJob{tm * BM_T, tn * (128 * CG) + n_off, kb0, min(p->num_kb, kb0 + p->kb_per_split), BM_T, s, 0,
-                   p->kchunk};
+                   p->kchunk, 0};
   }
 
   __device__ __forceinline__ const CUtensorMap* map(const TileJob&, int which) const { return maps[which]; }
 
   __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
+    if (kStreamK && j.sk) {   // a stream-K segment: its partial tile, (bm rows) x (128 * CG columns)
+      constexpr long long ldp = 128 * CG;
+      const uintptr_t slot = reinterpret_cast<uintptr_t>(p->partial + (long long)j.split * (BM_T * ldp));
+      const long long origin = (long long)j.m0 * ldp + (j.n0 - n_off);   // the slot holds elements from here on
+      return EpiJob{p->C, p->ldc, p->m, p->n, p->alpha, p->beta, OUT_PARTIAL,
+                    reinterpret_cast<float*>(slot - (uintptr_t)origin * sizeof(float)), nullptr, ldp};
+    }
     return EpiJob{p->C, p->ldc, p->m, p->n, p->alpha, p->beta, p->out_mode,
-                  p->partial ? p->partial + (long long)j.split * p->m * p->n : nullptr, cmap};
+                  p->partial ? p->partial + (long long)j.split * p->m * p->n : nullptr, cmap, p->n};
   }
 
   __device__ __forceinline__ bool conv() const { return p->conv != 0; }
@@ -275,7 +323,7 @@ struct GroupedSched {
     const int g = ti.x;
     const GroupDesc* d = gp->groups + g;
     const int tm = ti.y % d->tiles_m, tn = ti.y / d->tiles_m;
-    return TileJob{tm * d->bm, tn * 128, 0, d->num_kb, d->bm, 0, g, 0};
+    return TileJob{tm * d->bm, tn * 128, 0, d->num_kb, d->bm, 0, g, 0, 0};
   }
 
   __device__ __forceinline__ const CUtensorMap* map(const TileJob& j, int which) const {
@@ -284,7 +332,7 @@ struct GroupedSched {
 
   __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
     const GroupDesc* d = gp->groups + j.g;
-    return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr, nullptr};
+    return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr, nullptr, 0};
   }
 
   __device__ __forceinline__ bool conv() const { return false; }
@@ -371,6 +419,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       bool ok = true;
       for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
         const TileJob j = S.tile(t);
+        if (j.kb1 <= j.kb0) continue;   // an empty stream-K slot (every role skips it)
         // bytes this CTA stages per k-block; a pair's leader counts both CTAs'
         const uint32_t stage_bytes = T::kPlanes * (T::kBtBytes + (uint32_t)j.bm * 128u / CG);
         const int a_row = j.m0 + (int)rank * (j.bm / CG);
@@ -440,6 +489,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       };
       for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
         const TileJob j = S.tile(t);
+        if (j.kb1 <= j.kb0) continue;
         const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/!T::kBtKMajor, /*b_mn=*/false, 128 * CG, j.bm);
         const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
         for (int c0 = j.kb0; ok && c0 < j.kb1; c0 += span, ++lt) {
@@ -523,6 +573,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
     bool alive = true;
     for (int t = first_tile; alive && t < total_tiles; t += tile_stride) {
       const TileJob j = S.tile(t);
+      if (j.kb1 <= j.kb0) continue;
       const EpiJob e = S.epi(j);
       const float alpha = e.alpha * scale;
       const float beta = e.beta;
@@ -613,8 +664,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             const int i0 = j.m0 + r0 + rc * 32;
             const int iend = min(32, e.m - i0);
             const bool partial = e.out_mode == OUT_PARTIAL;
-            const long long ld = partial ? (long long)e.n : e.ldc;
-            int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.n + col
+            const long long ld = partial ? e.ldp : e.ldc;
+            int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.ldp + col
                               : static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
             const bool add_c = !partial && beta != 0.0f;
             int cv[32];   // the reads of C first: one memory round trip
@@ -670,8 +721,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           // would otherwise keep an address per row live across the tile).
           const int i0 = j.m0 + r0;
           const bool partial = e.out_mode == OUT_PARTIAL;
-          const long long ld = partial ? (long long)e.n : e.ldc;
-          int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.n + col
+          const long long ld = partial ? e.ldp : e.ldc;
+          int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.ldp + col
                             : static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
           const bool add_c = !partial && beta != 0.0f;
 #pragma unroll
@@ -723,10 +774,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             for (int i = 0; i < 32; ++i)
               if (i < iend) cp[i * e.ldc] = cv[i] + __float2int_rn(__uint_as_float(r[i]));
           } else {
-            float* pp = e.partial + (long long)i0 * e.n + col;
+            float* pp = e.partial + (long long)i0 * e.ldp + col;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (i < iend) pp[(long long)i * e.n] = __uint_as_float(r[i]);
+              if (i < iend) pp[(long long)i * e.ldp] = __uint_as_float(r[i]);
           }
         }
       };
@@ -803,7 +854,7 @@ __global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE, CG>::kThreads, 1)
     if (p.c_tma) tma_prefetch_desc(&tmC);
   }
   const int n_off = (CG == 2) ? 128 * (int)cluster_ctarank() : 0;
-  const SingleSched<BM_T, CG> S{&p, {&tmA, &tmB, &tmA1, &tmB1, &tmA2, &tmB2}, p.c_tma ? &tmC : nullptr, n_off};
+  const SingleSched<BM_T, CG, TcStreamK<BM_T, MODE>::value> S{&p, {&tmA, &tmB, &tmA1, &tmB1, &tmA2, &tmB2}, p.c_tma ? &tmC : nullptr, n_off};
   tc_gemm_body<BM_T, STAGES, MODE, CG>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
 }
 
