@@ -264,12 +264,9 @@ double tile_efficiency(const FamilyEntry& f) {
 // Slow-down of a member whose single accumulator set makes the MMA wait for
 // each tile's epilogue: epilogue time over main-loop time of one tile (the
 // epilogue reads and writes its bm x 128 block of C at about 45 bytes per ns
-// per SM, plus ~2 us of TMEM and barrier latency).  The exact-integer members
-// with sums in TMEM wait at every 1024-product chunk instead (measured 0.74 of
-// the 0.96 their tile reaches without chunks).
+// per SM, plus ~2 us of TMEM and barrier latency).
 double single_buffer_factor(const FamilyEntry& f, int num_kb) {
   if (f.bufs >= 2) return 1.0;
-  if (f.mode == TC_I8EMU) return 1.3;
   const double t_tile_ns = num_kb * kblock_clocks(f) / 1.9;
   const double t_epi_ns = f.bm * 128.0 * 8.0 / 45.0 + 2000.0;
   return 1.0 + t_epi_ns / std::max(t_tile_ns, 1.0);

@@ -12,7 +12,7 @@
 //               lives in TMEM (the "C resident" micro-kernel of Section 4.1 with
 //               TMEM in place of the register file), multi-buffered across tiles
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator, alpha/beta, stores
-//               (warps 2..9 for the exact-integer member with sums in TMEM)
+//               (warps 2..17 for the exact-integer member with bm = 256)
 //
 // Orientation.  The MMA computes D = Bt * At, i.e. the transpose of the C tile:
 // TMEM lane = column j of C (128 per tile), TMEM column = row i of C (bm per
@@ -174,21 +174,18 @@ struct TcConfig {
   static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16 || MODE == TC_6XBF16) ? 2 : 1;
   static constexpr uint32_t kSetCols = kAccPerTile * BM_T;
   static constexpr uint32_t kMaxBufs = 4;
-  // The exact-integer mode with bm = 256 keeps its int32 running sums in TMEM
-  // (columns 256-511, beside one chunk accumulator) instead of registers.
-  static constexpr bool kTmemSums = (MODE == TC_I8EMU && BM_T == 256);
-  static constexpr uint32_t kSumCol = 256;
-  static constexpr uint32_t kNumBufs =
-      kTmemSums ? 1 : ((512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs);
-  static constexpr uint32_t kTmemCols = kTmemSums ? 512 : kNumBufs * kSetCols;
+  static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
+  static constexpr uint32_t kTmemCols = kNumBufs * kSetCols;
   // Epilogue warps: one per TMEM lane quarter, each thread owning all bm rows
-  // of its column -- except the TMEM-sum member, which drains its accumulator
-  // every 1024 products while the MMA waits: eight warps (two per lane
-  // quarter, 128 rows each) halve that drain.  (With the int32 sums in
-  // registers eight warps were slower: at bm = 256 the unrolled epilogue
-  // starved the MMA thread of instruction fetch, and at bm = 128 the
-  // 168-register cap of ten warps made it spill.)
-  static constexpr int kEpiWarps = kTmemSums ? 8 : 4;
+  // of its column -- except the exact-integer member with bm = 256, whose
+  // int32 running sums (one per row of the thread's column) live in
+  // registers: sixteen warps (four per lane quarter, 64 rows each) keep them
+  // within the 96 registers an 18-warp CTA allows, and TMEM holds two chunk
+  // accumulators, so the drain of one 1024-product chunk overlaps the MMAs of
+  // the next.  (Earlier designs with the sums in TMEM beside a single chunk
+  // accumulator made the MMA wait at every chunk: 0.74 of the peak against
+  // 0.93 now; eight warps with 128 register sums spilled.)
+  static constexpr int kEpiWarps = (MODE == TC_I8EMU && BM_T == 256) ? 16 : 4;
   static constexpr int kEpiRows = BM_T / (kEpiWarps / 4);   // rows of the tile per epilogue thread
   // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128 columns x 4 bytes.
   static constexpr uint32_t kCStageBytes = 2 * 32 * 128 * 4;
@@ -240,12 +237,12 @@ static __device__ __noinline__ int4 stream_k_item(const TcParams* p, int u, int*
   return make_int4(tm, tn, kb0, kb1);
 }
 
-// Whether a member takes a stream-K tail: all but the exact-integer members
-// whose int32 sums live in registers (128 or 64 per epilogue thread), whose
-// epilogue has no registers to spare for per-tile output descriptors.
+// Whether a member takes a stream-K tail: all but the exact-integer members,
+// whose int32 running sums fill the epilogue's registers (64 or 128 per
+// thread) and leave none to spare for per-tile output descriptors.
 template <int BM_T, int MODE>
 struct TcStreamK {
-  static constexpr bool value = !(MODE == TC_I8EMU && BM_T < 256);
+  static constexpr bool value = MODE != TC_I8EMU;
 };
 
 template <int BM_T, int CG = 1, bool kStreamK = true>
@@ -353,7 +350,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   using Cfg = TcConfig<BM_T, STAGES, MODE, CG>;
   constexpr bool kPair = (CG == 2);
   constexpr bool kIntChunked = (MODE == TC_I8EMU);
-  static_assert(!kIntChunked || Cfg::kTmemSums || Cfg::kEpiRows <= 128,
+  static_assert(!kIntChunked || Cfg::kEpiRows <= 128,
                 "int32 running sums in registers: <= 128 rows");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -608,7 +605,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       };
       // exact-integer mode: int32 running sums of this thread's column, one per
       // row r0 .. r0 + kEpiRows - 1 of the tile
-      constexpr int kSums = (kIntChunked && !Cfg::kTmemSums) ? Cfg::kEpiRows : 1;
+      constexpr int kSums = kIntChunked ? Cfg::kEpiRows : 1;
       int isum[kSums];
 #pragma unroll
       for (int i = 0; i < kSums; ++i) isum[i] = 0;
@@ -633,53 +630,24 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           else mbar_arrive(&tmem_empty[acc]);
         }
       };
-      if constexpr (Cfg::kTmemSums) {
-        // Exact integers, running sums in TMEM: per 32-row block, load the
-        // chunk's FP32 sums (exact integers, <= 1024 products of |x| <= 2^14)
-        // and the int32 running sums, add in int32, and either put the sums
-        // back (tcgen05.st) or, after the last chunk, write them to C.
-        // This warp's rows are r0 .. r0 + kEpiRows - 1 of the tile.
-        const uint32_t tsum = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + Cfg::kSumCol + r0;
-        const uint32_t tacc = tbase + r0;
-        const bool first = kc == 0, last = kc == nkc - 1;
-        if (nchunks_mine == 0) release();   // no rows here (short tile): hand back at once
-        for (int rc = 0; rc < nchunks_mine; ++rc) {
-          uint32_t ra[32], rs[32];
-          tmem_ld_32x32b_x32(tacc + rc * 32, ra);
-          if (!first) tmem_ld_32x32b_x32(tsum + rc * 32, rs);
-          tmem_ld_wait();
-          if (rc == nchunks_mine - 1) release();
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            rs[i] = static_cast<uint32_t>((first ? 0 : static_cast<int>(rs[i])) +
-                                          __float2int_rn(__uint_as_float(ra[i])));
-          if (!last) {
-            tmem_st_32x32b_x32(tsum + rc * 32, rs);
-          } else if (use_tma) {
-            float* buf = stage_begin();
-#pragma unroll
-            for (int i = 0; i < 32; ++i) buf[i * 128] = __uint_as_float(rs[i]);
-            stage_end(rc);
-          } else if (cok) {
-            const int i0 = j.m0 + r0 + rc * 32;
-            const int iend = min(32, e.m - i0);
-            const bool partial = e.out_mode == OUT_PARTIAL;
-            const long long ld = partial ? e.ldp : e.ldc;
-            int* cp = partial ? reinterpret_cast<int*>(e.partial) + (long long)i0 * e.ldp + col
-                              : static_cast<int*>(e.C) + (long long)i0 * e.ldc + col;
-            const bool add_c = !partial && beta != 0.0f;
-            int cv[32];   // the reads of C first: one memory round trip
-#pragma unroll
-            for (int i = 0; i < 32; ++i) cv[i] = (add_c && i < iend) ? cp[i * ld] : 0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (i < iend) cp[i * ld] = cv[i] + static_cast<int>(rs[i]);
-          }
-        }
-        if (!last) tmem_st_wait();
-      } else if constexpr (kIntChunked) {
+      if constexpr (kIntChunked) {
         // Each chunk holds an integer-valued FP32 sum of at most 1024 products
         // of magnitude <= 2^14, hence exact; convert and add in int32.
+        if constexpr (Cfg::kEpiWarps == 16) {
+          // 64 sums per thread within the 96 registers of an 18-warp CTA:
+          // 8-row blocks, one at a time (the other accumulator set keeps the
+          // MMA busy meanwhile)
+#pragma unroll
+          for (int rc = 0; rc < Cfg::kEpiRows / 8; ++rc) {
+            if (rc < 4 * nchunks_mine) {
+              uint32_t rv[8];
+              tmem_ld_32x32b_x8(tbase + r0 + rc * 8, rv);
+              tmem_ld_wait();
+#pragma unroll
+              for (int i = 0; i < 8; ++i) isum[rc * 8 + i] += __float2int_rn(__uint_as_float(rv[i]));
+            }
+          }
+        } else {
         // 16-row blocks, software-pipelined: block b+1 loads while b is added.
         constexpr int kBlocks = Cfg::kEpiRows / 16;   // even
         const int nb = 2 * nchunks_mine;
@@ -704,6 +672,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
               if (has_a) tmem_ld_wait();
             }
           }
+        }
         }
         release();
         if (kc == nkc - 1 && use_tma) {

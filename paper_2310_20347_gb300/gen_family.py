@@ -49,10 +49,9 @@ MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8", "int8emu
              "6xbf16": "TC_6XBF16", "f16": "TC_F16", "tf32": "TC_TF32"}
 SPLIT_MODES = ("3xbf16", "6xbf16")   # two accumulators per tile (main + corrections)
 BMS = (256, 128, 64)
-# int8emu keeps one int32 running sum per row of its column in registers, or,
-# with bm = 256, in TMEM beside a single chunk accumulator
+# int8emu keeps one int32 running sum per row of its column in registers
+# (with bm = 256: sixteen epilogue warps of 64 rows each)
 MAX_BM = {"int8emu": 256}
-TMEM_SUMS = {("int8emu", 256)}
 # CTA-pair members: tile heights worth pairing (a pair of bm = 64 tiles would
 # stage 32-row halves of A, no better than a single bm = 128 CTA)
 PAIR_BMS = (256, 128)
@@ -91,8 +90,6 @@ def enumerate_family():
                 if max(fits) - 1 in fits and max(fits) > 3:
                     chosen.append(max(fits) - 1)
                 bufs = min(4, tmem // acc_cols)                     # accumulator sets across tiles
-                if (mode, bm) in TMEM_SUMS:
-                    bufs = 1                                        # the other 256 columns hold the sums
                 for st in chosen:
                     members.append({"mode": mode, "bm": bm, "stages": st, "cg": cg,
                                     "smem": smem_bytes(mode, bm, st, cg), "tmem_bufs": bufs})

@@ -118,7 +118,7 @@ def test_planner_choices(lib):
     st, cfg, sk, rs = L.g3_plan_query(512, 49, 4608, L.G3_BF16)
     assert sk > 1
     # INT8 runs on the exact-integer members (k chunked inside the kernel): the
-    # bm = 256 CTA pair with its int32 running sums in TMEM, no split needed
+    # bm = 256 CTA pair (16 epilogue warps, two chunk accumulators), no split needed
     st, cfg, sk, rs = L.g3_plan_query(8192, 8192, 8192, L.G3_INT8)
     assert fam[cfg]["mode"] == "int8emu" and fam[cfg]["bm"] == 256 and fam[cfg]["cg"] == 2 and sk == 1
     # FP32-accurate at k <= 512: the three-part split (6 products); above: two-part

@@ -399,10 +399,11 @@ def test_int8_every_member(config):
 @pytest.mark.parametrize("shape,beta,split", [((600, 300, 2200), 0, 0), ((257, 520, 3000), 1, 0),
                                               ((300, 129, 4100), 0, 3), ((1, 1, 1), 0, 0), ((513, 260, 1024), 1, 2)])
 @pytest.mark.parametrize("config", [f["index"] for f in FAMILY if f["mode"] == "int8emu" and f["bm"] == 256])
-def test_int8_tmem_sums(config, shape, beta, split):
-    # bm = 256 members keep the int32 running sums in TMEM: chunks of 1024
-    # products, ragged rows and columns, C by TMA stores (beta = 0) or added in
-    # place (beta = 1), and int32 split-K partials
+def test_int8_bm256(config, shape, beta, split):
+    # bm = 256 members: sixteen epilogue warps with 64 int32 running sums each,
+    # two chunk accumulators in TMEM taken in turn: chunks of 1024 products,
+    # ragged rows and columns, C written (beta = 0) or added in place
+    # (beta = 1), and int32 split-K partials
     m, n, k = shape
     p = synth.int8_problem(m, n, k, seed=25, beta=beta)
     A, B = dev(p.A), dev(p.B)
@@ -411,6 +412,20 @@ def test_int8_tmem_sums(config, shape, beta, split):
     torch.cuda.synchronize()
     check_guard(full, m, n)
     assert np.array_equal(C.cpu().numpy().astype(np.int64), oracle.gemm_i8(p.A, p.B, p.C, 1, beta))
+
+
+@pytest.mark.parametrize("config", [f["index"] for f in FAMILY if f["mode"] == "int8emu" and f["bm"] == 256])
+def test_int8_bm256_worst_case_chunks(config):
+    # all -128 at k = 4100: every chunk accumulator reaches 1024 * 2^14 = 2^24
+    # (the largest sum FP32 holds exactly), five chunks alternate between the
+    # two accumulators; every entry is 4100 * 2^14
+    A = np.full((300, 4100), -128, np.int8)
+    B = np.full((4100, 260), -128, np.int8)
+    full, C = guarded(300, 260, None, dtype=torch.int32)
+    torch_api.gemm(dev(A), dev(B), C, 1, 0, dtype=G3_INT8, config=config)
+    torch.cuda.synchronize()
+    check_guard(full, 300, 260)
+    assert np.all(C.cpu().numpy() == 4100 * (1 << 14))
 
 
 def test_int8_worst_case_magnitude():
