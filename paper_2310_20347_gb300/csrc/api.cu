@@ -25,6 +25,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 
 constexpr int kHostMaxBlocks = 8;   // row blocks of a g3_gemm_host pipeline
+constexpr int kHostMaxSlabs = 4;    // k-slabs in which g3_gemm_host sends B up (FP32-accurate)
 
 struct DevState {
   bool init = false;
@@ -39,7 +40,7 @@ struct DevState {
   void* hbuf = nullptr;
   size_t hbuf_bytes = 0;
   cudaStream_t up = nullptr, down = nullptr;
-  cudaEvent_t ev[2 * kHostMaxBlocks + 3] = {};
+  cudaEvent_t ev[2 * kHostMaxBlocks + kHostMaxSlabs + 3] = {};
 };
 
 std::mutex g_mu;
@@ -415,7 +416,15 @@ struct Layout {
   size_t total = 0;
 };
 
-Layout make_layout(const g3_gemm_args& a, const Plan& pl) {
+// B of the FP32-accurate mode already split into bf16 hi / lo planes (leading
+// dimension ld), as g3_gemm_host keeps them for all the row blocks of a call.
+struct PreparedB {
+  const uint16_t* hi;
+  const uint16_t* lo;
+  int64_t ld;
+};
+
+Layout make_layout(const g3_gemm_args& a, const Plan& pl, bool b_prepared = false) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -430,8 +439,10 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl) {
       L.ldb_p = round_up(n, 8);
       L.a_hi = take((size_t)m * L.lda_p * 2);
       L.a_lo = take((size_t)m * L.lda_p * 2);
-      L.b_hi = take((size_t)k * L.ldb_p * 2);
-      L.b_lo = take((size_t)k * L.ldb_p * 2);
+      if (!b_prepared) {
+        L.b_hi = take((size_t)k * L.ldb_p * 2);
+        L.b_lo = take((size_t)k * L.ldb_p * 2);
+      }
       if (tc_mode_of(a.dtype, k) == TC_6XBF16) {
         L.a_mid = take((size_t)m * L.lda_p * 2);
         L.b_mid = take((size_t)k * L.ldb_p * 2);
@@ -576,12 +587,14 @@ int run_simt(const g3_gemm_args& a, cudaStream_t s) {
   return G3_OK;
 }
 
-int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* conv = nullptr) {
+int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* conv = nullptr,
+           const PreparedB* pb = nullptr) {
   const bool dev_scales = a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b);
   const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d.sms, a.config, a.split_k, a.raster, !dev_scales);
   if (pl.member < 0) return G3_ERR_UNSUPPORTED;
   const FamilyEntry& fam = g_family[pl.member];
-  const Layout L = make_layout(a, pl);
+  if (pb && tc_mode_of(a.dtype, a.k) != TC_3XBF16) return G3_ERR_ARG;   // only the two-part split
+  const Layout L = make_layout(a, pl, pb != nullptr);
   uint8_t* ws = nullptr;
   int st = get_workspace(d, a, L.total, &ws);
   if (st != G3_OK) return st;
@@ -604,10 +617,16 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
     uint16_t *ah = (uint16_t*)(ws + L.a_hi), *al = (uint16_t*)(ws + L.a_lo);
     uint16_t *bh = (uint16_t*)(ws + L.b_hi), *bl = (uint16_t*)(ws + L.b_lo);
     G3_CHECK_CUDA(launch_split_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p, s));
-    G3_CHECK_CUDA(launch_split_bf16((const float*)a.B, (int)k, (int)n, a.ldb, bh, bl, L.ldb_p, s));
-    A_hi = ah; A_lo = al; B_hi = bh; B_lo = bl;
+    A_hi = ah; A_lo = al;
     lda = L.lda_p;
-    ldb = L.ldb_p;
+    if (pb) {
+      B_hi = pb->hi; B_lo = pb->lo;
+      ldb = pb->ld;
+    } else {
+      G3_CHECK_CUDA(launch_split_bf16((const float*)a.B, (int)k, (int)n, a.ldb, bh, bl, L.ldb_p, s));
+      B_hi = bh; B_lo = bl;
+      ldb = L.ldb_p;
+    }
   } else if (a.dtype == G3_TF32) {
     float *ah = (float*)(ws + L.a_hi), *bh = (float*)(ws + L.b_hi);
     G3_CHECK_CUDA(launch_convert_tf32((const float*)a.A, (int)m, (int)k, a.lda, ah, L.lda_p, s));
@@ -807,7 +826,7 @@ int untranspose(DevState& d, g3_gemm_args& a, cudaStream_t s) {
   return G3_OK;
 }
 
-int gemm_impl(g3_gemm_args a, cudaStream_t s) {
+int gemm_impl(g3_gemm_args a, cudaStream_t s, const PreparedB* pb = nullptr) {
   int st = validate(a);
   if (st != G3_OK) return st;
   if (a.m == 0 || a.n == 0) return G3_OK;
@@ -825,7 +844,7 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s) {
   // the split-K reduce cannot: no split-K then
   if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b) && a.split_k > 1) a.split_k = 1;
   if (a.dtype == G3_F32) return run_simt(a, s);
-  return run_tc(*d, a, s);
+  return run_tc(*d, a, s, nullptr, pb);
 }
 
 }  // namespace
@@ -868,11 +887,19 @@ bool take_withhold(unsigned long long* timeout_ns) {
 using namespace g3;
 
 // C := beta*C + alpha*A*B with A, B, C in host memory, as a pipeline on three
-// streams: B goes up first (every row block of C needs all of it); then each
-// row block of A (and of C when beta != 0) goes up on `up` while the previous
-// block is computed on the caller's stream, and each finished block of C
-// comes back on `down` while later blocks compute.  Device copies live in a
-// library buffer; the caller's stream waits for the last download.
+// streams: copies up on `up`, compute on the caller's stream, copies down on
+// `down`, ordered by events.  C is cut into row blocks (about 2048 rows, four
+// to eight of them); each finished block goes down while later blocks compute.
+// Every row block needs all of B, so in the plain order nothing computes until
+// B has arrived.  For the FP32-accurate mode with the two-part split (k > 512)
+// B goes up instead in k-slabs, after row block 0 of A (and of C): each slab
+// is split into bf16 planes once -- kept for every row block of the call --
+// and row block 0 accumulates slab by slab (beta for the first slab, then 1),
+// so the tensor cores start after the first slab; the later blocks use the
+// prepared planes.  (Row block 0 is rounded to FP32 once per slab: at most
+// kHostMaxSlabs - 1 extra roundings of 2^-24 relative to its partial sums.)
+// Device copies live in a library buffer; the caller's stream waits for the
+// last download.
 static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   int st = validate(a);
   if (st != G3_OK) return st;
@@ -884,8 +911,25 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   const size_t c_bytes = align256((size_t)m * ldc_d * 4);
   const bool products = k > 0 && a.alpha != 0.0;
   const bool read_c = a.beta != 0.0;
-  const int nb = (m >= 2048 && products) ? 4 : 1;
+  const int nb = (m >= 2048 && products) ? (int)std::max<int64_t>(4, std::min<int64_t>(kHostMaxBlocks, (m + 2047) / 2048))
+                                         : 1;
   const int64_t rb = round_up((m + nb - 1) / nb, 256);
+  // B in k-slabs (prepared planes): slabs of at least 2048, each above the
+  // three-part split's bound so that every call takes the two-part split
+  const bool prep = nb > 1 && a.dtype == G3_F32_3XBF16 && tc_mode_of(a.dtype, k) == TC_3XBF16;
+  int ns = 1;
+  int64_t ks = k;
+  if (prep) {
+    ns = (int)std::max<int64_t>(1, std::min<int64_t>(kHostMaxSlabs, k / 2048));
+    for (;;) {
+      ks = round_up((k + ns - 1) / ns, 64);
+      ns = (int)((k + ks - 1) / ks);
+      if (ns == 1 || k - (ns - 1) * ks > kSixProductMaxK) break;
+      --ns;
+    }
+  }
+  const int64_t ldp = round_up(n, 8);   // leading dimension of the prepared planes
+  const size_t plane_bytes = prep ? align256((size_t)k * ldp * 2) : 0;
   uint8_t* base = nullptr;
   cudaEvent_t* ev = nullptr;
   cudaStream_t up = nullptr, down = nullptr;
@@ -900,7 +944,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
       for (auto& e : d->ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return G3_ERR_CUDA;
     }
-    const size_t need = a_bytes + b_bytes + c_bytes;
+    const size_t need = a_bytes + b_bytes + c_bytes + 2 * plane_bytes;
     if (d->hbuf_bytes < need) {
       if (d->hbuf) {
         cudaDeviceSynchronize();
@@ -922,42 +966,111 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   uint8_t* dA = base;
   uint8_t* dB = base + a_bytes;
   uint8_t* dC = base + a_bytes + b_bytes;
+  uint16_t* Bhi = reinterpret_cast<uint16_t*>(dC + c_bytes);
+  uint16_t* Blo = reinterpret_cast<uint16_t*>(dC + c_bytes + plane_bytes);
+  // events: 0 start, 1 + b row block b up, 1 + kHostMaxBlocks + b row block b
+  // done, 2 kHostMaxBlocks + 1 last download, 2 kHostMaxBlocks + 2 + j slab j up
+  cudaEvent_t* ev_up = ev + 1;
+  cudaEvent_t* ev_done = ev + 1 + kHostMaxBlocks;
+  cudaEvent_t ev_last = ev[2 * kHostMaxBlocks + 1];
+  cudaEvent_t* ev_slab = ev + 2 * kHostMaxBlocks + 2;
   // the device copies may still be in use by an earlier call on this stream
   G3_CHECK_CUDA(cudaEventRecord(ev[0], s));
   G3_CHECK_CUDA(cudaStreamWaitEvent(up, ev[0], 0));
-  if (products)
-    G3_CHECK_CUDA(cudaMemcpy2DAsync(dB, ldb_d * es, a.B, a.ldb * es, n * es, k, cudaMemcpyHostToDevice, up));
-  for (int b = 0; b < nb; ++b) {
-    const int64_t r0 = b * rb, r1 = std::min(m, r0 + rb);
-    if (r0 >= r1) break;
-    const int64_t rows = r1 - r0;
+  auto rows_of = [&](int b, int64_t* r0, int64_t* r1) {
+    *r0 = b * rb;
+    *r1 = std::min(m, *r0 + rb);
+    return *r0 < *r1;
+  };
+  auto up_rows = [&](int b) -> int {   // A (and C) rows of block b
+    int64_t r0, r1;
+    if (!rows_of(b, &r0, &r1)) return G3_OK;
     if (products)
       G3_CHECK_CUDA(cudaMemcpy2DAsync(dA + (size_t)r0 * lda_d * es, lda_d * es,
                                       static_cast<const uint8_t*>(a.A) + (size_t)r0 * a.lda * es, a.lda * es, k * es,
-                                      rows, cudaMemcpyHostToDevice, up));
+                                      r1 - r0, cudaMemcpyHostToDevice, up));
     if (read_c)
       G3_CHECK_CUDA(cudaMemcpy2DAsync(dC + (size_t)r0 * ldc_d * 4, ldc_d * 4,
                                       static_cast<const uint8_t*>(a.C) + (size_t)r0 * a.ldc * 4, a.ldc * 4, n * 4,
-                                      rows, cudaMemcpyHostToDevice, up));
-    G3_CHECK_CUDA(cudaEventRecord(ev[1 + b], up));
-    G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev[1 + b], 0));
+                                      r1 - r0, cudaMemcpyHostToDevice, up));
+    return G3_OK;
+  };
+  auto up_B = [&](int64_t k0, int64_t k1) -> int {   // rows k0 .. k1-1 of B
+    G3_CHECK_CUDA(cudaMemcpy2DAsync(dB + (size_t)k0 * ldb_d * es, ldb_d * es,
+                                    static_cast<const uint8_t*>(a.B) + (size_t)k0 * a.ldb * es, a.ldb * es, n * es,
+                                    k1 - k0, cudaMemcpyHostToDevice, up));
+    return G3_OK;
+  };
+  auto block_args = [&](int b, int64_t r0, int64_t r1) {
     g3_gemm_args blk = a;
-    blk.m = rows;
+    blk.m = r1 - r0;
     blk.A = dA + (size_t)r0 * lda_d * es;
     blk.lda = lda_d;
     blk.B = dB;
     blk.ldb = ldb_d;
     blk.C = dC + (size_t)r0 * ldc_d * 4;
     blk.ldc = ldc_d;
-    if ((st = gemm_impl(blk, s)) != G3_OK) return st;
-    G3_CHECK_CUDA(cudaEventRecord(ev[1 + kHostMaxBlocks + b], s));
-    G3_CHECK_CUDA(cudaStreamWaitEvent(down, ev[1 + kHostMaxBlocks + b], 0));
+    (void)b;
+    return blk;
+  };
+  auto down_rows = [&](int b, int64_t r0, int64_t r1) -> int {
+    G3_CHECK_CUDA(cudaEventRecord(ev_done[b], s));
+    G3_CHECK_CUDA(cudaStreamWaitEvent(down, ev_done[b], 0));
     G3_CHECK_CUDA(cudaMemcpy2DAsync(static_cast<uint8_t*>(a.C) + (size_t)r0 * a.ldc * 4, a.ldc * 4,
-                                    dC + (size_t)r0 * ldc_d * 4, ldc_d * 4, n * 4, rows, cudaMemcpyDeviceToHost,
+                                    dC + (size_t)r0 * ldc_d * 4, ldc_d * 4, n * 4, r1 - r0, cudaMemcpyDeviceToHost,
                                     down));
+    return G3_OK;
+  };
+  if (prep) {
+    // up: row block 0, the slabs of B, then the other row blocks
+    if ((st = up_rows(0)) != G3_OK) return st;
+    for (int j = 0; j < ns; ++j) {
+      if ((st = up_B(j * ks, std::min(k, (j + 1) * ks))) != G3_OK) return st;
+      G3_CHECK_CUDA(cudaEventRecord(ev_slab[j], up));
+    }
+    for (int b = 1; b < nb; ++b) {
+      if ((st = up_rows(b)) != G3_OK) return st;
+      G3_CHECK_CUDA(cudaEventRecord(ev_up[b], up));
+    }
+    // compute: row block 0 slab by slab, splitting each slab of B once
+    int64_t r0, r1;
+    rows_of(0, &r0, &r1);
+    for (int j = 0; j < ns; ++j) {
+      const int64_t k0 = j * ks, k1 = std::min(k, (j + 1) * ks);
+      G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_slab[j], 0));
+      G3_CHECK_CUDA(launch_split_bf16(reinterpret_cast<const float*>(dB + (size_t)k0 * ldb_d * es), (int)(k1 - k0),
+                                      (int)n, ldb_d, Bhi + k0 * ldp, Blo + k0 * ldp, ldp, s));
+      g3_gemm_args blk = block_args(0, r0, r1);
+      blk.k = k1 - k0;
+      blk.A = dA + (size_t)r0 * lda_d * es + (size_t)k0 * es;
+      blk.B = dB + (size_t)k0 * ldb_d * es;
+      if (j > 0) blk.beta = 1.0;
+      const PreparedB pb{Bhi + k0 * ldp, Blo + k0 * ldp, ldp};
+      if ((st = gemm_impl(blk, s, &pb)) != G3_OK) return st;
+    }
+    if ((st = down_rows(0, r0, r1)) != G3_OK) return st;
+    const PreparedB pb{Bhi, Blo, ldp};
+    for (int b = 1; b < nb; ++b) {
+      if (!rows_of(b, &r0, &r1)) break;
+      G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_up[b], 0));
+      if ((st = gemm_impl(block_args(b, r0, r1), s, &pb)) != G3_OK) return st;
+      if ((st = down_rows(b, r0, r1)) != G3_OK) return st;
+    }
+  } else {
+    // B up first (every row block of C needs all of it), then the row blocks
+    if (products && (st = up_B(0, k)) != G3_OK) return st;
+    for (int b = 0; b < nb; ++b) {
+      int64_t r0, r1;
+      if (!rows_of(b, &r0, &r1)) break;
+      if ((st = up_rows(b)) != G3_OK) return st;
+      G3_CHECK_CUDA(cudaEventRecord(ev_up[b], up));
+      G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_up[b], 0));
+      if ((st = gemm_impl(block_args(b, r0, r1), s)) != G3_OK) return st;
+      if ((st = down_rows(b, r0, r1)) != G3_OK) return st;
+    }
   }
-  G3_CHECK_CUDA(cudaEventRecord(ev[2 * kHostMaxBlocks + 1], down));
-  G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev[2 * kHostMaxBlocks + 1], 0));
+  G3_CHECK_CUDA(cudaEventRecord(ev_last, down));
+  G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_last, 0));
   return G3_OK;
 }
 

@@ -19,16 +19,23 @@ def pinned(x, pad=0):
     return full[:, : x.shape[1]]
 
 
-@pytest.mark.parametrize("m,n,k,dtype,pad", [(300, 200, 150, G3_F32, 0), (2500, 300, 700, G3_F32_3XBF16, 3),
-                                             (2049, 130, 64, G3_F32_3XBF16, 0), (700, 520, 300, G3_F32, 5)])
-def test_host_fp32(m, n, k, dtype, pad):
-    p = synth.uniform_problem(m, n, k, seed=40, alpha=1.25, beta=0.5)
-    hA, hB, hC = pinned(torch.from_numpy(p.A), pad), pinned(torch.from_numpy(p.B), pad), pinned(torch.from_numpy(p.C), pad)
+# (2100, 300, 4500) and (4200, 260, 9000): B goes up in two and four k-slabs,
+# row block 0 accumulating slab by slab on prepared bf16 planes of B
+@pytest.mark.parametrize("m,n,k,dtype,pad,beta", [(300, 200, 150, G3_F32, 0, 0.5), (2500, 300, 700, G3_F32_3XBF16, 3, 0.5),
+                                                  (2049, 130, 64, G3_F32_3XBF16, 0, 0.5), (700, 520, 300, G3_F32, 5, 0.5),
+                                                  (2100, 300, 4500, G3_F32_3XBF16, 2, 0.5),
+                                                  (4200, 260, 9000, G3_F32_3XBF16, 0, 0.0)])
+def test_host_fp32(m, n, k, dtype, pad, beta):
+    p = synth.uniform_problem(m, n, k, seed=40, alpha=1.25, beta=beta)
+    hA, hB = pinned(torch.from_numpy(p.A), pad), pinned(torch.from_numpy(p.B), pad)
+    # beta = 0: C is never read (NaN must be overwritten)
+    hC = pinned(torch.from_numpy(p.C) if p.C is not None else torch.full((m, n), float("nan")), pad)
     s = torch.cuda.current_stream()
     torch_api.gemm_host(hA, hB, hC, p.alpha, p.beta, dtype=dtype, stream=s)
     s.synchronize()
     D = oracle.absprod(p.A, p.B, p.alpha)
-    e = rel_err(hC.numpy(), oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), D, p.beta * p.C.astype(np.float64))
+    bc = None if p.C is None else p.beta * p.C.astype(np.float64)
+    e = rel_err(hC.numpy(), oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), D, bc)
     assert e <= 2e-6, e
 
 
