@@ -74,6 +74,9 @@ def _load():
             lib.oracle_gemm_rows_6xbf16_f64.argtypes = [i64, vp, i64, i64, dbl, vp, i64, vp,
                                                         i64, dbl, vp, i64, vp, i64, i32]
             lib.oracle_split3_bf16.argtypes = [ctypes.c_float, vp, vp, vp]
+            lib.oracle_split_tf32.argtypes = [ctypes.c_float, vp, vp]
+            lib.oracle_gemm_rows_3xtf32_f64.argtypes = [i64, vp, i64, i64, dbl, vp, i64, vp,
+                                                        i64, dbl, vp, i64, vp, i64, i32]
             lib.oracle_max_threads.restype = i32
             _lib = lib
     return _lib
@@ -186,6 +189,33 @@ def gemm_6xbf16(A, B, C=None, alpha=1.0, beta=0.0, rows=None, nthreads=0):
                                         _ptr(B), max(n, 1), float(beta), _ptr(Cin), max(n, 1),
                                         _ptr(out), max(n, 1), int(nthreads))
     return out
+
+
+def gemm_3xtf32(A, B, C=None, alpha=1.0, beta=0.0, rows=None, nthreads=0):
+    """The 3-product method on the two-part TF32 split, in binary64."""
+    A = _c(A, np.float32)
+    B = _c(B, np.float32)
+    m, k = A.shape
+    n = B.shape[1]
+    Cin = _c(C, np.float64) if (C is not None and beta != 0.0) else None
+    r, nr = _rows_arg(rows, m)
+    out = np.empty((nr, n), np.float64)
+    _load().oracle_gemm_rows_3xtf32_f64(nr, _ptr(r), n, k, float(alpha), _ptr(A), max(k, 1),
+                                        _ptr(B), max(n, 1), float(beta), _ptr(Cin), max(n, 1),
+                                        _ptr(out), max(n, 1), int(nthreads))
+    return out
+
+
+def split_tf32(x):
+    """(hi, lo) float32 arrays with hi = tf32(x), lo = tf32(x - hi)."""
+    lib = _load()
+    x = _c(x, np.float32)
+    hi, lo = np.empty_like(x), np.empty_like(x)
+    h, l = ctypes.c_float(), ctypes.c_float()
+    for idx, v in enumerate(x.ravel()):
+        lib.oracle_split_tf32(float(v), ctypes.byref(h), ctypes.byref(l))
+        hi.flat[idx], lo.flat[idx] = h.value, l.value
+    return hi, lo
 
 
 def split3_bf16(x):

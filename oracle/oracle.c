@@ -390,3 +390,60 @@ void oracle_gemm_rows_3xbf16_f64(int64_t nrows, const int64_t* rows, int64_t n, 
     free(Bh);
     free(Bl);
 }
+
+void oracle_split_tf32(float x, float* hi, float* lo) {
+    float h = oracle_round_tf32(x);
+    float d = x - h;   /* exact in binary32: h is x rounded to 11 significant bits */
+    *hi = h;
+    *lo = oracle_round_tf32(d);
+}
+
+/* The 3-product method on the TF32 split: 1) split both operands in two,
+ * 2) form the three kept products per term, 3) sum over p in binary64.       */
+void oracle_gemm_rows_3xtf32_f64(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
+                                 double alpha, const float* A, int64_t lda,
+                                 const float* B, int64_t ldb, double beta,
+                                 const double* C_in, int64_t ldc_in,
+                                 double* C_out, int64_t ldc_out, int nthreads) {
+    if (nrows <= 0 || n <= 0) return;
+    int nt = threads_for(nthreads);
+    size_t kn = (size_t)(k > 0 ? k : 1) * (size_t)n;
+    double* Bh = (double*)malloc(sizeof(double) * kn);
+    double* Bl = (double*)malloc(sizeof(double) * kn);
+    for (int64_t p = 0; p < k; ++p)
+        for (int64_t j = 0; j < n; ++j) {
+            float h, l;
+            oracle_split_tf32(B[p * ldb + j], &h, &l);
+            Bh[p * n + j] = h;
+            Bl[p * n + j] = l;
+        }
+#pragma omp parallel num_threads(nt)
+    {
+        double* acc = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t r = 0; r < nrows; ++r) {
+            int64_t i = row_index(rows, r);
+            for (int64_t j = 0; j < n; ++j) acc[j] = 0.0;
+            if (alpha != 0.0) {
+                for (int64_t p = 0; p < k; ++p) {
+                    float ah_f, al_f;
+                    oracle_split_tf32(A[i * lda + p], &ah_f, &al_f);
+                    double ah = ah_f, al = al_f;
+                    const double* bh = Bh + p * n;
+                    const double* bl = Bl + p * n;
+                    for (int64_t j = 0; j < n; ++j)
+                        acc[j] += ah * bh[j] + ah * bl[j] + al * bh[j];
+                }
+            }
+            double* crow = C_out + r * ldc_out;
+            for (int64_t j = 0; j < n; ++j) {
+                double ab = (alpha != 0.0) ? alpha * acc[j] : 0.0;
+                double bc = (beta != 0.0) ? beta * C_in[i * ldc_in + j] : 0.0;
+                crow[j] = bc + ab;
+            }
+        }
+        free(acc);
+    }
+    free(Bh);
+    free(Bl);
+}

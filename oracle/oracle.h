@@ -88,6 +88,22 @@ void  oracle_round_bf16_array(const float* x, float* y, int64_t count);
 float oracle_round_tf32(float x);
 void  oracle_round_tf32_array(const float* x, float* y, int64_t count);
 
+/* --- A second FP32-accurate split on TF32 (a further datatype of Section 8.6's
+ *     study): x_hi = tf32(x), x_lo = tf32(x - x_hi), both rounded to nearest
+ *     even on the TF32 grid (the difference is exact in binary32: x_hi is x
+ *     rounded to 11 significant bits).  |x - x_hi - x_lo| <= 2^-22 |x| for
+ *     normal x.                                                              */
+void oracle_split_tf32(float x, float* hi, float* lo);
+
+/* The 3-product method on the TF32 split, step by step, in binary64:
+ * S = sum_p (Ahi*Bhi + Ahi*Blo + Alo*Bhi), the Alo*Blo term dropped;
+ * C_out = beta*C_in + alpha*S, for the rows given (as oracle_gemm_rows_f64). */
+void oracle_gemm_rows_3xtf32_f64(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
+                                 double alpha, const float* A, int64_t lda,
+                                 const float* B, int64_t ldb, double beta,
+                                 const double* C_in, int64_t ldc_in,
+                                 double* C_out, int64_t ldc_out, int nthreads);
+
 /* OCP FP8 E4M3 ("fn"): 1 sign, 4 exponent (bias 7), 3 fraction bits, no
  * infinities, NaN = S.1111.111, largest finite 448.  Decoding is the format
  * definition; encoding picks the nearest finite value with ties to the even

@@ -219,3 +219,51 @@ def test_tf32_closed_forms_and_overflow(oracle):
     assert list(got) == [0x7F7FE000, 0x7F7FE000, 0x7F800000, 0xFF800000, 0x7F800000]
     sub = _f32([0x00000FFF, 0x00001000, 0x00003000, 0x00001001])   # subnormals: spacing 2^-136
     assert list(oracle.round_tf32(sub).view(np.uint32)) == [0x0, 0x0, 0x4000, 0x2000]
+
+
+# ---------------------------------------------------------------- 3xTF32
+def test_split_tf32_error_bound_and_grid(oracle):
+    # hi = tf32(x) keeps 11 significant bits, so x - hi is exact and lo = tf32(x - hi)
+    # leaves |x - hi - lo| <= 2^-11 |x - hi| <= 2^-22 |x|
+    r = np.random.default_rng(70)
+    x = np.concatenate([r.uniform(-1, 1, 50000), r.standard_normal(50000) * 1e6,
+                        r.standard_normal(1000) * 1e-30]).astype(np.float32)
+    hi, lo = oracle.split_tf32(x)
+    assert np.all((hi.view(np.uint32) & 0x1FFF) == 0) and np.all((lo.view(np.uint32) & 0x1FFF) == 0)
+    assert np.array_equal(hi, oracle.round_tf32(x))
+    err = np.abs(x.astype(np.float64) - hi.astype(np.float64) - lo.astype(np.float64))
+    assert np.all(err <= np.abs(x.astype(np.float64)) * 2.0 ** -22)
+    # values with at most 22 significant bits split exactly
+    y = (r.integers(-(1 << 21), 1 << 21, 10000) * 2.0 ** -30).astype(np.float32)
+    h, l = oracle.split_tf32(y)
+    assert np.array_equal(h.astype(np.float64) + l.astype(np.float64), y.astype(np.float64))
+
+
+def test_3xtf32_closed_form(oracle):
+    # a = 1 + 2^-12 splits as (1, 2^-12) (TF32's spacing at 1 is 2^-10);
+    # b = 1 + 2^-13 as (1, 2^-13).  ab = 1 + 2^-12 + 2^-13 + 2^-25; the
+    # 3-product method drops lo*lo = 2^-25.
+    a = np.array([[1 + 2.0 ** -12]], np.float32)
+    b = np.array([[1 + 2.0 ** -13]], np.float32)
+    got = oracle.gemm_3xtf32(a, b)[0, 0]
+    assert got == 1 + 2.0 ** -12 + 2.0 ** -13
+    assert oracle.gemm(a, b)[0, 0] - got == 2.0 ** -25
+
+
+def test_3xtf32_exact_on_tf32_inputs(oracle):
+    p = synth.small_int_problem(23, 31, 45, seed=71, alpha=0.5, beta=2.0)
+    assert np.array_equal(oracle.gemm_3xtf32(p.A, p.B, p.C, 0.5, 2.0), oracle.gemm(p.A, p.B, p.C, 0.5, 2.0))
+
+
+def test_3xtf32_within_split_bound(oracle):
+    # a = ah + al + ea with |al| <= 2^-11 |a|, |ea| <= 2^-22 |a| (likewise b):
+    # |ab - (ah bh + ah bl + al bh)| <= (3 * 2^-22 + 2^-33)|a||b| to first order
+    bound = 3 * 2.0 ** -22 + 2.0 ** -32
+    for seed, (m, n, k) in enumerate([(40, 50, 16), (20, 30, 600)]):
+        p = synth.uniform_problem(m, n, k, seed=72 + seed)
+        exact = oracle.gemm(p.A, p.B)
+        approx = oracle.gemm_3xtf32(p.A, p.B)
+        rel = np.max(np.abs(approx - exact) / oracle.absprod(p.A, p.B))
+        assert 0 < rel <= bound
+        # against the two-part bfloat16 split: the 22-bit split is far closer
+        assert rel < np.max(np.abs(oracle.gemm_3xbf16(p.A, p.B) - exact) / oracle.absprod(p.A, p.B)) / 8
