@@ -287,7 +287,7 @@ def run_workload(args):
 
     import oracle
     import paper_2310_20347_gb300 as pkg
-    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib, synth,
+    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib, synth,
                                         torch_api)
     torch.cuda.set_device(0)
     pkg.load()
@@ -527,9 +527,17 @@ def run_workload(args):
                "per_shape": per})
         return
 
-    if args.workload in ("int8", "fp8", "bf16", "fp16", "tf32"):
+    if args.workload in ("int8", "fp8", "bf16", "fp16", "tf32", "3xtf32"):
         n = args.dsize
-        if args.workload == "tf32":
+        if args.workload == "3xtf32":
+            # the second FP32-accurate mode, on the headline's inputs (uniform,
+            # beta = 0.5 with C)
+            p = synth.uniform_problem(n, n, n, seed=0, alpha=1.0, beta=0.5)
+            A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+            C0 = torch.from_numpy(p.C).to(dev)
+            C = C0.clone()
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.5, dtype=G3_F32_3XTF32, config=args.config)
+        elif args.workload == "tf32":
             p = synth.normal_problem(n, n, n, seed=0)
             A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
             C = torch.empty(n, n, dtype=torch.float32, device=dev)
@@ -563,6 +571,9 @@ def run_workload(args):
         got = C[torch.from_numpy(rows).to(dev)].cpu().numpy()
         if args.workload == "int8":
             err = {"exact": bool(np.array_equal(got.astype(np.int64), oracle.gemm_i8(p.A, p.B, rows=rows)))}
+        elif args.workload == "3xtf32":
+            err = sample_err(got.astype(np.float64), rows, p.A, p.B, p.C, 1.0, 0.5)
+            C.copy_(C0)
         else:
             err = sample_err(got.astype(np.float64), rows, p.A, p.B, None, 1.0, 0.0)
         for _ in range(args.warmup):
@@ -570,22 +581,28 @@ def run_workload(args):
         ms = _call_ms(fn, args.reps, flush)
         kms = _kernel_ms(_lib, fn, args.reps, flush)
         flops = 2.0 * n ** 3
-        tensor_peak = bf16_peak * {"fp8": 2.0, "tf32": 0.5}.get(args.workload, 1.0)
+        tensor_peak = bf16_peak * {"fp8": 2.0, "tf32": 0.5, "3xtf32": 0.5}.get(args.workload, 1.0)
+        tensor_flops = flops * (3.0 if args.workload == "3xtf32" else 1.0)   # three TF32 products per term
         _line(args, flops / ms / 1e9, "TOPS" if args.workload == "int8" else "TFLOPS",
-              {"workload": f"{args.workload} GEMM m=n=k={n}, alpha=1, beta=0",
+              {"workload": f"{args.workload} GEMM m=n=k={n}, alpha=1, "
+                           + ("beta=0.5, uniform [-1, 1]" if args.workload == "3xtf32" else "beta=0"),
                "path": {"int8": "exact: int8 -> bf16 pre-pass, k-chunks of 1024 on the BF16 tensor path, "
                                 "int32 split-K reduce (tcgen05 kind::i8 does not exist on sm_103a)",
                         "fp8": "tcgen05 kind::f8f6f4 E4M3, per-tensor scales",
                         "bf16": "tcgen05 kind::f16 BF16, FP32 accumulation",
                         "fp16": "tcgen05 kind::f16 FP16, FP32 accumulation",
-                        "tf32": "TF32 rounding pre-pass + tcgen05 kind::tf32, FP32 accumulation"}[args.workload]},
+                        "tf32": "TF32 rounding pre-pass + tcgen05 kind::tf32, FP32 accumulation",
+                        "3xtf32": "FP32-accurate: hi/lo TF32 split pre-pass + 3 tcgen05 kind::tf32 products "
+                                  "(main and correction accumulators)"}[args.workload]},
               {"dtype": args.workload, "ms": ms, "kernel_ms": kms, "err": err,
-               "roofline": {"bound": "tensor", "achieved": flops / kms / 1e9, "peak": tensor_peak,
-                            "unit": "TFLOP/s", "frac": flops / kms / 1e9 / tensor_peak, "traffic": None,
+               "roofline": {"bound": "tensor", "achieved": tensor_flops / kms / 1e9, "peak": tensor_peak,
+                            "unit": "TFLOP/s", "frac": tensor_flops / kms / 1e9 / tensor_peak, "traffic": None,
                             "peak_source": f"{peak_src} bf16 burst" + {
                                 "fp8": " x 2 (fp8 nominal ratio)",
-                                "tf32": " x 0.5 (tf32 nominal ratio)"}.get(args.workload, ""),
-                            "algorithmic": "2 n^3 per call (INT8: of the main kernel's bf16 work)"}})
+                                "tf32": " x 0.5 (tf32 nominal ratio)",
+                                "3xtf32": " x 0.5 (tf32 nominal ratio)"}.get(args.workload, ""),
+                            "algorithmic": "2 n^3 per call (INT8: of the main kernel's bf16 work; "
+                                           "3xTF32: 3 x 2 n^3 tf32 tensor flops)"}})
         return
 
     if args.workload == "conv":
@@ -740,7 +757,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "conv",
+                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "conv",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

@@ -67,7 +67,14 @@ extern "C" {
  *   G3_FP16        A, B IEEE binary16 (raw 16-bit patterns); C float32.
  *   G3_TF32        A, B, C float32; A and B rounded to TF32 (10 fraction
  *                  bits, nearest even) by a pre-pass, products on kind::tf32
- *                  with FP32 accumulation.                                 */
+ *                  with FP32 accumulation.
+ *   G3_F32_3XTF32  A, B, C float32; a second FP32-accurate mode: each operand
+ *                  split into hi + lo TF32 parts (hi = tf32(x), lo =
+ *                  tf32(x - hi): 22 significant bits), C += Ahi*Bhi + Ahi*Blo
+ *                  + Alo*Bhi on kind::tf32 with FP32 accumulation (lo*lo is
+ *                  dropped; at most 3*2^-22 of |a||b| per product).  Twice
+ *                  the tensor time of G3_F32_3XBF16; single GEMMs only (the
+ *                  grouped calls take G3_BF16 and G3_F32_3XBF16).          */
 typedef enum {
   G3_F32 = 0,
   G3_F32_3XBF16 = 1,
@@ -75,7 +82,8 @@ typedef enum {
   G3_FP8_E4M3 = 3,
   G3_INT8 = 4,
   G3_FP16 = 5,
-  G3_TF32 = 6
+  G3_TF32 = 6,
+  G3_F32_3XTF32 = 7
 } g3_dtype;
 
 /* g3_gemm_args.split_k value that asks for a stream-K tail (see there).    */
@@ -212,6 +220,12 @@ G3_API int g3_convert_tf32(const float* x, int64_t rows, int64_t cols, int64_t l
 /* hi = bf16(x), lo = bf16(x - hi): the split of the FP32-accurate mode.     */
 G3_API int g3_split_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* lo, int64_t ldy,
                   void* cuda_stream);
+
+/* hi = tf32(x), lo = tf32(x - hi) (nearest even on the TF32 grid, stored as
+ * float32; the difference is exact): the split of G3_F32_3XTF32.  Errors as
+ * g3_split_bf16.                                                            */
+G3_API int g3_split_tf32(const float* x, int64_t rows, int64_t cols, int64_t ldx, float* hi, float* lo, int64_t ldy,
+                         void* cuda_stream);
 
 /* hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid): the three-part
  * split the FP32-accurate mode uses for k <= 512 (both differences are exact

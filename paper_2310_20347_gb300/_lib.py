@@ -15,10 +15,10 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libg3gemm.so")
 
-G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP8_E4M3, G3_INT8, G3_FP16, G3_TF32 = 0, 1, 2, 3, 4, 5, 6
+G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP8_E4M3, G3_INT8, G3_FP16, G3_TF32, G3_F32_3XTF32 = 0, 1, 2, 3, 4, 5, 6, 7
 G3_SPLIT_STREAM_K = -1   # g3_gemm_args.split_k: a stream-K tail
 DTYPES = {"f32": G3_F32, "3xbf16": G3_F32_3XBF16, "bf16": G3_BF16, "fp8": G3_FP8_E4M3, "int8": G3_INT8,
-          "fp16": G3_FP16, "tf32": G3_TF32}
+          "fp16": G3_FP16, "tf32": G3_TF32, "3xtf32": G3_F32_3XTF32}
 
 G3_OK, G3_ERR_ARG, G3_ERR_UNSUPPORTED, G3_ERR_CUDA, G3_ERR_NOMEM, G3_ERR_TIMEOUT, G3_ERR_NOT_INIT = (
     0, -1, -2, -3, -4, -5, -6)
@@ -26,7 +26,7 @@ G3_OK, G3_ERR_ARG, G3_ERR_UNSUPPORTED, G3_ERR_CUDA, G3_ERR_NOMEM, G3_ERR_TIMEOUT
 # Every symbol include/g3gemm.h declares (checked against the header by the tests).
 EXPORTED = (
     "g3_gemm", "g3_gemm_host", "g3_conv2d", "g3_set_stream", "g3_gemm_args_init", "g3_gemm_ex", "g3_gemm_workspace_size",
-    "g3_convert_bf16", "g3_convert_tf32", "g3_split_bf16", "g3_split3_bf16", "g3_quantize_fp8",
+    "g3_convert_bf16", "g3_convert_tf32", "g3_split_bf16", "g3_split3_bf16", "g3_split_tf32", "g3_quantize_fp8",
     "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
     "g3_plan_query", "g3_launch_count", "g3_kernel_timing", "g3_kernel_time_ms",
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
             "g3_split_bf16": ([vp, i64, i64, i64, vp, vp, i64, vp], i32),
             "g3_split3_bf16": ([vp, i64, i64, i64, vp, vp, vp, i64, vp], i32),
             "g3_convert_tf32": ([vp, i64, i64, i64, vp, i64, vp], i32),
+            "g3_split_tf32": ([vp, i64, i64, i64, vp, vp, i64, vp], i32),
             "g3_quantize_fp8": ([vp, i64, i64, i64, vp, i64, vp, vp], i32),
             "g3_grouped_plan_create": ([i32, ctypes.POINTER(g3_gemm_desc), i32, ctypes.POINTER(vp)], i32),
             "g3_grouped_plan_execute": ([vp, vp], i32),
@@ -169,6 +170,10 @@ def g3_split_bf16(x, rows, cols, ldx, hi, lo, ldy, stream=None) -> int:
 
 def g3_convert_tf32(x, rows, cols, ldx, y, ldy, stream=None) -> int:
     return load().g3_convert_tf32(x, rows, cols, ldx, y, ldy, stream)
+
+
+def g3_split_tf32(x, rows, cols, ldx, hi, lo, ldy, stream=None) -> int:
+    return load().g3_split_tf32(x, rows, cols, ldx, hi, lo, ldy, stream)
 
 
 def g3_split3_bf16(x, rows, cols, ldx, hi, mid, lo, ldy, stream=None) -> int:

@@ -73,6 +73,7 @@ void family_init() {
   register_family_6xbf16(g_family);
   register_family_f16(g_family);
   register_family_tf32(g_family);
+  register_family_3xtf32(g_family);
   g_family_ready = true;
 }
 
@@ -217,6 +218,7 @@ int tc_mode_of(int dtype, int64_t k) {
     case G3_BF16: return TC_BF16;
     case G3_FP16: return TC_F16;
     case G3_TF32: return TC_TF32;
+    case G3_F32_3XTF32: return TC_3XTF32;
     case G3_F32_3XBF16: return k <= kSixProductMaxK ? TC_6XBF16 : TC_3XBF16;
     case G3_FP8_E4M3: return TC_FP8;
     case G3_INT8: return TC_I8EMU;  // exact emulation: int8 values are exact in bfloat16
@@ -225,7 +227,7 @@ int tc_mode_of(int dtype, int64_t k) {
 }
 
 // k per k-block: one 128-byte row of the swizzled tile
-int kblock_of(int mode) { return mode == TC_FP8 ? 128 : (mode == TC_TF32 ? 32 : 64); }
+int kblock_of(int mode) { return mode == TC_FP8 ? 128 : ((mode == TC_TF32 || mode == TC_3XTF32) ? 32 : 64); }
 
 struct Plan {
   int member = -1;
@@ -245,7 +247,7 @@ struct Plan {
 // have landed) spread over its stages -- whichever is largest; a two-stage
 // ring exposes part of every refill.
 double kblock_clocks(const FamilyEntry& f) {
-  const int products = f.mode == TC_3XBF16 ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
+  const int products = (f.mode == TC_3XBF16 || f.mode == TC_3XTF32) ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
   const double mma = 4.0 * products * 73.0 * f.bm / 128.0;
   const double stage_bytes = (double)(f.smem - 1024 - 2 * 32 * 128 * 4 - 256) / f.stages;
   const double fill = stage_bytes / 64.0;
@@ -257,7 +259,7 @@ double kblock_clocks(const FamilyEntry& f) {
 
 // Fraction of the tensor peak a member sustains in its main loop.
 double tile_efficiency(const FamilyEntry& f) {
-  const int products = f.mode == TC_3XBF16 ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
+  const int products = (f.mode == TC_3XBF16 || f.mode == TC_3XTF32) ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
   const double mma = 4.0 * products * 73.0 * f.bm / 128.0;
   return std::min(0.97, mma / kblock_clocks(f));
 }
@@ -375,6 +377,12 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     splits = std::max(splits, 1);
   }
   if (!allow_splitk) splits = 1;
+  // 3xTF32: at most 8192 of k per FP32 accumulator.  The tensor core adds each
+  // 8-deep TF32 k-step to its FP32 accumulator with truncation, so the error
+  // grows as sqrt(k) / 8 * 2^-23 of sum |a||b| (measured 1.9e-6 at k = 16384,
+  // against the 2e-6 of the FP32-accurate modes); s partial sums added in
+  // round-to-nearest cut it by s.
+  if (mode == TC_3XTF32 && force_split == 0) splits = std::max(splits, (pl.num_kb + 255) / 256);
   splits = std::min(splits, pl.num_kb);
   pl.kb_per_split = (pl.num_kb + splits - 1) / splits;
   pl.splits = (pl.num_kb + pl.kb_per_split - 1) / pl.kb_per_split;
@@ -454,6 +462,15 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl, bool b_prepared = fals
       L.ldb_p = round_up(k, 4);
       L.a_hi = take((size_t)m * L.lda_p * 4);
       L.b_hi = take((size_t)n * L.ldb_p * 4);
+      break;
+    case G3_F32_3XTF32:   // hi / lo TF32 planes, binary32; B's transposed (n x k, K-major)
+      L.pack_a = L.pack_b = true;
+      L.lda_p = round_up(k, 4);
+      L.ldb_p = round_up(k, 4);
+      L.a_hi = take((size_t)m * L.lda_p * 4);
+      L.a_lo = take((size_t)m * L.lda_p * 4);
+      L.b_hi = take((size_t)n * L.ldb_p * 4);
+      L.b_lo = take((size_t)n * L.ldb_p * 4);
       break;
     case G3_INT8:
       L.pack_a = L.pack_b = true;
@@ -545,7 +562,7 @@ int validate(const g3_gemm_args& a) {
   if (a.m < 0) return -101;
   if (a.n < 0) return -102;
   if (a.k < 0) return -103;
-  if (a.dtype < G3_F32 || a.dtype > G3_TF32) return -112;
+  if (a.dtype < G3_F32 || a.dtype > G3_F32_3XTF32) return -112;
   if (a.trans_a != 0 && a.trans_a != 1) return -119;
   if (a.trans_b != 0 && a.trans_b != 1) return -120;
   if (a.lda < std::max<int64_t>(1, a.trans_a ? a.m : a.k)) return -106;
@@ -600,7 +617,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   if (st != G3_OK) return st;
 
   const int64_t m = a.m, n = a.n, k = a.k;
-  const int es = (a.dtype == G3_FP8_E4M3) ? 1 : (a.dtype == G3_TF32 ? 4 : 2);
+  const int es = (a.dtype == G3_FP8_E4M3) ? 1 : ((a.dtype == G3_TF32 || a.dtype == G3_F32_3XTF32) ? 4 : 2);
   const void *A_hi = a.A, *A_lo = nullptr, *B_hi = a.B, *B_lo = nullptr, *A_mid = nullptr, *B_mid = nullptr;
   int64_t lda = a.lda, ldb = a.ldb;
 
@@ -632,6 +649,14 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
     G3_CHECK_CUDA(launch_convert_tf32((const float*)a.A, (int)m, (int)k, a.lda, ah, L.lda_p, s));
     G3_CHECK_CUDA(launch_convert_tf32_t((const float*)a.B, (int)k, (int)n, a.ldb, bh, L.ldb_p, s));
     A_hi = ah; B_hi = bh;
+    lda = L.lda_p;
+    ldb = L.ldb_p;
+  } else if (a.dtype == G3_F32_3XTF32) {
+    float *ah = (float*)(ws + L.a_hi), *al = (float*)(ws + L.a_lo);
+    float *bh = (float*)(ws + L.b_hi), *bl = (float*)(ws + L.b_lo);
+    G3_CHECK_CUDA(launch_split_tf32((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p, s));
+    G3_CHECK_CUDA(launch_split_tf32_t((const float*)a.B, (int)k, (int)n, a.ldb, bh, bl, L.ldb_p, s));
+    A_hi = ah; A_lo = al; B_hi = bh; B_lo = bl;
     lda = L.lda_p;
     ldb = L.ldb_p;
   } else if (a.dtype == G3_INT8) {
@@ -669,7 +694,8 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   } else if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, arows)) != G3_OK) {
     return st;
   }
-  if (a.dtype == G3_TF32) {   // B stored n x k: boxes of bk (k) x 128 (n rows)
+  const bool b_kmajor = a.dtype == G3_TF32 || a.dtype == G3_F32_3XTF32;
+  if (b_kmajor) {   // B stored n x k: boxes of bk (k) x 128 (n rows)
     if ((st = encode_2d(&maps[1], B_hi, es, k, n, ldb, bk, 128)) != G3_OK) return st;
   } else if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) {
     return st;
@@ -684,6 +710,9 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   } else if (a.dtype == G3_F32_3XBF16) {
     if ((st = encode_2d(&maps[2], A_lo, es, k, m, lda, bk, arows)) != G3_OK) return st;
     if ((st = encode_2d(&maps[3], B_lo, es, n, k, ldb, boxn, bk)) != G3_OK) return st;
+  } else if (a.dtype == G3_F32_3XTF32) {
+    if ((st = encode_2d(&maps[2], A_lo, es, k, m, lda, bk, arows)) != G3_OK) return st;
+    if ((st = encode_2d(&maps[3], B_lo, es, k, n, ldb, bk, 128)) != G3_OK) return st;
   }
 
   TcParams p;
@@ -786,7 +815,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
 }
 
 int input_esize(int dtype) {
-  if (dtype == G3_F32 || dtype == G3_F32_3XBF16 || dtype == G3_TF32) return 4;
+  if (dtype == G3_F32 || dtype == G3_F32_3XBF16 || dtype == G3_TF32 || dtype == G3_F32_3XTF32) return 4;
   return (dtype == G3_BF16 || dtype == G3_FP16) ? 2 : 1;
 }
 
@@ -1227,6 +1256,17 @@ int g3_convert_tf32(const float* x, int64_t rows, int64_t cols, int64_t ldx, flo
   return G3_OK;
 }
 
+int g3_split_tf32(const float* x, int64_t rows, int64_t cols, int64_t ldx, float* hi, float* lo, int64_t ldy,
+                  void* stream) {
+  int st = prep_check(x, rows, cols, ldx, hi, ldy, 7);
+  if (st != G3_OK) return st;
+  if (rows > 0 && cols > 0 && !lo) return -106;
+  if (rows == 0 || cols == 0) return G3_OK;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  G3_CHECK_CUDA(launch_split_tf32(x, (int)rows, (int)cols, ldx, hi, lo, ldy, s));
+  return G3_OK;
+}
+
 int g3_split3_bf16(const float* x, int64_t rows, int64_t cols, int64_t ldx, void* hi, void* mid, void* lo,
                    int64_t ldy, void* stream) {
   int st = prep_check(x, rows, cols, ldx, hi, ldy, 8);
@@ -1295,7 +1335,7 @@ int g3_family_describe(int index, char* buf, size_t len) {
     family_init();
   }
   const FamilyEntry& f = g_family[index];
-  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16", "f16", "tf32"};
+  static const char* names[] = {"bf16", "3xbf16", "fp8", "int8emu", "6xbf16", "f16", "tf32", "3xtf32"};
   std::snprintf(buf, len, "mode=%s bm=%d bn=%d stages=%d smem=%d bufs=%d cg=%d", names[f.mode], f.bm, 128 * f.cg,
                 f.stages, f.smem, f.bufs, f.cg);
   return G3_OK;
@@ -1305,7 +1345,7 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   if (m < 0) return -101;
   if (n < 0) return -102;
   if (k < 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_TF32) return -104;
+  if (dtype < G3_F32 || dtype > G3_F32_3XTF32) return -104;
   if (dtype == G3_F32) {
     if (config) *config = -1;
     if (split_k) *split_k = 1;
@@ -1366,7 +1406,7 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   if (m <= 0) return -101;
   if (n <= 0) return -102;
   if (k <= 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_TF32) return -104;
+  if (dtype < G3_F32 || dtype > G3_F32_3XTF32) return -104;
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || (dtype == G3_INT8 && k > 131072)) return G3_ERR_UNSUPPORTED;
   if (dtype == G3_F32) {   // one kernel: nothing to choose
     if (best_config) *best_config = -1;

@@ -35,6 +35,7 @@ void register_family_int8emu(FamilyEntry* table);
 void register_family_6xbf16(FamilyEntry* table);
 void register_family_f16(FamilyEntry* table);
 void register_family_tf32(FamilyEntry* table);
+void register_family_3xtf32(FamilyEntry* table);
 
 using GroupedLaunchFn = cudaError_t (*)(const GroupedParams& p, int grid, cudaStream_t s);
 
@@ -55,6 +56,7 @@ void register_grouped_int8emu(GroupedEntry* table);
 void register_grouped_6xbf16(GroupedEntry* table);
 void register_grouped_f16(GroupedEntry* table);
 void register_grouped_tf32(GroupedEntry* table);
+void register_grouped_3xtf32(GroupedEntry* table);
 
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.
@@ -71,6 +73,11 @@ cudaError_t launch_convert_tf32_t(const float* x, int rows, int cols, long long 
                                   cudaStream_t s);
 cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s);
+// hi = tf32(x), lo = tf32(x - hi); the _t form writes both transposed (cols x rows).
+cudaError_t launch_split_tf32(const float* x, int rows, int cols, long long ldx, float* hi, float* lo,
+                             long long ldy, cudaStream_t s);
+cudaError_t launch_split_tf32_t(const float* x, int rows, int cols, long long ldx, float* hi, float* lo,
+                               long long ldy, cudaStream_t s);
 cudaError_t launch_int8_to_bf16(const int8_t* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s);
 // y (cols x rows) := transpose of x (rows x cols), elements of esize bytes (1, 2 or 4).

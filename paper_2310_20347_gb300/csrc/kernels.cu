@@ -69,6 +69,25 @@ cudaError_t launch_convert_tf32_t(const float* x, int rows, int cols, long long 
   return cudaGetLastError();
 }
 
+cudaError_t launch_split_tf32(const float* x, int rows, int cols, long long ldx, float* hi, float* lo,
+                             long long ldy, cudaStream_t s) {
+  const bool vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && ldx % 4 == 0 && reinterpret_cast<uintptr_t>(hi) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(lo) % 16 == 0 && ldy % 4 == 0;
+  if (vec) split_tf32_kernel<true><<<rows_grid(rows, cols, 4), 256, 0, s>>>(x, rows, cols, ldx, hi, lo, ldy);
+  else split_tf32_kernel<false><<<rows_grid(rows, cols, 1), 256, 0, s>>>(x, rows, cols, ldx, hi, lo, ldy);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_tf32_t(const float* x, int rows, int cols, long long ldx, float* hi, float* lo,
+                               long long ldy, cudaStream_t s) {
+  const long long tiles = (long long)((rows + 31) / 32) * ((cols + 31) / 32);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, 152LL * 16));
+  split_tf32_t_kernel<<<grid, dim3(32, 8, 1), 0, s>>>(x, rows, cols, ldx, hi, lo, ldy);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* y, long long ldy,
                                 cudaStream_t s) {
   convert_bf16_kernel<<<rows_grid(rows, cols, 4), 256, 0, s>>>(x, rows, cols, ldx, y, ldy);

@@ -139,6 +139,68 @@ __global__ void convert_tf32_kernel(const float* __restrict__ x, int rows, int c
   }
 }
 
+// The two-part TF32 split: hi = tf32(x), lo = tf32(x - hi) (the difference is
+// exact in binary32); 4 elements per thread step with 16-byte accesses when
+// all rows are 16-byte aligned (vec), else one by one.
+__device__ __forceinline__ void split_tf32(float v, float& h, float& l) {
+  h = tf32_rne(v);
+  l = tf32_rne(__fsub_rn(v, h));
+}
+
+template <bool VEC>
+__global__ void split_tf32_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                  float* __restrict__ hi, float* __restrict__ lo, long long ldy) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const float* xr = x + r * ldx;
+    float* hr = hi + r * ldy;
+    float* lr = lo + r * ldy;
+    if (VEC) {
+      const int cols4 = cols >> 2;
+      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols4; c += gridDim.x * blockDim.x) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(xr) + c);
+        float4 h, l;
+        split_tf32(a.x, h.x, l.x);
+        split_tf32(a.y, h.y, l.y);
+        split_tf32(a.z, h.z, l.z);
+        split_tf32(a.w, h.w, l.w);
+        reinterpret_cast<float4*>(hr)[c] = h;
+        reinterpret_cast<float4*>(lr)[c] = l;
+      }
+      if (blockIdx.x == 0)
+        for (int c = (cols4 << 2) + threadIdx.x; c < cols; c += blockDim.x) split_tf32(xr[c], hr[c], lr[c]);
+    } else {
+      for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
+        split_tf32(xr[c], hr[c], lr[c]);
+    }
+  }
+}
+
+// The same split written transposed (hi, lo: cols x rows): B of the 3xTF32
+// mode, K-major, through a 32 x 33 shared tile (block (32, 8)).
+__global__ void split_tf32_t_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                    float* __restrict__ hi, float* __restrict__ lo, long long ldy) {
+  __shared__ float tile[32][33];
+  const int tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+  for (long long t = blockIdx.x; t < (long long)tr * tc; t += gridDim.x) {
+    const int r0 = (int)(t / tc) * 32, c0 = (int)(t % tc) * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int r = r0 + i, c = c0 + threadIdx.x;
+      if (r < rows && c < cols) tile[i][threadIdx.x] = x[(long long)r * ldx + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int c = c0 + i, r = r0 + threadIdx.x;   // output row c, column r
+      if (c < cols && r < rows) {
+        float h, l;
+        split_tf32(tile[threadIdx.x][i], h, l);
+        hi[(long long)c * ldy + r] = h;
+        lo[(long long)c * ldy + r] = l;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void convert_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
                                     uint16_t* __restrict__ y, long long ldy) {
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {

@@ -63,7 +63,11 @@ namespace g3 {
 // the epilogue adds the chunks in int32.
 // TC_6XBF16: the FP32-accurate mode for small k: operands split in three
 // bfloat16 parts (hi + mid + lo), six products per k-step.
-enum TcMode : int { TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3, TC_6XBF16 = 4, TC_F16 = 5, TC_TF32 = 6 };
+// TC_3XTF32: a second FP32-accurate mode: operands split in two TF32 parts
+// (hi + lo, 22 significant bits), three kind::tf32 products per k-step.
+enum TcMode : int {
+  TC_BF16 = 0, TC_3XBF16 = 1, TC_FP8 = 2, TC_I8EMU = 3, TC_6XBF16 = 4, TC_F16 = 5, TC_TF32 = 6, TC_3XTF32 = 7
+};
 enum OutMode : int { OUT_F32 = 0, OUT_I32 = 1, OUT_PARTIAL = 2 };
 
 // Watchdog status codes (written to the device status word; see g3gemm.h).
@@ -137,8 +141,9 @@ struct GroupedParams {
 
 template <int MODE>
 struct TcTraits {
-  static constexpr int kPlanes = (MODE == TC_3XBF16) ? 2 : (MODE == TC_6XBF16 ? 3 : 1);   // operand planes
-  static constexpr int kElem = (MODE == TC_FP8) ? 1 : (MODE == TC_TF32 ? 4 : 2);   // bytes per element
+  static constexpr bool kTf32 = (MODE == TC_TF32 || MODE == TC_3XTF32);
+  static constexpr int kPlanes = (MODE == TC_3XBF16 || MODE == TC_3XTF32) ? 2 : (MODE == TC_6XBF16 ? 3 : 1);
+  static constexpr int kElem = (MODE == TC_FP8) ? 1 : (kTf32 ? 4 : 2);   // bytes per element
   static constexpr int kBK = 128 / kElem;                        // k per block: one 128-B row
   static constexpr int kKStep = 32 / kElem;                      // k per MMA instruction
   static constexpr int kKSteps = kBK / kKStep;                   // = 4
@@ -147,7 +152,7 @@ struct TcTraits {
   static constexpr uint32_t kBtBytes = 128 * 128;                // 128 n x 128 bytes of k
   // operand format code: 0 = E4M3 (kind::f8f6f4) or F16 (kind::f16), 1 = BF16,
   // 2 = TF32 (kind::tf32)
-  static constexpr uint32_t kAFmt = (MODE == TC_FP8 || MODE == TC_F16) ? 0u : (MODE == TC_TF32 ? 2u : 1u);
+  static constexpr uint32_t kAFmt = (MODE == TC_FP8 || MODE == TC_F16) ? 0u : (kTf32 ? 2u : 1u);
   // Leading byte offset of the MN-major Bt operand: the distance between its
   // 128-byte-wide n groups (one TMA box each).  With a single group (FP8) the
   // field is unused; 1024 keeps every address inside the stage either way.
@@ -155,7 +160,7 @@ struct TcTraits {
   // TF32 operands must be K-major on the tensor core (measured: an MN-major
   // TF32 operand reads wrong elements): B arrives transposed (n x k) from the
   // rounding pre-pass and its tile is staged like A's, 128 n-rows of 128 bytes.
-  static constexpr bool kBtKMajor = (MODE == TC_TF32);
+  static constexpr bool kBtKMajor = kTf32;
 };
 
 template <int BM_T, int STAGES, int MODE, int CG = 1>
@@ -171,7 +176,7 @@ struct TcConfig {
   // nearest, in the epilogue.  Accumulator sets are multi-buffered across
   // output tiles as far as TMEM (512 columns) allows, up to kMaxBufs, so that
   // the MMA can run several short tiles ahead of the epilogue.
-  static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16 || MODE == TC_6XBF16) ? 2 : 1;
+  static constexpr uint32_t kAccPerTile = (MODE == TC_3XBF16 || MODE == TC_6XBF16 || MODE == TC_3XTF32) ? 2 : 1;
   static constexpr uint32_t kSetCols = kAccPerTile * BM_T;
   static constexpr uint32_t kMaxBufs = 4;
   static constexpr uint32_t kNumBufs = (512 / kSetCols) < kMaxBufs ? (512 / kSetCols) : kMaxBufs;
@@ -535,6 +540,15 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
               mma_f16<CG>(d_corr, bt_lo, a_hi, idesc, 1u);
               mma_f16<CG>(d_corr, bt_mid, a_mid, idesc, 1u);
               mma_f16<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
+            } else if (MODE == TC_3XTF32) {
+              // both planes K-major (TF32): Bhi*Alo + Blo*Ahi into the
+              // corrections, then Bhi*Ahi; Blo*Alo is dropped
+              const uint32_t lo = Cfg::kPlaneBytes;
+              const uint64_t bt_lo = smem_desc_sw128(st + lo + bt_off, 16, 1024);
+              const uint64_t a_lo = smem_desc_sw128(st + lo + a_off, 16, 1024);
+              mma_tf32<CG>(d_corr, bt_hi, a_lo, idesc, accumulate);
+              mma_tf32<CG>(d_corr, bt_lo, a_hi, idesc, 1u);
+              mma_tf32<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else if (MODE == TC_FP8) {
               mma_f8<CG>(d_tmem, bt_hi, a_hi, idesc, accumulate);
             } else if (MODE == TC_TF32) {
@@ -750,7 +764,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           }
         }
       };
-      if (MODE == TC_3XBF16 || MODE == TC_6XBF16) {
+      if (MODE == TC_3XBF16 || MODE == TC_6XBF16 || MODE == TC_3XTF32) {
         for (int c = 0; c < nchunks; ++c) {
           uint32_t r[32], rc[32];
           tmem_ld_32x32b_x32(tbase + c * 32, r);

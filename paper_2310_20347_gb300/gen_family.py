@@ -44,10 +44,11 @@ MODES = {            # name: (planes, element bytes)
     "6xbf16": (3, 2),    # FP32-accurate, three-part split, 6 products: used for small k
     "f16": (1, 2),       # IEEE binary16 operands on kind::f16
     "tf32": (1, 4),      # TF32 operands (binary32 storage) on kind::tf32
+    "3xtf32": (2, 4),    # FP32-accurate on a two-part TF32 split, 3 kind::tf32 products
 }
 MODE_ENUM = {"bf16": "TC_BF16", "3xbf16": "TC_3XBF16", "fp8": "TC_FP8", "int8emu": "TC_I8EMU",
-             "6xbf16": "TC_6XBF16", "f16": "TC_F16", "tf32": "TC_TF32"}
-SPLIT_MODES = ("3xbf16", "6xbf16")   # two accumulators per tile (main + corrections)
+             "6xbf16": "TC_6XBF16", "f16": "TC_F16", "tf32": "TC_TF32", "3xtf32": "TC_3XTF32"}
+SPLIT_MODES = ("3xbf16", "6xbf16", "3xtf32")   # two accumulators per tile (main + corrections)
 BMS = (256, 128, 64)
 # int8emu keeps one int32 running sum per row of its column in registers
 # (with bm = 256: sixteen epilogue warps of 64 rows each)

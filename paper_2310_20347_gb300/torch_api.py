@@ -7,12 +7,12 @@ from __future__ import annotations
 import torch
 
 from . import _lib
-from ._lib import G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, check
+from ._lib import G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, check
 
 _ELEM = {G3_F32: (torch.float32, torch.float32), G3_F32_3XBF16: (torch.float32, torch.float32),
          G3_BF16: (torch.bfloat16, torch.float32), G3_FP8_E4M3: (torch.uint8, torch.float32),
          G3_INT8: (torch.int8, torch.int32), G3_FP16: (torch.float16, torch.float32),
-         G3_TF32: (torch.float32, torch.float32)}
+         G3_TF32: (torch.float32, torch.float32), G3_F32_3XTF32: (torch.float32, torch.float32)}
 
 
 def _stream(stream):
@@ -127,6 +127,15 @@ def split_bf16(x: torch.Tensor, stream=None):
     lo = torch.empty_like(hi)
     check(_lib.g3_split_bf16(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), hi.data_ptr(),
                              lo.data_ptr(), max(x.shape[1], 1), _stream(stream)), "g3_split_bf16")
+    return hi, lo
+
+
+def split_tf32(x: torch.Tensor, stream=None):
+    """(hi, lo) float32 tensors of the two-part TF32 split, shaped like x."""
+    hi = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    lo = torch.empty_like(hi)
+    check(_lib.g3_split_tf32(x.data_ptr(), x.shape[0], x.shape[1], _ld(x, "x"), hi.data_ptr(), lo.data_ptr(),
+                             max(x.shape[1], 1), _stream(stream)), "g3_split_tf32")
     return hi, lo
 
 

@@ -76,6 +76,11 @@ def test_argument_errors(lib):
     assert L.g3_split3_bf16(p, 4, 8, 8, p, p, None, 8) == -107
     assert L.g3_split3_bf16(p, 4, 8, 8, p, p, p, 7) == -108
     assert L.g3_split3_bf16(p, 0, 8, 8, None, None, None, 8) == 0
+    assert L.g3_split_tf32(p, 4, 8, 8, p, p, 7) == -107
+    assert L.g3_split_tf32(p, 4, 8, 8, p, None, 8) == -106
+    assert L.g3_split_tf32(p, 0, 8, 8, None, None, 8) == 0
+    # a dtype beyond the last one
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 8) == -112
     # INT8 accepts only alpha == 1 and beta in {0, 1}
     assert L.g3_gemm(4, 4, 8, 2.0, p, 8, p, 4, 0.0, p, 4, 4) == L.G3_ERR_UNSUPPORTED
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.5, p, 4, 4) == L.G3_ERR_UNSUPPORTED

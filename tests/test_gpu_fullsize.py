@@ -3,6 +3,7 @@ configuration the benchmark times (the planner's member and split), checked on
 sampled rows of C that the oracle computes in binary64 (int64 for INT8):
 
   FP32-accurate 16384^3 (alpha 1, beta 0.5, uniform [-1, 1], seed 0)  gate 2e-6
+  the 3xTF32 FP32-accurate mode on the same inputs at 8192^3             gate 2e-6
   BF16 / FP16 / TF32 / FP8 / INT8 8192^3          8e-3 / 2e-3 / 2e-3 / 6e-2 / bit-exact
   the 20 im2col layer shapes (batch 16) in BF16    kernel check 1e-5, gate 8e-3
   the 1000-problem grouped batches (BF16 and FP32-accurate), every 25th
@@ -13,7 +14,8 @@ import pytest
 import torch
 
 import oracle
-from paper_2310_20347_gb300 import G3_BF16, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, synth, torch_api
+from paper_2310_20347_gb300 import (G3_BF16, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32,
+                                    synth, torch_api)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +39,19 @@ def test_fp32_accurate_16384_cubed():
     del A, B, C
     e = sampled_err(got, rows, p.A, p.B, p.C, 1.0, 0.5)
     print(f"16384^3 FP32-accurate sampled error {e:.3e}")
+    assert e <= 2e-6
+
+
+def test_3xtf32_8192_cubed():
+    n = 8192
+    p = synth.uniform_problem(n, n, n, seed=0, alpha=1.0, beta=0.5)
+    A, B, C = (torch.from_numpy(x).cuda() for x in (p.A, p.B, p.C))
+    torch_api.gemm(A, B, C, 1.0, 0.5, dtype=G3_F32_3XTF32)
+    rows = np.array([0, 1, 4097, n - 1])
+    got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    del A, B, C
+    e = sampled_err(got, rows, p.A, p.B, p.C, 1.0, 0.5)
+    print(f"8192^3 3xTF32 sampled error {e:.3e}")
     assert e <= 2e-6
 
 

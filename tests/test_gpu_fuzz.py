@@ -8,17 +8,17 @@ import torch
 
 import oracle
 from gpu_util import check_guard, guarded, rel_err
-from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32,
+from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32,
                                     gen_family, synth, torch_api)
 
 pytestmark = pytest.mark.gpu
 FAMILY = gen_family.enumerate_family()
 MODE_OF = {G3_BF16: ("bf16",), G3_FP16: ("f16",), G3_TF32: ("tf32",), G3_FP8_E4M3: ("fp8",),
-           G3_INT8: ("int8emu",), G3_F32_3XBF16: ("3xbf16", "6xbf16"), G3_F32: ()}
+           G3_INT8: ("int8emu",), G3_F32_3XBF16: ("3xbf16", "6xbf16"), G3_F32_3XTF32: ("3xtf32",), G3_F32: ()}
 
 
 def draw(rng):
-    dtype = int(rng.choice([G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP16, G3_TF32, G3_FP8_E4M3, G3_INT8]))
+    dtype = int(rng.choice([G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP16, G3_TF32, G3_FP8_E4M3, G3_INT8, G3_F32_3XTF32]))
     m, n, k = (int(x) for x in np.exp(rng.uniform(0, np.log(1100), 3)).astype(int) + 1)
     members = [f["index"] for f in FAMILY if f["mode"] in MODE_OF[dtype]]
     if dtype == G3_F32_3XBF16:   # the member must be of the mode the library picks at this depth
@@ -79,7 +79,7 @@ def test_random_case(seed):
             Aq, Bq = p.A, p.B
         A, B = dev_operand(Aq if dtype in (G3_BF16, G3_FP16) else p.A, ta, dtype), \
             dev_operand(Bq if dtype in (G3_BF16, G3_FP16) else p.B, tb, dtype)
-        tol = 2e-6 if dtype in (G3_F32, G3_F32_3XBF16) else 1e-5
+        tol = 2e-6 if dtype in (G3_F32, G3_F32_3XBF16, G3_F32_3XTF32) else 1e-5
     full, C = guarded(m, n, p.C)
     torch_api.gemm(A, B, C, alpha, beta, dtype=dtype, config=config, split_k=split, trans_a=ta, trans_b=tb,
                    **scales)

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from gpu_util import rel_err
-from paper_2310_20347_gb300 import G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_INT8, G3_TF32, synth, torch_api
+from paper_2310_20347_gb300 import G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_INT8, G3_TF32, synth, torch_api
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +24,8 @@ def pinned(x, pad=0):
 @pytest.mark.parametrize("m,n,k,dtype,pad,beta", [(300, 200, 150, G3_F32, 0, 0.5), (2500, 300, 700, G3_F32_3XBF16, 3, 0.5),
                                                   (2049, 130, 64, G3_F32_3XBF16, 0, 0.5), (700, 520, 300, G3_F32, 5, 0.5),
                                                   (2100, 300, 4500, G3_F32_3XBF16, 2, 0.5),
-                                                  (4200, 260, 9000, G3_F32_3XBF16, 0, 0.0)])
+                                                  (4200, 260, 9000, G3_F32_3XBF16, 0, 0.0),
+                                                  (2300, 200, 700, G3_F32_3XTF32, 1, 0.5)])
 def test_host_fp32(m, n, k, dtype, pad, beta):
     p = synth.uniform_problem(m, n, k, seed=40, alpha=1.25, beta=beta)
     hA, hB = pinned(torch.from_numpy(p.A), pad), pinned(torch.from_numpy(p.B), pad)

@@ -17,7 +17,7 @@ import torch
 
 import oracle
 from gpu_util import check_guard, dev, guarded, rel_err
-from paper_2310_20347_gb300 import (G3_BF16, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib,
+from paper_2310_20347_gb300 import (G3_BF16, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib,
                                     gen_family, synth, torch_api)
 
 pytestmark = pytest.mark.gpu
@@ -470,3 +470,64 @@ def test_watchdog_reports_timeout_without_hanging():
     # the context is still usable and the next call is correct
     bf16_check(p)
     assert torch_api.device_status()[0] == 0
+
+
+# ---------------------------------------------------------------- 3xTF32
+def test_tf32_split_matches_oracle():
+    r = np.random.default_rng(73)
+    bits = r.integers(0, 1 << 32, 40000, dtype=np.uint64).astype(np.uint32)
+    bits[:2048] = (bits[:2048] & 0xFFFFE000) | 0x1000          # ties of the first rounding
+    bits[2048:4096] &= 0x80001FFF                              # subnormals
+    bits[4096:4100] = [0, 0x80000000, 0x3F800000, 0x7F7FFFFF]
+    x = bits.view(np.float32)
+    x = np.where(np.isfinite(x), x, np.float32(1.5)).astype(np.float32).reshape(200, 200)
+    hi, lo = torch_api.split_tf32(torch.from_numpy(x.copy()).cuda())
+    ohi, olo = oracle.split_tf32(x)
+    assert np.array_equal(hi.cpu().numpy().view(np.uint32), ohi.view(np.uint32))
+    assert np.array_equal(lo.cpu().numpy().view(np.uint32), olo.view(np.uint32))
+
+
+def x3t_check(p, config=-1, split_k=0):
+    full, C = guarded(p.m, p.n, p.C)
+    torch_api.gemm(dev(p.A), dev(p.B), C, p.alpha, p.beta, dtype=G3_F32_3XTF32, config=config, split_k=split_k)
+    torch.cuda.synchronize()
+    check_guard(full, p.m, p.n)
+    got = C.cpu().numpy()
+    bc = None if p.C is None else p.beta * p.C.astype(np.float64)
+    D = oracle.absprod(p.A, p.B, p.alpha)
+    e_k = rel_err(got, oracle.gemm_3xtf32(p.A, p.B, p.C, p.alpha, p.beta), D, bc)
+    e_g = rel_err(got, oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), D, bc)
+    # the method itself stays within 3 * 2^-22 of the exact product; the
+    # kernel adds FP32 accumulation (main and correction sums kept apart)
+    assert e_k <= 2e-6, ("kernel", e_k)
+    assert e_g <= 2e-6, ("gate", e_g)
+    return e_k, e_g
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_3xtf32_shapes(shape):
+    m, n, k = shape
+    x3t_check(synth.uniform_problem(m, n, k, seed=74, alpha=-0.75, beta=0.5))
+
+
+@pytest.mark.parametrize("config", members("3xtf32"))
+def test_3xtf32_every_member(config):
+    x3t_check(synth.uniform_problem(300, 520, 700, seed=75, alpha=1.25, beta=0.0), config=config)
+    x3t_check(synth.uniform_problem(600, 700, 130, seed=76, beta=-1.0), config=config)
+
+
+def test_3xtf32_split_k_and_integers_exact():
+    x3t_check(synth.uniform_problem(96, 200, 3000, seed=77, beta=1.0), split_k=3)
+    p = synth.small_int_problem(250, 330, 1000, seed=78, alpha=1.0, beta=2.0)
+    C = dev(p.C)
+    torch_api.gemm(dev(p.A), dev(p.B), C, 1.0, 2.0, dtype=G3_F32_3XTF32)
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), oracle.gemm(p.A, p.B, p.C, 1.0, 2.0))
+
+
+def test_3xtf32_deep_k_within_gate():
+    # k = 32768: the planner keeps at most 8192 of k per FP32 accumulator
+    # (split-K), which holds the accumulation error inside the 2e-6 gate
+    st, cfg, sk, _ = _lib.g3_plan_query(160, 200, 32768, G3_F32_3XTF32)
+    assert sk >= 4
+    x3t_check(synth.uniform_problem(160, 200, 32768, seed=79, beta=0.5))

@@ -6,7 +6,7 @@ import torch
 
 import oracle
 from gpu_util import check_guard, guarded, rel_err
-from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32,
+from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32,
                                     synth, torch_api)
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +22,7 @@ def stored(x, trans, pad):
 
 
 @pytest.mark.parametrize("ta,tb", COMBOS)
-@pytest.mark.parametrize("dtype,tol", [(G3_F32, 2e-6), (G3_F32_3XBF16, 2e-6)])
+@pytest.mark.parametrize("dtype,tol", [(G3_F32, 2e-6), (G3_F32_3XBF16, 2e-6), (G3_F32_3XTF32, 2e-6)])
 def test_trans_fp32(ta, tb, dtype, tol):
     p = synth.uniform_problem(130, 200, 300, seed=50, alpha=1.5, beta=0.5)
     A, B = stored(p.A, ta, 3), stored(p.B, tb, 5)
