@@ -377,12 +377,15 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     splits = std::max(splits, 1);
   }
   if (!allow_splitk) splits = 1;
-  // 3xTF32: at most 8192 of k per FP32 accumulator.  The tensor core adds each
-  // 8-deep TF32 k-step to its FP32 accumulator with truncation, so the error
-  // grows as sqrt(k) / 8 * 2^-23 of sum |a||b| (measured 1.9e-6 at k = 16384,
-  // against the 2e-6 of the FP32-accurate modes); s partial sums added in
-  // round-to-nearest cut it by s.
-  if (mode == TC_3XTF32 && force_split == 0) splits = std::max(splits, (pl.num_kb + 255) / 256);
+  // FP32-accurate modes: a bounded k per FP32 accumulator.  The tensor core
+  // adds each k-step's products to its FP32 accumulator with truncation, so the
+  // error grows as sqrt(k) / (k-step depth) * 2^-23 of sum |a||b| -- measured
+  // 1.04e-6 for 3xBF16 (16-deep steps) and 1.9e-6 for 3xTF32 (8-deep) at
+  // k = 16384, against the 2e-6 these modes promise; s partial sums added in
+  // round-to-nearest cut it by s.  At most 32768 of k (3xBF16) or 8192
+  // (3xTF32) per accumulator; split-K beyond.
+  if (force_split == 0 && mode == TC_3XTF32) splits = std::max(splits, (pl.num_kb + 255) / 256);
+  if (force_split == 0 && mode == TC_3XBF16) splits = std::max(splits, (pl.num_kb + 511) / 512);
   splits = std::min(splits, pl.num_kb);
   pl.kb_per_split = (pl.num_kb + splits - 1) / splits;
   pl.splits = (pl.num_kb + pl.kb_per_split - 1) / pl.kb_per_split;

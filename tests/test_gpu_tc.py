@@ -531,3 +531,10 @@ def test_3xtf32_deep_k_within_gate():
     st, cfg, sk, _ = _lib.g3_plan_query(160, 200, 32768, G3_F32_3XTF32)
     assert sk >= 4
     x3t_check(synth.uniform_problem(160, 200, 32768, seed=79, beta=0.5))
+
+
+def test_3xbf16_deep_k_within_gate():
+    # k = 65536: the planner keeps at most 32768 of k per FP32 accumulator
+    st, cfg, sk, _ = _lib.g3_plan_query(128, 160, 65536, G3_F32_3XBF16)
+    assert sk >= 2
+    x3_check(synth.uniform_problem(128, 160, 65536, seed=80, beta=0.5))
