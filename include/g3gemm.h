@@ -343,8 +343,10 @@ G3_API int g3_debug_withhold_next(int64_t timeout_ms);
  * bfloat16 copies of A and B are kept in a 64 MiB array built into the library
  * instead of allocated workspace; the call issues no cudaMalloc, cudaFree or
  * other allocating routine.  Limit: 4 * (m * ceil8(k) + k * ceil8(n)) bytes
- * plus alignment must fit in 64 MiB (e.g. m = n = k = 2800); larger problems
- * return G3_ERR_UNSUPPORTED before anything is launched.
+ * plus alignment must fit in 64 MiB (e.g. m = n = k = 2800), and k <= 32768
+ * (beyond it g3_gemm splits k to keep the FP32 accumulation within 2e-6,
+ * which needs workspace); other problems return G3_ERR_UNSUPPORTED before
+ * anything is launched.
  *
  * - The first call on a device looks up that device's copy of the array; make
  *   that first call before any stream capture.

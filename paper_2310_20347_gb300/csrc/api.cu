@@ -1559,6 +1559,7 @@ extern "C" int g3_gemm_3xbf16_noalloc(int64_t m, int64_t n, int64_t k, double al
   if (m == 0 || n == 0) return G3_OK;
   std::lock_guard<std::mutex> lock(g_mu);
   family_init();
+  if (k > 32768) return G3_ERR_UNSUPPORTED;   // one FP32 accumulator per tile: k bounded for 2e-6
   if (k > 0 && alpha != 0.0) {
     // the planes' size depends on m, n, k only, not on the tile the planner picks
     const Plan pl = make_plan(m, n, k, G3_F32_3XBF16, 152, -1, 1, 0);

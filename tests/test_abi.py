@@ -79,6 +79,8 @@ def test_argument_errors(lib):
     assert L.g3_split_tf32(p, 4, 8, 8, p, p, 7) == -107
     assert L.g3_split_tf32(p, 4, 8, 8, p, None, 8) == -106
     assert L.g3_split_tf32(p, 0, 8, 8, None, None, 8) == 0
+    # allocation-free entry: k beyond one FP32 accumulator's bound (no device touched)
+    assert L.g3_gemm_3xbf16_noalloc(64, 64, 40000, 1.0, p, 40000, p, 64, 0.0, p, 64, None) == L.G3_ERR_UNSUPPORTED
     # a dtype beyond the last one
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 8) == -112
     # INT8 accepts only alpha == 1 and beta in {0, 1}
