@@ -287,7 +287,7 @@ def run_workload(args):
 
     import oracle
     import paper_2310_20347_gb300 as pkg
-    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib, synth,
+    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_F64, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib, synth,
                                         torch_api)
     torch.cuda.set_device(0)
     pkg.load()
@@ -527,9 +527,15 @@ def run_workload(args):
                "per_shape": per})
         return
 
-    if args.workload in ("int8", "fp8", "bf16", "fp16", "tf32", "3xtf32"):
-        n = args.dsize
-        if args.workload == "3xtf32":
+    if args.workload in ("int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64"):
+        n = args.dsize if args.workload != "fp64" else min(args.dsize, 4096)
+        if args.workload == "fp64":
+            rng = np.random.default_rng(0)
+            p = synth.Problem(n, n, n, 1.0, 0.0, rng.uniform(-1, 1, (n, n)), rng.standard_normal((n, n)), None)
+            A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+            C = torch.empty(n, n, dtype=torch.float64, device=dev)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_F64)
+        elif args.workload == "3xtf32":
             # the second FP32-accurate mode, on the headline's inputs (uniform,
             # beta = 0.5 with C)
             p = synth.uniform_problem(n, n, n, seed=0, alpha=1.0, beta=0.5)
@@ -581,6 +587,17 @@ def run_workload(args):
         ms = _call_ms(fn, args.reps, flush)
         kms = _kernel_ms(_lib, fn, args.reps, flush)
         flops = 2.0 * n ** 3
+        if args.workload == "fp64":
+            # FP64 FMAs on the CUDA cores: against the nominal FP64 rate
+            _line(args, flops / ms / 1e9, "TFLOPS",
+                  {"workload": f"fp64 GEMM m=n=k={n}, alpha=1, beta=0, A uniform [-1, 1], B normal(0, 1)",
+                   "path": "FP64 SIMT kernel (64 x 64 CTA tiles, 4 x 4 register micro-tiles)"},
+                  {"dtype": "f64", "ms": ms, "kernel_ms": kms, "err": err,
+                   "roofline": {"bound": "alu", "achieved": flops / kms / 1e9, "peak": 1.25, "unit": "TFLOP/s",
+                                "frac": flops / kms / 1e9 / 1.25, "traffic": None,
+                                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                                "algorithmic": "2 n^3 FP64 flops per call"}})
+            return
         tensor_peak = bf16_peak * {"fp8": 2.0, "tf32": 0.5, "3xtf32": 0.5}.get(args.workload, 1.0)
         tensor_flops = flops * (3.0 if args.workload == "3xtf32" else 1.0)   # three TF32 products per term
         _line(args, flops / ms / 1e9, "TOPS" if args.workload == "int8" else "TFLOPS",
@@ -757,7 +774,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "conv",
+                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "conv",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

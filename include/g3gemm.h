@@ -74,7 +74,10 @@ extern "C" {
  *                  + Alo*Bhi on kind::tf32 with FP32 accumulation (lo*lo is
  *                  dropped; at most 3*2^-22 of |a||b| per product).  Twice
  *                  the tensor time of G3_F32_3XBF16; single GEMMs only (the
- *                  grouped calls take G3_BF16 and G3_F32_3XBF16).          */
+ *                  grouped calls take G3_BF16 and G3_F32_3XBF16).
+ *   G3_F64         A, B, C float64; FP64 FMA on the CUDA cores (the binary64
+ *                  entry of the datatype study); alpha and beta are used in
+ *                  binary64.  Single GEMMs only.                           */
 typedef enum {
   G3_F32 = 0,
   G3_F32_3XBF16 = 1,
@@ -83,7 +86,8 @@ typedef enum {
   G3_INT8 = 4,
   G3_FP16 = 5,
   G3_TF32 = 6,
-  G3_F32_3XTF32 = 7
+  G3_F32_3XTF32 = 7,
+  G3_F64 = 8
 } g3_dtype;
 
 /* g3_gemm_args.split_k value that asks for a stream-K tail (see there).    */
@@ -100,7 +104,8 @@ typedef enum {
 } g3_status;
 
 /* C := beta*C + alpha*A*B on the current stream (Section 3.1).
- * `dtype` is a g3_dtype; alpha and beta are converted to float.  For
+ * `dtype` is a g3_dtype; alpha and beta are converted to float (kept in
+ * binary64 for G3_F64).  For
  * G3_FP8_E4M3 the scales are 1; use g3_gemm_ex to pass scales.  May allocate
  * library workspace on first use of a size class (3xBF16 operand planes,
  * split-K partials, re-packed operands).                                   */

@@ -565,7 +565,7 @@ int validate(const g3_gemm_args& a) {
   if (a.m < 0) return -101;
   if (a.n < 0) return -102;
   if (a.k < 0) return -103;
-  if (a.dtype < G3_F32 || a.dtype > G3_F32_3XTF32) return -112;
+  if (a.dtype < G3_F32 || a.dtype > G3_F64) return -112;
   if (a.trans_a != 0 && a.trans_a != 1) return -119;
   if (a.trans_b != 0 && a.trans_b != 1) return -120;
   if (a.lda < std::max<int64_t>(1, a.trans_a ? a.m : a.k)) return -106;
@@ -604,6 +604,26 @@ int run_simt(const g3_gemm_args& a, cudaStream_t s) {
                    a.ldc % 4 == 0;
   TimedRegion tr(s);
   G3_CHECK_CUDA(launch_simt(p, vec, s));
+  return G3_OK;
+}
+
+int run_simt64(const g3_gemm_args& a, cudaStream_t s) {
+  SimtParams64 p;
+  p.m = (int)a.m;
+  p.n = (int)a.n;
+  p.k = (int)a.k;
+  p.alpha = a.alpha;
+  p.beta = a.beta;
+  p.A = static_cast<const double*>(a.A);
+  p.lda = a.lda;
+  p.B = static_cast<const double*>(a.B);
+  p.ldb = a.ldb;
+  p.C = static_cast<double*>(a.C);
+  p.ldc = a.ldc;
+  const bool vec = (reinterpret_cast<uintptr_t>(a.A) % 16 == 0) && (reinterpret_cast<uintptr_t>(a.B) % 16 == 0) &&
+                   a.lda % 2 == 0 && a.ldb % 2 == 0;
+  TimedRegion tr(s);
+  G3_CHECK_CUDA(launch_simt64(p, vec, s));
   return G3_OK;
 }
 
@@ -818,6 +838,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
 }
 
 int input_esize(int dtype) {
+  if (dtype == G3_F64) return 8;
   if (dtype == G3_F32 || dtype == G3_F32_3XBF16 || dtype == G3_TF32 || dtype == G3_F32_3XTF32) return 4;
   return (dtype == G3_BF16 || dtype == G3_FP16) ? 2 : 1;
 }
@@ -868,14 +889,18 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s, const PreparedB* pb = nullptr) {
   if ((a.trans_a || a.trans_b) && a.k > 0 && a.alpha != 0.0 && (st = untranspose(*d, a, s)) != G3_OK) return st;
   const bool is_int = a.dtype == G3_INT8;
   if (a.k == 0 || a.alpha == 0.0) {
-    if (is_int && a.beta == 1.0) return G3_OK;
-    G3_CHECK_CUDA(launch_scale_c(a.C, is_int, (int)a.m, (int)a.n, a.ldc, (float)a.beta, s));
+    if ((is_int || a.dtype == G3_F64) && a.beta == 1.0) return G3_OK;
+    if (a.dtype == G3_F64)
+      G3_CHECK_CUDA(launch_scale_c_f64(static_cast<double*>(a.C), (int)a.m, (int)a.n, a.ldc, a.beta, s));
+    else
+      G3_CHECK_CUDA(launch_scale_c(a.C, is_int, (int)a.m, (int)a.n, a.ldc, (float)a.beta, s));
     return G3_OK;
   }
   // device scales apply in the kernel epilogue or the stream-K fix-up, which
   // the split-K reduce cannot: no split-K then
   if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b) && a.split_k > 1) a.split_k = 1;
   if (a.dtype == G3_F32) return run_simt(a, s);
+  if (a.dtype == G3_F64) return run_simt64(a, s);
   return run_tc(*d, a, s, nullptr, pb);
 }
 
@@ -940,7 +965,8 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   const int es = input_esize(a.dtype);
   const int64_t lda_d = round_up(std::max<int64_t>(k, 1), 16), ldb_d = round_up(n, 16), ldc_d = round_up(n, 16);
   const size_t a_bytes = align256((size_t)m * lda_d * es), b_bytes = align256((size_t)std::max<int64_t>(k, 1) * ldb_d * es);
-  const size_t c_bytes = align256((size_t)m * ldc_d * 4);
+  const int ces = a.dtype == G3_F64 ? 8 : 4;   // bytes per element of C
+  const size_t c_bytes = align256((size_t)m * ldc_d * ces);
   const bool products = k > 0 && a.alpha != 0.0;
   const bool read_c = a.beta != 0.0;
   const int nb = (m >= 2048 && products) ? (int)std::max<int64_t>(4, std::min<int64_t>(kHostMaxBlocks, (m + 2047) / 2048))
@@ -1022,9 +1048,9 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
                                       static_cast<const uint8_t*>(a.A) + (size_t)r0 * a.lda * es, a.lda * es, k * es,
                                       r1 - r0, cudaMemcpyHostToDevice, up));
     if (read_c)
-      G3_CHECK_CUDA(cudaMemcpy2DAsync(dC + (size_t)r0 * ldc_d * 4, ldc_d * 4,
-                                      static_cast<const uint8_t*>(a.C) + (size_t)r0 * a.ldc * 4, a.ldc * 4, n * 4,
-                                      r1 - r0, cudaMemcpyHostToDevice, up));
+      G3_CHECK_CUDA(cudaMemcpy2DAsync(dC + (size_t)r0 * ldc_d * ces, ldc_d * ces,
+                                      static_cast<const uint8_t*>(a.C) + (size_t)r0 * a.ldc * ces, a.ldc * ces,
+                                      n * ces, r1 - r0, cudaMemcpyHostToDevice, up));
     return G3_OK;
   };
   auto up_B = [&](int64_t k0, int64_t k1) -> int {   // rows k0 .. k1-1 of B
@@ -1040,7 +1066,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
     blk.lda = lda_d;
     blk.B = dB;
     blk.ldb = ldb_d;
-    blk.C = dC + (size_t)r0 * ldc_d * 4;
+    blk.C = dC + (size_t)r0 * ldc_d * ces;
     blk.ldc = ldc_d;
     (void)b;
     return blk;
@@ -1048,9 +1074,9 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   auto down_rows = [&](int b, int64_t r0, int64_t r1) -> int {
     G3_CHECK_CUDA(cudaEventRecord(ev_done[b], s));
     G3_CHECK_CUDA(cudaStreamWaitEvent(down, ev_done[b], 0));
-    G3_CHECK_CUDA(cudaMemcpy2DAsync(static_cast<uint8_t*>(a.C) + (size_t)r0 * a.ldc * 4, a.ldc * 4,
-                                    dC + (size_t)r0 * ldc_d * 4, ldc_d * 4, n * 4, r1 - r0, cudaMemcpyDeviceToHost,
-                                    down));
+    G3_CHECK_CUDA(cudaMemcpy2DAsync(static_cast<uint8_t*>(a.C) + (size_t)r0 * a.ldc * ces, a.ldc * ces,
+                                    dC + (size_t)r0 * ldc_d * ces, ldc_d * ces, n * ces, r1 - r0,
+                                    cudaMemcpyDeviceToHost, down));
     return G3_OK;
   };
   if (prep) {
@@ -1204,7 +1230,9 @@ int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
   *bytes = 0;
   int st = validate(*args);
   if (st != G3_OK) return st;
-  if (args->m == 0 || args->n == 0 || args->k == 0 || args->alpha == 0.0 || args->dtype == G3_F32) return G3_OK;
+  if (args->m == 0 || args->n == 0 || args->k == 0 || args->alpha == 0.0 || args->dtype == G3_F32 ||
+      args->dtype == G3_F64)
+    return G3_OK;
   std::lock_guard<std::mutex> lock(g_mu);
   DevState* d = nullptr;
   if ((st = ensure_device(&d)) != G3_OK) return st;
@@ -1348,8 +1376,8 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   if (m < 0) return -101;
   if (n < 0) return -102;
   if (k < 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_F32_3XTF32) return -104;
-  if (dtype == G3_F32) {
+  if (dtype < G3_F32 || dtype > G3_F64) return -104;
+  if (dtype == G3_F32 || dtype == G3_F64) {
     if (config) *config = -1;
     if (split_k) *split_k = 1;
     if (raster) *raster = 0;
@@ -1409,9 +1437,9 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   if (m <= 0) return -101;
   if (n <= 0) return -102;
   if (k <= 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_F32_3XTF32) return -104;
+  if (dtype < G3_F32 || dtype > G3_F64) return -104;
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || (dtype == G3_INT8 && k > 131072)) return G3_ERR_UNSUPPORTED;
-  if (dtype == G3_F32) {   // one kernel: nothing to choose
+  if (dtype == G3_F32 || dtype == G3_F64) {   // one kernel: nothing to choose
     if (best_config) *best_config = -1;
     if (best_split) *best_split = 1;
     if (best_ms) *best_ms = 0.0;

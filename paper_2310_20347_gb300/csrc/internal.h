@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <mutex>
 
+#include "simt_dgemm.cuh"
 #include "simt_sgemm.cuh"
 #include "tc_gemm.cuh"
 
@@ -61,6 +62,9 @@ void register_grouped_3xtf32(GroupedEntry* table);
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.
 cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s);
+cudaError_t launch_simt64(const SimtParams64& p, bool vec, cudaStream_t s);
+// C := beta * C in binary64 (beta == 0 writes zeros without reading C).
+cudaError_t launch_scale_c_f64(double* C, int rows, int cols, long long ldc, double beta, cudaStream_t s);
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* lo,
                               long long ldy, cudaStream_t s);
 cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,

@@ -69,6 +69,28 @@ cudaError_t launch_convert_tf32_t(const float* x, int rows, int cols, long long 
   return cudaGetLastError();
 }
 
+cudaError_t launch_simt64(const SimtParams64& p, bool vec, cudaStream_t s) {
+  dim3 grid((p.n + 63) / 64, (p.m + 63) / 64, 1);
+  if (vec) simt_dgemm_kernel<true><<<grid, 256, 0, s>>>(p);
+  else simt_dgemm_kernel<false><<<grid, 256, 0, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void scale_c_f64_kernel(double* __restrict__ C, int rows, int cols, long long ldc, double beta) {
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    double* cr = C + r * ldc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
+      cr[c] = (beta == 0.0) ? 0.0 : beta * cr[c];
+  }
+}
+
+cudaError_t launch_scale_c_f64(double* C, int rows, int cols, long long ldc, double beta, cudaStream_t s) {
+  scale_c_f64_kernel<<<rows_grid(rows, cols, 1), 256, 0, s>>>(C, rows, cols, ldc, beta);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_tf32(const float* x, int rows, int cols, long long ldx, float* hi, float* lo,
                              long long ldy, cudaStream_t s) {
   const bool vec = reinterpret_cast<uintptr_t>(x) % 16 == 0 && ldx % 4 == 0 && reinterpret_cast<uintptr_t>(hi) % 16 == 0 &&
@@ -114,7 +136,10 @@ cudaError_t launch_transpose(const void* x, int rows, int cols, long long ldx, v
   const long long tiles = (long long)((rows + 31) / 32) * ((cols + 31) / 32);
   const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, 152LL * 16));
   const dim3 block(32, 8, 1);
-  if (esize == 4)
+  if (esize == 8)
+    transpose_kernel<uint64_t><<<grid, block, 0, s>>>(static_cast<const uint64_t*>(x), rows, cols, ldx,
+                                                       static_cast<uint64_t*>(y), ldy);
+  else if (esize == 4)
     transpose_kernel<uint32_t><<<grid, block, 0, s>>>(static_cast<const uint32_t*>(x), rows, cols, ldx,
                                                        static_cast<uint32_t*>(y), ldy);
   else if (esize == 2)

@@ -82,7 +82,7 @@ def test_argument_errors(lib):
     # allocation-free entry: k beyond one FP32 accumulator's bound (no device touched)
     assert L.g3_gemm_3xbf16_noalloc(64, 64, 40000, 1.0, p, 40000, p, 64, 0.0, p, 64, None) == L.G3_ERR_UNSUPPORTED
     # a dtype beyond the last one
-    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 8) == -112
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 9) == -112
     # INT8 accepts only alpha == 1 and beta in {0, 1}
     assert L.g3_gemm(4, 4, 8, 2.0, p, 8, p, 4, 0.0, p, 4, 4) == L.G3_ERR_UNSUPPORTED
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.5, p, 4, 4) == L.G3_ERR_UNSUPPORTED
