@@ -75,6 +75,8 @@ def _load():
                                                         i64, dbl, vp, i64, vp, i64, i32]
             lib.oracle_split3_bf16.argtypes = [ctypes.c_float, vp, vp, vp]
             lib.oracle_split_tf32.argtypes = [ctypes.c_float, vp, vp]
+            lib.oracle_gemm_rows_i16_i64.argtypes = [i64, vp, i64, i64, i64, vp, i64, vp, i64,
+                                                     i64, vp, i64, vp, i64, i32]
             lib.oracle_gemm_rows_3xtf32_f64.argtypes = [i64, vp, i64, i64, dbl, vp, i64, vp,
                                                         i64, dbl, vp, i64, vp, i64, i32]
             lib.oracle_max_threads.restype = i32
@@ -158,6 +160,21 @@ def gemm_i8(A, B, C=None, alpha=1, beta=0, rows=None, nthreads=0):
     _load().oracle_gemm_rows_i8_i64(nr, _ptr(r), n, k, int(alpha), _ptr(A), max(k, 1), _ptr(B),
                                     max(n, 1), int(beta), _ptr(Cin), max(n, 1), _ptr(out),
                                     max(n, 1), int(nthreads))
+    return out
+
+
+def gemm_i16(A, B, C=None, alpha=1, beta=0, rows=None, nthreads=0):
+    """beta*C + alpha*A@B exactly in int64 for int16 A, B (int64 C)."""
+    A = _c(A, np.int16)
+    B = _c(B, np.int16)
+    m, k = A.shape
+    n = B.shape[1]
+    Cin = _c(C, np.int64) if (C is not None and beta != 0) else None
+    r, nr = _rows_arg(rows, m)
+    out = np.empty((nr, n), np.int64)
+    _load().oracle_gemm_rows_i16_i64(nr, _ptr(r), n, k, int(alpha), _ptr(A), max(k, 1), _ptr(B),
+                                     max(n, 1), int(beta), _ptr(Cin), max(n, 1), _ptr(out),
+                                     max(n, 1), int(nthreads))
     return out
 
 

@@ -134,6 +134,35 @@ void oracle_gemm_rows_i8_i64(int64_t nrows, const int64_t* rows, int64_t n, int6
     }
 }
 
+void oracle_gemm_rows_i16_i64(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
+                              int64_t alpha, const int16_t* A, int64_t lda,
+                              const int16_t* B, int64_t ldb, int64_t beta,
+                              const int64_t* C_in, int64_t ldc_in,
+                              int64_t* C_out, int64_t ldc_out, int nthreads) {
+    if (nrows <= 0 || n <= 0) return;
+    int nt = threads_for(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        int64_t* acc = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t r = 0; r < nrows; ++r) {
+            int64_t i = row_index(rows, r);
+            for (int64_t j = 0; j < n; ++j) acc[j] = 0;
+            for (int64_t p = 0; p < k; ++p) {
+                int64_t a = A[i * lda + p];
+                const int16_t* brow = B + p * ldb;
+                for (int64_t j = 0; j < n; ++j) acc[j] += a * (int64_t)brow[j];
+            }
+            int64_t* crow = C_out + r * ldc_out;
+            for (int64_t j = 0; j < n; ++j) {
+                int64_t bc = (beta != 0) ? beta * C_in[i * ldc_in + j] : 0;
+                crow[j] = bc + alpha * acc[j];
+            }
+        }
+        free(acc);
+    }
+}
+
 /* ---------------------------------------------------------------------------
  * Number formats, written from their bit-level definitions.                   */
 

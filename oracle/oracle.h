@@ -59,6 +59,14 @@ void oracle_gemm_rows_i8_i64(int64_t nrows, const int64_t* rows, int64_t n, int6
                              const int32_t* C_in, int64_t ldc_in,
                              int64_t* C_out, int64_t ldc_out, int nthreads);
 
+/* The same for 16-bit integer inputs and a 64-bit C (the INT16 entry of the
+ * datatype study, Section 8.6), exact in int64 for k < 2^33.               */
+void oracle_gemm_rows_i16_i64(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
+                              int64_t alpha, const int16_t* A, int64_t lda,
+                              const int16_t* B, int64_t ldb, int64_t beta,
+                              const int64_t* C_in, int64_t ldc_in,
+                              int64_t* C_out, int64_t ldc_out, int nthreads);
+
 /* --- Convolution --------------------------------------------------------------
  * y := beta*y + alpha*conv(x, w), the convolution layers the paper casts to
  * GEMM (Section 8.1, Table 1), by its definition: x is N x H x W x C (NHWC),

@@ -144,6 +144,24 @@ def test_int8_oracle(oracle):
     assert np.all(oracle.gemm_i8(A2, B) == -127 * 128 * 8192)
 
 
+def test_int16_oracle(oracle):
+    r = np.random.default_rng(81)
+    A = r.integers(-(1 << 15), 1 << 15, (23, 410)).astype(np.int16)
+    B = r.integers(-(1 << 15), 1 << 15, (410, 17)).astype(np.int16)
+    C = r.integers(-(1 << 40), 1 << 40, (23, 17)).astype(np.int64)
+    got = oracle.gemm_i16(A, B, C, alpha=1, beta=1)
+    assert np.array_equal(got, C + A.astype(np.int64) @ B.astype(np.int64))
+    # worst case: all -32768 at k = 8192 gives 8192 * 2^30 = 2^43 exactly (beyond int32)
+    A = np.full((2, 8192), -32768, np.int16)
+    B = np.full((8192, 3), -32768, np.int16)
+    assert np.all(oracle.gemm_i16(A, B) == 1 << 43)
+    A2 = np.full((2, 8192), 32767, np.int16)
+    assert np.all(oracle.gemm_i16(A2, B) == -32767 * 32768 * 8192)
+    # int8-range inputs: the same as the int8 definition
+    p = synth.int8_problem(11, 13, 70, seed=82)
+    assert np.array_equal(oracle.gemm_i16(p.A.astype(np.int16), p.B.astype(np.int16)), oracle.gemm_i8(p.A, p.B))
+
+
 def test_int8_matches_f64_on_integer_inputs(oracle):
     # Two independent code paths of the oracle agree where both are exact.
     p = synth.int8_problem(17, 9, 64, seed=9)
