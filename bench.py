@@ -287,7 +287,7 @@ def run_workload(args):
 
     import oracle
     import paper_2310_20347_gb300 as pkg
-    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_F64, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, _lib, synth,
+    from paper_2310_20347_gb300 import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_F64, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_INT16, G3_TF32, _lib, synth,
                                         torch_api)
     torch.cuda.set_device(0)
     pkg.load()
@@ -527,9 +527,16 @@ def run_workload(args):
                "per_shape": per})
         return
 
-    if args.workload in ("int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64"):
-        n = args.dsize if args.workload != "fp64" else min(args.dsize, 4096)
-        if args.workload == "fp64":
+    if args.workload in ("int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "int16"):
+        n = args.dsize if args.workload not in ("fp64", "int16") else min(args.dsize, 4096)
+        if args.workload == "int16":
+            rng = np.random.default_rng(0)
+            p = synth.Problem(n, n, n, 1, 0, rng.integers(-(1 << 15), 1 << 15, (n, n)).astype(np.int16),
+                              rng.integers(-(1 << 15), 1 << 15, (n, n)).astype(np.int16), None)
+            A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+            C = torch.empty(n, n, dtype=torch.int64, device=dev)
+            fn = lambda: torch_api.gemm(A, B, C, 1, 0, dtype=G3_INT16)
+        elif args.workload == "fp64":
             rng = np.random.default_rng(0)
             p = synth.Problem(n, n, n, 1.0, 0.0, rng.uniform(-1, 1, (n, n)), rng.standard_normal((n, n)), None)
             A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
@@ -577,6 +584,8 @@ def run_workload(args):
         got = C[torch.from_numpy(rows).to(dev)].cpu().numpy()
         if args.workload == "int8":
             err = {"exact": bool(np.array_equal(got.astype(np.int64), oracle.gemm_i8(p.A, p.B, rows=rows)))}
+        elif args.workload == "int16":
+            err = {"exact": bool(np.array_equal(got.astype(np.int64), oracle.gemm_i16(p.A, p.B, rows=rows)))}
         elif args.workload == "3xtf32":
             err = sample_err(got.astype(np.float64), rows, p.A, p.B, p.C, 1.0, 0.5)
             C.copy_(C0)
@@ -587,6 +596,19 @@ def run_workload(args):
         ms = _call_ms(fn, args.reps, flush)
         kms = _kernel_ms(_lib, fn, args.reps, flush)
         flops = 2.0 * n ** 3
+        if args.workload == "int16":
+            # int64 multiply-adds of widened int16 products on the CUDA cores;
+            # against 152 SMs x 64 int32 multiplies per clock x 2.07 GHz x 2
+            int_peak = 152 * 64 * 2.07e9 * 2 / 1e12
+            _line(args, flops / ms / 1e9, "TOPS",
+                  {"workload": f"int16 GEMM m=n=k={n}, alpha=1, beta=0, uniform int16",
+                   "path": "INT16 SIMT kernel, int64 accumulation (64 x 64 CTA tiles, 4 x 4 micro-tiles)"},
+                  {"dtype": "int16", "ms": ms, "kernel_ms": kms, "err": err,
+                   "roofline": {"bound": "alu", "achieved": flops / kms / 1e9, "peak": int_peak, "unit": "TOP/s",
+                                "frac": flops / kms / 1e9 / int_peak, "traffic": None,
+                                "peak_source": "152 SMs x 64 int32 multiplies/clock x 2.07 GHz x 2 ops",
+                                "algorithmic": "2 n^3 integer ops per call"}})
+            return
         if args.workload == "fp64":
             # FP64 FMAs on the CUDA cores: against the nominal FP64 rate
             _line(args, flops / ms / 1e9, "TFLOPS",
@@ -774,7 +796,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "conv",
+                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "int16", "conv",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

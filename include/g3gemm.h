@@ -77,7 +77,10 @@ extern "C" {
  *                  grouped calls take G3_BF16 and G3_F32_3XBF16).
  *   G3_F64         A, B, C float64; FP64 FMA on the CUDA cores (the binary64
  *                  entry of the datatype study); alpha and beta are used in
- *                  binary64.  Single GEMMs only.                           */
+ *                  binary64.  Single GEMMs only.
+ *   G3_INT16       A, B int16; C int64; alpha must be 1 and beta 0 or 1;
+ *                  exact (products widened to 64 bits on the CUDA cores).
+ *                  Single GEMMs only.                                      */
 typedef enum {
   G3_F32 = 0,
   G3_F32_3XBF16 = 1,
@@ -87,7 +90,8 @@ typedef enum {
   G3_FP16 = 5,
   G3_TF32 = 6,
   G3_F32_3XTF32 = 7,
-  G3_F64 = 8
+  G3_F64 = 8,
+  G3_INT16 = 9
 } g3_dtype;
 
 /* g3_gemm_args.split_k value that asks for a stream-K tail (see there).    */

@@ -8,7 +8,7 @@ torch CUDA tensors.  ``synth`` holds the seeded input generators.
 Importing the package loads nothing; the library is loaded on first use.
 """
 from ._lib import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, DTYPES,  # noqa: F401
-                   G3_F32_3XTF32, G3_F64, G3_SPLIT_STREAM_K, G3Error, load)
+                   G3_F32_3XTF32, G3_F64, G3_INT16, G3_SPLIT_STREAM_K, G3Error, load)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

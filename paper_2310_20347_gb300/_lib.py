@@ -15,10 +15,10 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libg3gemm.so")
 
-G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP8_E4M3, G3_INT8, G3_FP16, G3_TF32, G3_F32_3XTF32, G3_F64 = range(9)
+G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP8_E4M3, G3_INT8, G3_FP16, G3_TF32, G3_F32_3XTF32, G3_F64, G3_INT16 = range(10)
 G3_SPLIT_STREAM_K = -1   # g3_gemm_args.split_k: a stream-K tail
 DTYPES = {"f32": G3_F32, "3xbf16": G3_F32_3XBF16, "bf16": G3_BF16, "fp8": G3_FP8_E4M3, "int8": G3_INT8,
-          "fp16": G3_FP16, "tf32": G3_TF32, "3xtf32": G3_F32_3XTF32, "f64": G3_F64}
+          "fp16": G3_FP16, "tf32": G3_TF32, "3xtf32": G3_F32_3XTF32, "f64": G3_F64, "int16": G3_INT16}
 
 G3_OK, G3_ERR_ARG, G3_ERR_UNSUPPORTED, G3_ERR_CUDA, G3_ERR_NOMEM, G3_ERR_TIMEOUT, G3_ERR_NOT_INIT = (
     0, -1, -2, -3, -4, -5, -6)

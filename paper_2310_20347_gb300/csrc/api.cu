@@ -565,7 +565,7 @@ int validate(const g3_gemm_args& a) {
   if (a.m < 0) return -101;
   if (a.n < 0) return -102;
   if (a.k < 0) return -103;
-  if (a.dtype < G3_F32 || a.dtype > G3_F64) return -112;
+  if (a.dtype < G3_F32 || a.dtype > G3_INT16) return -112;
   if (a.trans_a != 0 && a.trans_a != 1) return -119;
   if (a.trans_b != 0 && a.trans_b != 1) return -120;
   if (a.lda < std::max<int64_t>(1, a.trans_a ? a.m : a.k)) return -106;
@@ -582,6 +582,10 @@ int validate(const g3_gemm_args& a) {
     if (a.alpha != 1.0 && a.k > 0) return G3_ERR_UNSUPPORTED;
     if (a.beta != 0.0 && a.beta != 1.0) return G3_ERR_UNSUPPORTED;
     if (a.k > 131072) return G3_ERR_UNSUPPORTED;
+  }
+  if (a.dtype == G3_INT16) {
+    if (a.alpha != 1.0 && a.k > 0) return G3_ERR_UNSUPPORTED;
+    if (a.beta != 0.0 && a.beta != 1.0) return G3_ERR_UNSUPPORTED;
   }
   return G3_OK;
 }
@@ -624,6 +628,23 @@ int run_simt64(const g3_gemm_args& a, cudaStream_t s) {
                    a.lda % 2 == 0 && a.ldb % 2 == 0;
   TimedRegion tr(s);
   G3_CHECK_CUDA(launch_simt64(p, vec, s));
+  return G3_OK;
+}
+
+int run_simt_i16(const g3_gemm_args& a, cudaStream_t s) {
+  SimtParamsI16 p;
+  p.m = (int)a.m;
+  p.n = (int)a.n;
+  p.k = (int)a.k;
+  p.beta = a.beta != 0.0 ? 1 : 0;
+  p.A = static_cast<const int16_t*>(a.A);
+  p.lda = a.lda;
+  p.B = static_cast<const int16_t*>(a.B);
+  p.ldb = a.ldb;
+  p.C = static_cast<int64_t*>(a.C);
+  p.ldc = a.ldc;
+  TimedRegion tr(s);
+  G3_CHECK_CUDA(launch_simt_i16(p, s));
   return G3_OK;
 }
 
@@ -839,6 +860,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
 
 int input_esize(int dtype) {
   if (dtype == G3_F64) return 8;
+  if (dtype == G3_INT16) return 2;
   if (dtype == G3_F32 || dtype == G3_F32_3XBF16 || dtype == G3_TF32 || dtype == G3_F32_3XTF32) return 4;
   return (dtype == G3_BF16 || dtype == G3_FP16) ? 2 : 1;
 }
@@ -889,8 +911,10 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s, const PreparedB* pb = nullptr) {
   if ((a.trans_a || a.trans_b) && a.k > 0 && a.alpha != 0.0 && (st = untranspose(*d, a, s)) != G3_OK) return st;
   const bool is_int = a.dtype == G3_INT8;
   if (a.k == 0 || a.alpha == 0.0) {
-    if ((is_int || a.dtype == G3_F64) && a.beta == 1.0) return G3_OK;
-    if (a.dtype == G3_F64)
+    if ((is_int || a.dtype == G3_F64 || a.dtype == G3_INT16) && a.beta == 1.0) return G3_OK;
+    if (a.dtype == G3_INT16)   // beta == 0: zeros
+      G3_CHECK_CUDA(cudaMemset2DAsync(a.C, a.ldc * 8, 0, a.n * 8, a.m, s));
+    else if (a.dtype == G3_F64)
       G3_CHECK_CUDA(launch_scale_c_f64(static_cast<double*>(a.C), (int)a.m, (int)a.n, a.ldc, a.beta, s));
     else
       G3_CHECK_CUDA(launch_scale_c(a.C, is_int, (int)a.m, (int)a.n, a.ldc, (float)a.beta, s));
@@ -901,6 +925,7 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s, const PreparedB* pb = nullptr) {
   if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b) && a.split_k > 1) a.split_k = 1;
   if (a.dtype == G3_F32) return run_simt(a, s);
   if (a.dtype == G3_F64) return run_simt64(a, s);
+  if (a.dtype == G3_INT16) return run_simt_i16(a, s);
   return run_tc(*d, a, s, nullptr, pb);
 }
 
@@ -965,7 +990,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   const int es = input_esize(a.dtype);
   const int64_t lda_d = round_up(std::max<int64_t>(k, 1), 16), ldb_d = round_up(n, 16), ldc_d = round_up(n, 16);
   const size_t a_bytes = align256((size_t)m * lda_d * es), b_bytes = align256((size_t)std::max<int64_t>(k, 1) * ldb_d * es);
-  const int ces = a.dtype == G3_F64 ? 8 : 4;   // bytes per element of C
+  const int ces = (a.dtype == G3_F64 || a.dtype == G3_INT16) ? 8 : 4;   // bytes per element of C
   const size_t c_bytes = align256((size_t)m * ldc_d * ces);
   const bool products = k > 0 && a.alpha != 0.0;
   const bool read_c = a.beta != 0.0;
@@ -1231,7 +1256,7 @@ int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
   int st = validate(*args);
   if (st != G3_OK) return st;
   if (args->m == 0 || args->n == 0 || args->k == 0 || args->alpha == 0.0 || args->dtype == G3_F32 ||
-      args->dtype == G3_F64)
+      args->dtype == G3_F64 || args->dtype == G3_INT16)
     return G3_OK;
   std::lock_guard<std::mutex> lock(g_mu);
   DevState* d = nullptr;
@@ -1376,8 +1401,8 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   if (m < 0) return -101;
   if (n < 0) return -102;
   if (k < 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_F64) return -104;
-  if (dtype == G3_F32 || dtype == G3_F64) {
+  if (dtype < G3_F32 || dtype > G3_INT16) return -104;
+  if (dtype == G3_F32 || dtype == G3_F64 || dtype == G3_INT16) {
     if (config) *config = -1;
     if (split_k) *split_k = 1;
     if (raster) *raster = 0;
@@ -1437,9 +1462,9 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   if (m <= 0) return -101;
   if (n <= 0) return -102;
   if (k <= 0) return -103;
-  if (dtype < G3_F32 || dtype > G3_F64) return -104;
+  if (dtype < G3_F32 || dtype > G3_INT16) return -104;
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || (dtype == G3_INT8 && k > 131072)) return G3_ERR_UNSUPPORTED;
-  if (dtype == G3_F32 || dtype == G3_F64) {   // one kernel: nothing to choose
+  if (dtype == G3_F32 || dtype == G3_F64 || dtype == G3_INT16) {   // one kernel: nothing to choose
     if (best_config) *best_config = -1;
     if (best_split) *best_split = 1;
     if (best_ms) *best_ms = 0.0;

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "simt_dgemm.cuh"
+#include "simt_i16gemm.cuh"
 #include "simt_sgemm.cuh"
 #include "tc_gemm.cuh"
 
@@ -63,6 +64,7 @@ void register_grouped_3xtf32(GroupedEntry* table);
 // launch's cudaError_t; sizes are validated by the caller.
 cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s);
 cudaError_t launch_simt64(const SimtParams64& p, bool vec, cudaStream_t s);
+cudaError_t launch_simt_i16(const SimtParamsI16& p, cudaStream_t s);
 // C := beta * C in binary64 (beta == 0 writes zeros without reading C).
 cudaError_t launch_scale_c_f64(double* C, int rows, int cols, long long ldc, double beta, cudaStream_t s);
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* lo,

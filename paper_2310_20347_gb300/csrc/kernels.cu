@@ -77,6 +77,13 @@ cudaError_t launch_simt64(const SimtParams64& p, bool vec, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_simt_i16(const SimtParamsI16& p, cudaStream_t s) {
+  dim3 grid((p.n + 63) / 64, (p.m + 63) / 64, 1);
+  simt_i16gemm_kernel<16><<<grid, 256, 0, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void scale_c_f64_kernel(double* __restrict__ C, int rows, int cols, long long ldc, double beta) {
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
     double* cr = C + r * ldc;

@@ -7,13 +7,14 @@ from __future__ import annotations
 import torch
 
 from . import _lib
-from ._lib import G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_F64, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_TF32, check
+from ._lib import (G3_BF16, G3_F32, G3_F32_3XBF16, G3_F32_3XTF32, G3_F64, G3_FP16, G3_FP8_E4M3, G3_INT8, G3_INT16,
+                   G3_TF32, check)
 
 _ELEM = {G3_F32: (torch.float32, torch.float32), G3_F32_3XBF16: (torch.float32, torch.float32),
          G3_BF16: (torch.bfloat16, torch.float32), G3_FP8_E4M3: (torch.uint8, torch.float32),
          G3_INT8: (torch.int8, torch.int32), G3_FP16: (torch.float16, torch.float32),
          G3_TF32: (torch.float32, torch.float32), G3_F32_3XTF32: (torch.float32, torch.float32),
-         G3_F64: (torch.float64, torch.float64)}
+         G3_F64: (torch.float64, torch.float64), G3_INT16: (torch.int16, torch.int64)}
 
 
 def _stream(stream):

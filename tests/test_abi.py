@@ -48,7 +48,7 @@ def test_argument_errors(lib):
     assert L.g3_gemm(4, 4, 8, 1.0, p, 7, p, 4, 0.0, p, 4, 0) == -106
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 3, 0.0, p, 4, 0) == -108
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 3, 0) == -111
-    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 9) == -112
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 10) == -112
     assert L.g3_gemm(4, 4, 8, 1.0, None, 8, p, 4, 0.0, p, 4, 0) == -105
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, None, 4, 0.0, p, 4, 0) == -107
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, None, 4, 0) == -110
@@ -82,7 +82,10 @@ def test_argument_errors(lib):
     # allocation-free entry: k beyond one FP32 accumulator's bound (no device touched)
     assert L.g3_gemm_3xbf16_noalloc(64, 64, 40000, 1.0, p, 40000, p, 64, 0.0, p, 64, None) == L.G3_ERR_UNSUPPORTED
     # a dtype beyond the last one
-    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 9) == -112
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.0, p, 4, 10) == -112
+    # INT16 accepts only alpha == 1 and beta in {0, 1}
+    assert L.g3_gemm(4, 4, 8, 2.0, p, 8, p, 4, 0.0, p, 4, L.G3_INT16) == L.G3_ERR_UNSUPPORTED
+    assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.5, p, 4, L.G3_INT16) == L.G3_ERR_UNSUPPORTED
     # INT8 accepts only alpha == 1 and beta in {0, 1}
     assert L.g3_gemm(4, 4, 8, 2.0, p, 8, p, 4, 0.0, p, 4, 4) == L.G3_ERR_UNSUPPORTED
     assert L.g3_gemm(4, 4, 8, 1.0, p, 8, p, 4, 0.5, p, 4, 4) == L.G3_ERR_UNSUPPORTED
