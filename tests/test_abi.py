@@ -161,3 +161,37 @@ def test_tuning_cache_overrides_planner(lib, tmp_path):
     assert L.g3_tune_cache_clear() == 0
     assert L.g3_plan_query(1000, 3000, 700, L.G3_BF16)[1:3] == (cfg0, sk0)
     assert L.g3_tune_cache_load(str(tmp_path / "missing.txt")) == -101
+
+
+def test_planner_invariants_over_random_shapes(lib):
+    # host logic only: for every dtype and 300 seeded shapes the plan names a
+    # member of the mode the dtype runs (the FP32-accurate mode by depth), a
+    # split count within [1, k-blocks], never a stream-K tail unasked, and the
+    # FP32-accurate modes keep at most 32768 (3xBF16) / 8192 (3xTF32) of k per
+    # accumulator; the CUDA-core dtypes report no member.
+    import numpy as np
+    from paper_2310_20347_gb300 import gen_family
+    fam = gen_family.enumerate_family()
+    L = lib
+    mode_of = {L.G3_BF16: "bf16", L.G3_FP16: "f16", L.G3_TF32: "tf32", L.G3_FP8_E4M3: "fp8",
+               L.G3_INT8: "int8emu", L.G3_F32_3XTF32: "3xtf32"}
+    kblock = {"bf16": 64, "f16": 64, "tf32": 32, "fp8": 128, "int8emu": 64, "3xtf32": 32, "3xbf16": 64,
+              "6xbf16": 64}
+    rng = np.random.default_rng(90)
+    for _ in range(300):
+        m, n = (int(x) for x in np.exp(rng.uniform(0, np.log(20000), 2)).astype(int) + 1)
+        k = int(np.exp(rng.uniform(0, np.log(70000))) + 1)
+        for dt in (L.G3_BF16, L.G3_FP16, L.G3_TF32, L.G3_FP8_E4M3, L.G3_INT8, L.G3_F32_3XTF32, L.G3_F32_3XBF16):
+            st, cfg, sk, rs = L.g3_plan_query(m, n, k, dt)
+            assert st == 0 and 0 <= cfg < len(fam), (m, n, k, dt)
+            mode = mode_of.get(dt) or ("6xbf16" if k <= 512 else "3xbf16")
+            assert fam[cfg]["mode"] == mode, (m, n, k, dt, fam[cfg])
+            num_kb = -(-k // kblock[mode])
+            assert sk != L.G3_SPLIT_STREAM_K and 1 <= sk <= num_kb, (m, n, k, dt, sk)
+            if mode == "3xtf32":
+                assert -(-num_kb // sk) <= 256, (k, sk)
+            if mode == "3xbf16":
+                assert -(-num_kb // sk) <= 512, (k, sk)
+            assert rs >= 1
+        for dt in (L.G3_F32, L.G3_F64, L.G3_INT16):
+            assert L.g3_plan_query(m, n, k, dt)[1] == -1
