@@ -57,8 +57,8 @@ extern "C" {
  *                  k <= 512 the split has three parts (hi + mid + lo) and six
  *                  products (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid):
  *                  at small k the two-part split's own error is above 2e-6
- *                  of sum |a||b|.  A grouped call takes the three-part split
- *                  for all its problems when one of them has k <= 512.
+ *                  of sum |a||b|.  A grouped call applies the same choice
+ *                  problem by problem (one persistent launch per kind).
  *   G3_BF16        A, B bfloat16 (raw 16-bit patterns); C float32.
  *   G3_FP8_E4M3    A, B OCP E4M3 bytes with per-tensor scales (g3_gemm_ex);
  *                  C float32 = alpha*scale_a*scale_b*(Aq Bq) + beta*C.
@@ -269,9 +269,11 @@ typedef struct g3_grouped_plan g3_grouped_plan;
  * to G3_ERR_ARG for i >= 900.                                               */
 G3_API int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** plan);
 
-/* Run every problem of the plan: pre-passes (if any) and ONE persistent
- * kernel launch.  No host synchronisation and no allocation, so the call can
- * be captured into a CUDA graph.                                            */
+/* Run every problem of the plan: pre-passes (if any) and one persistent
+ * kernel launch per kernel kind (BF16: one; FP32-accurate: one for the
+ * problems with k > 512 and one for those with k <= 512).  No host
+ * synchronisation and no allocation, so the call can be captured into a CUDA
+ * graph.                                                                    */
 G3_API int g3_grouped_plan_execute(g3_grouped_plan* plan, void* cuda_stream);
 
 G3_API int g3_grouped_plan_destroy(g3_grouped_plan* plan);

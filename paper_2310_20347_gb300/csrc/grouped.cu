@@ -8,8 +8,10 @@
 // a device table, and the preparation jobs (FP32 hi/lo or hi/mid/lo split,
 // re-packing of unaligned BF16 operands, C := beta*C for problems without
 // products).
-// Executing the plan is at most two launches -- one job kernel over all
-// preparation jobs and one tc_grouped_kernel over all tiles -- with no host
+// Executing the plan is one job kernel over all preparation jobs and one
+// tc_grouped_kernel per kernel kind over its tiles -- BF16: one; FP32-accurate:
+// the two-part split (3 products) for problems with k > 512 and the
+// three-part split (6 products) for those with k <= 512 -- with no host
 // synchronisation and no allocation.
 #include <algorithm>
 #include <cstdio>
@@ -146,12 +148,15 @@ struct g3_grouped_plan {
   int device = -1;
   int dtype = 0;
   int count = 0;
-  int entry = -1;        // index into the grouped kernel table
   int total_tiles = 0;
   int njobs = 0;
   int sms = 0;
   void* dmem = nullptr;  // one allocation: maps | problems | tile list | jobs | operand planes
-  GroupedParams params{};
+  // one persistent launch per kernel kind: its grouped kernel (index into the
+  // table) and its part of the tile list
+  int nparts = 0;
+  int entry[2] = {-1, -1};
+  GroupedParams params[2]{};
   PrepJob* d_jobs = nullptr;
 };
 
@@ -183,20 +188,22 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   int st = current_device_info(&dev);
   if (st != G3_OK) return st;
   grouped_init();
-  // FP32-accurate plans take the three-part split (6 products) for every
-  // problem as soon as one of them has k <= 512, where the two-part split's
-  // dropped terms exceed 2e-6 of sum |a||b|.
-  bool small_k = false;
-  for (int i = 0; i < count; ++i)
-    if (descs[i].m > 0 && descs[i].n > 0 && descs[i].k > 0 && descs[i].alpha != 0.0 && descs[i].k <= 512)
-      small_k = true;
-  const int mode = (dtype == G3_BF16) ? TC_BF16 : (small_k ? TC_6XBF16 : TC_3XBF16);
-  const bool split3 = mode == TC_6XBF16;
-  int entry = -1;
-  for (int i = 0; i < G3_GROUPED_SIZE; ++i)
-    if (g_grouped[i].launch && g_grouped[i].mode == mode) entry = i;
-  if (entry < 0) return G3_ERR_UNSUPPORTED;
-  const GroupedEntry& ge = g_grouped[entry];
+  // FP32-accurate problems with k <= 512 take the three-part split (6
+  // products), where the two-part split's dropped terms exceed 2e-6 of
+  // sum |a||b|; deeper ones the two-part split (3 products).  Each kind runs
+  // as its own persistent launch (part 0: BF16 or the two-part split; part 1:
+  // the three-part split).
+  auto entry_of = [](int mode) {
+    int e = -1;
+    for (int i = 0; i < G3_GROUPED_SIZE; ++i)
+      if (g_grouped[i].launch && g_grouped[i].mode == mode) e = i;
+    return e;
+  };
+  const int entries[2] = {entry_of(dtype == G3_BF16 ? TC_BF16 : TC_3XBF16),
+                          dtype == G3_BF16 ? -1 : entry_of(TC_6XBF16)};
+  if (entries[0] < 0 || (dtype != G3_BF16 && entries[1] < 0)) return G3_ERR_UNSUPPORTED;
+  auto part_of = [&](int64_t k) { return (dtype != G3_BF16 && k <= 512) ? 1 : 0; };
+  const int bm_max = std::min(g_grouped[entries[0]].bm_max, entries[1] >= 0 ? g_grouped[entries[1]].bm_max : 1 << 30);
 
   // ---- per-problem tiling, jobs and plane sizes (host)
   std::vector<GroupDesc> groups(count);
@@ -216,7 +223,7 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     g.alpha = (float)d.alpha; g.beta = (float)d.beta;
     g.C = static_cast<float*>(d.C);
     g.ldc = d.ldc;
-    g.bm = (d.m <= 64) ? 64 : std::min(128, ge.bm_max);   // size bucket
+    g.bm = (d.m <= 64) ? 64 : std::min(128, bm_max);   // size bucket
     if (d.m == 0 || d.n == 0) continue;
     if (d.k == 0 || d.alpha == 0.0) {
       PrepJob J{};
@@ -237,7 +244,7 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
       o.a_lo_off = take((size_t)d.m * o.lda * 2);
       o.b_off = take((size_t)d.k * o.ldb * 2);
       o.b_lo_off = take((size_t)d.k * o.ldb * 2);
-      if (split3) {
+      if (part_of(d.k) == 1) {
         o.a_mid_off = take((size_t)d.m * o.lda * 2);
         o.b_mid_off = take((size_t)d.k * o.ldb * 2);
       }
@@ -280,6 +287,7 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     const Operands& o = ops[i];
     const GroupDesc& g = groups[i];
     const void *a = d.A, *b = d.B, *a_lo = nullptr, *b_lo = nullptr, *a_mid = nullptr, *b_mid = nullptr;
+    const bool split3 = part_of(d.k) == 1;
     if (dtype == G3_F32_3XBF16) {
       a = d_planes + o.a_off; a_lo = d_planes + o.a_lo_off;
       b = d_planes + o.b_off; b_lo = d_planes + o.b_lo_off;
@@ -325,18 +333,22 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     return st;
   }
 
-  // global tile list, heaviest (deepest k) problems first; ties keep problem order
+  // tile list: part 0 then part 1, each heaviest (deepest k) problems first;
+  // ties keep problem order
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return groups[x].num_kb * groups[x].bm > groups[y].num_kb * groups[y].bm; });
   std::vector<int2> tiles;
   tiles.reserve((size_t)total_tiles);
-  for (int i : order) {
-    if (!ops[i].active) continue;
-    const int nt = groups[i].tiles_m * groups[i].tiles_n;
-    for (int t = 0; t < nt; ++t) tiles.push_back(make_int2(i, t));
-  }
+  int part_tiles[2] = {0, 0};
+  for (int part = 0; part < 2; ++part)
+    for (int i : order) {
+      if (!ops[i].active || part_of(descs[i].k) != part) continue;
+      const int nt = groups[i].tiles_m * groups[i].tiles_n;
+      for (int t = 0; t < nt; ++t) tiles.push_back(make_int2(i, t));
+      part_tiles[part] += nt;
+    }
 
   bool ok = true;
   ok = ok && cudaMemcpy(d_maps, maps.data(), sizeof(CUtensorMap) * kMapsPerProblem * (size_t)count,
@@ -357,18 +369,25 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   plan->device = dev.device;
   plan->dtype = dtype;
   plan->count = count;
-  plan->entry = entry;
   plan->total_tiles = (int)total_tiles;
   plan->njobs = (int)jobs.size();
   plan->sms = dev.sms;
   plan->d_jobs = d_jobs;
-  plan->params.groups = d_groups;
-  plan->params.maps = d_maps;
-  plan->params.tile_info = d_tiles;
-  plan->params.total_tiles = (int)total_tiles;
-  plan->params.timeout_ns = watchdog_timeout_ns();
-  plan->params.status = dev.status;
-  plan->params.debug_withhold = -1;
+  int first = 0;
+  for (int part = 0; part < 2; ++part) {
+    if (part_tiles[part] == 0) continue;
+    GroupedParams& p = plan->params[plan->nparts];
+    p.groups = d_groups;
+    p.maps = d_maps;
+    p.tile_info = d_tiles + first;
+    p.total_tiles = part_tiles[part];
+    p.timeout_ns = watchdog_timeout_ns();
+    p.status = dev.status;
+    p.debug_withhold = -1;
+    plan->entry[plan->nparts] = entries[part];
+    ++plan->nparts;
+    first += part_tiles[part];
+  }
   *out = plan;
   return G3_OK;
 }
@@ -388,14 +407,14 @@ int g3_grouped_plan_execute(g3_grouped_plan* plan, void* stream) {
     if (cudaGetLastError() != cudaSuccess) return G3_ERR_CUDA;
   }
   if (plan->total_tiles == 0) return G3_OK;
-  GroupedParams p = plan->params;
+  GroupedParams p[2] = {plan->params[0], plan->params[1]};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   {
     std::lock_guard<std::mutex> lock(api_mutex());
     unsigned long long t = 0;
-    if (take_withhold(&t)) {
-      p.debug_withhold = 0;
-      p.timeout_ns = t;
+    if (take_withhold(&t)) {   // failure-detection test hook: the first launch
+      p[0].debug_withhold = 0;
+      p[0].timeout_ns = t;
     }
     if (kernel_timing_enabled()) {
       cudaEventCreate(&e0);
@@ -403,8 +422,11 @@ int g3_grouped_plan_execute(g3_grouped_plan* plan, void* stream) {
     }
   }
   if (e0) cudaEventRecord(e0, s);
-  const int grid = std::min(plan->total_tiles, plan->sms);
-  const cudaError_t e = g_grouped[plan->entry].launch(p, grid, s);
+  cudaError_t e = cudaSuccess;
+  for (int part = 0; part < plan->nparts && e == cudaSuccess; ++part) {
+    const int grid = std::min(p[part].total_tiles, plan->sms);
+    e = g_grouped[plan->entry[part]].launch(p[part], grid, s);
+  }
   if (e1) {
     cudaEventRecord(e1, s);
     std::lock_guard<std::mutex> lock(api_mutex());

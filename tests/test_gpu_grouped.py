@@ -43,9 +43,8 @@ def make_batch(count, seed, lo=1, hi=300, dtype=G3_BF16, unaligned_every=5):
 
 
 def check_batch(probs, host, dtype):
-    # an FP32-accurate plan takes the three-part split for all of its problems
-    # as soon as one problem with products has k <= 512
-    split3 = any(p.m > 0 and p.n > 0 and 0 < p.k <= 512 and p.alpha != 0 for p, _ in host)
+    # an FP32-accurate plan takes the three-part split for problems with
+    # k <= 512 and the two-part split for deeper ones
     worst_k = worst_g = 0.0
     for (A, B, C, alpha, beta), (p, full) in zip(probs, host):
         f = full.cpu().numpy()
@@ -60,7 +59,7 @@ def check_batch(probs, host, dtype):
             D_k = oracle.absprod(Aq, Bq, p.alpha)
             gate = 8e-3
         else:
-            method = oracle.gemm_6xbf16 if split3 else oracle.gemm_3xbf16
+            method = oracle.gemm_6xbf16 if p.k <= 512 else oracle.gemm_3xbf16
             ref_k = method(p.A, p.B, p.C, p.alpha, p.beta)
             D_k = oracle.absprod(p.A, p.B, p.alpha)
             gate = 2e-6
