@@ -677,14 +677,17 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   } else if (a.dtype == G3_F32_3XBF16) {
     uint16_t *ah = (uint16_t*)(ws + L.a_hi), *al = (uint16_t*)(ws + L.a_lo);
     uint16_t *bh = (uint16_t*)(ws + L.b_hi), *bl = (uint16_t*)(ws + L.b_lo);
-    G3_CHECK_CUDA(launch_split_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p, s));
+    if (!pb)
+      G3_CHECK_CUDA(launch_split_bf16_pair((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p,
+                                           (const float*)a.B, (int)k, (int)n, a.ldb, bh, bl, L.ldb_p, s));
+    else
+      G3_CHECK_CUDA(launch_split_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, al, L.lda_p, s));
     A_hi = ah; A_lo = al;
     lda = L.lda_p;
     if (pb) {
       B_hi = pb->hi; B_lo = pb->lo;
       ldb = pb->ld;
     } else {
-      G3_CHECK_CUDA(launch_split_bf16((const float*)a.B, (int)k, (int)n, a.ldb, bh, bl, L.ldb_p, s));
       B_hi = bh; B_lo = bl;
       ldb = L.ldb_p;
     }

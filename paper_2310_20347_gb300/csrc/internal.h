@@ -69,6 +69,11 @@ cudaError_t launch_simt_i16(const SimtParamsI16& p, cudaStream_t s);
 cudaError_t launch_scale_c_f64(double* C, int rows, int cols, long long ldc, double beta, cudaStream_t s);
 cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* lo,
                               long long ldy, cudaStream_t s);
+// The split of both operands of a call in one launch (two launches when a
+// matrix's rows are not 16-byte aligned).
+cudaError_t launch_split_bf16_pair(const float* xa, int rows_a, int cols_a, long long lda, uint16_t* ahi, uint16_t* alo,
+                                   long long lda_p, const float* xb, int rows_b, int cols_b, long long ldb,
+                                   uint16_t* bhi, uint16_t* blo, long long ldb_p, cudaStream_t s);
 cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,
                                uint16_t* lo, long long ldy, cudaStream_t s);
 // y = x rounded to TF32 (nearest, ties to even), kept as binary32.

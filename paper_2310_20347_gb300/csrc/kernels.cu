@@ -42,6 +42,25 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx,
   return cudaGetLastError();
 }
 
+cudaError_t launch_split_bf16_pair(const float* xa, int rows_a, int cols_a, long long lda, uint16_t* ahi, uint16_t* alo,
+                                   long long lda_p, const float* xb, int rows_b, int cols_b, long long ldb,
+                                   uint16_t* bhi, uint16_t* blo, long long ldb_p, cudaStream_t s) {
+  auto vec = [](const float* x, long long ldx, const uint16_t* hi, const uint16_t* lo, long long ldy) {
+    return reinterpret_cast<uintptr_t>(x) % 16 == 0 && ldx % 4 == 0 && reinterpret_cast<uintptr_t>(hi) % 16 == 0 &&
+           reinterpret_cast<uintptr_t>(lo) % 16 == 0 && ldy % 8 == 0;
+  };
+  if (!vec(xa, lda, ahi, alo, lda_p) || !vec(xb, ldb, bhi, blo, ldb_p)) {
+    cudaError_t e = launch_split_bf16(xa, rows_a, cols_a, lda, ahi, alo, lda_p, s);
+    return e != cudaSuccess ? e : launch_split_bf16(xb, rows_b, cols_b, ldb, bhi, blo, ldb_p, s);
+  }
+  const dim3 ga = rows_grid(rows_a, cols_a, 8), gb = rows_grid(rows_b, cols_b, 8);
+  const dim3 grid(std::max(ga.x, gb.x), std::max(ga.y, gb.y), 2);
+  split_bf16_vec8_pair_kernel<<<grid, 256, 0, s>>>(SplitJob{xa, rows_a, cols_a, lda, ahi, alo, lda_p},
+                                                   SplitJob{xb, rows_b, cols_b, ldb, bhi, blo, ldb_p});
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,
                                uint16_t* lo, long long ldy, cudaStream_t s) {
   split3_bf16_kernel<<<rows_grid(rows, cols, 1), 256, 0, s>>>(x, rows, cols, ldx, hi, mid, lo, ldy);

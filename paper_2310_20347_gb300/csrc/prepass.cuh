@@ -50,8 +50,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(uint16_t lo_elem, uint16_t hi_el
 // 16-byte store per plane.  Requires 16-byte-aligned rows of x (ldx % 4 == 0)
 // and of the planes (ldy % 8 == 0); the last cols % 8 elements of a row are
 // done one by one.
-__global__ void split_bf16_vec8_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
-                                       uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, long long ldy) {
+__device__ __forceinline__ void split_bf16_vec8_rows(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                                    uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                                                    long long ldy) {
   const int cols8 = cols >> 3;
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
     const float* xr = x + r * ldx;
@@ -81,6 +82,27 @@ __global__ void split_bf16_vec8_kernel(const float* __restrict__ x, int rows, in
       }
     }
   }
+}
+
+__global__ void split_bf16_vec8_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                       uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, long long ldy) {
+  split_bf16_vec8_rows(x, rows, cols, ldx, hi, lo, ldy);
+}
+
+// Both operands of one call in a single launch: blockIdx.z selects the job
+// (0: A, 1: B), which saves a launch and its gap on small problems.
+struct SplitJob {
+  const float* x;
+  int rows, cols;
+  long long ldx;
+  uint16_t* hi;
+  uint16_t* lo;
+  long long ldy;
+};
+
+__global__ void split_bf16_vec8_pair_kernel(const SplitJob j0, const SplitJob j1) {
+  const SplitJob& J = blockIdx.z == 0 ? j0 : j1;
+  split_bf16_vec8_rows(J.x, J.rows, J.cols, J.ldx, J.hi, J.lo, J.ldy);
 }
 
 // Three-part split for the small-k FP32-accurate mode: hi = bf16(x),
