@@ -669,8 +669,8 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   if (fam.mode == TC_6XBF16) {
     uint16_t *ah = (uint16_t*)(ws + L.a_hi), *am = (uint16_t*)(ws + L.a_mid), *al = (uint16_t*)(ws + L.a_lo);
     uint16_t *bh = (uint16_t*)(ws + L.b_hi), *bm = (uint16_t*)(ws + L.b_mid), *bl = (uint16_t*)(ws + L.b_lo);
-    G3_CHECK_CUDA(launch_split3_bf16((const float*)a.A, (int)m, (int)k, a.lda, ah, am, al, L.lda_p, s));
-    G3_CHECK_CUDA(launch_split3_bf16((const float*)a.B, (int)k, (int)n, a.ldb, bh, bm, bl, L.ldb_p, s));
+    G3_CHECK_CUDA(launch_split3_bf16_pair((const float*)a.A, (int)m, (int)k, a.lda, ah, am, al, L.lda_p,
+                                          (const float*)a.B, (int)k, (int)n, a.ldb, bh, bm, bl, L.ldb_p, s));
     A_hi = ah; A_mid = am; A_lo = al; B_hi = bh; B_mid = bm; B_lo = bl;
     lda = L.lda_p;
     ldb = L.ldb_p;
@@ -708,8 +708,8 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
     ldb = L.ldb_p;
   } else if (a.dtype == G3_INT8) {
     uint16_t *ah = (uint16_t*)(ws + L.a_hi), *bh = (uint16_t*)(ws + L.b_hi);
-    G3_CHECK_CUDA(launch_int8_to_bf16((const int8_t*)a.A, (int)m, (int)k, a.lda, ah, L.lda_p, s));
-    G3_CHECK_CUDA(launch_int8_to_bf16((const int8_t*)a.B, (int)k, (int)n, a.ldb, bh, L.ldb_p, s));
+    G3_CHECK_CUDA(launch_int8_to_bf16_pair((const int8_t*)a.A, (int)m, (int)k, a.lda, ah, L.lda_p,
+                                           (const int8_t*)a.B, (int)k, (int)n, a.ldb, bh, L.ldb_p, s));
     A_hi = ah; B_hi = bh;
     lda = L.lda_p;
     ldb = L.ldb_p;

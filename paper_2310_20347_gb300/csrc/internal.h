@@ -74,6 +74,13 @@ cudaError_t launch_split_bf16(const float* x, int rows, int cols, long long ldx,
 cudaError_t launch_split_bf16_pair(const float* xa, int rows_a, int cols_a, long long lda, uint16_t* ahi, uint16_t* alo,
                                    long long lda_p, const float* xb, int rows_b, int cols_b, long long ldb,
                                    uint16_t* bhi, uint16_t* blo, long long ldb_p, cudaStream_t s);
+cudaError_t launch_split3_bf16_pair(const float* xa, int rows_a, int cols_a, long long lda, uint16_t* ahi,
+                                    uint16_t* amid, uint16_t* alo, long long lda_p, const float* xb, int rows_b,
+                                    int cols_b, long long ldb, uint16_t* bhi, uint16_t* bmid, uint16_t* blo,
+                                    long long ldb_p, cudaStream_t s);
+cudaError_t launch_int8_to_bf16_pair(const int8_t* xa, int rows_a, int cols_a, long long lda, uint16_t* ya,
+                                     long long lda_p, const int8_t* xb, int rows_b, int cols_b, long long ldb,
+                                     uint16_t* yb, long long ldb_p, cudaStream_t s);
 cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,
                                uint16_t* lo, long long ldy, cudaStream_t s);
 // y = x rounded to TF32 (nearest, ties to even), kept as binary32.

@@ -61,6 +61,37 @@ cudaError_t launch_split_bf16_pair(const float* xa, int rows_a, int cols_a, long
   return cudaGetLastError();
 }
 
+cudaError_t launch_split3_bf16_pair(const float* xa, int rows_a, int cols_a, long long lda, uint16_t* ahi,
+                                    uint16_t* amid, uint16_t* alo, long long lda_p, const float* xb, int rows_b,
+                                    int cols_b, long long ldb, uint16_t* bhi, uint16_t* bmid, uint16_t* blo,
+                                    long long ldb_p, cudaStream_t s) {
+  const dim3 ga = rows_grid(rows_a, cols_a, 1), gb = rows_grid(rows_b, cols_b, 1);
+  const dim3 grid(std::max(ga.x, gb.x), std::max(ga.y, gb.y), 2);
+  split3_bf16_pair_kernel<<<grid, 256, 0, s>>>(Split3Job{xa, rows_a, cols_a, lda, ahi, amid, alo, lda_p},
+                                               Split3Job{xb, rows_b, cols_b, ldb, bhi, bmid, blo, ldb_p});
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_int8_to_bf16_pair(const int8_t* xa, int rows_a, int cols_a, long long lda, uint16_t* ya,
+                                     long long lda_p, const int8_t* xb, int rows_b, int cols_b, long long ldb,
+                                     uint16_t* yb, long long ldb_p, cudaStream_t s) {
+  auto vec = [](const int8_t* x, long long ldx, const uint16_t* y, long long ldy) {
+    return reinterpret_cast<uintptr_t>(x) % 16 == 0 && ldx % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0 &&
+           ldy % 8 == 0;
+  };
+  if (!vec(xa, lda, ya, lda_p) || !vec(xb, ldb, yb, ldb_p)) {
+    cudaError_t e = launch_int8_to_bf16(xa, rows_a, cols_a, lda, ya, lda_p, s);
+    return e != cudaSuccess ? e : launch_int8_to_bf16(xb, rows_b, cols_b, ldb, yb, ldb_p, s);
+  }
+  const dim3 ga = rows_grid(rows_a, cols_a, 16), gb = rows_grid(rows_b, cols_b, 16);
+  const dim3 grid(std::max(ga.x, gb.x), std::max(ga.y, gb.y), 2);
+  int8_to_bf16_vec16_pair_kernel<<<grid, 256, 0, s>>>(I8Job{xa, rows_a, cols_a, lda, ya, lda_p},
+                                                      I8Job{xb, rows_b, cols_b, ldb, yb, ldb_p});
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split3_bf16(const float* x, int rows, int cols, long long ldx, uint16_t* hi, uint16_t* mid,
                                uint16_t* lo, long long ldy, cudaStream_t s) {
   split3_bf16_kernel<<<rows_grid(rows, cols, 1), 256, 0, s>>>(x, rows, cols, ldx, hi, mid, lo, ldy);

@@ -114,9 +114,9 @@ __device__ __forceinline__ void split3(float v, uint16_t& h, uint16_t& m, uint16
   l = bf16_bits(d - bf16_value(m));
 }
 
-__global__ void split3_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
-                                   uint16_t* __restrict__ hi, uint16_t* __restrict__ mid, uint16_t* __restrict__ lo,
-                                   long long ldy) {
+__device__ __forceinline__ void split3_bf16_rows(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                                 uint16_t* __restrict__ hi, uint16_t* __restrict__ mid,
+                                                 uint16_t* __restrict__ lo, long long ldy) {
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
     const float* xr = x + r * ldx;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
@@ -127,6 +127,26 @@ __global__ void split3_bf16_kernel(const float* __restrict__ x, int rows, int co
       lo[r * ldy + c] = l;
     }
   }
+}
+
+__global__ void split3_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
+                                   uint16_t* __restrict__ hi, uint16_t* __restrict__ mid, uint16_t* __restrict__ lo,
+                                   long long ldy) {
+  split3_bf16_rows(x, rows, cols, ldx, hi, mid, lo, ldy);
+}
+
+// Both operands of one call in a single launch (blockIdx.z: 0 = A, 1 = B).
+struct Split3Job {
+  const float* x;
+  int rows, cols;
+  long long ldx;
+  uint16_t *hi, *mid, *lo;
+  long long ldy;
+};
+
+__global__ void split3_bf16_pair_kernel(const Split3Job j0, const Split3Job j1) {
+  const Split3Job& J = blockIdx.z == 0 ? j0 : j1;
+  split3_bf16_rows(J.x, J.rows, J.cols, J.ldx, J.hi, J.mid, J.lo, J.ldy);
 }
 
 // TF32 round to nearest even on the encoding: add half an ulp of the 10-bit
@@ -252,8 +272,8 @@ __global__ void int8_to_bf16_kernel(const int8_t* __restrict__ x, int rows, int 
 // The same, 16 elements per thread step: one 16-byte load of x, two 16-byte
 // stores of y.  Requires 16-byte-aligned rows of x (ldx % 16 == 0) and of y
 // (ldy % 8 == 0); the last cols % 16 elements of a row are done one by one.
-__global__ void int8_to_bf16_vec16_kernel(const int8_t* __restrict__ x, int rows, int cols, long long ldx,
-                                          uint16_t* __restrict__ y, long long ldy) {
+__device__ __forceinline__ void int8_to_bf16_vec16_rows(const int8_t* __restrict__ x, int rows, int cols,
+                                                        long long ldx, uint16_t* __restrict__ y, long long ldy) {
   const int cols16 = cols >> 4;
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
     const int8_t* xr = x + r * ldx;
@@ -275,6 +295,25 @@ __global__ void int8_to_bf16_vec16_kernel(const int8_t* __restrict__ x, int rows
     if (blockIdx.x == 0)
       for (int c = (cols16 << 4) + threadIdx.x; c < cols; c += blockDim.x) yr[c] = bf16_bits(static_cast<float>(xr[c]));
   }
+}
+
+__global__ void int8_to_bf16_vec16_kernel(const int8_t* __restrict__ x, int rows, int cols, long long ldx,
+                                          uint16_t* __restrict__ y, long long ldy) {
+  int8_to_bf16_vec16_rows(x, rows, cols, ldx, y, ldy);
+}
+
+// Both int8 operands of one call in a single launch (blockIdx.z: 0 = A, 1 = B).
+struct I8Job {
+  const int8_t* x;
+  int rows, cols;
+  long long ldx;
+  uint16_t* y;
+  long long ldy;
+};
+
+__global__ void int8_to_bf16_vec16_pair_kernel(const I8Job j0, const I8Job j1) {
+  const I8Job& J = blockIdx.z == 0 ? j0 : j1;
+  int8_to_bf16_vec16_rows(J.x, J.rows, J.cols, J.ldx, J.y, J.ldy);
 }
 
 // Copy `cols` elements of `esize` bytes per row from a strided source into a
