@@ -109,12 +109,16 @@ cudaError_t launch_convert_tf32(const float* x, int rows, int cols, long long ld
   return cudaGetLastError();
 }
 
+// 64 x 64 tiles, up to eight resident blocks per SM
+static int transpose64_grid(int rows, int cols) {
+  const long long tiles = (long long)((rows + 63) / 64) * ((cols + 63) / 64);
+  return (int)std::max<long long>(1, std::min<long long>(tiles, 152LL * 8));
+}
+
 cudaError_t launch_convert_tf32_t(const float* x, int rows, int cols, long long ldx, float* y, long long ldy,
                                   cudaStream_t s) {
-  const long long tiles = (long long)((rows + 31) / 32) * ((cols + 31) / 32);
-  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, 152LL * 16));
-  transpose_kernel<uint32_t, true><<<grid, dim3(32, 8, 1), 0, s>>>(reinterpret_cast<const uint32_t*>(x), rows, cols,
-                                                                    ldx, reinterpret_cast<uint32_t*>(y), ldy);
+  transpose64_kernel<kTransposeTf32><<<transpose64_grid(rows, cols), dim3(32, 8, 1), 0, s>>>(
+      reinterpret_cast<const uint32_t*>(x), rows, cols, ldx, reinterpret_cast<uint32_t*>(y), nullptr, ldy);
   count_launch();
   return cudaGetLastError();
 }
@@ -160,9 +164,9 @@ cudaError_t launch_split_tf32(const float* x, int rows, int cols, long long ldx,
 
 cudaError_t launch_split_tf32_t(const float* x, int rows, int cols, long long ldx, float* hi, float* lo,
                                long long ldy, cudaStream_t s) {
-  const long long tiles = (long long)((rows + 31) / 32) * ((cols + 31) / 32);
-  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, 152LL * 16));
-  split_tf32_t_kernel<<<grid, dim3(32, 8, 1), 0, s>>>(x, rows, cols, ldx, hi, lo, ldy);
+  transpose64_kernel<kTransposeSplitTf32><<<transpose64_grid(rows, cols), dim3(32, 8, 1), 0, s>>>(
+      reinterpret_cast<const uint32_t*>(x), rows, cols, ldx, reinterpret_cast<uint32_t*>(hi),
+      reinterpret_cast<uint32_t*>(lo), ldy);
   count_launch();
   return cudaGetLastError();
 }
@@ -197,8 +201,8 @@ cudaError_t launch_transpose(const void* x, int rows, int cols, long long ldx, v
     transpose_kernel<uint64_t><<<grid, block, 0, s>>>(static_cast<const uint64_t*>(x), rows, cols, ldx,
                                                        static_cast<uint64_t*>(y), ldy);
   else if (esize == 4)
-    transpose_kernel<uint32_t><<<grid, block, 0, s>>>(static_cast<const uint32_t*>(x), rows, cols, ldx,
-                                                       static_cast<uint32_t*>(y), ldy);
+    transpose64_kernel<kTransposeCopy><<<transpose64_grid(rows, cols), block, 0, s>>>(
+        static_cast<const uint32_t*>(x), rows, cols, ldx, static_cast<uint32_t*>(y), nullptr, ldy);
   else if (esize == 2)
     transpose_kernel<uint16_t><<<grid, block, 0, s>>>(static_cast<const uint16_t*>(x), rows, cols, ldx,
                                                        static_cast<uint16_t*>(y), ldy);

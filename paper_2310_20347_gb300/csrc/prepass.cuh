@@ -217,32 +217,6 @@ __global__ void split_tf32_kernel(const float* __restrict__ x, int rows, int col
   }
 }
 
-// The same split written transposed (hi, lo: cols x rows): B of the 3xTF32
-// mode, K-major, through a 32 x 33 shared tile (block (32, 8)).
-__global__ void split_tf32_t_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
-                                    float* __restrict__ hi, float* __restrict__ lo, long long ldy) {
-  __shared__ float tile[32][33];
-  const int tr = (rows + 31) / 32, tc = (cols + 31) / 32;
-  for (long long t = blockIdx.x; t < (long long)tr * tc; t += gridDim.x) {
-    const int r0 = (int)(t / tc) * 32, c0 = (int)(t % tc) * 32;
-    for (int i = threadIdx.y; i < 32; i += 8) {
-      const int r = r0 + i, c = c0 + threadIdx.x;
-      if (r < rows && c < cols) tile[i][threadIdx.x] = x[(long long)r * ldx + c];
-    }
-    __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += 8) {
-      const int c = c0 + i, r = r0 + threadIdx.x;   // output row c, column r
-      if (c < cols && r < rows) {
-        float h, l;
-        split_tf32(tile[threadIdx.x][i], h, l);
-        hi[(long long)c * ldy + r] = h;
-        lo[(long long)c * ldy + r] = l;
-      }
-    }
-    __syncthreads();
-  }
-}
-
 __global__ void convert_bf16_kernel(const float* __restrict__ x, int rows, int cols, long long ldx,
                                     uint16_t* __restrict__ y, long long ldy) {
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
@@ -331,7 +305,7 @@ __global__ void pack_rows_kernel(const uint8_t* __restrict__ x, int rows, long l
 // y (cols x rows, leading dimension ldy) := transpose of x (rows x cols,
 // leading dimension ldx), elements of type T, through a 32 x 33 shared tile so
 // that both the reads and the writes are coalesced.  Block (32, 8).
-template <typename T, bool ROUND_TF32 = false>
+template <typename T>
 __global__ void transpose_kernel(const T* __restrict__ x, int rows, int cols, long long ldx, T* __restrict__ y,
                                  long long ldy) {
   __shared__ T tile[32][33];
@@ -340,15 +314,63 @@ __global__ void transpose_kernel(const T* __restrict__ x, int rows, int cols, lo
     const int r0 = (int)(t / tc) * 32, c0 = (int)(t % tc) * 32;
     for (int i = threadIdx.y; i < 32; i += 8) {
       const int r = r0 + i, c = c0 + threadIdx.x;
-      if (r < rows && c < cols) {
-        if constexpr (ROUND_TF32) tile[i][threadIdx.x] = __float_as_uint(tf32_rne(__uint_as_float(x[(long long)r * ldx + c])));
-        else tile[i][threadIdx.x] = x[(long long)r * ldx + c];
-      }
+      if (r < rows && c < cols) tile[i][threadIdx.x] = x[(long long)r * ldx + c];
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += 8) {
       const int c = c0 + i, r = r0 + threadIdx.x;   // output row c, column r
       if (c < cols && r < rows) y[(long long)c * ldy + r] = tile[threadIdx.x][i];
+    }
+    __syncthreads();
+  }
+}
+
+// Transpose of 4-byte elements through 64 x 64 tiles (block (32, 8), 16
+// elements per thread each way): every warp access covers 256 consecutive
+// bytes of a row, twice the 32 x 32 tile's segments, which keeps DRAM pages
+// open longer on both the read and the write side.  OP maps one input value
+// to the output value(s): kTransposeCopy, kTransposeTf32 (round), or
+// kTransposeSplitTf32 (hi -> y, lo -> y2).
+enum TransposeOp : int { kTransposeCopy = 0, kTransposeTf32 = 1, kTransposeSplitTf32 = 2 };
+
+template <int OP>
+__global__ void __launch_bounds__(256) transpose64_kernel(const uint32_t* __restrict__ x, int rows, int cols,
+                                                          long long ldx, uint32_t* __restrict__ y,
+                                                          uint32_t* __restrict__ y2, long long ldy) {
+  __shared__ uint32_t tile[64][65];
+  const int tr = (rows + 63) / 64, tc = (cols + 63) / 64;
+  for (long long t = blockIdx.x; t < (long long)tr * tc; t += gridDim.x) {
+    const int r0 = (int)(t / tc) * 64, c0 = (int)(t % tc) * 64;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + threadIdx.y + 8 * i;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + h * 32 + threadIdx.x;
+        if (r < rows && c < cols) tile[threadIdx.y + 8 * i][h * 32 + threadIdx.x] = __ldcs(x + (long long)r * ldx + c);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = c0 + threadIdx.y + 8 * i;   // output row
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + h * 32 + threadIdx.x;   // output column
+        if (c < cols && r < rows) {
+          const uint32_t v = tile[h * 32 + threadIdx.x][threadIdx.y + 8 * i];
+          if constexpr (OP == kTransposeCopy) {
+            y[(long long)c * ldy + r] = v;
+          } else if constexpr (OP == kTransposeTf32) {
+            y[(long long)c * ldy + r] = __float_as_uint(tf32_rne(__uint_as_float(v)));
+          } else {
+            const float f = __uint_as_float(v);
+            const float hi = tf32_rne(f);
+            y[(long long)c * ldy + r] = __float_as_uint(hi);
+            y2[(long long)c * ldy + r] = __float_as_uint(tf32_rne(__fsub_rn(f, hi)));
+          }
+        }
+      }
     }
     __syncthreads();
   }
