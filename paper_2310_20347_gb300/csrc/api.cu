@@ -1087,7 +1087,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
                                     k1 - k0, cudaMemcpyHostToDevice, up));
     return G3_OK;
   };
-  auto block_args = [&](int b, int64_t r0, int64_t r1) {
+  auto block_args = [&](int64_t r0, int64_t r1) {
     g3_gemm_args blk = a;
     blk.m = r1 - r0;
     blk.A = dA + (size_t)r0 * lda_d * es;
@@ -1096,7 +1096,6 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
     blk.ldb = ldb_d;
     blk.C = dC + (size_t)r0 * ldc_d * ces;
     blk.ldc = ldc_d;
-    (void)b;
     return blk;
   };
   auto down_rows = [&](int b, int64_t r0, int64_t r1) -> int {
@@ -1126,7 +1125,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
       G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_slab[j], 0));
       G3_CHECK_CUDA(launch_split_bf16(reinterpret_cast<const float*>(dB + (size_t)k0 * ldb_d * es), (int)(k1 - k0),
                                       (int)n, ldb_d, Bhi + k0 * ldp, Blo + k0 * ldp, ldp, s));
-      g3_gemm_args blk = block_args(0, r0, r1);
+      g3_gemm_args blk = block_args(r0, r1);
       blk.k = k1 - k0;
       blk.A = dA + (size_t)r0 * lda_d * es + (size_t)k0 * es;
       blk.B = dB + (size_t)k0 * ldb_d * es;
@@ -1139,7 +1138,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
     for (int b = 1; b < nb; ++b) {
       if (!rows_of(b, &r0, &r1)) break;
       G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_up[b], 0));
-      if ((st = gemm_impl(block_args(b, r0, r1), s, &pb)) != G3_OK) return st;
+      if ((st = gemm_impl(block_args(r0, r1), s, &pb)) != G3_OK) return st;
       if ((st = down_rows(b, r0, r1)) != G3_OK) return st;
     }
   } else {
@@ -1151,7 +1150,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
       if ((st = up_rows(b)) != G3_OK) return st;
       G3_CHECK_CUDA(cudaEventRecord(ev_up[b], up));
       G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_up[b], 0));
-      if ((st = gemm_impl(block_args(b, r0, r1), s)) != G3_OK) return st;
+      if ((st = gemm_impl(block_args(r0, r1), s)) != G3_OK) return st;
       if ((st = down_rows(b, r0, r1)) != G3_OK) return st;
     }
   }

@@ -6,7 +6,7 @@ search that keeps the best member per problem shape (Section 8.4).  This
 script plays the generator's role for the GPU kernels: it enumerates the
 parameter space
 
-    mode     bf16 | f16 | tf32 | 3xbf16 | 6xbf16 | fp8 | int8emu   operand format of the MMA
+    mode     bf16 | f16 | tf32 | 3xbf16 | 6xbf16 | 3xtf32 | fp8 | int8emu   operand format of the MMA
     bm       64 | 128 | 256           output rows per tile = MMA N
     cg       1 | 2                    CTAs per MMA: one SM (tile bm x 128), or a
                                       CTA pair on two SMs (tile bm x 256, each CTA
