@@ -257,22 +257,19 @@ double kblock_clocks(const FamilyEntry& f) {
   return t;
 }
 
-// Fraction of the tensor peak a member sustains in its main loop.
-double tile_efficiency(const FamilyEntry& f) {
-  const int products = (f.mode == TC_3XBF16 || f.mode == TC_3XTF32) ? 3 : (f.mode == TC_6XBF16 ? 6 : 1);
-  const double mma = 4.0 * products * 73.0 * f.bm / 128.0;
-  return std::min(0.97, mma / kblock_clocks(f));
-}
-
-// Slow-down of a member whose single accumulator set makes the MMA wait for
-// each tile's epilogue: epilogue time over main-loop time of one tile (the
-// epilogue reads and writes its bm x 128 block of C at about 45 bytes per ns
-// per SM, plus ~2 us of TMEM and barrier latency).
-double single_buffer_factor(const FamilyEntry& f, int num_kb) {
-  if (f.bufs >= 2) return 1.0;
-  const double t_tile_ns = num_kb * kblock_clocks(f) / 1.9;
-  const double t_epi_ns = f.bm * 128.0 * 8.0 / 45.0 + 2000.0;
-  return 1.0 + t_epi_ns / std::max(t_tile_ns, 1.0);
+// Time one CTA (or pair) spends on one output tile, in ns: the main loop
+// (k-blocks at kblock_clocks, 1.9 GHz) and the epilogue, which writes the
+// CTA's bm x 128 block of C at about 22 bytes per ns per SM (the rate C leaves
+// at when every SM writes, ~3.4 TB/s in all) plus ~1.5 us of TMEM, barrier and
+// store latency (0.6 us more for a pair's cluster hand-offs) -- fitted to the
+// im2col layers, where tiles of 1 to 8 k-blocks spend longer in the epilogue
+// than in the main loop.  With two or more accumulator sets the epilogue of
+// one tile overlaps the main loop of the next, so the slower of the two sets
+// the pace; with one set they add up.
+double tile_time_ns(const FamilyEntry& f, int num_kb) {
+  const double t_main = num_kb * kblock_clocks(f) / 1.9;
+  const double t_epi = f.bm * 128.0 * 4.0 / 22.0 + 1500.0 + (f.cg > 1 ? 600.0 : 0.0);
+  return f.bufs >= 2 ? std::max(t_main, t_epi) : t_main + t_epi;
 }
 
 
@@ -341,9 +338,39 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   const int mode = tc_mode_of(dtype, k);
   const int bk = kblock_of(mode);
   pl.num_kb = (int)((k + bk - 1) / bk);
+  // Modelled time of a member with s splits of k: waves of tiles (the
+  // member's resident CTAs or pairs, as the device reports them, else the SM
+  // count over the cluster size) x the time of one tile of ceil(num_kb / s)
+  // k-blocks, plus, when split, the reduce kernel (a launch and s partial
+  // planes plus C through HBM at ~5 TB/s).
+  const bool search_split = force_split == 0 && allow_splitk;
+  auto cost_of = [&](const FamilyEntry& f, int s) {
+    const long long tiles = ((m + f.bm - 1) / f.bm) * ((n + 128LL * f.cg - 1) / (128LL * f.cg));
+    const int resident = f.slots ? f.slots(sms) : 0;
+    const long long slots = resident > 0 ? resident : std::max(1, sms / f.cg);
+    const long long waves = (tiles * s + slots - 1) / slots;
+    const int kb = (pl.num_kb + s - 1) / s;
+    double t = (double)waves * tile_time_ns(f, kb);
+    if (s > 1) t += 3000.0 + (double)(s + 1) * (double)m * (double)n * 4.0 / 5000.0;
+    return t;
+  };
+  auto splits_for = [&](const FamilyEntry& f, auto&& visit) {
+    visit(1);
+    if (!search_split) return;
+    const long long tiles = ((m + f.bm - 1) / f.bm) * ((n + 128LL * f.cg - 1) / (128LL * f.cg));
+    const long long slots = std::max(1, sms / f.cg);
+    for (int s : {2, 3, 4, 6, 8, 12, 16})   // pieces of at least two k-blocks, at most ~2 waves of them
+      if (2 * s <= pl.num_kb && tiles * s <= 2 * slots) visit(s);
+  };
+  int best_split = 1;
   if (force_member >= 0 && force_member < G3_FAMILY_SIZE && g_family[force_member].mode == mode &&
       g_family[force_member].launch) {
     pl.member = force_member;
+    double best = 1e300;
+    splits_for(g_family[force_member], [&](int s) {
+      const double c = cost_of(g_family[force_member], s);
+      if (c < best * 0.999) { best = c; best_split = s; }
+    });
   } else {
     double best = 1e300;
     for (int i = 0; i < G3_FAMILY_SIZE; ++i) {
@@ -351,16 +378,10 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
       if (!f.launch || f.mode != mode) continue;
       // first (deepest) variant per (bm, cg)
       if (pl.member >= 0 && g_family[pl.member].bm == f.bm && g_family[pl.member].cg == f.cg) continue;
-      const long long tiles = ((m + f.bm - 1) / f.bm) * ((n + 128LL * f.cg - 1) / (128LL * f.cg));
-      const long long slots = std::max(1, sms / f.cg);   // tiles in flight at once
-      const long long waves = (tiles + slots - 1) / slots;
-      // (pairs: 2% for the cluster set-up, so that ties go to the single CTA)
-      const double cost = (double)waves * f.bm / tile_efficiency(f) * single_buffer_factor(f, pl.num_kb) *
-                          (f.cg > 1 ? 1.02 : 1.0);
-      if (cost < best * 0.999) {
-        best = cost;
-        pl.member = i;
-      }
+      splits_for(f, [&](int s) {
+        const double c = cost_of(f, s);
+        if (c < best * 0.999) { best = c; pl.member = i; best_split = s; }
+      });
     }
   }
   if (pl.member < 0) return pl;
@@ -369,13 +390,10 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   pl.tiles_n = (int)((n + 128LL * cg - 1) / (128LL * cg));
   pl.tiles_m = (int)((m + bm - 1) / bm);
   const long long tiles = (long long)pl.tiles_m * pl.tiles_n;
+  (void)tiles;
   int splits = 1;
-  if (force_split > 0) {
-    splits = force_split;
-  } else if (force_split == 0 && tiles * 2 <= sms / cg && pl.num_kb >= 8) {
-    splits = (int)std::min<long long>(sms / cg / tiles, std::min(pl.num_kb / 4, 16));
-    splits = std::max(splits, 1);
-  }
+  if (force_split > 0) splits = force_split;
+  else if (force_split == 0) splits = best_split;
   if (!allow_splitk) splits = 1;
   // FP32-accurate modes: a bounded k per FP32 accumulator.  The tensor core
   // adds each k-step's products to its FP32 accumulator with truncation, so the

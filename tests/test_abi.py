@@ -145,6 +145,7 @@ def test_tuning_cache_overrides_planner(lib, tmp_path):
     L = lib
     assert L.g3_tune_cache_clear() == 0
     st, cfg0, sk0, _ = L.g3_plan_query(1000, 3000, 700, L.G3_BF16)
+    _, cfg1, sk1, _ = L.g3_plan_query(1000, 3000, 1500, L.G3_BF16)   # another k bucket
     other = next(f["index"] for f in fam if f["mode"] == "bf16" and f["index"] != cfg0)
     # bucket of (1000, 3000, 700) = (10, 12, 10); dtype G3_BF16 = 2
     path = tmp_path / "tune.txt"
@@ -154,7 +155,7 @@ def test_tuning_cache_overrides_planner(lib, tmp_path):
     assert (cfg, sk) == (other, 3)
     # another shape of the same bucket follows the record; another bucket does not
     assert L.g3_plan_query(600, 2100, 513, L.G3_BF16)[1:3] == (other, 3)
-    assert L.g3_plan_query(1000, 3000, 1500, L.G3_BF16)[1:3] == (cfg0, sk0)
+    assert L.g3_plan_query(1000, 3000, 1500, L.G3_BF16)[1:3] == (cfg1, sk1)
     out = tmp_path / "saved.txt"
     assert L.g3_tune_cache_save(str(out)) == 0
     assert f"2 10 12 10 {other} 3" in out.read_text()
