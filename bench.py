@@ -311,6 +311,45 @@ def run_workload(args):
             e["kernel"] = float(np.max(np.abs(got_rows - refq) / np.maximum(Dq, 1e-300)))
         return e
 
+    if args.workload == "plain":
+        # the plain method alone: FP32 SIMT C := A*B at m = n = k = 512 (uniform
+        # [-1, 1], seed 0, beta = 0), every element checked against the
+        # binary64 oracle; FFMA-bound, so the roofline is the FP32 CUDA-core rate
+        n = 512
+        p = synth.uniform_problem(n, n, n, seed=0)
+        A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+        C = torch.empty(n, n, dtype=torch.float32, device=dev)
+        fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_F32)
+        fn()
+        torch.cuda.synchronize()
+        got = C.cpu().numpy().astype(np.float64)
+        A64, B64 = p.A.astype(np.float64), p.B.astype(np.float64)
+        t0 = time.perf_counter()
+        ref = oracle.gemm(A64, B64, None, 1.0, 0.0)
+        cpu_s = time.perf_counter() - t0
+        err = float(np.max(np.abs(got - ref) / np.maximum(oracle.absprod(A64, B64, 1.0), 1e-300)))
+        for _ in range(args.warmup):
+            fn()
+        ms = _call_ms(fn, args.reps, flush)
+        kms = _kernel_ms(_lib, fn, args.reps, flush)
+        flops = 2.0 * n ** 3
+        _, _, splits, _ = _lib.g3_plan_query(n, n, n, G3_F32)
+        sm_mhz = 2070.0
+        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        _line(args, flops / ms / 1e9, "TFLOPS",
+              {"workload": "plain FP32 GEMM C := A*B, m=n=k=512, uniform [-1, 1], seed 0, beta=0",
+               "path": f"FP32 SIMT kernel (the plain method): 64 x 64 CTA tiles, 4 x 4 micro-tiles, k cut over a "
+                       f"cluster of {splits} CTAs summed through distributed shared memory",
+               "flush": "256 MB L2 flush before every call"},
+              {"dtype": "f32", "ms": ms, "kernel_ms": kms, "err": {"gate_all_elements": err},
+               "roofline": {"bound": "alu", "achieved": flops / kms / 1e9, "peak": fp32_peak, "unit": "TFLOP/s",
+                            "frac": flops / kms / 1e9 / fp32_peak, "traffic": None,
+                            "peak_source": "152 SMs x 128 FP32 FMA/clock x 2 x 2.07 GHz (maximum SM clock)",
+                            "algorithmic": "2 n^3 FP32 flops per call"},
+               "cpu_baseline": {"value": flops / cpu_s / 1e12, "unit": "TFLOPS", "cores": oracle.max_threads(),
+                                "kind": "oracle", "sample": f"the whole 512^3 product in binary64, {cpu_s:.3f} s"}})
+        return
+
     if args.workload == "streamk":
         # Stream-K tail (split_k = G3_SPLIT_STREAM_K) against the plain walk on
         # shapes whose tiles leave the last wave partly idle: whole calls (L2
@@ -796,7 +835,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "int16", "conv",
+                    choices=["square", "sweep", "plain", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "int16", "conv",
                              "grouped", "grouped-3xbf16"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

@@ -170,6 +170,12 @@ G3_API int g3_set_stream(void* cuda_stream);
  *                      autotuner record): measured on GB300 it seldom pays.
  *                      FP8 with device scales takes no split-K (a forced
  *                      split is ignored) but may take the stream-K tail.
+ *                      G3_F32 (the SIMT kernel): split_k >= 2 (at most 8
+ *                      used) cuts k over a thread-block cluster of that many
+ *                      CTAs per 64 x 64 block of C, the partial blocks summed
+ *                      through distributed shared memory in a fixed order (no
+ *                      workspace); 1 forbids it; 0 lets the planner take it
+ *                      when fewer 64 x 64 blocks than SMs would run.
  *   raster             0: the planner's choice; >= 1 the band width (in tiles)
  *                      of the tile walk.
  *   trans_a, trans_b   0: A is m x k (lda >= k), B is k x n (ldb >= n);
@@ -302,7 +308,8 @@ G3_API int g3_family_describe(int index, char* buf, size_t len);
 
 /* Which configuration the planner picks for a problem (index into the family,
  * split count -- G3_SPLIT_STREAM_K when it takes a stream-K tail --, raster
- * band); -1 in *config for the FP32 SIMT kernel.                           */
+ * band); -1 in *config for the CUDA-core kernels (G3_F32, G3_F64,
+ * G3_INT16), with *split_k the FP32 SIMT kernel's cluster split (1: none).  */
 G3_API int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* split_k, int* raster);
 
 /* --- Autotuner: the per-shape search of the paper's Section 8.4 -------------

@@ -608,7 +608,29 @@ int validate(const g3_gemm_args& a) {
   return G3_OK;
 }
 
-int run_simt(const g3_gemm_args& a, cudaStream_t s) {
+// The FP32 SIMT kernel's blocking for an m x n x k problem: kind 0 (128 x 128
+// blocks) while those fill the SMs; else kind 1 (64 x 64 blocks), with k cut
+// over a cluster of 2, 4 or 8 CTAs while the grid stays within two CTAs per SM
+// and every CTA keeps at least two k-blocks of 16.  split_k >= 2 (at most 8)
+// forces that cluster split; split_k == 1 forbids it.
+struct SimtPlan {
+  int kind, splits;
+};
+
+SimtPlan simt_plan(int64_t m, int64_t n, int64_t k, int sms, int split_k) {
+  const int64_t tiles128 = ((m + 127) / 128) * ((n + 127) / 128);
+  const int64_t tiles64 = ((m + 63) / 64) * ((n + 63) / 64);
+  const bool fits64 = (m + 63) / 64 <= 65535;
+  if (split_k >= 2 && fits64) return {1, (int)std::min<int64_t>(std::min(split_k, 8), std::max<int64_t>(k, 1))};
+  if (tiles128 >= sms || !fits64) return {0, 1};
+  if (tiles64 >= sms || split_k == 1) return {1, 1};
+  int s = 1;
+  for (int c = 2; c <= 8; c *= 2)
+    if (tiles64 * c <= 2LL * sms && (k + c - 1) / c >= 32) s = c;
+  return {1, s};
+}
+
+int run_simt(const g3_gemm_args& a, int sms, cudaStream_t s) {
   SimtParams p;
   p.m = (int)a.m;
   p.n = (int)a.n;
@@ -624,8 +646,9 @@ int run_simt(const g3_gemm_args& a, cudaStream_t s) {
   const bool vec = (reinterpret_cast<uintptr_t>(a.A) % 16 == 0) && (reinterpret_cast<uintptr_t>(a.B) % 16 == 0) &&
                    (reinterpret_cast<uintptr_t>(a.C) % 16 == 0) && a.lda % 4 == 0 && a.ldb % 4 == 0 &&
                    a.ldc % 4 == 0;
+  const SimtPlan sp = simt_plan(a.m, a.n, a.k, sms, a.split_k);
   TimedRegion tr(s);
-  G3_CHECK_CUDA(launch_simt(p, vec, s));
+  G3_CHECK_CUDA(launch_simt(p, vec, sp.kind, sp.splits, s));
   return G3_OK;
 }
 
@@ -944,7 +967,7 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s, const PreparedB* pb = nullptr) {
   // device scales apply in the kernel epilogue or the stream-K fix-up, which
   // the split-K reduce cannot: no split-K then
   if (a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b) && a.split_k > 1) a.split_k = 1;
-  if (a.dtype == G3_F32) return run_simt(a, s);
+  if (a.dtype == G3_F32) return run_simt(a, d->sms, s);
   if (a.dtype == G3_F64) return run_simt64(a, s);
   if (a.dtype == G3_INT16) return run_simt_i16(a, s);
   return run_tc(*d, a, s, nullptr, pb);
@@ -1422,17 +1445,17 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   if (n < 0) return -102;
   if (k < 0) return -103;
   if (dtype < G3_F32 || dtype > G3_INT16) return -104;
-  if (dtype == G3_F32 || dtype == G3_F64 || dtype == G3_INT16) {
-    if (config) *config = -1;
-    if (split_k) *split_k = 1;
-    if (raster) *raster = 0;
-    return G3_OK;
-  }
   std::lock_guard<std::mutex> lock(g_mu);
   DevState* d = nullptr;
   int sms = 152;
-  family_init();
   if (ensure_device(&d) == G3_OK) sms = d->sms;
+  if (dtype == G3_F32 || dtype == G3_F64 || dtype == G3_INT16) {
+    if (config) *config = -1;
+    if (split_k) *split_k = dtype == G3_F32 ? simt_plan(m, n, k, sms, 0).splits : 1;
+    if (raster) *raster = 0;
+    return G3_OK;
+  }
+  family_init();
   // (FP8 calls are assumed to carry device scales: no split-K)
   const Plan pl = make_plan(m, n, std::max<int64_t>(k, 1), dtype, sms, -1, 0, 0, dtype != G3_FP8_E4M3);
   if (config) *config = pl.member;

@@ -62,7 +62,7 @@ void register_grouped_3xtf32(GroupedEntry* table);
 
 // kernels.cu: launchers of the non-tensor-core kernels.  Each returns the
 // launch's cudaError_t; sizes are validated by the caller.
-cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s);
+cudaError_t launch_simt(const SimtParams& p, bool vec, int kind, int splits, cudaStream_t s);
 cudaError_t launch_simt64(const SimtParams64& p, bool vec, cudaStream_t s);
 cudaError_t launch_simt_i16(const SimtParamsI16& p, cudaStream_t s);
 // C := beta * C in binary64 (beta == 0 writes zeros without reading C).

@@ -20,10 +20,34 @@ static dim3 rows_grid(int rows, long long cols, int per_thread) {
   return dim3((unsigned)xblocks, (unsigned)yblocks, 1);
 }
 
-cudaError_t launch_simt(const SimtParams& p, bool vec, cudaStream_t s) {
-  dim3 grid((p.n + 127) / 128, (p.m + 127) / 128, 1);
-  if (vec) simt_sgemm_kernel<true><<<grid, 256, 0, s>>>(p);
-  else simt_sgemm_kernel<false><<<grid, 256, 0, s>>>(p);
+// kind 0: 128 x 128 blocks; kind 1: 64 x 64 blocks, cut along k over a
+// cluster of `splits` CTAs when splits > 1 (1 <= splits <= 8).
+cudaError_t launch_simt(const SimtParams& p, bool vec, int kind, int splits, cudaStream_t s) {
+  if (kind == 0) {
+    dim3 grid((p.n + 127) / 128, (p.m + 127) / 128, 1);
+    if (vec) simt_sgemm_kernel<true><<<grid, 256, 0, s>>>(p);
+    else simt_sgemm_kernel<false><<<grid, 256, 0, s>>>(p);
+  } else if (splits <= 1) {
+    dim3 grid((p.n + 63) / 64, (p.m + 63) / 64, 1);
+    if (vec) simt_sgemm64_kernel<true, false><<<grid, 256, 0, s>>>(p);
+    else simt_sgemm64_kernel<false, false><<<grid, 256, 0, s>>>(p);
+  } else {
+    if (splits > 8) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.n + 63) / 64, (p.m + 63) / 64, splits);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = splits;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = vec ? cudaLaunchKernelEx(&cfg, simt_sgemm64_kernel<true, true>, p)
+                              : cudaLaunchKernelEx(&cfg, simt_sgemm64_kernel<false, true>, p);
+    if (e != cudaSuccess) return e;
+  }
   count_launch();
   return cudaGetLastError();
 }

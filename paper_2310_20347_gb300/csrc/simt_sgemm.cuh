@@ -140,4 +140,204 @@ __global__ void __launch_bounds__(256, 2) simt_sgemm_kernel(const SimtParams p) 
   }
 }
 
+// Four floats at shared::cluster address `caddr` (16-byte aligned), which may
+// lie in another CTA of the cluster.
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t caddr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(caddr)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void simt_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Epilogue of one row of four: C = alpha * v + beta * C (C not read when
+// beta == 0), float4 when the row is 16-byte aligned and whole.
+template <bool VEC>
+__device__ __forceinline__ void store4_epilogue(const SimtParams& p, int row, int col, const float (&acc)[4]) {
+  if (row >= p.m) return;
+  float* crow = p.C + (long long)row * p.ldc;
+  float v[4];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) v[jj] = p.alpha * acc[jj];
+  if (VEC && col + 3 < p.n) {
+    float4* cp = reinterpret_cast<float4*>(crow + col);
+    if (p.beta != 0.f) {
+      const float4 o = *cp;
+      v[0] = fmaf(p.beta, o.x, v[0]);
+      v[1] = fmaf(p.beta, o.y, v[1]);
+      v[2] = fmaf(p.beta, o.z, v[2]);
+      v[3] = fmaf(p.beta, o.w, v[3]);
+    }
+    *cp = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj)
+      if (col + jj < p.n) crow[col + jj] = (p.beta != 0.f) ? fmaf(p.beta, crow[col + jj], v[jj]) : v[jj];
+  }
+}
+
+// Asynchronous copies global -> shared (cp.async): `bytes` of 4 or 16, of
+// which the first `src_bytes` are read and the rest zero-filled (src_bytes 0
+// reads nothing).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The same method on 64 x 64 blocks of C with a 4 x 4 micro-tile per thread
+// and k-blocks of 16, for problems whose 128 x 128 grid would leave SMs idle
+// (four times the CTAs).  Thread (tx, ty) owns rows 4ty..4ty+3 and columns
+// 4tx..4tx+3.
+//
+// Small problems run few k-blocks per CTA, so the copies run STAGES - 1
+// k-blocks ahead of the arithmetic through a ring of shared-memory stages
+// filled by cp.async in 16-byte pieces (zero-filled past the edges), which
+// hides the DRAM latency that one block of register prefetch cannot.  A stays
+// row-major in shared memory; per four k a thread reads four 4-vectors of A
+// (its rows) and four of B, i.e. 64 FFMAs per 8 vector loads.
+//
+// SPLIT: the grid's z dimension is one thread-block cluster of S = gridDim.z
+// CTAs per block of C, CTA z taking the k-range [z kc, (z+1) kc) with kc =
+// ceil(k / S) rounded up to 16 (the loop pc of Section 4.1 shared out over
+// the cluster).  Each CTA leaves its 64 x 64 partial block in shared memory;
+// after a cluster barrier CTA z sums rows [64 z / S, 64 (z+1) / S) of the S
+// partials through distributed shared memory, always in the order 0..S-1
+// (deterministic), applies alpha and beta and stores them.  A second cluster
+// barrier keeps every partial readable until all sums are taken.
+template <bool VEC, bool SPLIT>
+__global__ void __launch_bounds__(256, SPLIT ? 3 : 4) simt_sgemm64_kernel(const SimtParams p) {
+  constexpr int BM = 64, BN = 64, BK = 16, APAD = 4, STAGES = 4;
+  constexpr int LDA_S = BK + APAD;   // 20 floats: rows 4 apart fall 16 banks apart
+  constexpr int A_STAGE = BM * LDA_S, B_STAGE = BK * BN;
+  static_assert(BM * BN <= STAGES * (A_STAGE + B_STAGE), "the partial block reuses the stage ring");
+  __shared__ __align__(16) float smem[STAGES * (A_STAGE + B_STAGE)];
+  float* const As = smem;                     // [STAGES][BM][LDA_S], row-major
+  float* const Bs = smem + STAGES * A_STAGE;  // [STAGES][BK][BN]
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int a_row = tid >> 2, a_col = (tid & 3) * 4;   // A: 64 rows x 16 k
+  const int b_row = tid >> 4, b_col = (tid & 15) * 4;  // B: 16 k x 64 cols
+  int kbeg = 0, kend = p.k;
+  if (SPLIT) {
+    const int kc = ((p.k + (int)gridDim.z - 1) / (int)gridDim.z + BK - 1) / BK * BK;
+    kbeg = min(p.k, (int)blockIdx.z * kc);
+    kend = min(p.k, kbeg + kc);
+  }
+  const int nkb = (kend - kbeg + BK - 1) / BK;
+
+  // copies of k-block kb into stage st (zero outside m x [kbeg, kend) x n)
+  const bool a_in = m0 + a_row < p.m;
+  const float* const a_src = p.A + (a_in ? (long long)(m0 + a_row) * p.lda : 0);
+  auto issue = [&](int kb, int st) {
+    const int k0 = kbeg + kb * BK;
+    float* as = As + st * A_STAGE + a_row * LDA_S + a_col;
+    const int ka = k0 + a_col;
+    const int a_left = a_in ? kend - ka : 0;   // valid elements from ka on
+    const int kr = k0 + b_row, col = n0 + b_col;
+    float* bs = Bs + st * B_STAGE + b_row * BN + b_col;
+    const float* b_src = p.B + (long long)kr * p.ldb + col;
+    const int b_left = kr < kend ? p.n - col : 0;
+    if (VEC) {
+      cp_async16(as, a_left > 0 ? a_src + ka : p.A, 4 * max(0, min(4, a_left)));
+      cp_async16(bs, b_left > 0 ? b_src : p.B, 4 * max(0, min(4, b_left)));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        cp_async4(as + j, j < a_left ? a_src + ka + j : p.A, j < a_left ? 4 : 0);
+        cp_async4(bs + j, j < b_left ? b_src + j : p.B, j < b_left ? 4 : 0);
+      }
+    }
+  };
+
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+#pragma unroll
+  for (int st = 0; st < STAGES - 1; ++st) {
+    if (st < nkb) issue(st, st);
+    cp_async_commit();
+  }
+  for (int kb = 0; kb < nkb; ++kb) {
+    cp_async_wait<STAGES - 2>();
+    __syncthreads();   // stage kb landed for every thread; stage kb - 1 is free
+    if (kb + STAGES - 1 < nkb) issue(kb + STAGES - 1, (kb + STAGES - 1) % STAGES);
+    cp_async_commit();
+    const float* as = As + (kb % STAGES) * A_STAGE + ty * 4 * LDA_S;
+    const float* bs = Bs + (kb % STAGES) * B_STAGE + tx * 4;
+#pragma unroll
+    for (int k4 = 0; k4 < BK; k4 += 4) {
+      float a[4][4];   // a[i][u]: row 4ty + i, k = k4 + u
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = *reinterpret_cast<const float4*>(as + i * LDA_S + k4);
+        a[i][0] = v.x;
+        a[i][1] = v.y;
+        a[i][2] = v.z;
+        a[i][3] = v.w;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 b4 = *reinterpret_cast<const float4*>(bs + (k4 + u) * BN);
+        const float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i][u], b[j], acc[i][j]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+
+  if constexpr (!SPLIT) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) store4_epilogue<VEC>(p, m0 + ty * 4 + i, n0 + tx * 4, acc[i]);
+  } else {
+    __syncthreads();   // every thread is done with the stage ring
+    float* const part = smem;   // [BM][BN]
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float4*>(part + (ty * 4 + i) * BN + tx * 4) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    simt_cluster_sync();
+    const int S = (int)gridDim.z, z = (int)blockIdx.z;
+    const int r0 = z * BM / S, r1 = (z + 1) * BM / S;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(part);
+    for (int idx = tid; idx < (r1 - r0) * (BN / 4); idx += 256) {
+      const int r = r0 + idx / (BN / 4), c = (idx % (BN / 4)) * 4;
+      const uint32_t off = base + (uint32_t)((r * BN + c) * 4);
+      float sum[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q < S; ++q) {
+        uint32_t caddr;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(caddr) : "r"(off), "r"(q));
+        const float4 v = ld_cluster_f4(caddr);
+        sum[0] += v.x;
+        sum[1] += v.y;
+        sum[2] += v.z;
+        sum[3] += v.w;
+      }
+      store4_epilogue<VEC>(p, m0 + r, n0 + c, sum);
+    }
+    simt_cluster_sync();
+  }
+}
+
 }  // namespace g3

@@ -137,6 +137,15 @@ def test_planner_choices(lib):
         assert st == 0 and fam[cfg]["mode"] == mode, (k, fam[cfg])
     st, cfg, sk, rs = L.g3_plan_query(128, 128, 100, L.G3_F32)
     assert cfg == -1
+    # FP32 SIMT: cluster split of k only while 64 x 64 blocks leave SMs idle,
+    # within two CTAs per SM and two k-blocks of 16 per CTA (152 SMs assumed
+    # without a GPU)
+    import torch
+    if not torch.cuda.is_available():
+        for (m, n, k), want in (((512, 512, 512), 4), ((128, 128, 100), 2), ((128, 128, 40), 1),
+                                ((256, 256, 4096), 8), ((1024, 1024, 1024), 1), ((4096, 4096, 64), 1)):
+            st, cfg, sk, rs = L.g3_plan_query(m, n, k, L.G3_F32)
+            assert st == 0 and cfg == -1 and sk == want, (m, n, k, sk)
 
 
 def test_tuning_cache_overrides_planner(lib, tmp_path):

@@ -93,3 +93,90 @@ def test_deterministic():
     a = run(p)
     b = run(p)
     assert np.array_equal(a, b)
+
+
+def test_large_grid_ragged():
+    # enough 128 x 128 blocks to fill every SM (the 128 x 128 kernel), ragged
+    # in m, n and k
+    p = synth.uniform_problem(1667, 1500, 301, seed=8, alpha=0.75, beta=-0.5)
+    check(p)
+
+
+def test_tile_size_switch_bit_identical():
+    # Both block sizes accumulate each element's products in k order with one
+    # FMA each, so a problem just above the SM-count threshold (128 x 128
+    # blocks) and its column slice just below it (64 x 64 blocks) agree
+    # bit for bit on the shared columns.
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rows_blocks = 8
+    cols_blocks = -(-sms // rows_blocks)          # rows_blocks * cols_blocks >= sms
+    m, k = rows_blocks * 128, 200
+    n_big = cols_blocks * 128
+    n_small = (cols_blocks - 1) * 128 - 3         # fewer blocks than SMs, ragged
+    assert rows_blocks * (-(-n_small // 128)) < sms <= rows_blocks * cols_blocks
+    p = synth.uniform_problem(m, n_big, k, seed=9)
+    A, B = dev(p.A), dev(p.B)
+    C_big = torch.empty(m, n_big, device="cuda")
+    torch_api.gemm(A, B, C_big, 1.0, 0.0, dtype=G3_F32)
+    Bs = B[:, :n_small].contiguous()
+    C_small = torch.empty(m, n_small, device="cuda")
+    torch_api.gemm(A, Bs, C_small, 1.0, 0.0, dtype=G3_F32)
+    torch.cuda.synchronize()
+    assert torch.equal(C_big[:, :n_small], C_small)
+    ref = oracle.gemm(p.A, p.B[:, :n_small], None, 1.0, 0.0)
+    D = oracle.absprod(p.A, p.B[:, :n_small], 1.0)
+    assert rel_err(C_small.cpu().numpy(), ref, D, None) <= TOL
+
+
+@pytest.mark.parametrize("splits", [2, 3, 4, 5, 8])
+def test_cluster_split_k(splits):
+    # k cut over a cluster of `splits` CTAs per 64 x 64 block (forced), ragged
+    # m, n and k, beta != 0 with C, unaligned leading dimension of A
+    for (m, n, k) in ((70, 130, 301), (64, 64, 16 * splits), (200, 33, 1000)):
+        p = synth.uniform_problem(m, n, k, seed=splits * 7 + k, alpha=-0.75, beta=0.5)
+        A, B = dev(p.A), dev(p.B)
+        full, C = guarded(p.m, p.n, p.C)
+        torch_api.gemm(A, B, C, p.alpha, p.beta, dtype=G3_F32, split_k=splits)
+        torch.cuda.synchronize()
+        check_guard(full, p.m, p.n)
+        ref = oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta)
+        D = oracle.absprod(p.A, p.B, p.alpha)
+        assert rel_err(C.cpu().numpy(), ref, D, p.beta * p.C.astype(np.float64)) <= TOL
+    p = synth.uniform_problem(131, 67, 301, seed=4, alpha=1.5, beta=-1.0)
+    A = torch.zeros(p.m, p.k + 1, device="cuda")[:, :p.k].copy_(dev(p.A))
+    full, C = guarded(p.m, p.n, p.C)
+    torch_api.gemm(A, dev(p.B), C, p.alpha, p.beta, dtype=G3_F32, split_k=splits)
+    torch.cuda.synchronize()
+    ref = oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta)
+    assert rel_err(C.cpu().numpy(), ref, oracle.absprod(p.A, p.B, p.alpha),
+                   p.beta * p.C.astype(np.float64)) <= TOL
+
+
+def test_cluster_split_more_ctas_than_k_blocks():
+    # k = 20 over 8 CTAs: two CTAs hold k-blocks, six hold empty ranges and
+    # contribute zero partials
+    p = synth.uniform_problem(90, 70, 20, seed=11, beta=0.25)
+    A, B = dev(p.A), dev(p.B)
+    full, C = guarded(p.m, p.n, p.C)
+    torch_api.gemm(A, B, C, 1.0, 0.25, dtype=G3_F32, split_k=8)
+    torch.cuda.synchronize()
+    check_guard(full, p.m, p.n)
+    ref = oracle.gemm(p.A, p.B, p.C, 1.0, 0.25)
+    assert rel_err(C.cpu().numpy(), ref, oracle.absprod(p.A, p.B, 1.0), 0.25 * p.C.astype(np.float64)) <= TOL
+
+
+def test_cluster_split_deterministic_and_planned():
+    # the 512^3 problem takes the planner's cluster split; repeated calls are
+    # bit-identical (partials summed in a fixed order)
+    from paper_2310_20347_gb300 import _lib
+    st, cfg, sk, rs = _lib.g3_plan_query(512, 512, 512, G3_F32)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert sk > 1 and 64 * sk <= 2 * sms
+    p = synth.uniform_problem(512, 512, 512, seed=0)
+    a = run(p)
+    b = run(p)
+    assert np.array_equal(a, b)
+    C = torch.empty(512, 512, device="cuda")
+    torch_api.gemm(dev(p.A), dev(p.B), C, 1.0, 0.0, dtype=G3_F32, split_k=sk)
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy(), a)
