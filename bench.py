@@ -177,6 +177,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Dense tensor peaks of GB300 from NVIDIA's datasheet (per GPU, no sparsity),
+# reported beside the measured-peak fractions.
+NOMINAL_TFLOPS = {"bf16": 2250.0, "fp8": 4500.0, "tf32": 1125.0}
+
 # Sources of the headline kernel (its device code and launcher).  A
 # DRAM-traffic record taken with ncu is reported as the roofline's "traffic"
 # only while these files hash to the recorded value and the member and size
@@ -679,6 +683,8 @@ def run_workload(args):
                                 "fp8": " x 2 (fp8 nominal ratio)",
                                 "tf32": " x 0.5 (tf32 nominal ratio)",
                                 "3xtf32": " x 0.5 (tf32 nominal ratio)"}.get(args.workload, ""),
+                            "frac_of_nominal": tensor_flops / kms / 1e9 / NOMINAL_TFLOPS[
+                                {"fp8": "fp8", "tf32": "tf32", "3xtf32": "tf32"}.get(args.workload, "bf16")],
                             "algorithmic": "2 n^3 per call (INT8: of the main kernel's bf16 work; "
                                            "3xTF32: 3 x 2 n^3 tf32 tensor flops)"}})
         return
@@ -991,6 +997,8 @@ def main():
                      "kernel": f"tc_gemm_kernel ({member})",
                      "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json)",
                      "frac_of_sustained": achieved / float(peaks.get("bf16_tflops_sustained", peak)),
+                     "frac_of_nominal": achieved / NOMINAL_TFLOPS["bf16"],
+                     "nominal_peak": NOMINAL_TFLOPS["bf16"],
                      "per_launch_ms": per_launch_ms, "launches_timed": kern_n,
                      "algorithmic": "6 n^3 bf16 tensor flops per launch"},
         "e2e": {"value": e2e_val, "unit": "TFLOPS", "h2d_bytes_per_step": 3 * n * n * 4,
