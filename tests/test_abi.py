@@ -205,3 +205,17 @@ def test_planner_invariants_over_random_shapes(lib):
             assert rs >= 1
         for dt in (L.G3_F32, L.G3_F64, L.G3_INT16):
             assert L.g3_plan_query(m, n, k, dt)[1] == -1
+        # FP32 SIMT: a cluster split of k (2, 4 or 8 CTAs) only while 64 x 64
+        # blocks leave SMs idle, within two CTAs per SM and two k-blocks of 16
+        # per CTA (152 SMs without a GPU); FP64 / INT16 never split
+        import torch
+        if not torch.cuda.is_available():
+            sk = L.g3_plan_query(m, n, k, L.G3_F32)[2]
+            tiles64 = -(-m // 64) * -(-n // 64)
+            assert sk in (1, 2, 4, 8), sk
+            if sk > 1:
+                assert tiles64 < 152 and tiles64 * sk <= 304 and -(-k // sk) >= 32, (m, n, k, sk)
+            elif tiles64 < 152 and -(-m // 128) * -(-n // 128) < 152:
+                assert tiles64 * 2 > 304 or -(-k // 2) < 32, (m, n, k)
+            assert L.g3_plan_query(m, n, k, L.G3_F64)[2] == 1
+            assert L.g3_plan_query(m, n, k, L.G3_INT16)[2] == 1
