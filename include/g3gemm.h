@@ -320,7 +320,9 @@ G3_API int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config
  * and ceil(log2) of each of m, n, k.  Later g3_gemm calls in that bucket use
  * the record instead of the planner's model.  Synchronous; allocates.
  * Outputs (any may be NULL): the member index, the split count, its time in
- * ms.  G3_F32 has a single kernel: *best_config = -1.
+ * ms.  The CUDA-core dtypes (G3_F32, G3_F64, G3_INT16) are not timed:
+ * *best_config = -1, *best_split = the planner's choice (for G3_F32 the SIMT
+ * kernel's cluster split, as g3_plan_query reports), *best_ms = 0.
  * g3_tune_cache_save / load write and read the records as text ("dtype
  * log2(m) log2(n) log2(k) member split ms" per line); the environment variable
  * G3_TUNE_CACHE names a file loaded on first planning.  clear forgets all.   */

@@ -1507,9 +1507,15 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   if (k <= 0) return -103;
   if (dtype < G3_F32 || dtype > G3_INT16) return -104;
   if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || (dtype == G3_INT8 && k > 131072)) return G3_ERR_UNSUPPORTED;
-  if (dtype == G3_F32 || dtype == G3_F64 || dtype == G3_INT16) {   // one kernel: nothing to choose
+  if (dtype == G3_F32 || dtype == G3_F64 || dtype == G3_INT16) {   // not timed: the planner's choice
+    int sms = 152;
+    {
+      std::lock_guard<std::mutex> lock(g_mu);
+      DevState* d = nullptr;
+      if (ensure_device(&d) == G3_OK) sms = d->sms;
+    }
     if (best_config) *best_config = -1;
-    if (best_split) *best_split = 1;
+    if (best_split) *best_split = dtype == G3_F32 ? simt_plan(m, n, k, sms, 0).splits : 1;
     if (best_ms) *best_ms = 0.0;
     return G3_OK;
   }

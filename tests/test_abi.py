@@ -146,6 +146,10 @@ def test_planner_choices(lib):
                                 ((256, 256, 4096), 8), ((1024, 1024, 1024), 1), ((4096, 4096, 64), 1)):
             st, cfg, sk, rs = L.g3_plan_query(m, n, k, L.G3_F32)
             assert st == 0 and cfg == -1 and sk == want, (m, n, k, sk)
+            # the autotuner does not time the CUDA-core kernels: it reports
+            # the planner's choice
+            assert L.g3_autotune(m, n, k, L.G3_F32) == (0, -1, want, 0.0)
+            assert L.g3_autotune(m, n, k, L.G3_F64) == (0, -1, 1, 0.0)
 
 
 def test_tuning_cache_overrides_planner(lib, tmp_path):
