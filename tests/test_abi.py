@@ -223,3 +223,31 @@ def test_planner_invariants_over_random_shapes(lib):
                 assert tiles64 * 2 > 304 or -(-k // 2) < 32, (m, n, k)
             assert L.g3_plan_query(m, n, k, L.G3_F64)[2] == 1
             assert L.g3_plan_query(m, n, k, L.G3_INT16)[2] == 1
+
+
+def test_planner_thread_safe(lib):
+    # host threads planning at once (ctypes drops the GIL around each call)
+    # get the answers a single thread gets
+    import threading
+
+    import numpy as np
+    L = lib
+    rng = np.random.default_rng(7)
+    dts = (L.G3_F32, L.G3_BF16, L.G3_F32_3XBF16, L.G3_INT8, L.G3_FP8_E4M3, L.G3_F32_3XTF32)
+    queries = [(int(m), int(n), int(k), int(dts[i % len(dts)]))
+               for i, (m, n, k) in enumerate(np.exp(rng.uniform(0, np.log(30000), (400, 3))).astype(int) + 1)]
+    want = [L.g3_plan_query(*q) for q in queries]
+    errors = []
+
+    def worker(t):
+        for i in range(len(queries)):
+            j = (i * 7 + t) % len(queries)
+            if L.g3_plan_query(*queries[j]) != want[j]:
+                errors.append(queries[j])
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(8)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors[:5]
