@@ -64,7 +64,14 @@ def gemm_args(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, scale_a=None, scale_b=
 
 
 def gemm(A, B, C, alpha=1.0, beta=0.0, dtype=G3_F32, stream=None, **kw):
-    """C := beta*C + alpha*A@B in place through g3_gemm_ex; returns C."""
+    """C := beta*C + alpha*A@B in place through g3_gemm_ex; returns C.
+
+    Keyword options (the g3_gemm_args fields): scale_a / scale_b (one-element
+    float32 device tensors, FP8), config (a family member, -1 = planner),
+    split_k (0 = planner; >= 1 forced; G3_SPLIT_STREAM_K; for G3_F32 the size
+    of the thread-block cluster that shares out k), raster, workspace (a
+    caller-owned uint8 device tensor), trans_a / trans_b (A given as k x m,
+    B as n x k)."""
     a = gemm_args(A, B, C, alpha, beta, dtype, **kw)
     check(_lib.g3_gemm_ex(a, _stream(stream)), "g3_gemm_ex")
     return C
