@@ -80,7 +80,10 @@ extern "C" {
  *                  binary64.  Single GEMMs only.
  *   G3_INT16       A, B int16; C int64; alpha must be 1 and beta 0 or 1;
  *                  exact (products widened to 64 bits on the CUDA cores).
- *                  Single GEMMs only.                                      */
+ *                  Single GEMMs only.
+ * The CUDA-core dtypes (G3_F32, G3_F64, G3_INT16) take m up to 65535 row
+ * blocks (8 388 480 rows for G3_F32, 4 194 240 for the others) when they
+ * compute a product; beyond that a call returns G3_ERR_UNSUPPORTED.        */
 typedef enum {
   G3_F32 = 0,
   G3_F32_3XBF16 = 1,

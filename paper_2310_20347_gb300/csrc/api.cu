@@ -605,6 +605,13 @@ int validate(const g3_gemm_args& a) {
     if (a.alpha != 1.0 && a.k > 0) return G3_ERR_UNSUPPORTED;
     if (a.beta != 0.0 && a.beta != 1.0) return G3_ERR_UNSUPPORTED;
   }
+  // the CUDA-core kernels put row blocks on grid.y: at most 65535 blocks of
+  // 128 rows for FP32, of 64 rows for FP64 and INT16 (C := beta*C alone,
+  // k == 0 or alpha == 0, has no such limit)
+  if (a.k > 0 && a.alpha != 0.0) {
+    if (a.dtype == G3_F32 && (a.m + 127) / 128 > 65535) return G3_ERR_UNSUPPORTED;
+    if ((a.dtype == G3_F64 || a.dtype == G3_INT16) && (a.m + 63) / 64 > 65535) return G3_ERR_UNSUPPORTED;
+  }
   return G3_OK;
 }
 

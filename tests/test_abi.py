@@ -61,6 +61,16 @@ def test_argument_errors(lib):
     assert L.g3_gemm_workspace_size(a)[0] == -108
     a.ldb, a.trans_b = 8, 2
     assert L.g3_gemm_workspace_size(a)[0] == -120
+    # CUDA-core dtypes: row blocks on grid.y, at most 65535 of them
+    a = L.g3_gemm_args_init()
+    a.n, a.k, a.A, a.B, a.C, a.alpha, a.lda, a.ldb, a.ldc = 4, 8, p, p, p, 1.0, 8, 4, 4
+    for dt, rows in ((L.G3_F32, 128), (L.G3_F64, 64), (L.G3_INT16, 64)):
+        a.dtype = dt
+        a.m = 65536 * rows
+        assert L.g3_gemm_workspace_size(a)[0] == L.G3_ERR_UNSUPPORTED, dt
+        a.k = 0                # C := beta*C alone has no such limit
+        assert L.g3_gemm_workspace_size(a)[0] == 0, dt
+        a.k = 8
     # host-buffer entry point: the same validation, nothing touches a device
     assert L.g3_gemm_host(-1, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, 0, None) == -101
     assert L.g3_gemm_host(4, 4, 8, 1.0, p, 7, p, 4, 0.0, p, 4, 0, None) == -106
