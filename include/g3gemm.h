@@ -338,6 +338,13 @@ G3_API int g3_tune_cache_clear(void);
 /* Kernel launches issued by the library since the process started.         */
 G3_API uint64_t g3_launch_count(void);
 
+/* Device allocations (cudaMalloc calls that succeeded) the library has made
+ * since the process started, on all devices: workspace growth, transpose and
+ * host-entry buffers, grouped plans and the autotuner's scratch operands.
+ * Lets a caller (or a test) confirm that a sequence of calls allocated
+ * nothing, e.g. g3_gemm_3xbf16_noalloc.                                      */
+G3_API int64_t g3_debug_device_allocations(void);
+
 /* When enabled, the library brackets its main GEMM kernel launch with CUDA
  * events on the launching stream; g3_kernel_time_ms returns (after
  * synchronising) the summed device time of those kernels since the last
@@ -365,11 +372,15 @@ G3_API int g3_debug_withhold_next(int64_t timeout_ms);
  * without split-K, on `cuda_stream` (NULL = the current stream).  The hi/lo
  * bfloat16 copies of A and B are kept in a 64 MiB array built into the library
  * instead of allocated workspace; the call issues no cudaMalloc, cudaFree or
- * other allocating routine.  Limit: 4 * (m * ceil8(k) + k * ceil8(n)) bytes
- * plus alignment must fit in 64 MiB (e.g. m = n = k = 2800), and k <= 32768
- * (beyond it g3_gemm splits k to keep the FP32 accumulation within 2e-6,
- * which needs workspace); other problems return G3_ERR_UNSUPPORTED before
- * anything is launched.
+ * other allocating routine.  Limit: the bfloat16 planes of A and B, each
+ * plane rounded up to 256 bytes, must fit in 64 MiB; that is
+ *   4 * (m * ceil8(k) + k * ceil8(n)) bytes for k > 512 (hi and lo planes,
+ *       e.g. m = n = k = 2800), and
+ *   6 * (m * ceil8(k) + k * ceil8(n)) bytes for k <= 512 (the three-part
+ *       split the FP32-accurate mode takes there: hi, mid and lo planes),
+ * and k <= 32768 (beyond it g3_gemm splits k to keep the FP32 accumulation
+ * within 2e-6, which needs workspace); other problems return
+ * G3_ERR_UNSUPPORTED before anything is launched.
  *
  * - The first call on a device looks up that device's copy of the array; make
  *   that first call before any stream capture.

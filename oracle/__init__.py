@@ -292,11 +292,18 @@ def split_bf16(x):
     return hi, lo
 
 
+_E4M3_TABLE = None
+
+
 def e4m3_decode(codes):
-    lib = _load()
+    """Values of E4M3 codes: each of the 256 codes is decoded once by the C
+    definition (oracle_e4m3_decode) and the codes are looked up in that table."""
+    global _E4M3_TABLE
+    if _E4M3_TABLE is None:
+        lib = _load()
+        _E4M3_TABLE = np.array([lib.oracle_e4m3_decode(c) for c in range(256)], np.float32)
     codes = _c(codes, np.uint8)
-    return np.array([lib.oracle_e4m3_decode(int(c)) for c in codes.ravel()],
-                    np.float32).reshape(codes.shape)
+    return _E4M3_TABLE[codes]
 
 
 def e4m3_encode(x):

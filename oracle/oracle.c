@@ -195,8 +195,8 @@ void oracle_conv2d_nhwc_f64(int64_t N, int64_t H, int64_t W, int64_t C, int64_t 
                             const double* y_in, double* y_out, int nthreads) {
     const int64_t P = (H + 2 * pad_h - dil_h * (R - 1) - 1) / str_h + 1;
     const int64_t Q = (W + 2 * pad_w - dil_w * (S - 1) - 1) / str_w + 1;
-    if (nthreads <= 0) nthreads = omp_get_max_threads();
-#pragma omp parallel for num_threads(nthreads) collapse(2) schedule(dynamic)
+    const int nt = threads_for(nthreads);
+#pragma omp parallel for num_threads(nt) collapse(2) schedule(dynamic)
     for (int64_t n = 0; n < N; ++n) {
         for (int64_t p = 0; p < P; ++p) {
             for (int64_t q = 0; q < Q; ++q) {

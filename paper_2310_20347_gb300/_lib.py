@@ -29,7 +29,7 @@ EXPORTED = (
     "g3_convert_bf16", "g3_convert_tf32", "g3_split_bf16", "g3_split3_bf16", "g3_split_tf32", "g3_quantize_fp8",
     "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
-    "g3_plan_query", "g3_launch_count", "g3_kernel_timing", "g3_kernel_time_ms",
+    "g3_plan_query", "g3_launch_count", "g3_debug_device_allocations", "g3_kernel_timing", "g3_kernel_time_ms",
     "g3_debug_withhold_next", "g3_gemm_3xbf16_noalloc",
     "g3_autotune", "g3_tune_cache_save", "g3_tune_cache_load", "g3_tune_cache_clear",
 )
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
             "g3_plan_query": ([i64, i64, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                ctypes.POINTER(i32)], i32),
             "g3_launch_count": ([], ctypes.c_uint64),
+            "g3_debug_device_allocations": ([], ctypes.c_int64),
             "g3_kernel_timing": ([i32], i32),
             "g3_kernel_time_ms": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
             "g3_debug_withhold_next": ([i64], i32),
@@ -232,6 +233,10 @@ def g3_plan_query(m, n, k, dtype):
 
 def g3_launch_count() -> int:
     return int(load().g3_launch_count())
+
+
+def g3_debug_device_allocations() -> int:
+    return int(load().g3_debug_device_allocations())
 
 
 def g3_kernel_timing(enable: bool) -> int:

@@ -2,6 +2,7 @@
 // (per-shape choice of a member of the generated kernel family, split-K and
 // raster), library workspace, TMA descriptor encoding and dispatch.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -19,6 +20,16 @@ namespace g3 {
 
 __device__ int g_device_status;   // first watchdog code raised since the last query
 uint64_t launch_count();
+
+namespace {
+std::atomic<long long> g_device_allocs{0};
+}
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_device_allocs.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
 
 namespace {
 
@@ -540,7 +551,7 @@ int get_workspace(DevState& d, const g3_gemm_args& a, size_t need, uint8_t** out
       d.ws_bytes = 0;
     }
     const size_t sz = std::max<size_t>(round_up((int64_t)need, 64 << 20), 64 << 20);
-    if (cudaMalloc(&d.ws, sz) != cudaSuccess) {
+    if (device_alloc(&d.ws, sz) != cudaSuccess) {
       cudaGetLastError();
       d.ws = nullptr;
       return G3_ERR_NOMEM;
@@ -930,7 +941,7 @@ int untranspose(DevState& d, g3_gemm_args& a, cudaStream_t s) {
       d.tbuf = nullptr;
       d.tbuf_bytes = 0;
     }
-    if (cudaMalloc(&d.tbuf, a_bytes + b_bytes) != cudaSuccess) {
+    if (device_alloc(&d.tbuf, a_bytes + b_bytes) != cudaSuccess) {
       cudaGetLastError();
       return G3_ERR_NOMEM;
     }
@@ -1086,7 +1097,7 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
         d->hbuf = nullptr;
         d->hbuf_bytes = 0;
       }
-      if (cudaMalloc(&d->hbuf, need) != cudaSuccess) {
+      if (device_alloc(&d->hbuf, need) != cudaSuccess) {
         cudaGetLastError();
         return G3_ERR_NOMEM;
       }
@@ -1473,6 +1484,8 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
 
 uint64_t g3_launch_count(void) { return g3::launch_count(); }
 
+int64_t g3_debug_device_allocations(void) { return g3::g_device_allocs.load(std::memory_order_relaxed); }
+
 int g3_debug_withhold_next(int64_t timeout_ms) {
   if (timeout_ms <= 0 || timeout_ms > 10000) return -101;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -1548,8 +1561,8 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
     cudaFree(C);
     cudaGetLastError();
   };
-  if (cudaMalloc(&A, (size_t)m * lda * es_in) != cudaSuccess || cudaMalloc(&B, (size_t)k * ldb * es_in) != cudaSuccess ||
-      cudaMalloc(&C, (size_t)m * n * 4) != cudaSuccess) {
+  if (device_alloc(&A, (size_t)m * lda * es_in) != cudaSuccess || device_alloc(&B, (size_t)k * ldb * es_in) != cudaSuccess ||
+      device_alloc(&C, (size_t)m * n * 4) != cudaSuccess) {
     cleanup();
     return G3_ERR_NOMEM;
   }

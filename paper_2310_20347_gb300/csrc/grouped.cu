@@ -267,7 +267,7 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
   const size_t jobs_bytes = align256(sizeof(PrepJob) * std::max<size_t>(njobs_max, 1));
   const size_t header = maps_bytes + groups_bytes + tiles_bytes + jobs_bytes;
   g3_grouped_plan* plan = new g3_grouped_plan();
-  if (cudaMalloc(&plan->dmem, header + planes) != cudaSuccess) {
+  if (device_alloc(&plan->dmem, header + planes) != cudaSuccess) {
     cudaGetLastError();
     delete plan;
     return G3_ERR_NOMEM;

@@ -144,4 +144,8 @@ bool kernel_timing_enabled();
 void kernel_timing_push(cudaEvent_t e0, cudaEvent_t e1);
 bool take_withhold(unsigned long long* timeout_ns);   // one-shot failure-detection test hook
 
+// Every device allocation the library makes goes through device_alloc, which
+// counts the successful ones (g3_debug_device_allocations reads the count).
+cudaError_t device_alloc(void** p, size_t bytes);
+
 }  // namespace g3

@@ -1,5 +1,6 @@
 """Helpers of the GPU parity tests: device transfer, guard-banded output
-buffers and the error metric max |C - C_ref| / (|alpha| |A| |B|)_ij."""
+buffers and the error metric max |C - C_ref| / (|alpha| |A| |B|)_ij, both as
+stated (strict) and with |beta C| added to the denominator."""
 import numpy as np
 import torch
 
@@ -47,3 +48,27 @@ def rel_err(got, ref, D, beta_c=None):
         den = den + np.abs(beta_c)
     den = np.maximum(den, np.finfo(np.float32).tiny)
     return float(np.max(diff / den)) if diff.size else 0.0
+
+
+def rel_errs(got, ref, D, beta_c=None):
+    """(strict, with_beta): the error over |alpha||A||B| alone, as the targets
+    state it, and over |alpha||A||B| + |beta C| (rel_err).  Identical when
+    beta == 0.  Entries whose denominator is 0 are compared against FLT_MIN."""
+    strict = rel_err(got, ref, D, None)
+    return strict, (strict if beta_c is None else rel_err(got, ref, D, beta_c))
+
+
+# From this depth on the stated metric is met with beta != 0 as well: the
+# float32 rounding of |beta C| (at most 2^-24 |beta C|) is then far below
+# 2e-6 of |alpha||A||B|, which grows with k.
+STRICT_MIN_K = 256
+
+
+def gate(got, ref, D, beta_c, k, tol):
+    """Assert the tolerance on the metric with |beta C| in the denominator
+    and, for k >= STRICT_MIN_K, on the strict metric too; returns both."""
+    strict, with_beta = rel_errs(got, ref, D, beta_c)
+    assert with_beta <= tol, ("gate", with_beta)
+    if k >= STRICT_MIN_K:
+        assert strict <= tol, ("strict gate", strict)
+    return strict, with_beta

@@ -38,6 +38,19 @@ def test_reference_arm_line():
     assert "workload" in line["config"]
 
 
+def test_reference_arm_config_matches_gpu_arm():
+    # both arms describe the headline workload with the same config object,
+    # and by default each host thread gets 8 rows of C per step
+    sys.path.insert(0, ROOT)
+    import bench
+    r = _run(["--impl", "reference", "--size", "192", "--steps", "1", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["config"] == bench.square_config(192)
+    cores = line["cpu_baseline"]["cores"]
+    assert line["cpu_baseline"]["sample"].startswith(f"{8 * cores} full rows")
+
+
 def test_reference_arm_other_ranks_silent():
     r = _run(["--impl", "reference", "--size", "64", "--steps", "1", "--warmup", "3"],
              {"RANK": "1", "WORLD_SIZE": "2"})

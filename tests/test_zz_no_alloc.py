@@ -3,19 +3,28 @@ device memory (a framework that owns every byte of it, a fixed memory budget,
 or code that must not trigger the synchronisation cudaMalloc can cause).
 
 It must give the same result as the allocating entry point, g3_gemm_ex with
-G3_F32_3XBF16 and no split-K, on two calls in a row: the second call sees the
-scratch array exactly as the first one left it.  This file is collected last
-so that a run stopping at its first failure has already run every other test.
+G3_F32_3XBF16 and no split-K, bit for bit: both run the same member on the
+same bfloat16 planes, only the planes' address differs.  Three problems run
+back to back, so each call sees the scratch array as the previous one left it;
+the third has k <= 512, where the mode takes the three-part split and the
+array holds three planes per operand at other offsets.  A fresh process checks
+that the calls allocate nothing.  This file is collected last so that a run
+stopping at its first failure has already run every other test.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from gpu_util import rel_err
+from gpu_util import gate
 from paper_2310_20347_gb300 import G3_F32_3XBF16, _lib, synth, torch_api
 
-TOL = 1e-6   # relative to |alpha||A||B| + |beta C|; both calls run the same kernels
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SCRATCH = 64 << 20   # bytes of the library's fixed array
 
 
 def noalloc(p, C):
@@ -38,23 +47,88 @@ def reference(p):
 
 
 @pytest.mark.gpu
-def test_noalloc_matches_allocating_entry_point_twice():
-    # two different problems back to back through the same scratch array
+def test_noalloc_matches_allocating_entry_point_three_calls():
+    # three different problems back to back through the same scratch array;
+    # the last (k = 300 <= 512) takes the three-part split
     for p in (synth.uniform_problem(700, 900, 1300, seed=21, alpha=1.0, beta=0.5),
-              synth.uniform_problem(333, 257, 2049, seed=22, alpha=-0.75, beta=0.25)):
+              synth.uniform_problem(333, 257, 2049, seed=22, alpha=-0.75, beta=0.25),
+              synth.uniform_problem(700, 900, 300, seed=23, alpha=1.0, beta=0.5)):
         got = noalloc(p, torch.from_numpy(p.C).cuda())
         want = reference(p)
-        D = oracle.absprod(p.A, p.B, p.alpha)
-        e = rel_err(got, want.astype(np.float64), D, p.beta * p.C.astype(np.float64))
-        assert e <= TOL, e
-    # the result is also right against the binary64 oracle (the mode's 2e-6)
-    ref = oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta)
-    assert rel_err(got, ref, D, p.beta * p.C.astype(np.float64)) <= 2e-6
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), (p.m, p.n, p.k)
+        # and right against the binary64 oracle: the mode's 2e-6, on the stated
+        # metric as well (k >= 256)
+        ref = oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta)
+        gate(got, ref, oracle.absprod(p.A, p.B, p.alpha), p.beta * p.C.astype(np.float64), p.k, 2e-6)
+
+
+def planes_bytes(m, n, k):
+    # bfloat16 planes of A (m x ceil8(k)) and B (k x ceil8(n)), each rounded up
+    # to 256 bytes: two planes per operand for k > 512, three for k <= 512
+    planes = 3 if k <= 512 else 2
+    r8 = lambda x: (x + 7) // 8 * 8
+    r256 = lambda x: (x + 255) // 256 * 256
+    return planes * (r256(2 * m * r8(k)) + r256(2 * k * r8(n)))
+
+
+@pytest.mark.gpu
+def test_noalloc_limits_per_split():
+    # 4 * (m*k + k*n) bytes fit at k = 520 (two-part split): accepted and equal
+    # to the allocating entry point; at k = 512 the same shape needs the
+    # three-part split's 6 bytes per element and is rejected before any launch
+    p = synth.uniform_problem(30000, 8, 520, seed=24, alpha=1.0, beta=0.5)
+    assert planes_bytes(p.m, p.n, p.k) <= SCRATCH
+    got = noalloc(p, torch.from_numpy(p.C).cuda())
+    assert np.array_equal(got.view(np.uint32), reference(p).view(np.uint32))
+    assert 4 * (30000 * 512 + 512 * 8) <= SCRATCH < planes_bytes(30000, 8, 512)
+    A = torch.zeros(30000, 512, device="cuda")
+    B = torch.zeros(512, 8, device="cuda")
+    C = torch.zeros(30000, 8, device="cuda")
+    assert _lib.g3_gemm_3xbf16_noalloc(30000, 8, 512, 1.0, A.data_ptr(), 512, B.data_ptr(), 8, 0.0, C.data_ptr(), 8,
+                                       None) == _lib.G3_ERR_UNSUPPORTED
 
 
 @pytest.mark.gpu
 def test_noalloc_rejects_problems_beyond_the_scratch():
-    # 4 * (m*k + k*n) bytes of bfloat16 planes exceed the 64 MiB array
+    # 4 * (m*k + k*n) bytes of bfloat16 planes exceed the 64 MiB array; the
+    # call returns before it touches the (dummy) pointers
     p = 16
     assert _lib.g3_gemm_3xbf16_noalloc(4096, 4096, 4096, 1.0, p, 4096, p, 4096, 0.0, p, 4096,
                                        None) == _lib.G3_ERR_UNSUPPORTED
+    assert _lib.g3_gemm_3xbf16_noalloc(64, 64, 32769, 1.0, p, 32769, p, 64, 0.0, p, 64,
+                                       None) == _lib.G3_ERR_UNSUPPORTED
+
+
+_CHILD = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2310_20347_gb300 import _lib, synth
+_lib.load()
+ps = [synth.uniform_problem(640, 768, 1100, seed=25, alpha=1.0, beta=0.5),
+      synth.uniform_problem(640, 768, 200, seed=26, alpha=0.5, beta=-1.0)]
+bufs = [tuple(torch.from_numpy(x).cuda() for x in (p.A, p.B, p.C)) for p in ps]
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+a0 = _lib.g3_debug_device_allocations()
+for p, (A, B, C) in zip(ps, bufs):
+    st = _lib.g3_gemm_3xbf16_noalloc(p.m, p.n, p.k, p.alpha, A.data_ptr(), p.k, B.data_ptr(), p.n, p.beta,
+                                     C.data_ptr(), p.n, None)
+    assert st == 0, st
+torch.cuda.synchronize()
+print(a0, _lib.g3_debug_device_allocations(), free0, torch.cuda.mem_get_info()[0])
+"""
+
+
+@pytest.mark.gpu
+def test_noalloc_allocates_nothing_in_a_fresh_process():
+    # the library's first calls in a fresh process are two allocation-free
+    # calls: its allocation counter stays at 0 and the device's free memory is
+    # unchanged (kernels loaded eagerly, so that module loading does not count)
+    env = dict(os.environ, CUDA_MODULE_LOADING="EAGER")
+    r = subprocess.run([sys.executable, "-c", _CHILD, ROOT], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    a0, a1, free0, free1 = (int(x) for x in r.stdout.split())
+    assert a0 == 0 and a1 == 0, (a0, a1)
+    assert free1 == free0, (free0, free1)
