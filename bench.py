@@ -288,11 +288,19 @@ def _call_ms(fn, reps, flush):
     return tot / reps
 
 
+# When a list, _line appends each workload's result here instead of printing
+# it (the default run collects the other configurations into its own line).
+_COLLECT = None
+
+
 def _line(args, metric_value, unit, config, extra):
     line = {"metric": METRIC, "value": metric_value, "unit": unit, "n_gpus": 1, "steps": args.reps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic", "config": config}
     line.update(extra)
+    if _COLLECT is not None:
+        _COLLECT.append(line)
+        return
     print(json.dumps(line), flush=True)
 
 
@@ -492,6 +500,10 @@ def run_workload(args):
             elif kind == "bf16":
                 err = sample_err(got.astype(np.float64), rows, p.A, p.B, None, 1.0, 0.0,
                                  oracle.round_bf16(p.A), oracle.round_bf16(p.B))
+            elif args.compact:
+                # the gate only: the kernel check against the oracle's own
+                # quantisation of every operand is the parity tests' job
+                err = sample_err(got.astype(np.float64), rows, p.A, p.B, None, 1.0, 0.0)
             else:
                 oqa, osa = oracle.fp8_quantize(p.A)
                 oqb, osb = oracle.fp8_quantize(p.B)
@@ -519,14 +531,16 @@ def run_workload(args):
                 calls[i]()
             torch.cuda.synchronize()
             # kernel-only device time (events around each GEMM kernel), eager calls
-            _lib.g3_kernel_timing(True)
-            _lib.g3_kernel_time_ms(reset=True)
-            for i in range(nrep):
-                calls[i % sets]()
-            torch.cuda.synchronize()
-            kms_tot, kn = _lib.g3_kernel_time_ms(reset=True)
-            _lib.g3_kernel_timing(False)
-            kms = kms_tot / max(kn, 1)
+            kms = None
+            if not args.compact:
+                _lib.g3_kernel_timing(True)
+                _lib.g3_kernel_time_ms(reset=True)
+                for i in range(nrep):
+                    calls[i % sets]()
+                torch.cuda.synchronize()
+                kms_tot, kn = _lib.g3_kernel_time_ms(reset=True)
+                _lib.g3_kernel_timing(False)
+                kms = kms_tot / max(kn, 1)
             # whole calls back to back, replayed from a CUDA graph (no host
             # overhead between the GEMMs, as in a captured network)
             gs = torch.cuda.Stream()
@@ -547,7 +561,7 @@ def run_workload(args):
             ms = e0.elapsed_time(e1) / nrep
             del graph
             # cold single call after an L2 flush, for reference
-            cold_ms = _call_ms(fn, 5, flush)
+            cold_ms = None if args.compact else _call_ms(fn, 5, flush)
             del copies, calls
             flops = 2.0 * m * n * k
             st, cfg, sk, rs = _lib.g3_plan_query(m, n, k, {"bf16": G3_BF16, "fp8": G3_FP8_E4M3,
@@ -813,7 +827,7 @@ def run_workload(args):
         per_call()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        reps_eager = 3
+        reps_eager = 1 if args.compact else 3
         for _ in range(reps_eager):
             per_call()
         torch.cuda.synchronize()
@@ -840,6 +854,66 @@ def run_workload(args):
         return
 
 
+# The other configurations, measured compactly (fewer repetitions, no cold or
+# eager-only passes) after the headline step and reported in its JSON line
+# under "configs", each with its own clock sample.
+OTHER_CONFIGS = (
+    ("1_plain_fp32_512", "plain"),
+    ("3_im2col_bf16", "im2col"),
+    ("4_grouped_bf16", "grouped"),
+    ("4_grouped_3xbf16", "grouped-3xbf16"),
+    ("5_bf16_8192", "bf16"),
+    ("5_fp8_8192", "fp8"),
+    ("5_int8_8192", "int8"),
+    ("5_im2col_fp8", "im2col-fp8"),
+    ("5_im2col_int8", "im2col-int8"),
+)
+
+
+def _summary(line):
+    """The figures of one configuration's line that the default line carries."""
+    keep = {"value": line["value"], "unit": line["unit"]}
+    rf = line.get("roofline")
+    if rf:
+        keep["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac") if k in rf}
+    for k in ("ms", "kernel_ms", "err", "worst_err", "total_ms_20_layers", "grouped_graph_ms", "grouped_kernel_ms",
+              "per_call_graph_ms", "per_call_eager_wall_ms", "speedup_vs_eager", "speedup_vs_graph_of_calls",
+              "max_rel_err_sampled", "nonfinite_sampled", "total_gflop"):
+        if k in line:
+            keep[k] = line[k]
+    if "per_shape" in line:
+        keep["per_shape"] = [{"shape": r["shape"], "us": round(r["ms"] * 1e3, 2), "hbm_frac": round(r["hbm_frac"], 3),
+                              "member": r["member"], "split_k": r["split_k"]} for r in line["per_shape"]]
+    keep["workload"] = line["config"].get("workload")
+    return keep
+
+
+def other_configs(args, gpu_index):
+    global _COLLECT
+    import copy
+    out = {}
+    for key, wl in OTHER_CONFIGS:
+        a = copy.copy(args)
+        a.workload, a.reps, a.compact, a.only, a.tune, a.config, a.dsize = wl, 10, True, "", False, -1, 8192
+        _COLLECT = []
+        clk = Clocks(gpu_index)
+        clk.start()
+        t0 = time.perf_counter()
+        err = None
+        try:
+            run_workload(a)
+        except Exception as e:  # noqa: BLE001 -- reported in the line, the headline stands
+            err = f"{type(e).__name__}: {e}"
+        wall = time.perf_counter() - t0
+        c = clk.stop()
+        lines, _COLLECT = _COLLECT, None
+        entry = _summary(lines[0]) if lines else {"error": err or "no result"}
+        entry["clocks"] = c
+        entry["wall_s"] = round(wall, 1)
+        out[key] = entry
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -862,7 +936,10 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--only", default="", help="im2col workloads: comma-separated layer names (e.g. L1,L12)")
     ap.add_argument("--tune", action="store_true", help="im2col workloads: autotune every shape first")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default run: skip the compact measurements of the other configurations")
     args = ap.parse_args()
+    args.compact = False
     args.warmup = max(args.warmup, 3)
     if args.print_kernel_hash:
         print(kernel_sources_hash())
@@ -1018,6 +1095,10 @@ def main():
     }
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_oracle_sample(p)
+    if not args.no_configs and world == 1:
+        del A, B, C0, C, hA, hB, hC
+        torch.cuda.empty_cache()
+        line["configs"] = other_configs(args, local)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
