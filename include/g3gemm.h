@@ -321,7 +321,10 @@ G3_API int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config
  * k-blocks), on scratch operands of shape m x n x k it allocates and frees,
  * and records the fastest (member, split) for the shape's size bucket: dtype
  * and ceil(log2) of each of m, n, k.  Later g3_gemm calls in that bucket use
- * the record instead of the planner's model.  Synchronous; allocates.
+ * the record instead of the planner's model.  Each candidate is timed as
+ * calls run inside a captured network: a CUDA graph of back-to-back calls
+ * over copies of the operands that together exceed four times the L2 cache,
+ * replayed; the time per call is reported.  Synchronous; allocates.
  * Outputs (any may be NULL): the member index, the split count, its time in
  * ms.  The CUDA-core dtypes (G3_F32, G3_F64, G3_INT16) are not timed:
  * *best_config = -1, *best_split = the planner's choice (for G3_F32 the SIMT

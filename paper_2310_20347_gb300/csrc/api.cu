@@ -1547,28 +1547,40 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
     if (st != G3_OK) return st;
     sms = d->sms;
   }
+  // Candidates are timed the way layers of a captured network run: R calls
+  // back to back, replayed from a CUDA graph, cycling over enough copies of
+  // the operands that together they exceed L2 four times (so that each call
+  // reads operands that left L2 long ago).  Per-call time = replay time / R.
   const int es_in = input_esize(dtype);
   const int64_t lda = round_up(k, 16), ldb = round_up(n, 16);
-  void *A = nullptr, *B = nullptr, *C = nullptr;
+  const size_t a_bytes = (size_t)m * lda * es_in, b_bytes = (size_t)k * ldb * es_in, c_bytes = (size_t)m * n * 4;
+  const size_t set_bytes = a_bytes + b_bytes + c_bytes;
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, 0) != cudaSuccess || l2 <= 0) {
+    cudaGetLastError();
+    l2 = 128 << 20;
+  }
+  const int sets = (int)std::max<size_t>(1, std::min<size_t>(16, (4 * (size_t)l2 + set_bytes - 1) / set_bytes));
+  std::vector<void*> bufs;
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (s) cudaStreamDestroy(s);
-    cudaFree(A);
-    cudaFree(B);
-    cudaFree(C);
+    for (void* b : bufs) cudaFree(b);
     cudaGetLastError();
   };
-  if (device_alloc(&A, (size_t)m * lda * es_in) != cudaSuccess || device_alloc(&B, (size_t)k * ldb * es_in) != cudaSuccess ||
-      device_alloc(&C, (size_t)m * n * 4) != cudaSuccess) {
-    cleanup();
-    return G3_ERR_NOMEM;
+  for (int q = 0; q < sets; ++q) {
+    void* b = nullptr;
+    if (device_alloc(&b, set_bytes) != cudaSuccess) {
+      cleanup();
+      return G3_ERR_NOMEM;
+    }
+    bufs.push_back(b);
+    // small non-zero operands (0x3C in every byte): representative tensor-core power
+    cudaMemset(b, 0x3C, a_bytes + b_bytes);
   }
-  // small non-zero operands (0x3C in every byte): representative tensor-core power
-  cudaMemset(A, 0x3C, (size_t)m * lda * es_in);
-  cudaMemset(B, 0x3C, (size_t)k * ldb * es_in);
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess) {
     cleanup();
@@ -1579,34 +1591,66 @@ int g3_autotune(int64_t m, int64_t n, int64_t k, int dtype, int* best_config, in
   const int num_kb = (int)((k + bk - 1) / bk);
   int best_member = -1, best_sk = 1;
   double best = 1e30;
+  auto args_for = [&](int set, int member, int sk) {
+    g3_gemm_args a;
+    g3_gemm_args_init(&a);
+    uint8_t* base = static_cast<uint8_t*>(bufs[set]);
+    a.m = m; a.n = n; a.k = k;
+    a.alpha = 1.0; a.beta = 0.0;
+    a.A = base; a.lda = lda; a.B = base + a_bytes; a.ldb = ldb; a.C = base + a_bytes + b_bytes; a.ldc = n;
+    a.dtype = dtype;
+    a.config = member;
+    a.split_k = sk;
+    return a;
+  };
+  // Time of one candidate (ms per call), or 1e30 if it cannot run.
+  auto time_candidate = [&](int member, int sk) -> double {
+    g3_gemm_args a = args_for(0, member, sk);
+    if (gemm_impl(a, s) != G3_OK) return 1e30;   // warm-up (and workspace growth) outside the capture
+    float ms = 0.f;
+    cudaEventRecord(e0, s);
+    const int st0 = gemm_impl(a, s);
+    cudaEventRecord(e1, s);
+    if (st0 != G3_OK || cudaEventSynchronize(e1) != cudaSuccess) return 1e30;
+    cudaEventElapsedTime(&ms, e0, e1);
+    // about 2 ms of replay per measurement, at least two passes over the sets
+    const int reps = std::max(2 * sets, std::min(64, std::max(4, (int)(2.0 / std::max(ms, 1e-3f)))));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return 1e30;
+    int st = G3_OK;
+    for (int r = 0; r < reps && st == G3_OK; ++r) {
+      g3_gemm_args ar = args_for(r % sets, member, sk);
+      st = gemm_impl(ar, s);
+    }
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    double t = 1e30;
+    if (st == G3_OK && ce == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess &&
+        cudaGraphLaunch(exec, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess) {
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        cudaGraphLaunch(exec, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          t = 1e30;
+          break;
+        }
+        cudaEventElapsedTime(&ms, e0, e1);
+        t = std::min(t, (double)ms / reps);
+      }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return t;
+  };
   for (int i = 0; i < G3_FAMILY_SIZE; ++i) {
     if (!g_family[i].launch || g_family[i].mode != mode) continue;
     for (int sk : {1, G3_SPLIT_STREAM_K, 2, 3, 4, 6, 8, 12, 16}) {
       if (sk > num_kb) break;
-      g3_gemm_args a;
-      g3_gemm_args_init(&a);
-      a.m = m; a.n = n; a.k = k;
-      a.alpha = 1.0; a.beta = 0.0;
-      a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = n;
-      a.dtype = dtype;
-      a.config = i;
-      a.split_k = sk;
-      if (gemm_impl(a, s) != G3_OK) continue;   // warm-up (and workspace growth)
-      double t_min = 1e30;
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, s);
-        const int st = gemm_impl(a, s);
-        cudaEventRecord(e1, s);
-        if (st != G3_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-          t_min = 1e30;
-          break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        t_min = std::min(t_min, (double)ms);
-      }
-      if (t_min < best) {
-        best = t_min;
+      const double t = time_candidate(i, sk);
+      if (t < best) {
+        best = t;
         best_member = i;
         best_sk = sk;
       }
