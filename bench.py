@@ -778,13 +778,30 @@ def run_workload(args):
                "per_layer": per})
         return
 
-    if args.workload in ("grouped", "grouped-3xbf16"):
-        dt = G3_BF16 if args.workload == "grouped" else G3_F32_3XBF16
+    if args.workload in ("grouped", "grouped-3xbf16", "grouped-fp8"):
+        dt = {"grouped": G3_BF16, "grouped-3xbf16": G3_F32_3XBF16, "grouped-fp8": G3_FP8_E4M3}[args.workload]
         shapes = synth.grouped_shapes(1000, seed=0)
         probs = []
+        masters = {}
         flops = 0.0
         rng = np.random.default_rng(0)
         for gi, (m, n, k) in enumerate(shapes):
+            a32 = (rng.standard_normal((m, k)) / np.sqrt(k)).astype(np.float32)
+            b32 = rng.standard_normal((k, n)).astype(np.float32)
+            if dt == G3_FP8_E4M3:
+                lda, ldb = -(-k // 16) * 16, -(-n // 16) * 16      # 16-byte rows for TMA
+                (qa, sa), (qb, sb) = torch_api.quantize_fp8(torch.from_numpy(a32).to(dev)), torch_api.quantize_fp8(
+                    torch.from_numpy(b32).to(dev))
+                A = torch.zeros(m, lda, dtype=torch.uint8, device=dev)[:, :k]
+                B = torch.zeros(k, ldb, dtype=torch.uint8, device=dev)[:, :n]
+                A.copy_(qa)
+                B.copy_(qb)
+                C = torch.empty(m, n, device=dev)
+                probs.append((A, B, C, 1.0, 0.0, float(sa.item()), float(sb.item())))
+                if gi % 50 == 0:
+                    masters[gi] = (a32, b32)
+                flops += 2.0 * m * n * k
+                continue
             lda, ldb = -(-k // 8) * 8, -(-n // 8) * 8      # 16-byte rows for TMA
             if dt == G3_BF16:
                 A = torch.zeros(m, lda, dtype=torch.bfloat16, device=dev)[:, :k]
@@ -792,18 +809,33 @@ def run_workload(args):
             else:
                 A = torch.zeros(m, lda, dtype=torch.float32, device=dev)[:, :k]
                 B = torch.zeros(k, ldb, dtype=torch.float32, device=dev)[:, :n]
-            A.copy_(torch.from_numpy((rng.standard_normal((m, k)) / np.sqrt(k)).astype(np.float32)))
-            B.copy_(torch.from_numpy(rng.standard_normal((k, n)).astype(np.float32)))
+            A.copy_(torch.from_numpy(a32))
+            B.copy_(torch.from_numpy(b32))
             C = torch.empty(m, n, device=dev)
             probs.append((A, B, C, 1.0, 0.0))
             flops += 2.0 * m * n * k
+        tuned_buckets, tune_s = 0, 0.0
+        if args.tune:
+            # per-bucket selection of the tile height (g3_autotune_grouped):
+            # one timing per (log2 m, log2 n, log2 k) bucket of the batch
+            _lib.g3_tune_cache_clear()
+            t0 = time.perf_counter()
+            seen = set()
+            for (m, n, k) in shapes:
+                key = tuple(int(np.ceil(np.log2(x))) for x in (m, n, k))
+                if key not in seen:
+                    seen.add(key)
+                    _lib.g3_autotune_grouped(m, n, k, dt)
+            tuned_buckets, tune_s = len(seen), time.perf_counter() - t0
         plan = torch_api.GroupedPlan(probs, dt)
+        heights = [_lib.g3_grouped_plan_describe(plan.plan, i)[1] for i in range(len(probs))]
         plan.execute()
         torch.cuda.synchronize()
         errs, nonfinite = [], 0
         for gi in range(0, 1000, 50):
-            A, B, C, _, _ = probs[gi]
-            a, b = A.float().cpu().numpy(), B.float().cpu().numpy()
+            A, B, C = probs[gi][:3]
+            # the gate: against the FP32 masters (FP8), or the operands the GPU got
+            a, b = masters[gi] if dt == G3_FP8_E4M3 else (A.float().cpu().numpy(), B.float().cpu().numpy())
             rows = np.arange(min(4, a.shape[0]))
             got = C.cpu().numpy()[rows].astype(np.float64)
             nonfinite += int(np.count_nonzero(~np.isfinite(got)))
@@ -821,8 +853,12 @@ def run_workload(args):
         kms = _kernel_ms(_lib, plan.execute, args.reps, flush)
 
         def per_call():
-            for (A, B, C, a, b) in probs:
-                torch_api.gemm(A, B, C, a, b, dtype=dt)
+            for pr in probs:
+                A, B, C, a, b = pr[:5]
+                if dt == G3_FP8_E4M3:   # the scales folded into alpha, as the plan does
+                    torch_api.gemm(A, B, C, a * pr[5] * pr[6], b, dtype=dt)
+                else:
+                    torch_api.gemm(A, B, C, a, b, dtype=dt)
 
         per_call()
         torch.cuda.synchronize()
@@ -843,13 +879,15 @@ def run_workload(args):
         graph_calls_ms = _call_ms(g2.replay, max(3, args.reps // 4), flush)
         _line(args, flops / grouped_ms / 1e9, "TFLOPS",
               {"workload": f"1000 GEMMs, m,n,k log-uniform in [16,1024] (seed 0), "
-                           f"{'bf16' if dt == G3_BF16 else '3xbf16 (fp32 in/out)'}, fp32 C, beta=0",
+                           f"{ {G3_BF16: 'bf16', G3_F32_3XBF16: '3xbf16 (fp32 in/out)', G3_FP8_E4M3: 'fp8 e4m3 with per-problem scales'}[dt] }, fp32 C, beta=0",
                "l2": "flushed before every replay"},
-              {"dtype": "bf16" if dt == G3_BF16 else "bf16x3->f32", "total_gflop": flops / 1e9,
+              {"dtype": {G3_BF16: "bf16", G3_F32_3XBF16: "bf16x3->f32", G3_FP8_E4M3: "fp8"}[dt], "total_gflop": flops / 1e9,
                "grouped_graph_ms": grouped_ms, "grouped_kernel_ms": kms,
                "per_call_eager_wall_ms": eager_ms, "per_call_graph_ms": graph_calls_ms,
                "speedup_vs_eager": eager_ms / grouped_ms, "speedup_vs_graph_of_calls": graph_calls_ms / grouped_ms,
-               "max_rel_err_sampled": float(np.max(np.array(errs))), "nonfinite_sampled": nonfinite})
+               "max_rel_err_sampled": float(np.max(np.array(errs))), "nonfinite_sampled": nonfinite,
+               "autotuned": bool(args.tune), "tuned_buckets": tuned_buckets, "tune_s": round(tune_s, 1),
+               "tile_heights": {str(h): heights.count(h) for h in sorted(set(heights))}})
         plan.close()
         return
 
@@ -927,7 +965,7 @@ def main():
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
                     choices=["square", "sweep", "plain", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "int16", "conv",
-                             "grouped", "grouped-3xbf16"],
+                             "grouped", "grouped-3xbf16", "grouped-fp8"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--dsize", type=int, default=8192, help="int8 / fp8 / bf16 workloads: m = n = k")
@@ -935,7 +973,8 @@ def main():
                     help="print the hash of the headline kernel's sources (for the DRAM-traffic record) and exit")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--only", default="", help="im2col workloads: comma-separated layer names (e.g. L1,L12)")
-    ap.add_argument("--tune", action="store_true", help="im2col workloads: autotune every shape first")
+    ap.add_argument("--tune", action="store_true",
+                    help="im2col workloads: autotune every shape first; grouped workloads: every size bucket")
     ap.add_argument("--no-configs", action="store_true",
                     help="default run: skip the compact measurements of the other configurations")
     args = ap.parse_args()

@@ -259,7 +259,10 @@ G3_API int g3_quantize_fp8(const float* x, int64_t rows, int64_t cols, int64_t l
 
 /* --- Grouped GEMM: many independent problems in one persistent launch ------
  * One descriptor per problem, same conventions as g3_gemm; all problems of a
- * call share one dtype (G3_BF16 or G3_F32_3XBF16).                          */
+ * call share one dtype: G3_BF16, G3_F32_3XBF16 or G3_FP8_E4M3 (C float32).
+ * scale_a, scale_b: the per-tensor scales of a G3_FP8_E4M3 problem (host
+ * values, finite and > 0: C := beta*C + alpha*scale_a*scale_b*A*B over the
+ * decoded E4M3 codes); ignored by the other dtypes.                          */
 typedef struct g3_gemm_desc {
   int64_t m, n, k;
   int64_t lda, ldb, ldc;
@@ -267,6 +270,7 @@ typedef struct g3_gemm_desc {
   const void* A;
   const void* B;
   void* C;
+  float scale_a, scale_b;
 } g3_gemm_desc;
 
 typedef struct g3_grouped_plan g3_grouped_plan;
@@ -274,18 +278,38 @@ typedef struct g3_grouped_plan g3_grouped_plan;
 /* Validate the descriptors, bucket the shapes, encode the per-problem tensor
  * maps into a device table and allocate the plan's workspace.  Synchronous.
  * The caller must keep A, B, C of every problem alive until the plan is
- * destroyed.  Descriptor i with an invalid field returns -(100 + i) clipped
- * to G3_ERR_ARG for i >= 900.                                               */
+ * destroyed.  Descriptor i with an invalid field (including, for
+ * G3_FP8_E4M3, a scale that is not finite and > 0) returns -(100 + i)
+ * clipped to G3_ERR_ARG for i >= 900.                                       */
 G3_API int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** plan);
 
 /* Run every problem of the plan: pre-passes (if any) and one persistent
- * kernel launch per kernel kind (BF16: one; FP32-accurate: one for the
+ * kernel launch per kernel kind (BF16, FP8: one; FP32-accurate: one for the
  * problems with k > 512 and one for those with k <= 512).  No host
  * synchronisation and no allocation, so the call can be captured into a CUDA
  * graph.                                                                    */
 G3_API int g3_grouped_plan_execute(g3_grouped_plan* plan, void* cuda_stream);
 
 G3_API int g3_grouped_plan_destroy(g3_grouped_plan* plan);
+
+/* Introspection: the tile height (64 or 128 rows) and kernel kind (0: the
+ * plan's first launch -- BF16, FP8 or the FP32-accurate two-part split; 1:
+ * the three-part split) of problem `index`; both -1 for a problem without
+ * products.  -101: plan is NULL; -102: index out of range.                  */
+G3_API int g3_grouped_plan_describe(const g3_grouped_plan* plan, int index, int* bm, int* kind);
+
+/* Per-bucket selection for grouped plans (the paper's Section 8.4 search,
+ * applied to the grouped kernel): times a plan of problems of shape
+ * m x n x k (dtype as g3_grouped_plan_create) with every problem on tiles of
+ * 64 and of 128 rows -- each a CUDA graph of back-to-back executions over
+ * scratch operands the call allocates and frees -- and records the faster
+ * height for the size bucket (dtype, ceil(log2) of m, n, k).  Plans created
+ * later take that height for every problem in the bucket instead of the
+ * fixed rule (64 rows for m <= 64, 128 above).  The records live in the
+ * tuning cache (saved, loaded and cleared with the g3_tune_cache_* calls).
+ * Outputs (any may be NULL): the height, its time per execution in ms.
+ * Synchronous; allocates.  -101..-104: bad m, n, k, dtype.                  */
+G3_API int g3_autotune_grouped(int64_t m, int64_t n, int64_t k, int dtype, int* best_bm, double* best_ms);
 
 /* Convenience: create, execute, destroy (synchronises on destroy).          */
 G3_API int g3_gemm_grouped(int count, const g3_gemm_desc* descs, int dtype, void* cuda_stream);

@@ -28,6 +28,7 @@ EXPORTED = (
     "g3_gemm", "g3_gemm_host", "g3_conv2d", "g3_set_stream", "g3_gemm_args_init", "g3_gemm_ex", "g3_gemm_workspace_size",
     "g3_convert_bf16", "g3_convert_tf32", "g3_split_bf16", "g3_split3_bf16", "g3_split_tf32", "g3_quantize_fp8",
     "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
+    "g3_grouped_plan_describe", "g3_autotune_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
     "g3_plan_query", "g3_launch_count", "g3_debug_device_allocations", "g3_kernel_timing", "g3_kernel_time_ms",
     "g3_debug_withhold_next", "g3_gemm_3xbf16_noalloc",
@@ -58,7 +59,8 @@ class g3_gemm_desc(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
-                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("scale_a", ctypes.c_float), ("scale_b", ctypes.c_float)]
 
 
 _lock = threading.Lock()
@@ -93,6 +95,8 @@ def load(path: str = LIB_PATH):
             "g3_grouped_plan_execute": ([vp, vp], i32),
             "g3_grouped_plan_destroy": ([vp], i32),
             "g3_gemm_grouped": ([i32, ctypes.POINTER(g3_gemm_desc), i32, vp], i32),
+            "g3_grouped_plan_describe": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+            "g3_autotune_grouped": ([i64, i64, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)], i32),
             "g3_get_last_device_status": ([ctypes.POINTER(i32)], i32),
             "g3_status_string": ([i32], ctypes.c_char_p),
             "g3_family_size": ([], i32),
@@ -198,6 +202,18 @@ def g3_grouped_plan_execute(plan, stream=None) -> int:
 
 def g3_grouped_plan_destroy(plan) -> int:
     return load().g3_grouped_plan_destroy(plan)
+
+
+def g3_grouped_plan_describe(plan, index):
+    bm, kind = ctypes.c_int(0), ctypes.c_int(0)
+    st = load().g3_grouped_plan_describe(plan, index, ctypes.byref(bm), ctypes.byref(kind))
+    return st, bm.value, kind.value
+
+
+def g3_autotune_grouped(m, n, k, dtype):
+    bm, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+    st = load().g3_autotune_grouped(m, n, k, dtype, ctypes.byref(bm), ctypes.byref(ms))
+    return st, bm.value, ms.value
 
 
 def g3_gemm_grouped(descs, dtype, stream=None) -> int:

@@ -298,6 +298,9 @@ struct TuneVal {
   double ms;
 };
 std::map<TuneKey, TuneVal> g_tune;
+// Records of g3_autotune_grouped share the table under dtype + kGroupedTuneTag;
+// their "member" is the tile height (64 or 128 rows) of a grouped problem.
+constexpr int kGroupedTuneTag = 100;
 bool g_tune_env_loaded = false;
 
 int size_bucket(int64_t x) {
@@ -319,8 +322,11 @@ int tune_load_locked(const char* path) {
     TuneVal val;
     if (line[0] == '#') continue;
     if (std::sscanf(line, "%d %d %d %d %d %d %lf", &key.dtype, &key.bm, &key.bn, &key.bk, &val.member, &val.split,
-                    &val.ms) == 7 &&
-        val.member >= 0 && val.member < G3_FAMILY_SIZE && (val.split >= 1 || val.split == G3_SPLIT_STREAM_K)) {
+                    &val.ms) != 7)
+      continue;
+    const bool grouped = key.dtype >= kGroupedTuneTag;   // grouped record: member = tile height
+    if (grouped ? ((val.member == 64 || val.member == 128) && val.split == 1)
+                : (val.member >= 0 && val.member < G3_FAMILY_SIZE && (val.split >= 1 || val.split == G3_SPLIT_STREAM_K))) {
       g_tune[key] = val;
       ++loaded;
     }
@@ -1018,6 +1024,16 @@ unsigned long long watchdog_timeout_ns() { return watchdog_ns(); }
 bool kernel_timing_enabled() { return g_timing; }
 
 void kernel_timing_push(cudaEvent_t e0, cudaEvent_t e1) { g_events.emplace_back(e0, e1); }
+
+int tuned_grouped_bm(int64_t m, int64_t n, int64_t k, int dtype) {
+  tune_env_once();
+  auto it = g_tune.find(tune_key(m, n, k, dtype + kGroupedTuneTag));
+  return it == g_tune.end() ? 0 : it->second.member;
+}
+
+void store_grouped_tuning(int64_t m, int64_t n, int64_t k, int dtype, int bm, double ms) {
+  g_tune[tune_key(m, n, k, dtype + kGroupedTuneTag)] = TuneVal{bm, 1, ms};
+}
 
 bool take_withhold(unsigned long long* timeout_ns) {
   if (!g_withhold_next) return false;

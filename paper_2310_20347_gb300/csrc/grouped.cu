@@ -6,14 +6,15 @@
 // ordered by decreasing k-depth (heaviest tiles first, so that the static
 // stride of the persistent CTAs balances), six TMA descriptors per problem in
 // a device table, and the preparation jobs (FP32 hi/lo or hi/mid/lo split,
-// re-packing of unaligned BF16 operands, C := beta*C for problems without
-// products).
+// re-packing of unaligned BF16 / FP8 operands, C := beta*C for problems
+// without products).
 // Executing the plan is one job kernel over all preparation jobs and one
-// tc_grouped_kernel per kernel kind over its tiles -- BF16: one; FP32-accurate:
+// tc_grouped_kernel per kernel kind over its tiles -- BF16, FP8: one; FP32-accurate:
 // the two-part split (3 products) for problems with k > 512 and the
 // three-part split (6 products) for those with k <= 512 -- with no host
 // synchronisation and no allocation.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -28,13 +29,13 @@
 namespace g3 {
 namespace {
 
-enum PrepKind : int { PREP_SPLIT = 0, PREP_COPY16 = 1, PREP_SCALE_C = 2, PREP_SPLIT3 = 3 };
+enum PrepKind : int { PREP_SPLIT = 0, PREP_COPY16 = 1, PREP_SCALE_C = 2, PREP_SPLIT3 = 3, PREP_COPY8 = 4 };
 
 // One preparation job of a grouped plan.
 struct PrepJob {
   const void* src;
   long long ld_src;   // elements
-  void* hi;           // PREP_SPLIT(3): hi plane; PREP_COPY16: destination
+  void* hi;           // PREP_SPLIT(3): hi plane; PREP_COPY16 / PREP_COPY8: destination
   void* lo;           // PREP_SPLIT(3): lo plane
   void* mid;          // PREP_SPLIT3: mid plane
   long long ld_dst;   // elements; destination rows start on 16-byte boundaries
@@ -68,6 +69,20 @@ __global__ void grouped_prep_kernel(const PrepJob* __restrict__ jobs, int njobs)
         const unsigned r = e / cols, c = e - r * cols;
         float* p = static_cast<float*>(const_cast<void*>(J.src)) + r * J.ld_src + c;
         *p = (J.beta == 0.f) ? 0.f : J.beta * *p;
+      }
+      continue;
+    }
+    if (J.kind == PREP_COPY8) {   // 8-bit elements, 16 per unit, destination rows 16-byte aligned
+      const unsigned upr8 = ((unsigned)J.cols + 15u) >> 4;
+      const unsigned total8 = (unsigned)J.rows * upr8;
+      for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < total8; u += gridDim.x * blockDim.x) {
+        const unsigned r = u / upr8, c0 = (u - r * upr8) << 4;
+        const int cnt = min(16, J.cols - (int)c0);
+        const uint8_t* xr = static_cast<const uint8_t*>(J.src) + (long long)r * J.ld_src + c0;
+        uint8_t* yr = static_cast<uint8_t*>(J.hi) + (long long)r * J.ld_dst + c0;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        for (int i = 0; i < cnt; ++i) w[i >> 2] |= static_cast<uint32_t>(xr[i]) << (8 * (i & 3));
+        *reinterpret_cast<uint4*>(yr) = make_uint4(w[0], w[1], w[2], w[3]);
       }
       continue;
     }
@@ -158,16 +173,23 @@ struct g3_grouped_plan {
   int entry[2] = {-1, -1};
   GroupedParams params[2]{};
   PrepJob* d_jobs = nullptr;
+  // per problem: tile height and kernel kind (0: the plan's first launch, 1:
+  // the three-part split), -1 / -1 for problems without products
+  std::vector<int> bms, kinds;
 };
 
-extern "C" {
+namespace {
 
-int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** out) {
+// force_bm > 0: every problem takes tiles of force_bm rows (g3_autotune_grouped);
+// otherwise the tuning record of the problem's size bucket, else the fixed
+// rule (64 rows for m <= 64, 128 above).
+int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g3_grouped_plan** out) {
   if (!out) return G3_ERR_ARG;
   *out = nullptr;
   if (count < 0) return -101;
   if (count > 0 && !descs) return -102;
-  if (dtype != G3_BF16 && dtype != G3_F32_3XBF16) return G3_ERR_UNSUPPORTED;
+  if (dtype != G3_BF16 && dtype != G3_F32_3XBF16 && dtype != G3_FP8_E4M3) return G3_ERR_UNSUPPORTED;
+  const bool fp8 = dtype == G3_FP8_E4M3;
   for (int i = 0; i < count; ++i) {
     const g3_gemm_desc& d = descs[i];
     const int code = i < 900 ? -(100 + i) : G3_ERR_ARG;
@@ -182,6 +204,8 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
       if (!d.C) return code;
       if (d.k > 0 && d.alpha != 0.0 && (!d.A || !d.B)) return code;
     }
+    if (fp8 && !(std::isfinite(d.scale_a) && std::isfinite(d.scale_b) && d.scale_a > 0.f && d.scale_b > 0.f))
+      return code;
   }
   std::lock_guard<std::mutex> lock(api_mutex());
   DeviceInfo dev;
@@ -199,10 +223,13 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
       if (g_grouped[i].launch && g_grouped[i].mode == mode) e = i;
     return e;
   };
-  const int entries[2] = {entry_of(dtype == G3_BF16 ? TC_BF16 : TC_3XBF16),
-                          dtype == G3_BF16 ? -1 : entry_of(TC_6XBF16)};
-  if (entries[0] < 0 || (dtype != G3_BF16 && entries[1] < 0)) return G3_ERR_UNSUPPORTED;
-  auto part_of = [&](int64_t k) { return (dtype != G3_BF16 && k <= 512) ? 1 : 0; };
+  const bool split_mode = dtype == G3_F32_3XBF16;
+  const int entries[2] = {entry_of(dtype == G3_BF16 ? TC_BF16 : (fp8 ? TC_FP8 : TC_3XBF16)),
+                          split_mode ? entry_of(TC_6XBF16) : -1};
+  if (entries[0] < 0 || (split_mode && entries[1] < 0)) return G3_ERR_UNSUPPORTED;
+  auto part_of = [&](int64_t k) { return (split_mode && k <= 512) ? 1 : 0; };
+  const int es = fp8 ? 1 : 2;          // bytes per operand element on the tensor core
+  const int bk = fp8 ? 128 : 64;       // k per k-block: one 128-byte row
   const int bm_max = std::min(g_grouped[entries[0]].bm_max, entries[1] >= 0 ? g_grouped[entries[1]].bm_max : 1 << 30);
 
   // ---- per-problem tiling, jobs and plane sizes (host)
@@ -220,10 +247,12 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     GroupDesc& g = groups[i];
     std::memset(&g, 0, sizeof(g));
     g.m = (int)d.m; g.n = (int)d.n; g.k = (int)d.k;
-    g.alpha = (float)d.alpha; g.beta = (float)d.beta;
+    g.alpha = (float)(fp8 ? d.alpha * (double)d.scale_a * (double)d.scale_b : d.alpha);
+    g.beta = (float)d.beta;
     g.C = static_cast<float*>(d.C);
     g.ldc = d.ldc;
-    g.bm = (d.m <= 64) ? 64 : std::min(128, bm_max);   // size bucket
+    const int tuned = force_bm > 0 ? force_bm : tuned_grouped_bm(d.m, d.n, d.k, dtype);
+    g.bm = std::min(tuned > 0 ? tuned : ((d.m <= 64) ? 64 : 128), bm_max);   // size bucket
     if (d.m == 0 || d.n == 0) continue;
     if (d.k == 0 || d.alpha == 0.0) {
       PrepJob J{};
@@ -235,7 +264,7 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     o.active = true;
     g.tiles_m = (g.m + g.bm - 1) / g.bm;
     g.tiles_n = (g.n + 127) / 128;
-    g.num_kb = (g.k + 63) / 64;
+    g.num_kb = (g.k + bk - 1) / bk;
     total_tiles += (long long)g.tiles_m * g.tiles_n;
     if (dtype == G3_F32_3XBF16) {
       o.lda = round_up(d.k, 8);
@@ -249,12 +278,12 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
         o.b_mid_off = take((size_t)d.k * o.ldb * 2);
       }
     } else {
-      o.pack_a = !aligned16(d.A, d.lda, 2);
-      o.pack_b = !aligned16(d.B, d.ldb, 2);
-      o.lda = o.pack_a ? round_up(d.k, 8) : d.lda;
-      o.ldb = o.pack_b ? round_up(d.n, 8) : d.ldb;
-      if (o.pack_a) o.a_off = take((size_t)d.m * o.lda * 2);
-      if (o.pack_b) o.b_off = take((size_t)d.k * o.ldb * 2);
+      o.pack_a = !aligned16(d.A, d.lda, es);
+      o.pack_b = !aligned16(d.B, d.ldb, es);
+      o.lda = o.pack_a ? round_up(d.k, 16 / es) : d.lda;
+      o.ldb = o.pack_b ? round_up(d.n, 16 / es) : d.ldb;
+      if (o.pack_a) o.a_off = take((size_t)d.m * o.lda * es);
+      if (o.pack_b) o.b_off = take((size_t)d.k * o.ldb * es);
     }
   }
   if (total_tiles > INT32_MAX) return G3_ERR_UNSUPPORTED;
@@ -300,20 +329,22 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
       jobs.push_back(PrepJob{d.A, d.lda, (void*)a, (void*)a_lo, (void*)a_mid, o.lda, g.m, g.k, kind, 0.f, va});
       jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, (void*)b_lo, (void*)b_mid, o.ldb, g.k, g.n, kind, 0.f, vb});
     } else {
+      const int copy = fp8 ? PREP_COPY8 : PREP_COPY16;
       if (o.pack_a) {
         a = d_planes + o.a_off;
-        jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, nullptr, o.lda, g.m, g.k, PREP_COPY16, 0.f, 0});
+        jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, nullptr, o.lda, g.m, g.k, copy, 0.f, 0});
       }
       if (o.pack_b) {
         b = d_planes + o.b_off;
-        jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, nullptr, o.ldb, g.k, g.n, PREP_COPY16, 0.f, 0});
+        jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, nullptr, o.ldb, g.k, g.n, copy, 0.f, 0});
       }
     }
     // maps 2p, 2p+1 = A, B of plane p: hi; then lo (two-part) or mid, lo
     // (three-part); unused planes repeat plane 0
     CUtensorMap* mp = &maps[kMapsPerProblem * (size_t)i];
-    st = encode_tensor_2d(&mp[0], a, 2, g.k, g.m, o.lda, 64, g.bm);
-    if (st == G3_OK) st = encode_tensor_2d(&mp[1], b, 2, g.n, g.k, o.ldb, 64, 64);
+    // A: boxes of one 128-byte k-block row x bm rows; B: 128 bytes of n x one k-block
+    st = encode_tensor_2d(&mp[0], a, es, g.k, g.m, o.lda, bk, g.bm);
+    if (st == G3_OK) st = encode_tensor_2d(&mp[1], b, es, g.n, g.k, o.ldb, 128 / es, bk);
     mp[2] = mp[4] = mp[0];
     mp[3] = mp[5] = mp[1];
     const void* p1a = split3 ? a_mid : a_lo;
@@ -366,6 +397,13 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     delete plan;
     return G3_ERR_CUDA;
   }
+  plan->bms.assign(count, -1);
+  plan->kinds.assign(count, -1);
+  for (int i = 0; i < count; ++i)
+    if (ops[i].active) {
+      plan->bms[i] = groups[i].bm;
+      plan->kinds[i] = part_of(descs[i].k);
+    }
   plan->device = dev.device;
   plan->dtype = dtype;
   plan->count = count;
@@ -389,6 +427,22 @@ int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_g
     first += part_tiles[part];
   }
   *out = plan;
+  return G3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** out) {
+  return plan_create(count, descs, dtype, 0, out);
+}
+
+int g3_grouped_plan_describe(const g3_grouped_plan* plan, int index, int* bm, int* kind) {
+  if (!plan) return -101;
+  if (index < 0 || index >= plan->count) return -102;
+  if (bm) *bm = plan->bms[index];
+  if (kind) *kind = plan->kinds[index];
   return G3_OK;
 }
 
@@ -460,6 +514,113 @@ int g3_gemm_grouped(int count, const g3_gemm_desc* descs, int dtype, void* strea
   }
   g3_grouped_plan_destroy(plan);
   return st;
+}
+
+// Per size bucket: a plan of P problems of shape m x n x k (about two waves
+// of 128-row tiles, at most 256 problems and 1 GiB of operands) is timed with
+// every problem on tiles of 64 rows and of 128 rows, each as a CUDA graph of
+// back-to-back plan executions; the faster height is recorded for the bucket.
+int g3_autotune_grouped(int64_t m, int64_t n, int64_t k, int dtype, int* best_bm, double* best_ms) {
+  if (m <= 0) return -101;
+  if (n <= 0) return -102;
+  if (k <= 0) return -103;
+  if (dtype != G3_BF16 && dtype != G3_F32_3XBF16 && dtype != G3_FP8_E4M3) return -104;
+  if (m * k > INT32_MAX || k * n > INT32_MAX || m * n > INT32_MAX) return G3_ERR_UNSUPPORTED;
+  int sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(api_mutex());
+    DeviceInfo dev;
+    const int st = current_device_info(&dev);
+    if (st != G3_OK) return st;
+    sms = dev.sms;
+  }
+  const int es = dtype == G3_F32_3XBF16 ? 4 : (dtype == G3_FP8_E4M3 ? 1 : 2);
+  const int64_t lda = round_up(k, 16), ldb = round_up(n, 16);
+  const size_t a_bytes = align256((size_t)m * lda * es), b_bytes = align256((size_t)k * ldb * es);
+  const size_t c_bytes = align256((size_t)m * n * 4);
+  const size_t per = a_bytes + b_bytes + c_bytes;
+  const long long tiles128 = ((m + 127) / 128) * ((n + 127) / 128);
+  int P = (int)std::min<long long>(256, std::max<long long>(4, (2LL * sms + tiles128 - 1) / tiles128));
+  while (P > 1 && (size_t)P * per > (size_t(1) << 30)) --P;
+  void* buf = nullptr;
+  if (device_alloc(&buf, (size_t)P * per) != cudaSuccess) {
+    cudaGetLastError();
+    return G3_ERR_NOMEM;
+  }
+  cudaMemset(buf, 0x3C, (size_t)P * per);   // small non-zero operands in every format
+  std::vector<g3_gemm_desc> descs(P);
+  for (int i = 0; i < P; ++i) {
+    uint8_t* base = static_cast<uint8_t*>(buf) + (size_t)i * per;
+    g3_gemm_desc& d = descs[i];
+    std::memset(&d, 0, sizeof(d));
+    d.m = m; d.n = n; d.k = k;
+    d.lda = lda; d.ldb = ldb; d.ldc = n;
+    d.alpha = 1.0; d.beta = 0.0;
+    d.A = base; d.B = base + a_bytes; d.C = base + a_bytes + b_bytes;
+    d.scale_a = d.scale_b = 1.0f;
+  }
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = G3_OK;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    st = G3_ERR_CUDA;
+  int best = 0;
+  double best_t = 1e30;
+  for (int bm : {128, 64}) {
+    if (st != G3_OK) break;
+    g3_grouped_plan* plan = nullptr;
+    if (plan_create(P, descs.data(), dtype, bm, &plan) != G3_OK) continue;
+    float ms = 0.f;
+    double t = 1e30;
+    cudaEventRecord(e0, s);
+    const int st0 = g3_grouped_plan_execute(plan, s);
+    cudaEventRecord(e1, s);
+    if (st0 == G3_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+      cudaEventElapsedTime(&ms, e0, e1);
+      const int reps = std::min(64, std::max(4, (int)(2.0 / std::max(ms, 1e-3f))));
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      int sc = G3_OK;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        for (int r = 0; r < reps && sc == G3_OK; ++r) sc = g3_grouped_plan_execute(plan, s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (sc == G3_OK && ce == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess &&
+            cudaGraphLaunch(exec, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess) {
+          for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, s);
+            cudaGraphLaunch(exec, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, (double)ms / reps);
+          }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+      }
+    }
+    cudaGetLastError();
+    g3_grouped_plan_destroy(plan);
+    if (t < best_t) {
+      best_t = t;
+      best = bm;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(buf);
+  cudaGetLastError();
+  if (st != G3_OK) return st;
+  if (best == 0) return G3_ERR_UNSUPPORTED;
+  {
+    std::lock_guard<std::mutex> lock(api_mutex());
+    store_grouped_tuning(m, n, k, dtype, best, best_t);
+  }
+  if (best_bm) *best_bm = best;
+  if (best_ms) *best_ms = best_t;
+  return G3_OK;
 }
 
 }  // extern "C"

@@ -143,6 +143,10 @@ unsigned long long watchdog_timeout_ns();
 bool kernel_timing_enabled();
 void kernel_timing_push(cudaEvent_t e0, cudaEvent_t e1);
 bool take_withhold(unsigned long long* timeout_ns);   // one-shot failure-detection test hook
+// Tile height (64 or 128) g3_autotune_grouped recorded for the size bucket of
+// (m, n, k) and dtype, 0 if none; store one.
+int tuned_grouped_bm(int64_t m, int64_t n, int64_t k, int dtype);
+void store_grouped_tuning(int64_t m, int64_t n, int64_t k, int dtype, int bm, double ms);
 
 // Every device allocation the library makes goes through device_alloc, which
 // counts the successful ones (g3_debug_device_allocations reads the count).

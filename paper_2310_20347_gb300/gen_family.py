@@ -102,7 +102,7 @@ def enumerate_family():
 # Grouped launches: problems of at most 1024 x 1024 take tiles of 64 or 128
 # rows (chosen per problem by the planner's size bucket), so the kernel's
 # buffers are sized for bm_max = 128; one member per mode with the deepest ring.
-GROUPED_MODES = ("bf16", "3xbf16", "6xbf16")
+GROUPED_MODES = ("bf16", "3xbf16", "6xbf16", "fp8")
 GROUPED_BM_MAX = 128
 
 

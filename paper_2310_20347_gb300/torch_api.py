@@ -173,23 +173,31 @@ def device_status():
 
 
 class GroupedPlan:
-    """A g3_grouped_plan over (A, B, C, alpha, beta) tuples of torch tensors.
-    The tensors must stay alive while the plan exists."""
+    """A g3_grouped_plan over (A, B, C, alpha, beta) tuples of torch tensors
+    -- (A, B, C, alpha, beta, scale_a, scale_b) for G3_FP8_E4M3, the scales
+    as Python floats or one-element tensors (read once here).  The tensors
+    must stay alive while the plan exists."""
 
     def __init__(self, problems, dtype):
         in_t = _ELEM[dtype][0]
         descs = []
         self._keep = []
-        for (A, B, C, alpha, beta) in problems:
+        for prob in problems:
+            A, B, C, alpha, beta = prob[:5]
+            sa, sb = (prob[5], prob[6]) if len(prob) > 5 else (1.0, 1.0)
             m, k = A.shape
             n = B.shape[1]
-            if A.dtype != in_t or B.dtype != in_t or C.dtype != torch.float32:
+            ok_in = (A.dtype == in_t or (dtype == G3_FP8_E4M3 and A.dtype == torch.float8_e4m3fn)) and \
+                    (B.dtype == in_t or (dtype == G3_FP8_E4M3 and B.dtype == torch.float8_e4m3fn))
+            if not ok_in or C.dtype != torch.float32:
                 raise TypeError("operand dtypes do not match the plan's dtype")
             d = _lib.g3_gemm_desc()
             d.m, d.n, d.k = m, n, k
             d.lda, d.ldb, d.ldc = _ld(A, "A"), _ld(B, "B"), _ld(C, "C")
             d.alpha, d.beta = float(alpha), float(beta)
             d.A, d.B, d.C = _ptr(A), _ptr(B), _ptr(C)
+            d.scale_a = float(sa.item()) if torch.is_tensor(sa) else float(sa)
+            d.scale_b = float(sb.item()) if torch.is_tensor(sb) else float(sb)
             descs.append(d)
             self._keep.append((A, B, C))
         st, plan = _lib.g3_grouped_plan_create(descs, dtype)

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from gpu_util import SENTINEL, rel_err
-from paper_2310_20347_gb300 import G3_BF16, G3_F32_3XBF16, _lib, synth, torch_api
+from paper_2310_20347_gb300 import G3_BF16, G3_F32_3XBF16, G3_FP8_E4M3, _lib, synth, torch_api
 
 pytestmark = pytest.mark.gpu
 
@@ -157,8 +157,18 @@ def test_grouped_argument_errors():
     bad.A = bad.B = bad.C = 16
     st, plan = _lib.g3_grouped_plan_create([good, good, bad], G3_BF16)
     assert st == -102
-    st, plan = _lib.g3_grouped_plan_create([good], _lib.G3_FP8_E4M3)
+    st, plan = _lib.g3_grouped_plan_create([good], _lib.G3_INT8)
     assert st == _lib.G3_ERR_UNSUPPORTED
+    # FP8 problems need finite, positive scales
+    good.scale_a = good.scale_b = 0.5
+    bad_scale = _lib.g3_gemm_desc()
+    bad_scale.m = bad_scale.n = bad_scale.k = 4
+    bad_scale.lda = bad_scale.ldb = bad_scale.ldc = 4
+    bad_scale.A = bad_scale.B = bad_scale.C = 16
+    for sa in (0.0, -1.0, float("inf"), float("nan")):
+        bad_scale.scale_a, bad_scale.scale_b = sa, 1.0
+        st, plan = _lib.g3_grouped_plan_create([good, bad_scale], G3_FP8_E4M3)
+        assert st == -101, sa
 
 
 def test_grouped_watchdog():
@@ -175,3 +185,99 @@ def test_grouped_watchdog():
     torch.cuda.synchronize()
     check_batch(probs, host, G3_BF16)
     assert torch_api.device_status()[0] == 0
+
+
+def test_grouped_fp8_parity():
+    # FP8 E4M3 problems with per-problem scales (host values): each problem's
+    # operands quantised per tensor by the library; the result equals the
+    # oracle on the decoded codes times the scales (kernel check 1e-5 of
+    # |alpha| |A||B|), and the FP32 masters within the FP8 gate (6e-2 for
+    # k >= 64, the format bound 2 * 2^-4 + 2^-8 below; reading R2).  Every
+    # fourth problem has rows that are not 16-byte multiples (re-packed).
+    shapes = synth.grouped_shapes(48, seed=7, lo=1, hi=400)
+    probs, host = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        p = synth.normal_problem(m, n, k, seed=700 + i, alpha=1.0 if i % 3 else 0.75, beta=0.0 if i % 2 else 0.5)
+        (qa, sa), (qb, sb) = (torch_api.quantize_fp8(torch.from_numpy(x).cuda()) for x in (p.A, p.B))
+        pad = 5 if i % 4 == 0 else 0
+        A = torch.zeros(m, k + pad, dtype=torch.uint8, device="cuda")[:, :k]
+        A.copy_(qa)
+        B = torch.zeros(k, n + pad, dtype=torch.uint8, device="cuda")[:, :n]
+        B.copy_(qb)
+        full = torch.full((m + 2, n + 7), SENTINEL, device="cuda")
+        C = full[1:1 + m, 3:3 + n]
+        if p.C is not None:
+            C.copy_(torch.from_numpy(p.C))
+        probs.append((A, B, C, p.alpha, p.beta, sa, sb))
+        host.append((p, full, qa.cpu().numpy(), float(sa.item()), qb.cpu().numpy(), float(sb.item())))
+    plan = torch_api.GroupedPlan(probs, G3_FP8_E4M3)
+    plan.execute()
+    torch.cuda.synchronize()
+    worst_k = worst_g = 0.0
+    for (A, B, C, *_), (p, full, qa, sa, qb, sb) in zip(probs, host):
+        f = full.cpu().numpy()
+        mask = np.ones(f.shape, bool)
+        mask[1:1 + p.m, 3:3 + p.n] = False
+        assert np.all(f[mask] == np.float32(SENTINEL)), "guard band overwritten"
+        got = C.cpu().numpy()
+        bc = None if p.C is None else p.beta * p.C.astype(np.float64)
+        Ad = oracle.e4m3_decode(qa).astype(np.float64) * sa
+        Bd = oracle.e4m3_decode(qb).astype(np.float64) * sb
+        e_k = rel_err(got, oracle.gemm(Ad, Bd, p.C, p.alpha, p.beta), oracle.absprod(Ad, Bd, p.alpha), bc)
+        e_g = rel_err(got, oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta), oracle.absprod(p.A, p.B, p.alpha), bc)
+        assert e_k <= 1e-5, (p.m, p.n, p.k, "kernel", e_k)
+        assert e_g <= (6e-2 if p.k >= 64 else 2 * 2.0 ** -4 + 2.0 ** -8), (p.m, p.n, p.k, "gate", e_g)
+        worst_k, worst_g = max(worst_k, e_k), max(worst_g, e_g)
+    print(f"grouped fp8: kernel {worst_k:.3e} gate {worst_g:.3e}")
+    plan.close()
+
+
+def _bucket(x):
+    b = 0
+    while (1 << b) < x:
+        b += 1
+    return b
+
+
+def test_grouped_plan_uses_tuned_tile_height(tmp_path):
+    # a tuning record for the bucket of 100 x 300 x 200 BF16 problems asks for
+    # 64-row tiles (the fixed rule would take 128 for m > 64): a plan created
+    # after loading it takes 64 rows for the problems in that bucket only, and
+    # every problem still matches the oracle
+    _lib.g3_tune_cache_clear()
+    rec = tmp_path / "tune.txt"
+    rec.write_text(f"# grouped record\n{100 + G3_BF16} {_bucket(100)} {_bucket(300)} {_bucket(200)} 64 1 0.01\n")
+    assert _lib.g3_tune_cache_load(str(rec)) == 0
+    probs, host = [], []
+    for i, (m, n, k) in enumerate([(100, 300, 200), (120, 260, 150), (200, 300, 200), (90, 70, 40)]):
+        p = synth.uniform_problem(m, n, k, seed=900 + i, alpha=1.0, beta=0.5)
+        A = torch_api.convert_bf16(torch.from_numpy(p.A).cuda())
+        B = torch_api.convert_bf16(torch.from_numpy(p.B).cuda())
+        full = torch.full((m + 2, n + 7), SENTINEL, device="cuda")
+        C = full[1:1 + m, 3:3 + n]
+        C.copy_(torch.from_numpy(p.C))
+        probs.append((A, B, C, p.alpha, p.beta))
+        host.append((p, full))
+    plan = torch_api.GroupedPlan(probs, G3_BF16)
+    heights = [_lib.g3_grouped_plan_describe(plan.plan, i)[1] for i in range(4)]
+    assert heights == [64, 64, 128, 128], heights
+    plan.execute()
+    torch.cuda.synchronize()
+    check_batch(probs, host, G3_BF16)
+    plan.close()
+    _lib.g3_tune_cache_clear()
+
+
+@pytest.mark.parametrize("dtype", [G3_BF16, G3_F32_3XBF16, G3_FP8_E4M3])
+def test_autotune_grouped_records_the_bucket(dtype):
+    _lib.g3_tune_cache_clear()
+    st, bm, ms = _lib.g3_autotune_grouped(150, 400, 300, dtype)
+    assert st == 0 and bm in (64, 128) and ms > 0, (st, bm, ms)
+    A = torch.zeros(150, 300, dtype=torch_api._ELEM[dtype][0], device="cuda")
+    B = torch.zeros(300, 400, dtype=torch_api._ELEM[dtype][0], device="cuda")
+    C = torch.zeros(150, 400, device="cuda")
+    prob = (A, B, C, 1.0, 0.0, 1.0, 1.0) if dtype == G3_FP8_E4M3 else (A, B, C, 1.0, 0.0)
+    plan = torch_api.GroupedPlan([prob], dtype)
+    assert _lib.g3_grouped_plan_describe(plan.plan, 0)[1:] == (bm, 1 if dtype == G3_F32_3XBF16 else 0)
+    plan.close()
+    _lib.g3_tune_cache_clear()
