@@ -273,6 +273,26 @@ def _rotating_graph_ms(calls, nrep):
     return e0.elapsed_time(e1) / nrep
 
 
+def _traffic_floor_ms(lib, read_bytes, write_bytes, nrep=None):
+    """Per-call time of the library's streaming yardstick moving read_bytes in
+    and write_bytes out in the same proportion (g3_stream_traffic), back to
+    back from a CUDA graph over rotating buffers that together exceed 4x L2:
+    the floor of any kernel with that memory traffic."""
+    import torch
+    r16, w16 = -(-int(read_bytes) // 16) * 16, -(-int(write_bytes) // 16) * 16
+    sets = max(2, min(64, -(-(512 << 20) // (r16 + w16))))
+    bufs = [(torch.empty(r16, dtype=torch.uint8, device="cuda"), torch.empty(w16, dtype=torch.uint8, device="cuda"))
+            for _ in range(sets)]
+    calls = [lambda a=a, b=b: lib.g3_stream_traffic(a.data_ptr(), r16, b.data_ptr(), w16,
+                                                    torch.cuda.current_stream().cuda_stream) for a, b in bufs]
+    for c in calls:
+        assert c() == 0
+    torch.cuda.synchronize()
+    ms = _rotating_graph_ms(calls, nrep or max(40, 2 * sets))
+    del bufs
+    return ms
+
+
 def _call_ms(fn, reps, flush):
     """Mean device time of whole calls (all their launches), L2 flushed between."""
     import torch
@@ -458,7 +478,7 @@ def run_workload(args):
         shapes += [(f"b1:{m}x{n}x{k}", m, n, k) for (m, n, k) in synth.IM2COL_BATCH1_EXAMPLES]
         if args.only:
             shapes = [s for s in shapes if s[0] in args.only.split(",")]
-        per, tot_ms, tot_bytes, tot_flops, worst = [], 0.0, 0.0, 0.0, {}
+        per, tot_ms, tot_bytes, tot_flops, worst, tot_floor = [], 0.0, 0.0, 0.0, {}, 0.0
         tuned = {}
         if args.tune:
             # per-shape selection (the paper's Section 8.4 search): time every
@@ -566,14 +586,19 @@ def run_workload(args):
             flops = 2.0 * m * n * k
             st, cfg, sk, rs = _lib.g3_plan_query(m, n, k, {"bf16": G3_BF16, "fp8": G3_FP8_E4M3,
                                                            "int8": G3_INT8}[kind])
+            # the same bytes, in the same read/write proportion, through the
+            # streaming yardstick: the floor of this layer's memory traffic
+            floor_ms = _traffic_floor_ms(_lib, esz * (m * k + k * n), csz * m * n)
             per.append({"shape": name, "m": m, "n": n, "k": k, "ms": ms, "kernel_ms": kms, "cold_call_ms": cold_ms,
                         "rotating_sets": sets,
                         "tflops": flops / ms / 1e9, "gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / hbm,
+                        "traffic_floor_ms": floor_ms, "frac_of_traffic_floor": floor_ms / ms,
                         "member": _lib.g3_family_describe(cfg) if cfg >= 0 else None, "split_k": sk, "err": err})
             if name.startswith("L"):
                 tot_ms += ms
                 tot_bytes += nbytes
                 tot_flops += flops
+                tot_floor += floor_ms
             for kk, v in err.items():
                 worst[kk] = (worst.get(kk, 0.0) if kk != "exact" else True)
                 worst[kk] = (worst[kk] and v) if kk == "exact" else max(worst[kk], v)
@@ -588,8 +613,13 @@ def run_workload(args):
                "l2": "rotating operand copies, together >= 512 MiB (4x L2), per shape; cold_call_ms: one "
                      "call after a 256 MiB L2 flush"},
               {"dtype": kind, "total_ms_20_layers": tot_ms, "worst_err": worst, "autotuned": bool(args.tune),
+               "traffic_floor_ms_20_layers": tot_floor,
                "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                             "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                            "frac_of_traffic_floor": tot_floor / tot_ms,
+                            "traffic_floor": "the 20 layers' bytes, each layer in its own read/write proportion, "
+                                             "through the streaming yardstick (g3_stream_traffic), back to back "
+                                             "from a CUDA graph over rotating buffers",
                             "algorithmic": f"{'1' if kind != 'bf16' else '2'} B per A/B element + 4 B per C "
                                            f"element, summed over the 20 layers"},
                "per_shape": per})
@@ -913,15 +943,18 @@ def _summary(line):
     keep = {"value": line["value"], "unit": line["unit"]}
     rf = line.get("roofline")
     if rf:
-        keep["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac") if k in rf}
-    for k in ("ms", "kernel_ms", "err", "worst_err", "total_ms_20_layers", "grouped_graph_ms", "grouped_kernel_ms",
+        keep["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "frac_of_traffic_floor")
+                            if k in rf}
+    for k in ("ms", "kernel_ms", "err", "worst_err", "total_ms_20_layers", "traffic_floor_ms_20_layers",
+              "grouped_graph_ms", "grouped_kernel_ms",
               "per_call_graph_ms", "per_call_eager_wall_ms", "speedup_vs_eager", "speedup_vs_graph_of_calls",
               "max_rel_err_sampled", "nonfinite_sampled", "total_gflop"):
         if k in line:
             keep[k] = line[k]
     if "per_shape" in line:
         keep["per_shape"] = [{"shape": r["shape"], "us": round(r["ms"] * 1e3, 2), "hbm_frac": round(r["hbm_frac"], 3),
-                              "member": r["member"], "split_k": r["split_k"]} for r in line["per_shape"]]
+                              "floor_us": round(r["traffic_floor_ms"] * 1e3, 2), "member": r["member"],
+                              "split_k": r["split_k"]} for r in line["per_shape"]]
     keep["workload"] = line["config"].get("workload")
     return keep
 

@@ -365,6 +365,18 @@ G3_API int g3_tune_cache_clear(void);
 /* Kernel launches issued by the library since the process started.         */
 G3_API uint64_t g3_launch_count(void);
 
+/* Memory-traffic yardstick (no counterpart in the paper): one streaming
+ * kernel that reads in_bytes from `in` and writes out_bytes to `out` (device
+ * buffers, 16-byte aligned, sizes multiples of 16 and at most 32 GiB), the two streams
+ * interleaved in their own proportion, on `cuda_stream` (NULL = the current
+ * stream).  Timing it gives the rate HBM sustains for a given read/write mix
+ * -- the floor of a memory-bound GEMM with the same mix (on GB300 a stream
+ * with twice as many bytes written as read moves fewer bytes per second than
+ * either alone).  The data written are the data read (or filler where the
+ * write stream is the longer one).  -101..-104: bad in, in_bytes, out,
+ * out_bytes.                                                                */
+G3_API int g3_stream_traffic(const void* in, int64_t in_bytes, void* out, int64_t out_bytes, void* cuda_stream);
+
 /* Device allocations (cudaMalloc calls that succeeded) the library has made
  * since the process started, on all devices: workspace growth, transpose and
  * host-entry buffers, grouped plans and the autotuner's scratch operands.

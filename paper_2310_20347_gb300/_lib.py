@@ -30,7 +30,7 @@ EXPORTED = (
     "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
     "g3_grouped_plan_describe", "g3_autotune_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
-    "g3_plan_query", "g3_launch_count", "g3_debug_device_allocations", "g3_kernel_timing", "g3_kernel_time_ms",
+    "g3_plan_query", "g3_launch_count", "g3_debug_device_allocations", "g3_stream_traffic", "g3_kernel_timing", "g3_kernel_time_ms",
     "g3_debug_withhold_next", "g3_gemm_3xbf16_noalloc",
     "g3_autotune", "g3_tune_cache_save", "g3_tune_cache_load", "g3_tune_cache_clear",
 )
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
                                ctypes.POINTER(i32)], i32),
             "g3_launch_count": ([], ctypes.c_uint64),
             "g3_debug_device_allocations": ([], ctypes.c_int64),
+            "g3_stream_traffic": ([vp, i64, vp, i64, vp], i32),
             "g3_kernel_timing": ([i32], i32),
             "g3_kernel_time_ms": ([ctypes.POINTER(dbl), ctypes.POINTER(i32), i32], i32),
             "g3_debug_withhold_next": ([i64], i32),
@@ -253,6 +254,10 @@ def g3_launch_count() -> int:
 
 def g3_debug_device_allocations() -> int:
     return int(load().g3_debug_device_allocations())
+
+
+def g3_stream_traffic(in_ptr, in_bytes, out_ptr, out_bytes, stream=None) -> int:
+    return load().g3_stream_traffic(in_ptr, in_bytes, out_ptr, out_bytes, stream)
 
 
 def g3_kernel_timing(enable: bool) -> int:

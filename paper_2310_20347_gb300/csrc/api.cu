@@ -1500,6 +1500,28 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
 
 uint64_t g3_launch_count(void) { return g3::launch_count(); }
 
+int g3_stream_traffic(const void* in, int64_t in_bytes, void* out, int64_t out_bytes, void* stream) {
+  // at most 32 GiB per stream, so that the interleave products fit 64 bits
+  if (in_bytes < 0 || in_bytes % 16 || in_bytes > (int64_t(1) << 35)) return -102;
+  if (out_bytes < 0 || out_bytes % 16 || out_bytes > (int64_t(1) << 35)) return -104;
+  if (in_bytes > 0 && (!in || reinterpret_cast<uintptr_t>(in) % 16)) return -101;
+  if (out_bytes > 0 && (!out || reinterpret_cast<uintptr_t>(out) % 16)) return -103;
+  int sms = 152;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    DevState* d = nullptr;
+    const int st = ensure_device(&d);
+    if (st != G3_OK) return st;
+    sms = d->sms;
+  }
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g_stream;
+  if (launch_stream_traffic(in, in_bytes / 16, out, out_bytes / 16, sms, s) != cudaSuccess) {
+    cudaGetLastError();
+    return G3_ERR_CUDA;
+  }
+  return G3_OK;
+}
+
 int64_t g3_debug_device_allocations(void) { return g3::g_device_allocs.load(std::memory_order_relaxed); }
 
 int g3_debug_withhold_next(int64_t timeout_ms) {

@@ -125,6 +125,8 @@ struct SkFixup {
   bool is_int;
 };
 cudaError_t launch_streamk_fixup(const SkFixup& f, cudaStream_t s);
+cudaError_t launch_stream_traffic(const void* in, long long in_units, void* out, long long out_units, int sms,
+                                  cudaStream_t s);
 
 // Number of kernel launches the library has issued (all translation units).
 void count_launch(int n = 1);

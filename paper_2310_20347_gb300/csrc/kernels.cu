@@ -370,6 +370,40 @@ __global__ void __launch_bounds__(kFixupThreads) streamk_fixup_kernel(const SkFi
   }
 }
 
+// Memory-traffic yardstick: reads nin and writes nout 16-byte units, the two
+// streams interleaved in their proportion (Bresenham: slot j of the longer
+// stream carries one unit of the shorter one whenever floor(j * short / long)
+// steps), consecutive slots on consecutive threads, streaming cache hints.
+// The written data depend on the loads, so no load can be dropped.
+__global__ void __launch_bounds__(256) stream_traffic_kernel(const uint4* __restrict__ in, long long nin,
+                                                             uint4* __restrict__ out, long long nout) {
+  const long long N = nin > nout ? nin : nout;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride) {
+    if (nin >= nout) {
+      const uint4 v = __ldcs(in + j);
+      const long long k0 = j * nout / nin, k1 = (j + 1) * nout / nin;
+      if (k1 > k0) __stcs(out + k0, v);
+    } else {
+      uint4 v = make_uint4((unsigned)j, 0u, 0u, 0u);
+      const long long k0 = j * nin / nout, k1 = (j + 1) * nin / nout;
+      if (k1 > k0) v = __ldcs(in + k0);
+      __stcs(out + j, v);
+    }
+  }
+}
+
+cudaError_t launch_stream_traffic(const void* in, long long in_units, void* out, long long out_units, int sms,
+                                  cudaStream_t s) {
+  const long long n = std::max(in_units, out_units);
+  if (n == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, (long long)sms * 8);
+  stream_traffic_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint4*>(in), in_units,
+                                                          static_cast<uint4*>(out), out_units);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_streamk_fixup(const SkFixup& f, cudaStream_t s) {
   if (f.tail <= 0) return cudaSuccess;
   if (f.streams > kFixupMaxStreams || f.bn % 4 != 0) return cudaErrorInvalidValue;

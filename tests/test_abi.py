@@ -261,3 +261,16 @@ def test_planner_thread_safe(lib):
     for th in threads:
         th.join()
     assert not errors, errors[:5]
+
+
+def test_stream_traffic_argument_errors(lib):
+    # sizes must be non-negative multiples of 16 bytes (at most 32 GiB), and
+    # pointers 16-byte aligned when their size is non-zero; checked before any
+    # device work
+    assert lib.g3_stream_traffic(16, 17, 16, 16) == -102
+    assert lib.g3_stream_traffic(16, -16, 16, 16) == -102
+    assert lib.g3_stream_traffic(16, 1 << 36, 16, 16) == -102
+    assert lib.g3_stream_traffic(16, 16, 16, 24) == -104
+    assert lib.g3_stream_traffic(None, 16, 16, 16) == -101
+    assert lib.g3_stream_traffic(8, 16, 16, 16) == -101
+    assert lib.g3_stream_traffic(16, 16, None, 16) == -103

@@ -60,3 +60,25 @@ def test_graph_replay_matches_eager(dtype, shape):
         graph.replay()
         torch.cuda.synchronize()
         assert torch.equal(C, eager), dtype
+
+
+@pytest.mark.gpu
+def test_stream_traffic_yardstick_moves_the_data():
+    # the streaming yardstick of the benchmark's traffic floors: with equal
+    # sizes it copies; with twice as many bytes out, every second 16-byte unit
+    # carries the next input unit (the others are filler); with half, every
+    # second input unit is written
+    from paper_2310_20347_gb300 import _lib
+    x = torch.arange(1 << 16, dtype=torch.int32, device="cuda")
+    y = torch.zeros_like(x)
+    assert _lib.g3_stream_traffic(x.data_ptr(), x.numel() * 4, y.data_ptr(), y.numel() * 4) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+    y2 = torch.zeros(2 * x.numel(), dtype=torch.int32, device="cuda")
+    assert _lib.g3_stream_traffic(x.data_ptr(), x.numel() * 4, y2.data_ptr(), y2.numel() * 4) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(y2.view(-1, 2, 4)[:, 1, :].reshape(-1), x)
+    y3 = torch.zeros(x.numel() // 2, dtype=torch.int32, device="cuda")
+    assert _lib.g3_stream_traffic(x.data_ptr(), x.numel() * 4, y3.data_ptr(), y3.numel() * 4) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(y3.view(-1, 4), x.view(-1, 2, 4)[:, 1, :])
