@@ -372,9 +372,8 @@ G3_API uint64_t g3_launch_count(void);
  * stream).  Timing it gives the rate HBM sustains for a given read/write mix
  * -- the floor of a memory-bound GEMM with the same mix (on GB300 a stream
  * with twice as many bytes written as read moves fewer bytes per second than
- * either alone).  The data written are the data read (or filler where the
- * write stream is the longer one).  -101..-104: bad in, in_bytes, out,
- * out_bytes.                                                                */
+ * either alone).  The data written are filler; `in` is only read.
+ * -101..-104: bad in, in_bytes, out, out_bytes.                             */
 G3_API int g3_stream_traffic(const void* in, int64_t in_bytes, void* out, int64_t out_bytes, void* cuda_stream);
 
 /* Device allocations (cudaMalloc calls that succeeded) the library has made

@@ -211,6 +211,23 @@ int encode_c_2d(CUtensorMap* map, void* base, bool is_int, uint64_t n, uint64_t 
   return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
 }
 
+// The split-K partial planes (splits x m rows x n columns of 4-byte elements,
+// row stride ldp, plane stride m * ldp) for TMA stores of 32-row x
+// 128-column boxes into plane z; a box is clipped at its plane's edges.
+int encode_partial_3d(CUtensorMap* map, void* base, bool is_int, uint64_t n, uint64_t m, uint64_t splits,
+                      uint64_t ldp) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return G3_ERR_CUDA;
+  cuuint64_t dims[3] = {n, m, splits};
+  cuuint64_t strides[2] = {ldp * 4, m * ldp * 4};
+  cuuint32_t box[3] = {128, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, is_int ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
+}
+
 bool tma_ok(const void* p, int64_t ld, int esize) {
   return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((ld * esize) % 16 == 0);
 }
@@ -532,7 +549,8 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl, bool b_prepared = fals
     default:
       break;
   }
-  if (a.dtype != G3_F32 && pl.splits > 1) L.partial = take((size_t)pl.splits * m * n * 4);
+  // split-K partial planes: rows padded to whole 128-byte lines
+  if (a.dtype != G3_F32 && pl.splits > 1) L.partial = take((size_t)pl.splits * m * round_up(n, 32) * 4);
   if (a.dtype != G3_F32 && pl.sk_streams > 0) {
     const FamilyEntry& f = g_family[pl.member];
     L.partial = take((size_t)pl.sk_streams * pl.sk_segs * f.bm * 128 * f.cg * 4);
@@ -876,6 +894,9 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   if (pl.splits > 1) {
     p.out_mode = OUT_PARTIAL;
     p.partial = reinterpret_cast<float*>(ws + L.partial);
+    p.ldp = round_up(n, 32);
+    // partial tiles leave through TMA stores into their split's plane
+    if (encode_partial_3d(&maps[6], p.partial, is_int, n, m, pl.splits, p.ldp) == G3_OK) p.c_tma = 1;
   } else {
     p.out_mode = is_int ? OUT_I32 : OUT_F32;
     // C without a read of its old values goes out through TMA stores when its
@@ -896,8 +917,8 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
       // is not possible on the host, so FP8 never splits (see make_plan callers)
       return G3_ERR_UNSUPPORTED;
     }
-    G3_CHECK_CUDA(launch_splitk_reduce(p.partial, pl.splits, (int)m, (int)n, alpha, (float)a.beta, a.C, a.ldc,
-                                       is_int, s));
+    G3_CHECK_CUDA(launch_splitk_reduce(p.partial, pl.splits, (int)m, (int)n, p.ldp, alpha, (float)a.beta, a.C,
+                                       a.ldc, is_int, s));
   }
   if (pl.sk_streams > 0) {
     SkFixup fx;

@@ -106,8 +106,8 @@ cudaError_t launch_pack_rows(const void* x, int rows, long long row_bytes, long 
 cudaError_t launch_quantize_e4m3(const float* x, int rows, int cols, long long ldx, unsigned int* amax_bits,
                                  uint8_t* q, long long ldq, float* scale, cudaStream_t s);
 cudaError_t launch_scale_c(void* C, bool is_int, int rows, int cols, long long ldc, float beta, cudaStream_t s);
-cudaError_t launch_splitk_reduce(const float* P, int splits, int rows, int cols, float alpha, float beta, void* C,
-                                 long long ldc, bool is_int, cudaStream_t s);
+cudaError_t launch_splitk_reduce(const float* P, int splits, int rows, int cols, long long ldp, float alpha,
+                                 float beta, void* C, long long ldc, bool is_int, cudaStream_t s);
 
 // Stream-K fix-up: for each of the `tail` last tiles of the walk (sched.cuh),
 // the sum of its segments' partial tiles in stream order, then

@@ -430,24 +430,62 @@ __global__ void scale_c_kernel(TC* __restrict__ C, int rows, int cols, long long
 // Deterministic split-K reduction: partial sums are added in split order 0..S-1.
 // INT: the partial planes hold int32 values (the exact-integer kernel writes
 // them as such); they are summed in int32, then C (beta in {0, 1}) is added.
-template <bool INT>
-__global__ void splitk_reduce_kernel(const float* __restrict__ P, int splits, int rows, int cols, float alpha,
-                                     float beta, void* C, long long ldc) {
-  const long long plane = (long long)rows * cols;
+// Plane s holds rows of ldp elements (whole 128-byte lines).  Each thread
+// takes 4 consecutive columns of a row; VEC: 16-byte loads of the partials
+// and 16-byte accesses of C (columns beyond the last full group of 4 one by
+// one).
+template <bool INT, bool VEC>
+__global__ void splitk_reduce_kernel(const float* __restrict__ P, int splits, int rows, int cols, long long ldp,
+                                     float alpha, float beta, void* C, long long ldc) {
+  const long long plane = (long long)rows * ldp;
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
-      const long long off = (long long)r * cols + c;
-      if (INT) {
-        int s32 = 0;
-        const int* Pi = reinterpret_cast<const int*>(P);
-        for (int s = 0; s < splits; ++s) s32 += Pi[s * plane + off];
-        int* cp = static_cast<int*>(C) + r * ldc + c;
-        *cp = (beta != 0.f) ? (*cp + s32) : s32;
-      } else {
-        float sum = 0.f;
-        for (int s = 0; s < splits; ++s) sum += P[s * plane + off];
-        float* cp = static_cast<float*>(C) + r * ldc + c;
-        *cp = (beta != 0.f) ? fmaf(alpha, sum, beta * *cp) : alpha * sum;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < cols; c += gridDim.x * blockDim.x * 4) {
+      const long long off = (long long)r * ldp + c;
+      if (VEC && c + 4 <= cols) {
+        if (INT) {
+          int4 acc = make_int4(0, 0, 0, 0);
+          for (int s = 0; s < splits; ++s) {
+            const int4 v = *reinterpret_cast<const int4*>(reinterpret_cast<const int*>(P) + s * plane + off);
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+          }
+          int4* cp = reinterpret_cast<int4*>(static_cast<int*>(C) + r * ldc + c);
+          if (beta != 0.f) {
+            const int4 o = *cp;
+            acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
+          }
+          *cp = acc;
+        } else {
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int s = 0; s < splits; ++s) {
+            const float4 v = *reinterpret_cast<const float4*>(P + s * plane + off);
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+          }
+          float4* cp = reinterpret_cast<float4*>(static_cast<float*>(C) + r * ldc + c);
+          if (beta != 0.f) {
+            const float4 o = *cp;
+            acc = make_float4(fmaf(alpha, acc.x, beta * o.x), fmaf(alpha, acc.y, beta * o.y),
+                              fmaf(alpha, acc.z, beta * o.z), fmaf(alpha, acc.w, beta * o.w));
+          } else {
+            acc = make_float4(alpha * acc.x, alpha * acc.y, alpha * acc.z, alpha * acc.w);
+          }
+          *cp = acc;
+        }
+        continue;
+      }
+      for (int u = c; u < c + 4 && u < cols; ++u) {
+        const long long o = (long long)r * ldp + u;
+        if (INT) {
+          int s32 = 0;
+          const int* Pi = reinterpret_cast<const int*>(P);
+          for (int s = 0; s < splits; ++s) s32 += Pi[s * plane + o];
+          int* cp = static_cast<int*>(C) + r * ldc + u;
+          *cp = (beta != 0.f) ? (*cp + s32) : s32;
+        } else {
+          float sum = 0.f;
+          for (int s = 0; s < splits; ++s) sum += P[s * plane + o];
+          float* cp = static_cast<float*>(C) + r * ldc + u;
+          *cp = (beta != 0.f) ? fmaf(alpha, sum, beta * *cp) : alpha * sum;
+        }
       }
     }
   }

@@ -92,13 +92,15 @@ struct TcParams {
   const float* scale_b;
   void* C;                // float (OUT_F32) or int32 (OUT_I32)
   long long ldc;
-  float* partial;         // OUT_PARTIAL: [splits][m][n] float; stream-K: [sk_streams * sk_segs] tiles
+  float* partial;         // OUT_PARTIAL: [splits][m][ldp] float; stream-K: [sk_streams * sk_segs] tiles
+  long long ldp;          // OUT_PARTIAL: row stride of the partial planes (elements, rows on 128-byte lines)
   int out_mode;
   unsigned long long timeout_ns;
   int* status;
   int debug_withhold;     // test hook: producer iteration whose stage never fills (-1: none)
   int kchunk;             // k-blocks per accumulation chunk (0: the whole k range of a tile)
-  int c_tma;              // 1: C (beta == 0) is written through TMA stores with the tmC map
+  int c_tma;              // 1: C (beta == 0) -- or, with split-K, the partial planes -- is written through
+                          // TMA stores with the tmC map (3-D for the partial planes: n x m x splits)
   // Implicit-GEMM convolution (conv = 1): A is the NHWC activation tensor read
   // through an im2col tensor map; row i of A is output pixel i = (n, p, q) and
   // k-block kb is filter tap (r, s) = divmod(kb / cblocks, S), channel block
@@ -223,8 +225,9 @@ struct EpiJob {
   // (split-K: this split's m x n plane, ldp = n; stream-K: a bm x 128*CG slot,
   // addressed through a base shifted back by the tile's origin)
   float* partial;
-  const CUtensorMap* cmap;    // non-null: store C (beta == 0) by TMA through this map
+  const CUtensorMap* cmap;    // non-null: store C (beta == 0) or the partial tile by TMA through this map
   long long ldp;
+  int cz;                     // >= 0: cmap is 3-D (split-K partial planes) and this is the tile's plane
 };
 
 // Stream-K work item u (>= 0) of the tail: segment u / streams of stream
@@ -289,10 +292,12 @@ struct SingleSched {
       const uintptr_t slot = reinterpret_cast<uintptr_t>(p->partial + (long long)j.split * (BM_T * ldp));
       const long long origin = (long long)j.m0 * ldp + (j.n0 - n_off);   // the slot holds elements from here on
       return EpiJob{p->C, p->ldc, p->m, p->n, p->alpha, p->beta, OUT_PARTIAL,
-                    reinterpret_cast<float*>(slot - (uintptr_t)origin * sizeof(float)), nullptr, ldp};
+                    reinterpret_cast<float*>(slot - (uintptr_t)origin * sizeof(float)), nullptr, ldp, -1};
     }
+    const bool part = p->out_mode == OUT_PARTIAL;
     return EpiJob{p->C, p->ldc, p->m, p->n, p->alpha, p->beta, p->out_mode,
-                  p->partial ? p->partial + (long long)j.split * p->m * p->n : nullptr, cmap, p->n};
+                  part ? p->partial + (long long)j.split * p->m * p->ldp : nullptr, cmap, p->ldp,
+                  part ? j.split : -1};
   }
 
   __device__ __forceinline__ bool conv() const { return p->conv != 0; }
@@ -334,7 +339,7 @@ struct GroupedSched {
 
   __device__ __forceinline__ EpiJob epi(const TileJob& j) const {
     const GroupDesc* d = gp->groups + j.g;
-    return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr, nullptr, 0};
+    return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr, nullptr, 0, -1};
   }
 
   __device__ __forceinline__ bool conv() const { return false; }
@@ -594,11 +599,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       const int nchunks = (rows_here + 31) >> 5;
       const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
       const int nkc = (j.kb1 - j.kb0 + span - 1) / span;
-      // Outputs that do not read C leave through shared memory and TMA stores
-      // (whole 32 x 128 boxes, clipped to C by the tensor map).
+      // Outputs that do not read C -- C with beta == 0, or a split's partial
+      // tile -- leave through shared memory and TMA stores (whole 32 x 128
+      // boxes, clipped to C or to the split's plane by the tensor map).
       // (staging assumes the four epilogue warps cover the same rows)
-      const bool use_tma = e.cmap != nullptr && beta == 0.0f && (e.out_mode == OUT_F32 || e.out_mode == OUT_I32) &&
-                           Cfg::kEpiWarps == 4;
+      const bool use_tma = e.cmap != nullptr && Cfg::kEpiWarps == 4 &&
+                           (e.out_mode == OUT_PARTIAL || (beta == 0.0f && (e.out_mode == OUT_F32 || e.out_mode == OUT_I32)));
       const int r0 = ((warp - 2) >> 2) * Cfg::kEpiRows;   // first tile row of this thread's rows
       // stage_begin: a free staging buffer (the store issued from it two chunks
       // ago has read it); this thread's column of the 32 rows goes to
@@ -612,7 +618,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
         fence_proxy_async_smem();
         named_barrier_sync(1, 128);
         if (threadIdx.x == 64) {
-          tma_store_2d(e.cmap, j.n0, j.m0 + c * 32, cstage + (schunk & 1u) * (32 * 128));
+          if (e.cz >= 0) tma_store_3d(e.cmap, j.n0, j.m0 + c * 32, e.cz, cstage + (schunk & 1u) * (32 * 128));
+          else tma_store_2d(e.cmap, j.n0, j.m0 + c * 32, cstage + (schunk & 1u) * (32 * 128));
           bulk_commit_group();
         }
         ++schunk;
@@ -723,6 +730,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           if (e.out_mode == OUT_I32) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) buf[i * 128] = __int_as_float(__float2int_rn(__uint_as_float(r[i])));
+          } else if (e.out_mode == OUT_PARTIAL) {   // the raw sum: alpha is applied by the reduction
+#pragma unroll
+            for (int i = 0; i < 32; ++i) buf[i * 128] = __uint_as_float(r[i]);
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i) buf[i * 128] = alpha * __uint_as_float(r[i]);

@@ -63,22 +63,40 @@ def test_graph_replay_matches_eager(dtype, shape):
 
 
 @pytest.mark.gpu
-def test_stream_traffic_yardstick_moves_the_data():
-    # the streaming yardstick of the benchmark's traffic floors: with equal
-    # sizes it copies; with twice as many bytes out, every second 16-byte unit
-    # carries the next input unit (the others are filler); with half, every
-    # second input unit is written
+def test_stream_traffic_yardstick_covers_its_output():
+    # the streaming yardstick of the benchmark's traffic floors writes every
+    # 16-byte unit of its output (filler) for several read/write proportions,
+    # leaves its input and the bytes past its output untouched, and moves
+    # bytes at a rate comparable to a plain device copy for a 1:1 mix
     from paper_2310_20347_gb300 import _lib
-    x = torch.arange(1 << 16, dtype=torch.int32, device="cuda")
-    y = torch.zeros_like(x)
-    assert _lib.g3_stream_traffic(x.data_ptr(), x.numel() * 4, y.data_ptr(), y.numel() * 4) == 0
+    x = torch.arange(1 << 20, dtype=torch.int32, device="cuda")
+    x0 = x.clone()
+    for out_units in (1, 511, 512, 513, 4096, 65536, 1 << 18, 1 << 20):
+        y = torch.zeros(4 * out_units + 8, dtype=torch.int32, device="cuda")
+        assert _lib.g3_stream_traffic(x.data_ptr(), x.numel() * 4, y.data_ptr(), out_units * 16) == 0
+        torch.cuda.synchronize()
+        head = y[:4 * out_units].view(-1, 4)
+        assert bool((head[:, 2] == 0).all() and (head[:, 3] == 0).all())
+        # filler (chunk + 1, thread + 1, 0, 0): every unit was written (y was zero)
+        assert bool((head[:, 0] > 0).all() and (head[:, 1] > 0).all())
+        assert bool((y[4 * out_units:] == 0).all())
+    assert torch.equal(x, x0)
+    big = torch.empty(1 << 28, dtype=torch.uint8, device="cuda")
+    big2 = torch.empty_like(big)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _lib.g3_stream_traffic(big.data_ptr(), big.numel(), big2.data_ptr(), big2.numel())
+    e0.record()
+    for _ in range(5):
+        _lib.g3_stream_traffic(big.data_ptr(), big.numel(), big2.data_ptr(), big2.numel())
+    e1.record()
     torch.cuda.synchronize()
-    assert torch.equal(x, y)
-    y2 = torch.zeros(2 * x.numel(), dtype=torch.int32, device="cuda")
-    assert _lib.g3_stream_traffic(x.data_ptr(), x.numel() * 4, y2.data_ptr(), y2.numel() * 4) == 0
+    t_y = e0.elapsed_time(e1) / 5
+    big2.copy_(big)
+    e0.record()
+    for _ in range(5):
+        big2.copy_(big)
+    e1.record()
     torch.cuda.synchronize()
-    assert torch.equal(y2.view(-1, 2, 4)[:, 1, :].reshape(-1), x)
-    y3 = torch.zeros(x.numel() // 2, dtype=torch.int32, device="cuda")
-    assert _lib.g3_stream_traffic(x.data_ptr(), x.numel() * 4, y3.data_ptr(), y3.numel() * 4) == 0
-    torch.cuda.synchronize()
-    assert torch.equal(y3.view(-1, 4), x.view(-1, 2, 4)[:, 1, :])
+    t_c = e0.elapsed_time(e1) / 5
+    print(f"yardstick 1:1 {2 * big.numel() / t_y / 1e6:.0f} GB/s, torch copy {2 * big.numel() / t_c / 1e6:.0f} GB/s")
+    assert t_y < 1.5 * t_c

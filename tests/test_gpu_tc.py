@@ -540,3 +540,29 @@ def test_3xbf16_deep_k_within_gate():
     st, cfg, sk, _ = _lib.g3_plan_query(128, 160, 65536, G3_F32_3XBF16)
     assert sk >= 2
     x3_check(synth.uniform_problem(128, 160, 65536, seed=80, beta=0.5))
+
+
+@pytest.mark.parametrize("split", [2, 3, 5])
+def test_split_k_partial_planes_ragged_rows(split):
+    # split-K partial tiles leave through TMA stores into their split's plane
+    # (a 3-D map: n x m x splits, rows padded to 128-byte lines); with m = 200
+    # the second tile row (rows 128..255) is clipped at row 200 of its own
+    # plane and must not spill into the next split's plane; n = 300 is not a
+    # multiple of 32 (padded rows)
+    bf16_check(synth.uniform_problem(200, 300, 3000, seed=40 + split, alpha=0.75, beta=0.0), split_k=split)
+    bf16_check(synth.uniform_problem(200, 300, 3000, seed=50 + split, alpha=0.75, beta=-0.5), split_k=split)
+
+
+@pytest.mark.parametrize("shape,beta,split", [((300, 129, 4100), 0, 3), ((257, 520, 3000), 1, 2),
+                                              ((200, 300, 2048), 0, 5)])
+@pytest.mark.parametrize("config", [f["index"] for f in FAMILY if f["mode"] == "int8emu" and f["bm"] == 128])
+def test_int8_bm128_split_k(config, shape, beta, split):
+    # int32 split-K partials of the bm = 128 members (TMA stores into an
+    # int32 3-D map), summed in int32 by the reduction: bit-exact
+    m, n, k = shape
+    p = synth.int8_problem(m, n, k, seed=26, beta=beta)
+    full, C = guarded(m, n, p.C, dtype=torch.int32)
+    torch_api.gemm(dev(p.A), dev(p.B), C, 1, beta, dtype=G3_INT8, config=config, split_k=split)
+    torch.cuda.synchronize()
+    check_guard(full, m, n)
+    assert np.array_equal(C.cpu().numpy().astype(np.int64), oracle.gemm_i8(p.A, p.B, p.C, 1, beta))
