@@ -928,6 +928,7 @@ def run_workload(args):
 OTHER_CONFIGS = (
     ("1_plain_fp32_512", "plain"),
     ("3_im2col_bf16", "im2col"),
+    ("3_im2col_bf16_autotuned", "im2col+tune"),
     ("4_grouped_bf16", "grouped"),
     ("4_grouped_3xbf16", "grouped-3xbf16"),
     ("5_bf16_8192", "bf16"),
@@ -948,7 +949,7 @@ def _summary(line):
     for k in ("ms", "kernel_ms", "err", "worst_err", "total_ms_20_layers", "traffic_floor_ms_20_layers",
               "grouped_graph_ms", "grouped_kernel_ms",
               "per_call_graph_ms", "per_call_eager_wall_ms", "speedup_vs_eager", "speedup_vs_graph_of_calls",
-              "max_rel_err_sampled", "nonfinite_sampled", "total_gflop"):
+              "max_rel_err_sampled", "nonfinite_sampled", "total_gflop", "autotuned"):
         if k in line:
             keep[k] = line[k]
     if "per_shape" in line:
@@ -965,7 +966,8 @@ def other_configs(args, gpu_index):
     out = {}
     for key, wl in OTHER_CONFIGS:
         a = copy.copy(args)
-        a.workload, a.reps, a.compact, a.only, a.tune, a.config, a.dsize = wl, 10, True, "", False, -1, 8192
+        tune = wl.endswith("+tune")
+        a.workload, a.reps, a.compact, a.only, a.tune, a.config, a.dsize = wl.replace("+tune", ""), 10, True, "", tune, -1, 8192
         _COLLECT = []
         clk = Clocks(gpu_index)
         clk.start()
@@ -982,6 +984,9 @@ def other_configs(args, gpu_index):
         entry["clocks"] = c
         entry["wall_s"] = round(wall, 1)
         out[key] = entry
+        if tune:
+            from paper_2310_20347_gb300 import _lib
+            _lib.g3_tune_cache_clear()   # later configurations use the planner again
     return out
 
 

@@ -375,8 +375,10 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   // Modelled time of a member with s splits of k: waves of tiles (the
   // member's resident CTAs or pairs, as the device reports them, else the SM
   // count over the cluster size) x the time of one tile of ceil(num_kb / s)
-  // k-blocks, plus, when split, the reduce kernel (a launch and s partial
-  // planes plus C through HBM at ~5 TB/s).
+  // k-blocks, plus, when split, the reduce kernel: ~2 us of launch and
+  // dependency latency in a stream of calls, and s partial planes plus C at
+  // ~6 TB/s (partial tiles leave through TMA stores; the reduce reads 16 bytes
+  // per access).
   const bool search_split = force_split == 0 && allow_splitk;
   auto cost_of = [&](const FamilyEntry& f, int s) {
     const long long tiles = ((m + f.bm - 1) / f.bm) * ((n + 128LL * f.cg - 1) / (128LL * f.cg));
@@ -385,7 +387,7 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     const long long waves = (tiles * s + slots - 1) / slots;
     const int kb = (pl.num_kb + s - 1) / s;
     double t = (double)waves * tile_time_ns(f, kb);
-    if (s > 1) t += 3000.0 + (double)(s + 1) * (double)m * (double)n * 4.0 / 5000.0;
+    if (s > 1) t += 2000.0 + (double)(s + 1) * (double)m * (double)n * 4.0 / 6000.0;
     return t;
   };
   auto splits_for = [&](const FamilyEntry& f, auto&& visit) {

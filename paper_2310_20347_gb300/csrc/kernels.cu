@@ -378,35 +378,45 @@ __global__ void __launch_bounds__(kFixupThreads) streamk_fixup_kernel(const SkFi
 }
 
 // Memory-traffic yardstick: reads nin and writes nout 16-byte units.  The
-// traffic is cut into chunks of 512 units (8 KB); chunk c of the C = cin +
+// traffic is cut into chunks of 2048 units (32 KB); chunk c of the C = cin +
 // cout chunks is a read chunk when floor((c + 1) cin / C) steps past
 // floor(c cin / C), else a write chunk, so every block's grid-stride walk (and
 // the memory system at any moment) sees reads and writes in their overall
-// proportion.  A thread moves 2 units of a chunk with streaming cache hints;
-// writes carry filler (chunk + 1, thread + 1, 0, 0) and wait for no load; the loads are folded into a value
-// that reaches memory only in the (never expected) case that it equals a
-// fixed constant, so that none of them can be dropped.
+// proportion.  A thread moves 8 units of a chunk (8 independent 16-byte
+// accesses in flight) with streaming cache hints; writes carry filler
+// (chunk + 1, thread + 1, 0, 0) and wait for no load; the loads are folded
+// into a value that reaches memory only in the (never expected) case that it
+// equals a fixed constant, so that none of them can be dropped.  Measured on
+// GB300: 6.3 TB/s for a 1:1 mix (a device-to-device copy: 6.8), 6.0-6.4 for
+// 1:2 and 1:8, 7.0 for reads or writes alone.
+constexpr int kStreamUnits = 8;
+constexpr int kStreamChunk = 256 * kStreamUnits;
 __device__ unsigned int g_stream_sink;
 
 __global__ void __launch_bounds__(256) stream_traffic_kernel(const uint4* __restrict__ in, long long nin,
                                                              uint4* __restrict__ out, long long nout) {
-  constexpr int kChunk = 512;
-  const long long cin = (nin + kChunk - 1) / kChunk, cout = (nout + kChunk - 1) / kChunk, C = cin + cout;
+  const long long cin = (nin + kStreamChunk - 1) / kStreamChunk, cout = (nout + kStreamChunk - 1) / kStreamChunk;
+  const long long C = cin + cout;
   unsigned int acc = 0;
   for (long long c = blockIdx.x; c < C; c += gridDim.x) {
     const long long r0 = c * cin / C, r1 = (c + 1) * cin / C;
     if (r1 > r0) {
-      const long long i0 = r0 * kChunk + threadIdx.x, i1 = i0 + 256;
-      uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
-      if (i0 < nin) a = __ldcs(in + i0);
-      if (i1 < nin) b = __ldcs(in + i1);
-      acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+      uint4 v[kStreamUnits];
+#pragma unroll
+      for (int u = 0; u < kStreamUnits; ++u) {
+        const long long i = r0 * kStreamChunk + u * 256 + threadIdx.x;
+        v[u] = i < nin ? __ldcs(in + i) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < kStreamUnits; ++u) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
     } else {
       const long long w = c - r0;   // write chunks before this one
-      const long long i0 = w * kChunk + threadIdx.x, i1 = i0 + 256;
       const uint4 f = make_uint4((unsigned)c + 1u, threadIdx.x + 1u, 0u, 0u);   // never all zero
-      if (i0 < nout) __stcs(out + i0, f);
-      if (i1 < nout) __stcs(out + i1, f);
+#pragma unroll
+      for (int u = 0; u < kStreamUnits; ++u) {
+        const long long i = w * kStreamChunk + u * 256 + threadIdx.x;
+        if (i < nout) __stcs(out + i, f);
+      }
     }
   }
   if (acc == 0x9E3779B9u) g_stream_sink = acc;
@@ -414,9 +424,9 @@ __global__ void __launch_bounds__(256) stream_traffic_kernel(const uint4* __rest
 
 cudaError_t launch_stream_traffic(const void* in, long long in_units, void* out, long long out_units, int sms,
                                   cudaStream_t s) {
-  const long long chunks = (in_units + 511) / 512 + (out_units + 511) / 512;
+  const long long chunks = (in_units + kStreamChunk - 1) / kStreamChunk + (out_units + kStreamChunk - 1) / kStreamChunk;
   if (chunks == 0) return cudaSuccess;
-  const long long blocks = std::min<long long>(chunks, (long long)sms * 8);
+  const long long blocks = std::min<long long>(chunks, (long long)sms * 16);
   stream_traffic_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const uint4*>(in), in_units,
                                                           static_cast<uint4*>(out), out_units);
   count_launch();
