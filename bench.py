@@ -393,6 +393,34 @@ def run_workload(args):
                                 "kind": "oracle", "sample": f"the whole 512^3 product in binary64, {cpu_s:.3f} s"}})
         return
 
+    if args.workload == "simt":
+        # the plain method alone at m = n = k = dsize (uniform [-1, 1], seed 0,
+        # beta 0): the FP32 SIMT kernel on the CUDA cores, L2 flushed between calls
+        n = args.dsize
+        p = synth.uniform_problem(n, n, n, seed=0)
+        A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
+        C = torch.empty(n, n, dtype=torch.float32, device=dev)
+        fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_F32, config=args.config)
+        fn()
+        torch.cuda.synchronize()
+        rows = np.array([0, n // 2, n - 1])
+        err = sample_err(C[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64), rows, p.A, p.B, None,
+                         1.0, 0.0)
+        for _ in range(args.warmup):
+            fn()
+        kms = _kernel_ms(_lib, fn, args.reps, flush)
+        flops = 2.0 * n ** 3
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        _line(args, flops / kms / 1e9, "TFLOPS",
+              {"workload": f"plain FP32 GEMM m=n=k={n}, uniform [-1, 1], seed 0, beta=0",
+               "path": "FP32 SIMT kernel (the plain method)", "flush": "256 MB L2 flush before every call"},
+              {"dtype": "f32", "kernel_ms": kms, "err": err,
+               "roofline": {"bound": "alu", "achieved": flops / kms / 1e9, "peak": fp32_peak, "unit": "TFLOP/s",
+                            "frac": flops / kms / 1e9 / fp32_peak, "traffic": None,
+                            "peak_source": "152 SMs x 128 FP32 FMA/clock x 2 x 2.07 GHz (maximum SM clock)",
+                            "algorithmic": "2 n^3 FP32 flops per call"}})
+        return
+
     if args.workload == "streamk":
         # Stream-K tail (split_k = G3_SPLIT_STREAM_K) against the plain walk on
         # shapes whose tiles leave the last wave partly idle: whole calls (L2
@@ -1002,7 +1030,7 @@ def main():
     ap.add_argument("--simt-steps", type=int, default=3)
     ap.add_argument("--config", type=int, default=-1, help="force a member of the kernel family")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "sweep", "plain", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "int16", "conv",
+                    choices=["square", "sweep", "plain", "simt", "streamk", "im2col", "im2col-fp8", "im2col-int8", "int8", "fp8", "bf16", "fp16", "tf32", "3xtf32", "fp64", "int16", "conv",
                              "grouped", "grouped-3xbf16", "grouped-fp8"],
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")

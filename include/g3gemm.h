@@ -160,6 +160,10 @@ G3_API int g3_set_stream(void* cuda_stream);
  *                      call allocates nothing; too small -> G3_ERR_ARG.
  *   config             -1: the planner's choice; otherwise the index of a
  *                      member of the generated kernel family (g3_family_*).
+ *                      G3_F32 (the SIMT kernel): the blocking -- 0: 128 x 128
+ *                      blocks of C, 1: 64 x 64 blocks, 2 / 3: 128 x 256
+ *                      blocks with k-blocks of 8 / 16 (all give the same
+ *                      result bit for bit; split_k applies to 64 x 64).
  *   split_k            0: the planner's choice; >= 1 forces that many splits
  *                      (k cut into equal ranges, partial planes of m x n
  *                      reduced by a second kernel); G3_SPLIT_STREAM_K (-1)

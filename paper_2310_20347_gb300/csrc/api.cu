@@ -666,7 +666,9 @@ SimtPlan simt_plan(int64_t m, int64_t n, int64_t k, int sms, int split_k) {
   const int64_t tiles64 = ((m + 63) / 64) * ((n + 63) / 64);
   const bool fits64 = (m + 63) / 64 <= 65535;
   if (split_k >= 2 && fits64) return {1, (int)std::min<int64_t>(std::min(split_k, 8), std::max<int64_t>(k, 1))};
-  if (tiles128 >= sms || !fits64) return {0, 1};
+  // enough 128 x 128 blocks for every SM: 128 x 256 blocks (8 x 16
+  // micro-tiles) unless n would leave much of their width empty
+  if (tiles128 >= sms || !fits64) return {(n % 256 == 0 || n >= 1024) ? 2 : 0, 1};
   if (tiles64 >= sms || split_k == 1) return {1, 1};
   int s = 1;
   for (int c = 2; c <= 8; c *= 2)
@@ -690,7 +692,13 @@ int run_simt(const g3_gemm_args& a, int sms, cudaStream_t s) {
   const bool vec = (reinterpret_cast<uintptr_t>(a.A) % 16 == 0) && (reinterpret_cast<uintptr_t>(a.B) % 16 == 0) &&
                    (reinterpret_cast<uintptr_t>(a.C) % 16 == 0) && a.lda % 4 == 0 && a.ldb % 4 == 0 &&
                    a.ldc % 4 == 0;
-  const SimtPlan sp = simt_plan(a.m, a.n, a.k, sms, a.split_k);
+  SimtPlan sp = simt_plan(a.m, a.n, a.k, sms, a.split_k);
+  if (a.config >= 0 && a.config <= 3 && a.config != sp.kind) {   // a forced blocking
+    if ((a.config != 1 && (a.m + 127) / 128 > 65535) || (a.config == 1 && (a.m + 63) / 64 > 65535))
+      return G3_ERR_UNSUPPORTED;
+    sp.kind = a.config;
+    if (sp.kind != 1) sp.splits = 1;
+  }
   TimedRegion tr(s);
   G3_CHECK_CUDA(launch_simt(p, vec, sp.kind, sp.splits, s));
   return G3_OK;

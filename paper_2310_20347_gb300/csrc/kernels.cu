@@ -20,10 +20,26 @@ static dim3 rows_grid(int rows, long long cols, int per_thread) {
   return dim3((unsigned)xblocks, (unsigned)yblocks, 1);
 }
 
+template <int BK>
+static cudaError_t launch_simt_wide(const SimtParams& p, bool vec, cudaStream_t s) {
+  constexpr int smem = simt_wide_smem_bytes<BK>();
+  auto kern = vec ? simt_sgemm_wide_kernel<true, BK> : simt_sgemm_wide_kernel<false, BK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((p.n + 255) / 256, (p.m + 127) / 128, 1);
+  kern<<<grid, 256, smem, s>>>(p);
+  return cudaSuccess;
+}
+
 // kind 0: 128 x 128 blocks; kind 1: 64 x 64 blocks, cut along k over a
-// cluster of `splits` CTAs when splits > 1 (1 <= splits <= 8).
+// cluster of `splits` CTAs when splits > 1 (1 <= splits <= 8); kind 2 / 3:
+// 128 x 256 blocks with k-blocks of 8 / 16 through double-buffered shared
+// memory.
 cudaError_t launch_simt(const SimtParams& p, bool vec, int kind, int splits, cudaStream_t s) {
-  if (kind == 0) {
+  if (kind == 2 || kind == 3) {
+    const cudaError_t e = kind == 2 ? launch_simt_wide<8>(p, vec, s) : launch_simt_wide<16>(p, vec, s);
+    if (e != cudaSuccess) return e;
+  } else if (kind == 0) {
     dim3 grid((p.n + 127) / 128, (p.m + 127) / 128, 1);
     if (vec) simt_sgemm_kernel<true><<<grid, 256, 0, s>>>(p);
     else simt_sgemm_kernel<false><<<grid, 256, 0, s>>>(p);

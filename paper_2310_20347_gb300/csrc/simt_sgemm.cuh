@@ -181,6 +181,109 @@ __device__ __forceinline__ void store4_epilogue(const SimtParams& p, int row, in
   }
 }
 
+// The same method on 128 x 256 blocks of C for large problems: every thread
+// keeps an 8 x 16 micro-tile (mr = 8, nr = 16: 128 FFMAs per six 128-bit
+// shared loads, against 64 per four on 128 x 128 blocks) and the register
+// fragments of the next k are loaded while the current k's outer product
+// runs.  Thread (tx, ty) owns rows {4ty..4ty+3, 64+4ty..64+4ty+3} and columns
+// {64q + 4tx .. 64q + 4tx + 3 : q = 0..3}.  k-blocks of BK (8 or 16) staged
+// through double-buffered shared memory with A transposed k-major on the way
+// in, one k-block of register prefetch; one CTA per SM (the micro-tile and
+// fragments take ~210 registers).  Each element's products are still added in
+// k order with one FMA each, so the result equals the other blockings' bit for
+// bit.
+template <bool VEC, int BK>
+__global__ void __launch_bounds__(256, 1) simt_sgemm_wide_kernel(const SimtParams p) {
+  constexpr int BM = 128, BN = 256, PAD = 4;
+  constexpr int A_V4 = BK / 8;                 // float4s of A per thread per k-block
+  constexpr int B_TPR = 256 / BK;              // threads per row of B's k-block
+  constexpr int B_V4 = BK / 4;                 // float4s of B per thread per k-block
+  extern __shared__ __align__(16) float wsmem[];
+  float (*As)[BK][BM + PAD] = reinterpret_cast<float (*)[BK][BM + PAD]>(wsmem);                 // [2][BK][BM+PAD]
+  float (*Bs)[BK][BN] = reinterpret_cast<float (*)[BK][BN]>(wsmem + 2 * BK * (BM + PAD));      // [2][BK][BN]
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int a_row = tid >> 1, a_k = (tid & 1) * (BK / 2);
+  const int b_row = tid / B_TPR, b_col = (tid % B_TPR) * 4;
+
+  float acc[8][16];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[i][j] = 0.f;
+
+  float4 ra[A_V4], rb[B_V4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int v = 0; v < A_V4; ++v) ra[v] = load4_guarded<VEC>(p.A, m0 + a_row, p.m, k0 + a_k + 4 * v, p.k, p.lda);
+#pragma unroll
+    for (int v = 0; v < B_V4; ++v)
+      rb[v] = load4_guarded<VEC>(p.B, k0 + b_row, p.k, n0 + b_col + v * (B_TPR * 4), p.n, p.ldb);
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < A_V4; ++v) {
+      As[buf][a_k + 4 * v + 0][a_row] = ra[v].x;
+      As[buf][a_k + 4 * v + 1][a_row] = ra[v].y;
+      As[buf][a_k + 4 * v + 2][a_row] = ra[v].z;
+      As[buf][a_k + 4 * v + 3][a_row] = ra[v].w;
+    }
+#pragma unroll
+    for (int v = 0; v < B_V4; ++v) *reinterpret_cast<float4*>(&Bs[buf][b_row][b_col + v * (B_TPR * 4)]) = rb[v];
+  };
+
+  fetch(0);
+  stash(0);
+  __syncthreads();
+
+  int buf = 0;
+  for (int k0 = 0; k0 < p.k; k0 += BK) {
+    const bool more = k0 + BK < p.k;
+    if (more) fetch(k0 + BK);
+    float fa[2][8], fb[2][16];
+    auto frag = [&](int kk, int f) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      fa[f][0] = a0.x; fa[f][1] = a0.y; fa[f][2] = a0.z; fa[f][3] = a0.w;
+      fa[f][4] = a1.x; fa[f][5] = a1.y; fa[f][6] = a1.z; fa[f][7] = a1.w;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][q * 64 + tx * 4]);
+        fb[f][4 * q + 0] = b.x; fb[f][4 * q + 1] = b.y; fb[f][4 * q + 2] = b.z; fb[f][4 * q + 3] = b.w;
+      }
+    };
+    frag(0, 0);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      if (kk + 1 < BK) frag(kk + 1, (kk + 1) & 1);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[i][j] = fmaf(fa[kk & 1][i], fb[kk & 1][j], acc[i][j]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = m0 + ((i < 4) ? (ty * 4 + i) : (64 + ty * 4 + i - 4));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float v[4] = {acc[i][4 * q], acc[i][4 * q + 1], acc[i][4 * q + 2], acc[i][4 * q + 3]};
+      store4_epilogue<VEC>(p, row, n0 + q * 64 + tx * 4, v);
+    }
+  }
+}
+
+template <int BK>
+constexpr int simt_wide_smem_bytes() {
+  return (2 * BK * (128 + 4) + 2 * BK * 256) * 4;
+}
+
 // Asynchronous copies global -> shared (cp.async): `bytes` of 4 or 16, of
 // which the first `src_bytes` are read and the rest zero-filled (src_bytes 0
 // reads nothing).

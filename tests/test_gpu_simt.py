@@ -178,3 +178,27 @@ def test_cluster_split_deterministic_and_planned():
     torch_api.gemm(dev(p.A), dev(p.B), C, 1.0, 0.0, dtype=G3_F32, split_k=sk)
     torch.cuda.synchronize()
     assert np.array_equal(C.cpu().numpy(), a)
+
+
+@pytest.mark.parametrize("blocking", [2, 3])
+def test_wide_blocks_parity_and_bit_identity(blocking):
+    # the 128 x 256 blocks (8 x 16 micro-tiles; k-blocks of 8 or 16): ragged
+    # m, n, k, beta != 0, unaligned leading dimensions, k = 1; within 2e-6 of
+    # the oracle and bit-identical to the 128 x 128 blocks (every element's
+    # products added in k order, one FMA each)
+    for (m, n, k, pad) in ((300, 520, 700, 0), (129, 257, 65, 0), (1, 1, 1, 0), (200, 300, 1, 0),
+                           (131, 517, 301, 1), (640, 1280, 1024, 0)):
+        p = synth.uniform_problem(m, n, k, seed=blocking * 100 + m, alpha=-0.75, beta=0.5)
+        A, B = dev(p.A), dev(p.B)
+        if pad:
+            A = torch.zeros(m, k + pad, device="cuda")[:, :k].copy_(A)
+        outs = []
+        for cfg in (0, blocking):
+            full, C = guarded(m, n, p.C)
+            torch_api.gemm(A, B, C, p.alpha, p.beta, dtype=G3_F32, config=cfg)
+            torch.cuda.synchronize()
+            check_guard(full, m, n)
+            outs.append(C.cpu().numpy())
+        assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32)), (m, n, k)
+        ref = oracle.gemm(p.A, p.B, p.C, p.alpha, p.beta)
+        gate(outs[1], ref, oracle.absprod(p.A, p.B, p.alpha), p.beta * p.C.astype(np.float64), k, TOL)
