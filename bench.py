@@ -324,6 +324,13 @@ def _line(args, metric_value, unit, config, extra):
     print(json.dumps(line), flush=True)
 
 
+def _stored(A, B, which):
+    """A and B as the GEMM reads them: stored transposed where `which` names
+    them ('a', 'b', 'ab'), with the matching trans_a / trans_b flags."""
+    ta, tb = "a" in which, "b" in which
+    return (A.t().contiguous() if ta else A, B.t().contiguous() if tb else B, {"trans_a": ta, "trans_b": tb})
+
+
 def run_workload(args):
     """The non-headline configurations, one JSON line each."""
     import torch
@@ -683,15 +690,15 @@ def run_workload(args):
             fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_TF32, config=args.config)
         elif args.workload == "fp16":
             p = synth.normal_problem(n, n, n, seed=0)
-            A, B = torch.from_numpy(p.A).to(dev).half(), torch.from_numpy(p.B).to(dev).half()
+            A, B, tkw = _stored(torch.from_numpy(p.A).to(dev).half(), torch.from_numpy(p.B).to(dev).half(), args.trans)
             C = torch.empty(n, n, dtype=torch.float32, device=dev)
-            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP16, config=args.config)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP16, config=args.config, **tkw)
         elif args.workload == "bf16":
             p = synth.normal_problem(n, n, n, seed=0)
-            A, B = torch_api.convert_bf16(torch.from_numpy(p.A).to(dev)), torch_api.convert_bf16(
-                torch.from_numpy(p.B).to(dev))
+            A, B, tkw = _stored(torch_api.convert_bf16(torch.from_numpy(p.A).to(dev)), torch_api.convert_bf16(
+                torch.from_numpy(p.B).to(dev)), args.trans)
             C = torch.empty(n, n, dtype=torch.float32, device=dev)
-            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_BF16, config=args.config)
+            fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_BF16, config=args.config, **tkw)
         elif args.workload == "int8":
             p = synth.int8_problem(n, n, n, seed=0)
             A, B = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
@@ -701,9 +708,10 @@ def run_workload(args):
             p = synth.normal_problem(n, n, n, seed=0)
             A32, B32 = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.B).to(dev)
             (A, sa), (B, sb) = torch_api.quantize_fp8(A32), torch_api.quantize_fp8(B32)
+            A, B, tkw = _stored(A, B, args.trans)
             C = torch.empty(n, n, dtype=torch.float32, device=dev)
             fn = lambda: torch_api.gemm(A, B, C, 1.0, 0.0, dtype=G3_FP8_E4M3, scale_a=sa, scale_b=sb,
-                                        config=args.config)
+                                        config=args.config, **tkw)
         fn()
         torch.cuda.synchronize()
         rows = np.array([0, n // 2, n - 1])
@@ -750,7 +758,9 @@ def run_workload(args):
         tensor_flops = flops * (3.0 if args.workload == "3xtf32" else 1.0)   # three TF32 products per term
         _line(args, flops / ms / 1e9, "TOPS" if args.workload == "int8" else "TFLOPS",
               {"workload": f"{args.workload} GEMM m=n=k={n}, alpha=1, "
-                           + ("beta=0.5, uniform [-1, 1]" if args.workload == "3xtf32" else "beta=0"),
+                           + ("beta=0.5, uniform [-1, 1]" if args.workload == "3xtf32" else "beta=0")
+                           + (f", stored transposed: {'A (k x m) ' if 'a' in args.trans else ''}"
+                              f"{'B (n x k)' if 'b' in args.trans else ''}, read in place" if args.trans else ""),
                "path": {"int8": "exact: int8 -> bf16 pre-pass, k-chunks of 1024 on the BF16 tensor path, "
                                 "int32 split-K reduce (tcgen05 kind::i8 does not exist on sm_103a)",
                         "fp8": "tcgen05 kind::f8f6f4 E4M3, per-tensor scales",
@@ -960,6 +970,7 @@ OTHER_CONFIGS = (
     ("4_grouped_bf16", "grouped"),
     ("4_grouped_3xbf16", "grouped-3xbf16"),
     ("5_bf16_8192", "bf16"),
+    ("5_bf16_8192_transposed", "bf16+trans"),
     ("5_fp8_8192", "fp8"),
     ("5_int8_8192", "int8"),
     ("5_im2col_fp8", "im2col-fp8"),
@@ -994,8 +1005,9 @@ def other_configs(args, gpu_index):
     out = {}
     for key, wl in OTHER_CONFIGS:
         a = copy.copy(args)
-        tune = wl.endswith("+tune")
-        a.workload, a.reps, a.compact, a.only, a.tune, a.config, a.dsize = wl.replace("+tune", ""), 10, True, "", tune, -1, 8192
+        tune, trans = wl.endswith("+tune"), wl.endswith("+trans")
+        a.workload, a.reps, a.compact, a.only, a.tune, a.config, a.dsize = wl.split("+")[0], 10, True, "", tune, -1, 8192
+        a.trans = "ab" if trans else ""
         _COLLECT = []
         clk = Clocks(gpu_index)
         clk.start()
@@ -1035,6 +1047,8 @@ def main():
                     help="square (default) is the headline step; the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--dsize", type=int, default=8192, help="int8 / fp8 / bf16 workloads: m = n = k")
+    ap.add_argument("--trans", default="", choices=["", "a", "b", "ab"],
+                    help="bf16 / fp16 / fp8 workloads: operands stored transposed (A k x m, B n x k), read in place")
     ap.add_argument("--print-kernel-hash", action="store_true",
                     help="print the hash of the headline kernel's sources (for the DRAM-traffic record) and exit")
     ap.add_argument("--reps", type=int, default=20)

@@ -188,10 +188,14 @@ G3_API int g3_set_stream(void* cuda_stream);
  *   trans_a, trans_b   0: A is m x k (lda >= k), B is k x n (ldb >= n);
  *                      1: the operand is stored transposed -- A as k x m
  *                      (lda >= m), B as n x k (ldb >= k) -- and C := beta*C
- *                      + alpha * op(A) op(B) (BLAS transa/transb).  A
- *                      transposed operand is first copied into the row-major
- *                      layout in a library-owned buffer (grown on first use,
- *                      even when `workspace` is given).                     */
+ *                      + alpha * op(A) op(B) (BLAS transa/transb).
+ *                      G3_BF16, G3_FP16 and G3_FP8_E4M3 read a transposed
+ *                      operand in place when its base address and row stride
+ *                      are 16-byte aligned (and, for A, unless the planner
+ *                      takes an FP8 member with 64 rows of A per CTA).  Every
+ *                      other case first copies the operand into the
+ *                      row-major layout in a library-owned buffer (grown on
+ *                      first use, even when `workspace` is given).          */
 typedef struct g3_gemm_args {
   int64_t m, n, k;
   double alpha, beta;

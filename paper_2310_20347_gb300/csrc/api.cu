@@ -741,12 +741,35 @@ int run_simt_i16(const g3_gemm_args& a, cudaStream_t s) {
   return G3_OK;
 }
 
+int input_esize(int dtype);
+int untranspose(DevState& d, g3_gemm_args& a, cudaStream_t s);
+
+// Whether dtype's kernels read a transposed operand in place (the one-plane
+// 8- and 16-bit modes); the others get a row-major copy first.
+bool reads_transposed(int dtype) { return dtype == G3_BF16 || dtype == G3_FP16 || dtype == G3_FP8_E4M3; }
+
 int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* conv = nullptr,
            const PreparedB* pb = nullptr) {
   const bool dev_scales = a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b);
   const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d.sms, a.config, a.split_k, a.raster, !dev_scales);
   if (pl.member < 0) return G3_ERR_UNSUPPORTED;
   const FamilyEntry& fam = g_family[pl.member];
+  if (a.trans_a || a.trans_b) {
+    // Transposed operands are read in place when TMA can address them (16-byte
+    // aligned base and row stride) and, for A stored k x m, when this CTA's
+    // rows of the tile (bm / cg) fill whole 128-byte swizzle rows -- all but
+    // the FP8 members with 64 rows per CTA.  Otherwise they are copied into
+    // the row-major layout first.
+    const int es = input_esize(a.dtype);
+    const bool in_place = reads_transposed(a.dtype) && !conv && !pb &&
+                          (!a.trans_a || (tma_ok(a.A, a.lda, es) && fam.bm / fam.cg * es >= 128)) &&
+                          (!a.trans_b || tma_ok(a.B, a.ldb, es));
+    if (!in_place) {
+      g3_gemm_args c = a;
+      const int st = untranspose(d, c, s);
+      return st != G3_OK ? st : run_tc(d, c, s, conv, pb);
+    }
+  }
   if (pb && tc_mode_of(a.dtype, a.k) != TC_3XBF16) return G3_ERR_ARG;   // only the two-part split
   const Layout L = make_layout(a, pl, pb != nullptr);
   uint8_t* ws = nullptr;
@@ -831,10 +854,12 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   const uint32_t arows = fam.bm / fam.cg;   // rows of A one CTA stages (half the tile in a pair)
   if (conv) {
     if ((st = encode_im2col(&maps[0], a.A, es, *conv, arows)) != G3_OK) return st;
+  } else if (a.trans_a) {   // A stored k x m: boxes of (128 bytes of m) x bk
+    if ((st = encode_2d(&maps[0], A_hi, es, m, k, lda, boxn, bk)) != G3_OK) return st;
   } else if ((st = encode_2d(&maps[0], A_hi, es, k, m, lda, bk, arows)) != G3_OK) {
     return st;
   }
-  const bool b_kmajor = a.dtype == G3_TF32 || a.dtype == G3_F32_3XTF32;
+  const bool b_kmajor = a.dtype == G3_TF32 || a.dtype == G3_F32_3XTF32 || a.trans_b;
   if (b_kmajor) {   // B stored n x k: boxes of bk (k) x 128 (n rows)
     if ((st = encode_2d(&maps[1], B_hi, es, k, n, ldb, bk, 128)) != G3_OK) return st;
   } else if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) {
@@ -875,6 +900,8 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   p.timeout_ns = watchdog_ns();
   p.status = d.status;
   p.debug_withhold = -1;
+  p.a_mn = a.trans_a ? 1 : 0;
+  p.b_km = a.trans_b ? 1 : 0;
   // INT8: at most 16 k-blocks (1024 products, |sum| <= 2^24) per FP32 accumulator
   p.kchunk = (a.dtype == G3_INT8) ? 16 : 0;
   if (conv) {
@@ -1007,7 +1034,10 @@ int gemm_impl(g3_gemm_args a, cudaStream_t s, const PreparedB* pb = nullptr) {
   std::lock_guard<std::mutex> lock(g_mu);
   DevState* d = nullptr;
   if ((st = ensure_device(&d)) != G3_OK) return st;
-  if ((a.trans_a || a.trans_b) && a.k > 0 && a.alpha != 0.0 && (st = untranspose(*d, a, s)) != G3_OK) return st;
+  // the 8- and 16-bit tensor-core modes take transposed operands in run_tc
+  if ((a.trans_a || a.trans_b) && a.k > 0 && a.alpha != 0.0 && !reads_transposed(a.dtype) &&
+      (st = untranspose(*d, a, s)) != G3_OK)
+    return st;
   const bool is_int = a.dtype == G3_INT8;
   if (a.k == 0 || a.alpha == 0.0) {
     if ((is_int || a.dtype == G3_F64 || a.dtype == G3_INT16) && a.beta == 1.0) return G3_OK;
@@ -1372,7 +1402,9 @@ int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
   g3_gemm_args a = *args;
   const bool dev_scales = a.dtype == G3_FP8_E4M3 && (a.scale_a || a.scale_b);
   if (dev_scales && a.split_k > 1) a.split_k = 1;
-  // a transposed operand reaches the kernel as an aligned row-major copy
+  // a transposed operand is read in place (when TMA can address it) or
+  // reaches the kernel as an aligned row-major copy in the transpose buffer:
+  // no workspace either way
   if (a.trans_a) { a.A = d->ws ? d->ws : reinterpret_cast<void*>(uintptr_t(256)); a.lda = round_up(a.k, 16); }
   if (a.trans_b) { a.B = d->ws ? d->ws : reinterpret_cast<void*>(uintptr_t(256)); a.ldb = round_up(a.n, 16); }
   const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d->sms, a.config, a.split_k, a.raster, !dev_scales);

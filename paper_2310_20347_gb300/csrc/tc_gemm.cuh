@@ -20,6 +20,9 @@
 // "MN-major"), its B operand the bm x k slice of A (k-contiguous, "K-major").
 // Each epilogue thread then owns one column of C and a warp's store of one row
 // is 32 consecutive floats: every global store is a full 128-byte line.
+// Transposed storage (BLAS transa/transb) changes only the staging: B stored
+// n x k is staged K-major, A stored k x m MN-major, each described as such to
+// the tensor core, so the one-plane 8- and 16-bit modes read them in place.
 //
 // The blocked loops of the paper's baseline algorithm (Figure "B3A2C0") map to:
 // L1/L3 (jc, ic) -> the persistent tile walk with a banded raster (a band of
@@ -114,6 +117,10 @@ struct TcParams {
   // in segments whose partial tiles (bm x 128*CG, FP32 or int32) go to
   // `partial`; the grid must then hold exactly sk_streams CTAs (or pairs).
   int sk_streams, sk_dp, sk_tail, sk_segs;
+  // Operands read in place in their transposed storage (one-plane 8- and
+  // 16-bit modes only): a_mn = 1, A stored k x m (lda >= m) and staged
+  // MN-major; b_km = 1, B stored n x k (ldb >= k) and staged K-major.
+  int a_mn, b_km;
 };
 
 // One problem of a grouped launch (device table entry).
@@ -163,6 +170,10 @@ struct TcTraits {
   // TF32 operand reads wrong elements): B arrives transposed (n x k) from the
   // rounding pre-pass and its tile is staged like A's, 128 n-rows of 128 bytes.
   static constexpr bool kBtKMajor = kTf32;
+  // One-plane 8- and 16-bit modes take either operand in either major order
+  // straight from the caller's storage (the INT8 and split modes stage
+  // converted row-major planes instead).
+  static constexpr bool kTransOk = kPlanes == 1 && !kTf32 && MODE != TC_I8EMU;
 };
 
 template <int BM_T, int STAGES, int MODE, int CG = 1>
@@ -301,6 +312,8 @@ struct SingleSched {
   }
 
   __device__ __forceinline__ bool conv() const { return p->conv != 0; }
+  __device__ __forceinline__ bool a_mn() const { return p->a_mn != 0; }
+  __device__ __forceinline__ bool b_km() const { return p->b_km != 0; }
   // im2col coordinates of k-block kb for the A rows starting at output pixel `pix`
   __device__ __forceinline__ void conv_coords(int pix, int kb, int (&xyzw)[4], uint16_t (&off)[2]) const {
     const int n = pix / p->conv_pq;
@@ -343,6 +356,8 @@ struct GroupedSched {
   }
 
   __device__ __forceinline__ bool conv() const { return false; }
+  __device__ __forceinline__ bool a_mn() const { return false; }
+  __device__ __forceinline__ bool b_km() const { return false; }
   __device__ __forceinline__ void conv_coords(int, int, int (&)[4], uint16_t (&)[2]) const {}
 };
 
@@ -418,6 +433,15 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   Watchdog wd{timeout_ns, status, abort_flag};
   const int total_tiles = pair_ok ? S.total() : 0;
+  // Operand layouts of this launch.  Bt (the instruction's A, 128*CG columns
+  // of C) is MN-major when B is stored k x n, K-major when stored n x k (and
+  // always for TF32).  The A tile (the instruction's B, bm rows of C) is
+  // K-major when A is stored m x k, MN-major when stored k x m: boxes of
+  // kBoxN rows of C x BK, which need this CTA's bm/CG rows to fill whole
+  // 128-byte swizzle rows (the host never sets a_mn otherwise).
+  constexpr int kAmnBoxes = (BM_T / CG) / T::kBoxN;
+  const bool bt_km = T::kBtKMajor || (T::kTransOk && S.b_km());
+  const bool a_mn = T::kTransOk && kAmnBoxes >= 1 && S.a_mn();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -444,7 +468,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             uint8_t* at = bt + T::kBtBytes;
             const CUtensorMap* mb = S.map(j, 2 * pl + 1);
             const CUtensorMap* ma = S.map(j, 2 * pl);
-            if constexpr (T::kBtKMajor) {
+            if (bt_km) {
               // B stored n x k: one box of 128 n-rows x kBK k
               if constexpr (kPair) tma_load_2d_pair(bt, mb, k0, j.n0, full_c);
               else tma_load_2d(bt, mb, k0, j.n0, &full[stage]);
@@ -465,6 +489,13 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
                 tma_load_im2col_4d_pair(at, ma, xyzw[0], xyzw[1], xyzw[2], xyzw[3], off[0], off[1], full_c);
               else
                 tma_load_im2col_4d(at, ma, xyzw[0], xyzw[1], xyzw[2], xyzw[3], off[0], off[1], &full[stage]);
+            } else if (a_mn) {
+              // A stored k x m: kAmnBoxes boxes of kBoxN rows of C x kBK k
+#pragma unroll
+              for (int h = 0; h < kAmnBoxes; ++h) {
+                if constexpr (kPair) tma_load_2d_pair(at + h * (T::kBK * 128), ma, a_row + h * T::kBoxN, k0, full_c);
+                else tma_load_2d(at + h * (T::kBK * 128), ma, a_row + h * T::kBoxN, k0, &full[stage]);
+              }
             } else if constexpr (kPair) {
               tma_load_2d_pair(at, ma, k0, a_row, full_c);
             } else {
@@ -497,7 +528,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
         const TileJob j = S.tile(t);
         if (j.kb1 <= j.kb0) continue;
-        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/!T::kBtKMajor, /*b_mn=*/false, 128 * CG, j.bm);
+        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/!bt_km, /*b_mn=*/a_mn, 128 * CG, j.bm);
         const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
         for (int c0 = j.kb0; ok && c0 < j.kb1; c0 += span, ++lt) {
         const int c1 = min(j.kb1, c0 + span);
@@ -514,14 +545,15 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
           const uint32_t st = smem_u32(smem + stage * Cfg::kStageBytes);
 #pragma unroll
           for (int ks = 0; ks < T::kKSteps; ++ks) {
-            // MN-major Bt: a k-step is kKStep whole 128-byte rows (kKStep/8 atoms);
-            // LBO = distance between 64-/128-wide n boxes, SBO = 8 rows.
-            // K-major A: a k-step is 32 bytes inside the swizzled 128-byte row.
-            const uint32_t bt_off = T::kBtKMajor ? ks * 32 : ks * T::kKStep * 128;
-            const uint32_t a_off = T::kBtBytes + ks * 32;
-            const uint64_t bt_hi = T::kBtKMajor ? smem_desc_sw128(st + bt_off, 16, 1024)
-                                                : smem_desc_sw128(st + bt_off, T::kBtLBO, 1024);
-            const uint64_t a_hi = smem_desc_sw128(st + a_off, 16, 1024);
+            // MN-major operand: a k-step is kKStep whole 128-byte rows (kKStep/8
+            // atoms); LBO = distance between its 128-byte-wide boxes, SBO = 8 rows.
+            // K-major operand: a k-step is 32 bytes inside the swizzled 128-byte row.
+            const uint32_t bt_off = bt_km ? ks * 32 : ks * T::kKStep * 128;
+            const uint32_t a_off = T::kBtBytes + (a_mn ? ks * T::kKStep * 128 : ks * 32);
+            const uint64_t bt_hi = bt_km ? smem_desc_sw128(st + bt_off, 16, 1024)
+                                         : smem_desc_sw128(st + bt_off, T::kBtLBO, 1024);
+            const uint64_t a_hi = a_mn ? smem_desc_sw128(st + a_off, T::kBK * 128, 1024)
+                                       : smem_desc_sw128(st + a_off, 16, 1024);
             if (MODE == TC_3XBF16) {
               const uint32_t lo = Cfg::kPlaneBytes;
               const uint64_t bt_lo = smem_desc_sw128(st + lo + bt_off, T::kBtLBO, 1024);

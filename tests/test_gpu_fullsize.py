@@ -7,6 +7,8 @@ sampled rows of C that the oracle computes in binary64 (int64 for INT8):
   FP32 SIMT kernel                                                       gate 2e-6
   the 3xTF32 FP32-accurate mode on the same inputs at 8192^3             gate 2e-6
   BF16 / FP16 / TF32 / FP8 / INT8 8192^3          8e-3 / 2e-3 / 2e-3 / 6e-2 / bit-exact
+  BF16 / FP8 8192^3 with both operands stored transposed (read in place)
+                                                   bit-identical to row-major
   the 20 im2col layer shapes (batch 16) in BF16    kernel check 1e-5, gate 8e-3
   the three batch-1 im2col examples in BF16         kernel check 1e-5, gate 8e-3
   the 20 im2col layer shapes in INT8               bit-exact (first, middle, last row)
@@ -126,6 +128,28 @@ def test_dtype_8192_cubed(kind):
     e = sampled_err(C[sel].double().cpu().numpy(), rows, p.A, p.B, None, 1.0, 0.0)
     print(f"{kind} 8192^3 sampled error {e:.3e}")
     assert e <= tol
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+def test_dtype_8192_cubed_transposed_in_place(kind):
+    # A stored k x m and B stored n x k, read in place by the planner's member
+    # for 8192^3: every element equal to the same plan on row-major storage
+    n = 8192
+    p = synth.normal_problem(n, n, n, seed=0)
+    A32, B32 = torch.from_numpy(p.A).cuda(), torch.from_numpy(p.B).cuda()
+    if kind == "bf16":
+        A, B, dt, kw = torch_api.convert_bf16(A32), torch_api.convert_bf16(B32), G3_BF16, {}
+    else:
+        (A, sa), (B, sb) = torch_api.quantize_fp8(A32), torch_api.quantize_fp8(B32)
+        dt, kw = G3_FP8_E4M3, {"scale_a": sa, "scale_b": sb}
+    del A32, B32
+    C_r = torch.empty(n, n, device="cuda")
+    torch_api.gemm(A, B, C_r, 1.0, 0.0, dtype=dt, **kw)
+    At, Bt = A.t().contiguous(), B.t().contiguous()
+    C_t = torch.empty(n, n, device="cuda")
+    torch_api.gemm(At, Bt, C_t, 1.0, 0.0, dtype=dt, trans_a=True, trans_b=True, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(C_t.view(torch.int32), C_r.view(torch.int32))
 
 
 def test_im2col_layers_bf16():
