@@ -126,10 +126,16 @@ G3_API int g3_gemm(int64_t m, int64_t n, int64_t k, double alpha, const void* A,
  * library-owned copy streams ordered against `cuda_stream` (NULL = the
  * current stream).  It returns before the work is done: the host buffers must
  * stay valid and untouched until `cuda_stream` has completed.  Page-locked
- * host memory is needed for the copies to overlap.  The device copies live in
- * one library buffer per device, grown on first use of a size: calls on
- * different streams must not overlap.  FP8 runs with unit scales.  Errors as
- * g3_gemm; G3_ERR_NOMEM when the device copies do not fit.                   */
+ * host memory is needed for the copies to overlap.  The device copies, and
+ * the scratch of the row blocks' GEMMs, live in a library buffer of the
+ * calling stream (grown on first use of a size), so calls on different
+ * streams may overlap: with requests alternating between two streams, one
+ * call's uploads run while the other computes.  Up to four streams keep
+ * buffers of their own; a fifth takes over the least recently used stream's
+ * buffer, after that stream's last call (ordered on the device, no host
+ * wait).  Calls on one stream from several host threads at once are not
+ * supported.  FP8 runs with unit scales.  Errors as g3_gemm; G3_ERR_NOMEM
+ * when the device copies do not fit.                                         */
 G3_API int g3_gemm_host(int64_t m, int64_t n, int64_t k, double alpha, const void* A, int64_t lda, const void* B,
                         int64_t ldb, double beta, void* C, int64_t ldc, int dtype, void* cuda_stream);
 

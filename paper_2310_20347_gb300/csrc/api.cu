@@ -37,6 +37,23 @@ constexpr int kMaxDevices = 64;
 
 constexpr int kHostMaxBlocks = 8;   // row blocks of a g3_gemm_host pipeline
 constexpr int kHostMaxSlabs = 4;    // k-slabs in which g3_gemm_host sends B up (FP32-accurate)
+constexpr int kHostPipes = 4;       // caller streams with g3_gemm_host device copies of their own
+
+// g3_gemm_host state of one caller stream: device copies of A, B, C (and
+// B's prepared planes), scratch for the block GEMMs, two copy streams and
+// the pipeline's events.  free_ev, recorded on the caller's stream after a
+// call's last download, orders the next call that takes these buffers.
+struct HostPipe {
+  bool used = false;
+  cudaStream_t owner = nullptr;
+  uint64_t last_use = 0;
+  void* buf = nullptr;
+  size_t bytes = 0;
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t ev[2 * kHostMaxBlocks + kHostMaxSlabs + 3] = {};
+  cudaEvent_t free_ev = nullptr;
+  bool free_recorded = false;
+};
 
 struct DevState {
   bool init = false;
@@ -47,11 +64,10 @@ struct DevState {
   // row-major copies of transposed operands (trans_a / trans_b)
   void* tbuf = nullptr;
   size_t tbuf_bytes = 0;
-  // g3_gemm_host: device copies of A, B, C and the copy streams / events
-  void* hbuf = nullptr;
-  size_t hbuf_bytes = 0;
-  cudaStream_t up = nullptr, down = nullptr;
-  cudaEvent_t ev[2 * kHostMaxBlocks + kHostMaxSlabs + 3] = {};
+  // g3_gemm_host: per caller stream (the least recently used one is taken
+  // over by a new stream)
+  HostPipe pipes[kHostPipes];
+  uint64_t pipe_tick = 0;
 };
 
 std::mutex g_mu;
@@ -1119,8 +1135,10 @@ using namespace g3;
 // so the tensor cores start after the first slab; the later blocks use the
 // prepared planes.  (Row block 0 is rounded to FP32 once per slab: at most
 // kHostMaxSlabs - 1 extra roundings of 2^-24 relative to its partial sums.)
-// Device copies live in a library buffer; the caller's stream waits for the
-// last download.
+// Device copies (and the block GEMMs' scratch) live in a library buffer of
+// the caller's stream, so calls on different streams overlap -- one call's
+// uploads run under another's compute; the caller's stream waits for the last
+// download.
 static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   int st = validate(a);
   if (st != G3_OK) return st;
@@ -1153,57 +1171,122 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   const int64_t ldp = round_up(n, 8);   // leading dimension of the prepared planes
   const size_t plane_bytes = prep ? align256((size_t)k * ldp * 2) : 0;
   uint8_t* base = nullptr;
+  uint8_t *dA = nullptr, *dB = nullptr, *dC = nullptr, *dW = nullptr;
+  uint16_t *Bhi = nullptr, *Blo = nullptr;
+  size_t ws_bytes = 0;
+  auto place = [&](uint8_t* b) {
+    base = b;
+    dA = base;
+    dB = base + a_bytes;
+    dC = base + a_bytes + b_bytes;
+    Bhi = reinterpret_cast<uint16_t*>(dC + c_bytes);
+    Blo = reinterpret_cast<uint16_t*>(dC + c_bytes + plane_bytes);
+    dW = dC + c_bytes + 2 * plane_bytes;
+  };
+  auto rows_of = [&](int b, int64_t* r0, int64_t* r1) {
+    *r0 = b * rb;
+    *r1 = std::min(m, *r0 + rb);
+    return *r0 < *r1;
+  };
+  auto block_args = [&](int64_t r0, int64_t r1) {
+    g3_gemm_args blk = a;
+    blk.m = r1 - r0;
+    blk.A = dA + (size_t)r0 * lda_d * es;
+    blk.lda = lda_d;
+    blk.B = dB;
+    blk.ldb = ldb_d;
+    blk.C = dC + (size_t)r0 * ldc_d * ces;
+    blk.ldc = ldc_d;
+    blk.workspace = ws_bytes ? dW : nullptr;
+    blk.workspace_bytes = ws_bytes;
+    return blk;
+  };
+  auto slab_args = [&](int64_t r0, int64_t r1, int j) {   // row block r0..r1 on k-slab j
+    const int64_t k0 = j * ks, k1 = std::min(k, (j + 1) * ks);
+    g3_gemm_args blk = block_args(r0, r1);
+    blk.k = k1 - k0;
+    blk.A = dA + (size_t)r0 * lda_d * es + (size_t)k0 * es;
+    blk.B = dB + (size_t)k0 * ldb_d * es;
+    if (j > 0) blk.beta = 1.0;
+    return blk;
+  };
   cudaEvent_t* ev = nullptr;
   cudaStream_t up = nullptr, down = nullptr;
+  HostPipe* P = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
     DevState* d = nullptr;
     if ((st = ensure_device(&d)) != G3_OK) return st;
-    if (!d->up) {
-      if (cudaStreamCreateWithFlags(&d->up, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaStreamCreateWithFlags(&d->down, cudaStreamNonBlocking) != cudaSuccess)
+    // the caller stream's buffers, else a free set, else the least recently used
+    for (auto& q : d->pipes)
+      if (q.used && q.owner == s) P = &q;
+    if (!P)
+      for (auto& q : d->pipes)
+        if (!q.used && !P) P = &q;
+    if (!P) {
+      P = &d->pipes[0];
+      for (auto& q : d->pipes)
+        if (q.last_use < P->last_use) P = &q;
+    }
+    P->used = true;
+    P->owner = s;
+    P->last_use = ++d->pipe_tick;
+    if (!P->up) {
+      if (cudaStreamCreateWithFlags(&P->up, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&P->down, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&P->free_ev, cudaEventDisableTiming) != cudaSuccess)
         return G3_ERR_CUDA;
-      for (auto& e : d->ev)
+      for (auto& e : P->ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return G3_ERR_CUDA;
     }
-    const size_t need = a_bytes + b_bytes + c_bytes + 2 * plane_bytes;
-    if (d->hbuf_bytes < need) {
-      if (d->hbuf) {
-        cudaDeviceSynchronize();
-        cudaFree(d->hbuf);
-        d->hbuf = nullptr;
-        d->hbuf_bytes = 0;
+    // scratch of the block GEMMs (operand planes, split-K partials): the
+    // largest any block needs, laid out on a 256-byte aligned stand-in base
+    place(reinterpret_cast<uint8_t*>(uintptr_t(256)));
+    if (products && d->sms > 0 && a.dtype != G3_F32 && a.dtype != G3_F64 && a.dtype != G3_INT16) {
+      auto need_of = [&](const g3_gemm_args& blk, bool prepared) {
+        const Plan pl = make_plan(blk.m, blk.n, blk.k, blk.dtype, d->sms, blk.config, blk.split_k, blk.raster, true);
+        return pl.member < 0 ? size_t(0) : make_layout(blk, pl, prepared).total;
+      };
+      for (int b = 0; b < nb; ++b) {
+        int64_t r0, r1;
+        if (!rows_of(b, &r0, &r1)) break;
+        if (prep && b == 0)
+          for (int j = 0; j < ns; ++j) ws_bytes = std::max(ws_bytes, need_of(slab_args(r0, r1, j), true));
+        else
+          ws_bytes = std::max(ws_bytes, need_of(block_args(r0, r1), prep));
       }
-      if (device_alloc(&d->hbuf, need) != cudaSuccess) {
+      ws_bytes = align256(ws_bytes);
+    }
+    const size_t need = a_bytes + b_bytes + c_bytes + 2 * plane_bytes + ws_bytes;
+    if (P->bytes < need) {
+      if (P->buf) {
+        cudaDeviceSynchronize();
+        cudaFree(P->buf);
+        P->buf = nullptr;
+        P->bytes = 0;
+      }
+      if (device_alloc(&P->buf, need) != cudaSuccess) {
         cudaGetLastError();
         return G3_ERR_NOMEM;
       }
-      d->hbuf_bytes = need;
+      P->bytes = need;
     }
-    base = static_cast<uint8_t*>(d->hbuf);
-    ev = d->ev;
-    up = d->up;
-    down = d->down;
+    place(static_cast<uint8_t*>(P->buf));
+    ev = P->ev;
+    up = P->up;
+    down = P->down;
   }
-  uint8_t* dA = base;
-  uint8_t* dB = base + a_bytes;
-  uint8_t* dC = base + a_bytes + b_bytes;
-  uint16_t* Bhi = reinterpret_cast<uint16_t*>(dC + c_bytes);
-  uint16_t* Blo = reinterpret_cast<uint16_t*>(dC + c_bytes + plane_bytes);
   // events: 0 start, 1 + b row block b up, 1 + kHostMaxBlocks + b row block b
   // done, 2 kHostMaxBlocks + 1 last download, 2 kHostMaxBlocks + 2 + j slab j up
   cudaEvent_t* ev_up = ev + 1;
   cudaEvent_t* ev_done = ev + 1 + kHostMaxBlocks;
   cudaEvent_t ev_last = ev[2 * kHostMaxBlocks + 1];
   cudaEvent_t* ev_slab = ev + 2 * kHostMaxBlocks + 2;
-  // the device copies may still be in use by an earlier call on this stream
+  // the uploads follow the caller's earlier work on its stream and the last
+  // call that used these buffers (on this stream or the one they came from)
   G3_CHECK_CUDA(cudaEventRecord(ev[0], s));
   G3_CHECK_CUDA(cudaStreamWaitEvent(up, ev[0], 0));
-  auto rows_of = [&](int b, int64_t* r0, int64_t* r1) {
-    *r0 = b * rb;
-    *r1 = std::min(m, *r0 + rb);
-    return *r0 < *r1;
-  };
+  if (P->free_recorded) G3_CHECK_CUDA(cudaStreamWaitEvent(up, P->free_ev, 0));
   auto up_rows = [&](int b) -> int {   // A (and C) rows of block b
     int64_t r0, r1;
     if (!rows_of(b, &r0, &r1)) return G3_OK;
@@ -1222,17 +1305,6 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
                                     static_cast<const uint8_t*>(a.B) + (size_t)k0 * a.ldb * es, a.ldb * es, n * es,
                                     k1 - k0, cudaMemcpyHostToDevice, up));
     return G3_OK;
-  };
-  auto block_args = [&](int64_t r0, int64_t r1) {
-    g3_gemm_args blk = a;
-    blk.m = r1 - r0;
-    blk.A = dA + (size_t)r0 * lda_d * es;
-    blk.lda = lda_d;
-    blk.B = dB;
-    blk.ldb = ldb_d;
-    blk.C = dC + (size_t)r0 * ldc_d * ces;
-    blk.ldc = ldc_d;
-    return blk;
   };
   auto down_rows = [&](int b, int64_t r0, int64_t r1) -> int {
     G3_CHECK_CUDA(cudaEventRecord(ev_done[b], s));
@@ -1261,13 +1333,8 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
       G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_slab[j], 0));
       G3_CHECK_CUDA(launch_split_bf16(reinterpret_cast<const float*>(dB + (size_t)k0 * ldb_d * es), (int)(k1 - k0),
                                       (int)n, ldb_d, Bhi + k0 * ldp, Blo + k0 * ldp, ldp, s));
-      g3_gemm_args blk = block_args(r0, r1);
-      blk.k = k1 - k0;
-      blk.A = dA + (size_t)r0 * lda_d * es + (size_t)k0 * es;
-      blk.B = dB + (size_t)k0 * ldb_d * es;
-      if (j > 0) blk.beta = 1.0;
       const PreparedB pb{Bhi + k0 * ldp, Blo + k0 * ldp, ldp};
-      if ((st = gemm_impl(blk, s, &pb)) != G3_OK) return st;
+      if ((st = gemm_impl(slab_args(r0, r1, j), s, &pb)) != G3_OK) return st;
     }
     if ((st = down_rows(0, r0, r1)) != G3_OK) return st;
     const PreparedB pb{Bhi, Blo, ldp};
@@ -1292,6 +1359,11 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
   }
   G3_CHECK_CUDA(cudaEventRecord(ev_last, down));
   G3_CHECK_CUDA(cudaStreamWaitEvent(s, ev_last, 0));
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    G3_CHECK_CUDA(cudaEventRecord(P->free_ev, s));
+    P->free_recorded = true;
+  }
   return G3_OK;
 }
 

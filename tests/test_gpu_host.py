@@ -93,3 +93,39 @@ def test_host_back_to_back_calls_reuse_the_device_copies():
     for prob, out in ((p, hC), (q, gC)):
         e = rel_err(out.numpy(), oracle.gemm(prob.A, prob.B, None, 1.0, 0.0), oracle.absprod(prob.A, prob.B, 1.0))
         assert e <= 2e-6, e
+
+
+def _queued(problems, streams, dtype):
+    """Queue one call per problem (round robin over `streams`) without any host
+    synchronisation; return the results."""
+    outs = []
+    for i, prob in enumerate(problems):
+        hA, hB = pinned(torch.from_numpy(prob.A)), pinned(torch.from_numpy(prob.B))
+        hC = pinned(torch.from_numpy(prob.C) if prob.C is not None else torch.zeros(prob.m, prob.n))
+        torch_api.gemm_host(hA, hB, hC, prob.alpha, prob.beta, dtype=dtype, stream=streams[i % len(streams)])
+        outs.append(hC)
+    torch.cuda.synchronize()
+    return [o.numpy().copy() for o in outs]
+
+
+@pytest.mark.parametrize("nstreams", [2, 6])
+def test_host_calls_on_several_streams_overlap_and_match_one_stream(nstreams):
+    # Each stream has its own device copies and block scratch, so calls on
+    # different streams run concurrently (uploads of one under the compute of
+    # another); six streams exceed the four buffer sets, and the fifth and
+    # sixth take over the least recently used sets.  Every result must equal
+    # the same call queued alone on one stream, bit for bit: FP32-accurate
+    # multi-block calls with B in k-slabs (k = 4500), the plain row-block
+    # pipeline (k = 700) and a one-block call.
+    shapes = [(2100, 300, 4500, 0.5), (2500, 200, 700, 0.0), (600, 180, 300, 0.5), (2300, 260, 4200, 0.0)]
+    probs = [synth.uniform_problem(m, n, k, seed=90 + i, alpha=1.0, beta=b)
+             for i, (m, n, k, b) in enumerate(shapes * 2)][: max(4, nstreams + 1)]
+    alone = [_queued([prob], [torch.cuda.current_stream()], G3_F32_3XBF16)[0] for prob in probs]
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    got = _queued(probs, streams, G3_F32_3XBF16)
+    for prob, g, a in zip(probs, got, alone):
+        assert np.array_equal(g.view(np.uint32), a.view(np.uint32)), (prob.m, prob.n, prob.k)
+        bc = None if prob.C is None else prob.beta * prob.C.astype(np.float64)
+        e = rel_err(g, oracle.gemm(prob.A, prob.B, prob.C, prob.alpha, prob.beta),
+                    oracle.absprod(prob.A, prob.B, prob.alpha), bc)
+        assert e <= 2e-6, e
