@@ -1232,7 +1232,7 @@ def main():
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_oracle_sample(p)
     if not args.no_configs and world == 1:
-        del A, B, C0, C, hA, hB, hC
+        del A, B, C0, C, hosts
         torch.cuda.empty_cache()
         line["configs"] = other_configs(args, local)
     print(json.dumps(line), flush=True)
