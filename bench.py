@@ -945,6 +945,32 @@ def run_workload(args):
         torch.cuda.synchronize()
         g2.replay()
         graph_calls_ms = _call_ms(g2.replay, max(3, args.reps // 4), flush)
+        extra = {}
+        if dt == G3_F32_3XBF16:
+            # the same batch split inside the grouped kernels (G3_GROUPED_SPLIT_IN_KERNEL)
+            fz = torch_api.GroupedPlan(probs, dt, split_in_kernel=True)
+            fz.execute()
+            torch.cuda.synchronize()
+            s3 = torch.cuda.Stream()
+            s3.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s3):
+                g3 = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g3, stream=s3):
+                    fz.execute(stream=s3)
+            torch.cuda.synchronize()
+            g3.replay()
+            extra = {"split_in_kernel_graph_ms": _call_ms(g3.replay, args.reps, flush)}
+            fz.close()
+        # algorithmic bytes: each operand read once in its input format, C written once
+        es = {G3_BF16: 2, G3_F32_3XBF16: 4, G3_FP8_E4M3: 1}[dt]
+        alg_bytes = float(sum(es * (m * k + k * n) + 4 * m * n for (m, n, k) in shapes))
+        peaks, peak_src = load_peaks()
+        hbm = float(peaks["hbm_gbs"])
+        extra["roofline"] = {"bound": "hbm", "achieved": alg_bytes / grouped_ms / 1e6, "peak": hbm, "unit": "GB/s",
+                             "frac": alg_bytes / grouped_ms / 1e6 / hbm, "traffic": None,
+                             "peak_source": f"{peak_src} copy bandwidth",
+                             "algorithmic": f"{alg_bytes / 1e9:.3f} GB: A and B once in the input format "
+                                            f"({es} B per element), C written once (4 B)"}
         _line(args, flops / grouped_ms / 1e9, "TFLOPS",
               {"workload": f"1000 GEMMs, m,n,k log-uniform in [16,1024] (seed 0), "
                            f"{ {G3_BF16: 'bf16', G3_F32_3XBF16: '3xbf16 (fp32 in/out)', G3_FP8_E4M3: 'fp8 e4m3 with per-problem scales'}[dt] }, fp32 C, beta=0",
@@ -955,7 +981,7 @@ def run_workload(args):
                "speedup_vs_eager": eager_ms / grouped_ms, "speedup_vs_graph_of_calls": graph_calls_ms / grouped_ms,
                "max_rel_err_sampled": float(np.max(np.array(errs))), "nonfinite_sampled": nonfinite,
                "autotuned": bool(args.tune), "tuned_buckets": tuned_buckets, "tune_s": round(tune_s, 1),
-               "tile_heights": {str(h): heights.count(h) for h in sorted(set(heights))}})
+               "tile_heights": {str(h): heights.count(h) for h in sorted(set(heights))}, **extra})
         plan.close()
         return
 
@@ -986,7 +1012,7 @@ def _summary(line):
         keep["roofline"] = {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "frac_of_traffic_floor")
                             if k in rf}
     for k in ("ms", "kernel_ms", "err", "worst_err", "total_ms_20_layers", "traffic_floor_ms_20_layers",
-              "grouped_graph_ms", "grouped_kernel_ms",
+              "grouped_graph_ms", "grouped_kernel_ms", "split_in_kernel_graph_ms",
               "per_call_graph_ms", "per_call_eager_wall_ms", "speedup_vs_eager", "speedup_vs_graph_of_calls",
               "max_rel_err_sampled", "nonfinite_sampled", "total_gflop", "autotuned"):
         if k in line:

@@ -297,6 +297,22 @@ typedef struct g3_grouped_plan g3_grouped_plan;
  * clipped to G3_ERR_ARG for i >= 900.                                       */
 G3_API int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** plan);
 
+/* g3_grouped_plan_create with options.  flags = 0 (the same plan) or
+ * G3_GROUPED_SPLIT_IN_KERNEL: a G3_F32_3XBF16 plan splits inside the grouped
+ * kernels -- warps of the kernel read each tile's FP32 A and B (row-major,
+ * any alignment) and write their bfloat16 parts (the two-part split for
+ * k > 512, the three-part split for k <= 512, the pre-pass's arithmetic)
+ * into shared memory, on tiles of 64 rows -- so the plan holds no operand
+ * planes and runs no split pass (the paper's packing, Section 5.3, done in
+ * the kernel).  Results equal the default plan's bit for bit where both take
+ * 64-row tiles.  The default plan is faster on GB300 (the split-in-kernel
+ * warps cannot keep enough loads in flight within their registers); the
+ * option serves memory budgets that cannot hold the planes.  Other dtypes
+ * ignore the flag; other flag bits: G3_ERR_ARG.                             */
+#define G3_GROUPED_SPLIT_IN_KERNEL 1
+G3_API int g3_grouped_plan_create_ex(int count, const g3_gemm_desc* descs, int dtype, int flags,
+                                     g3_grouped_plan** plan);
+
 /* Run every problem of the plan: pre-passes (if any) and one persistent
  * kernel launch per kernel kind (BF16, FP8: one; FP32-accurate: one for the
  * problems with k > 512 and one for those with k <= 512).  No host

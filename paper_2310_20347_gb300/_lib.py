@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libg3gemm.so")
 
 G3_F32, G3_F32_3XBF16, G3_BF16, G3_FP8_E4M3, G3_INT8, G3_FP16, G3_TF32, G3_F32_3XTF32, G3_F64, G3_INT16 = range(10)
 G3_SPLIT_STREAM_K = -1   # g3_gemm_args.split_k: a stream-K tail
+G3_GROUPED_SPLIT_IN_KERNEL = 1   # g3_grouped_plan_create_ex: FP32-accurate split inside the kernel
 DTYPES = {"f32": G3_F32, "3xbf16": G3_F32_3XBF16, "bf16": G3_BF16, "fp8": G3_FP8_E4M3, "int8": G3_INT8,
           "fp16": G3_FP16, "tf32": G3_TF32, "3xtf32": G3_F32_3XTF32, "f64": G3_F64, "int16": G3_INT16}
 
@@ -27,7 +28,7 @@ G3_OK, G3_ERR_ARG, G3_ERR_UNSUPPORTED, G3_ERR_CUDA, G3_ERR_NOMEM, G3_ERR_TIMEOUT
 EXPORTED = (
     "g3_gemm", "g3_gemm_host", "g3_conv2d", "g3_set_stream", "g3_gemm_args_init", "g3_gemm_ex", "g3_gemm_workspace_size",
     "g3_convert_bf16", "g3_convert_tf32", "g3_split_bf16", "g3_split3_bf16", "g3_split_tf32", "g3_quantize_fp8",
-    "g3_grouped_plan_create", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
+    "g3_grouped_plan_create", "g3_grouped_plan_create_ex", "g3_grouped_plan_execute", "g3_grouped_plan_destroy", "g3_gemm_grouped",
     "g3_grouped_plan_describe", "g3_autotune_grouped",
     "g3_get_last_device_status", "g3_status_string", "g3_family_size", "g3_family_describe",
     "g3_plan_query", "g3_launch_count", "g3_debug_device_allocations", "g3_stream_traffic", "g3_kernel_timing", "g3_kernel_time_ms",
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
             "g3_split_tf32": ([vp, i64, i64, i64, vp, vp, i64, vp], i32),
             "g3_quantize_fp8": ([vp, i64, i64, i64, vp, i64, vp, vp], i32),
             "g3_grouped_plan_create": ([i32, ctypes.POINTER(g3_gemm_desc), i32, ctypes.POINTER(vp)], i32),
+            "g3_grouped_plan_create_ex": ([i32, ctypes.POINTER(g3_gemm_desc), i32, i32, ctypes.POINTER(vp)], i32),
             "g3_grouped_plan_execute": ([vp, vp], i32),
             "g3_grouped_plan_destroy": ([vp], i32),
             "g3_gemm_grouped": ([i32, ctypes.POINTER(g3_gemm_desc), i32, vp], i32),
@@ -190,10 +192,14 @@ def g3_quantize_fp8(x, rows, cols, ldx, q, ldq, scale, stream=None) -> int:
     return load().g3_quantize_fp8(x, rows, cols, ldx, q, ldq, scale, stream)
 
 
-def g3_grouped_plan_create(descs, dtype):
+def g3_grouped_plan_create(descs, dtype, flags=None):
+    """flags None: g3_grouped_plan_create; else g3_grouped_plan_create_ex with those flags."""
     arr = (g3_gemm_desc * len(descs))(*descs)
     plan = ctypes.c_void_p(None)
-    st = load().g3_grouped_plan_create(len(descs), arr, dtype, ctypes.byref(plan))
+    if flags is None:
+        st = load().g3_grouped_plan_create(len(descs), arr, dtype, ctypes.byref(plan))
+    else:
+        st = load().g3_grouped_plan_create_ex(len(descs), arr, dtype, flags, ctypes.byref(plan))
     return st, plan
 
 

@@ -12,7 +12,11 @@
 // tc_grouped_kernel per kernel kind over its tiles -- BF16, FP8: one; FP32-accurate:
 // the two-part split (3 products) for problems with k > 512 and the
 // three-part split (6 products) for those with k <= 512 -- with no host
-// synchronisation and no allocation.
+// synchronisation and no allocation.  On request (G3_GROUPED_SPLIT_IN_KERNEL)
+// FP32-accurate plans split inside the kernel instead
+// (tc_grouped_fused_kernel: loader-converter warps read each tile's FP32
+// operands and write its bf16 parts into shared memory), with no split jobs
+// and no planes.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -176,20 +180,24 @@ struct g3_grouped_plan {
   // per problem: tile height and kernel kind (0: the plan's first launch, 1:
   // the three-part split), -1 / -1 for problems without products
   std::vector<int> bms, kinds;
+  bool fused = false;   // FP32-accurate split inside the grouped kernels
 };
 
 namespace {
 
 // force_bm > 0: every problem takes tiles of force_bm rows (g3_autotune_grouped);
 // otherwise the tuning record of the problem's size bucket, else the fixed
-// rule (64 rows for m <= 64, 128 above).
-int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g3_grouped_plan** out) {
+// rule (64 rows for m <= 64, 128 above).  flags & G3_GROUPED_SPLIT_IN_KERNEL:
+// FP32-accurate plans split inside the kernel, on 64-row tiles.
+int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, int flags, g3_grouped_plan** out) {
   if (!out) return G3_ERR_ARG;
   *out = nullptr;
   if (count < 0) return -101;
   if (count > 0 && !descs) return -102;
   if (dtype != G3_BF16 && dtype != G3_F32_3XBF16 && dtype != G3_FP8_E4M3) return G3_ERR_UNSUPPORTED;
+  if (flags & ~G3_GROUPED_SPLIT_IN_KERNEL) return G3_ERR_ARG;
   const bool fp8 = dtype == G3_FP8_E4M3;
+  const bool fused = dtype == G3_F32_3XBF16 && (flags & G3_GROUPED_SPLIT_IN_KERNEL) && force_bm <= 0;
   for (int i = 0; i < count; ++i) {
     const g3_gemm_desc& d = descs[i];
     const int code = i < 900 ? -(100 + i) : G3_ERR_ARG;
@@ -217,10 +225,10 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g
   // sum |a||b|; deeper ones the two-part split (3 products).  Each kind runs
   // as its own persistent launch (part 0: BF16 or the two-part split; part 1:
   // the three-part split).
-  auto entry_of = [](int mode) {
+  auto entry_of = [fused](int mode) {
     int e = -1;
     for (int i = 0; i < G3_GROUPED_SIZE; ++i)
-      if (g_grouped[i].launch && g_grouped[i].mode == mode) e = i;
+      if (g_grouped[i].launch && g_grouped[i].mode == mode && (g_grouped[i].fused != 0) == fused) e = i;
     return e;
   };
   const bool split_mode = dtype == G3_F32_3XBF16;
@@ -251,7 +259,13 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g
     g.beta = (float)d.beta;
     g.C = static_cast<float*>(d.C);
     g.ldc = d.ldc;
-    const int tuned = force_bm > 0 ? force_bm : tuned_grouped_bm(d.m, d.n, d.k, dtype);
+    if (fused) {   // the loader-converter warps read the FP32 operands in place
+      g.A = static_cast<const float*>(d.A);
+      g.B = static_cast<const float*>(d.B);
+      g.lda = d.lda;
+      g.ldb = d.ldb;
+    }
+    const int tuned = fused ? 0 : (force_bm > 0 ? force_bm : tuned_grouped_bm(d.m, d.n, d.k, dtype));
     g.bm = std::min(tuned > 0 ? tuned : ((d.m <= 64) ? 64 : 128), bm_max);   // size bucket
     if (d.m == 0 || d.n == 0) continue;
     if (d.k == 0 || d.alpha == 0.0) {
@@ -266,7 +280,9 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g
     g.tiles_n = (g.n + 127) / 128;
     g.num_kb = (g.k + bk - 1) / bk;
     total_tiles += (long long)g.tiles_m * g.tiles_n;
-    if (dtype == G3_F32_3XBF16) {
+    if (fused) {
+      // no planes, no jobs
+    } else if (dtype == G3_F32_3XBF16) {
       o.lda = round_up(d.k, 8);
       o.ldb = round_up(d.n, 8);
       o.a_off = take((size_t)d.m * o.lda * 2);
@@ -311,7 +327,7 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g
   std::vector<CUtensorMap> maps(kMapsPerProblem * (size_t)std::max(count, 1));
   std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
   for (int i = 0; i < count && st == G3_OK; ++i) {
-    if (!ops[i].active) continue;
+    if (!ops[i].active || fused) continue;   // the fused kernels use no tensor maps
     const g3_gemm_desc& d = descs[i];
     const Operands& o = ops[i];
     const GroupDesc& g = groups[i];
@@ -406,6 +422,7 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g
     }
   plan->device = dev.device;
   plan->dtype = dtype;
+  plan->fused = fused;
   plan->count = count;
   plan->total_tiles = (int)total_tiles;
   plan->njobs = (int)jobs.size();
@@ -435,7 +452,11 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, g
 extern "C" {
 
 int g3_grouped_plan_create(int count, const g3_gemm_desc* descs, int dtype, g3_grouped_plan** out) {
-  return plan_create(count, descs, dtype, 0, out);
+  return plan_create(count, descs, dtype, 0, 0, out);
+}
+
+int g3_grouped_plan_create_ex(int count, const g3_gemm_desc* descs, int dtype, int flags, g3_grouped_plan** out) {
+  return plan_create(count, descs, dtype, 0, flags, out);
 }
 
 int g3_grouped_plan_describe(const g3_grouped_plan* plan, int index, int* bm, int* kind) {
@@ -570,7 +591,7 @@ int g3_autotune_grouped(int64_t m, int64_t n, int64_t k, int dtype, int* best_bm
   for (int bm : {128, 64}) {
     if (st != G3_OK) break;
     g3_grouped_plan* plan = nullptr;
-    if (plan_create(P, descs.data(), dtype, bm, &plan) != G3_OK) continue;
+    if (plan_create(P, descs.data(), dtype, bm, 0, &plan) != G3_OK) continue;
     float ms = 0.f;
     double t = 1e30;
     cudaEventRecord(e0, s);

@@ -41,7 +41,9 @@ void register_family_3xtf32(FamilyEntry* table);
 
 using GroupedLaunchFn = cudaError_t (*)(const GroupedParams& p, int grid, cudaStream_t s);
 
-// One persistent grouped kernel (tiles of at most bm_max rows).
+// One persistent grouped kernel (tiles of at most bm_max rows).  fused = 1:
+// the FP32-accurate split inside the kernel (FP32 A and B read through the
+// problem table, no preparation jobs for them).
 struct GroupedEntry {
   int index;
   int mode;
@@ -49,6 +51,7 @@ struct GroupedEntry {
   int stages;
   int smem;
   GroupedLaunchFn launch;
+  int fused;
 };
 
 void register_grouped_bf16(GroupedEntry* table);

@@ -91,10 +91,12 @@ void add_member(FamilyEntry* t) {
   }
 }
 
-template <int BM, int ST, int MODE>
+template <int BM, int ST, int MODE, bool FUSED>
 cudaError_t launch_grouped(const GroupedParams& p, int grid, cudaStream_t s) {
-  using Cfg = TcConfig<BM, ST, MODE>;
-  auto kern = tc_grouped_kernel<BM, ST, MODE>;
+  using Cfg = TcConfig<BM, ST, MODE, 1, FUSED>;
+  void (*kern)(const GroupedParams);
+  if constexpr (FUSED) kern = tc_grouped_fused_kernel<BM, ST, MODE>;
+  else kern = tc_grouped_kernel<BM, ST, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
@@ -104,10 +106,11 @@ cudaError_t launch_grouped(const GroupedParams& p, int grid, cudaStream_t s) {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int IDX, int MODE, int BM, int ST>
+template <int IDX, int MODE, int BM, int ST, int FUSED>
 void add_grouped(GroupedEntry* t) {
   if constexpr (MODE == G3_TU_MODE) {
-    t[IDX] = GroupedEntry{IDX, MODE, BM, ST, (int)TcConfig<BM, ST, MODE>::kSmemBytes, &launch_grouped<BM, ST, MODE>};
+    t[IDX] = GroupedEntry{IDX, MODE, BM, ST, (int)TcConfig<BM, ST, MODE, 1, FUSED != 0>::kSmemBytes,
+                          &launch_grouped<BM, ST, MODE, FUSED != 0>, FUSED};
   }
 }
 
@@ -117,7 +120,7 @@ void add_grouped(GroupedEntry* t) {
 void G3_TU_REGISTER(FamilyEntry* table) { G3_FAMILY_LIST(G3_ADD_MEMBER) }
 #undef G3_ADD_MEMBER
 
-#define G3_ADD_GROUPED(idx, mode, bm, st) add_grouped<idx, mode, bm, st>(table);
+#define G3_ADD_GROUPED(idx, mode, bm, st, fused) add_grouped<idx, mode, bm, st, fused>(table);
 void G3_TU_REGISTER_GROUPED(GroupedEntry* table) { G3_GROUPED_LIST(G3_ADD_GROUPED) }
 #undef G3_ADD_GROUPED
 

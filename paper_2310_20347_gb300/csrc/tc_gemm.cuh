@@ -46,6 +46,14 @@
 // the barriers of both CTAs; each CTA's epilogue drains its own TMEM (its 128
 // columns of C) and reports to the leader.
 //
+// Split inside the kernel (FUSED, grouped FP32-accurate launches on request):
+// sixteen loader-converter warps take the TMA producer's place.  They read FP32 A and
+// B from global memory (any alignment), split every element into bfloat16
+// parts exactly as the split pre-pass does, and store the parts where TMA
+// would have put them, so the MMA issuer and the epilogue are unchanged and
+// the FP32 operands cross the memory system once instead of three times
+// (read, planes written, planes read).
+//
 // Implicit-GEMM convolution (TcParams::conv): A is an NHWC activation tensor;
 // the producer loads each k-block of A (64 channels of one filter tap for bm
 // output pixels) with a TMA im2col load, so the convolution runs through the
@@ -55,6 +63,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "bf16.cuh"
 #include "ptx.cuh"
 #include "sched.cuh"
 
@@ -132,6 +141,11 @@ struct GroupDesc {
   float alpha, beta;
   float* C;
   long long ldc;
+  // FP32 operands read by the loader-converter warps of the FUSED kernels
+  // (row-major, leading dimensions in elements; null otherwise)
+  const float* A;
+  const float* B;
+  long long lda, ldb;
 };
 
 // Tensor maps of one problem: A and B of each operand plane (hi, then the
@@ -176,7 +190,7 @@ struct TcTraits {
   static constexpr bool kTransOk = kPlanes == 1 && !kTf32 && MODE != TC_I8EMU;
 };
 
-template <int BM_T, int STAGES, int MODE, int CG = 1>
+template <int BM_T, int STAGES, int MODE, int CG = 1, bool FUSED = false>
 struct TcConfig {
   using T = TcTraits<MODE>;
   static constexpr uint32_t kABytes = BM_T * 128 / CG;                 // this CTA's rows of A x 128 B
@@ -205,17 +219,29 @@ struct TcConfig {
   // 0.93 now; eight warps with 128 register sums spilled.)
   static constexpr int kEpiWarps = (MODE == TC_I8EMU && BM_T == 256) ? 16 : 4;
   static constexpr int kEpiRows = BM_T / (kEpiWarps / 4);   // rows of the tile per epilogue thread
-  // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128 columns x 4 bytes.
-  static constexpr uint32_t kCStageBytes = 2 * 32 * 128 * 4;
+  // Loader-converter warps of the FUSED members: two groups of eight, each
+  // group filling alternate k-blocks (one group's loads are in flight while
+  // the other splits and stores).  The loads in flight are bounded by the
+  // registers that hold them: six runs of eight per thread here (measured:
+  // 0.75 ms for the 1000-problem batch against 1.20 ms with groups of four
+  // and twelve runs per thread, which spill).
+  static constexpr int kConvWarpsPerGroup = 8;
+  static constexpr int kConvWarps = FUSED ? 2 * kConvWarpsPerGroup : 0;
+  // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128
+  // columns x 4 bytes (none for the FUSED members, whose grouped launches
+  // write C with plain stores).
+  static constexpr uint32_t kCStageBytes = FUSED ? 0 : 2 * 32 * 128 * 4;
   static constexpr uint32_t kBarBytes = 256;
   static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kCStageBytes + kBarBytes;
-  static constexpr int kThreads = 64 + 32 * kEpiWarps;
+  static constexpr int kThreads = 64 + 32 * kEpiWarps + 32 * kConvWarps;
   static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair");
   static_assert(kNumBufs >= 1, "TMEM budget");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
   static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32 && kTmemCols <= 512, "TMEM allocation");
   static_assert(8 * (2 * STAGES + 2 * kMaxBufs + 1) + 8 <= (int)kBarBytes, "barrier area");
+  static_assert(!FUSED || (CG == 1 && BM_T == 64 && (MODE == TC_3XBF16 || MODE == TC_6XBF16)),
+                "in-kernel split: single-CTA FP32-accurate members with 64-row tiles");
 };
 
 // One output tile: rows m0 .. m0+bm-1, columns n0 .. n0+127 of problem g, k-blocks kb0 .. kb1-1.
@@ -355,6 +381,8 @@ struct GroupedSched {
     return EpiJob{d->C, d->ldc, d->m, d->n, d->alpha, d->beta, OUT_F32, nullptr, nullptr, 0, -1};
   }
 
+  __device__ __forceinline__ const GroupDesc* desc(const TileJob& j) const { return gp->groups + j.g; }
+
   __device__ __forceinline__ bool conv() const { return false; }
   __device__ __forceinline__ bool a_mn() const { return false; }
   __device__ __forceinline__ bool b_km() const { return false; }
@@ -368,11 +396,65 @@ __device__ __forceinline__ uint32_t mapa_or_local(uint64_t* bar) {
   return kPair ? mapa_shared(smem_u32(bar), 0) : smem_u32(bar);
 }
 
-template <int BM_T, int STAGES, int MODE, int CG, class Sched>
+// Eight consecutive FP32 elements x[row][col0 .. col0+7] of a row-major
+// matrix (rows x cols, leading dimension ld) into v, zeros outside it; the
+// widest loads the address allows.
+__device__ __forceinline__ void load_run8(const float* __restrict__ x, long long ld, int row, int rows, int col0,
+                                          int cols, float (&v)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+  if (row >= rows || col0 >= cols) return;
+  const float* p = x + (long long)row * ld + col0;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  if (col0 + 8 <= cols && (a & 15u) == 0) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 w = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
+  } else if (col0 + 8 <= cols && (a & 7u) == 0) {
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const float2 u = __ldg(reinterpret_cast<const float2*>(p + e));
+      v[e] = u.x;
+      v[e + 1] = u.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (col0 + e < cols) v[e] = __ldg(p + e);
+  }
+}
+
+// The bfloat16 parts of eight FP32 values -- hi = bf16(x), then lo =
+// bf16(x - hi) (two planes) or mid = bf16(x - hi), lo = bf16((x - hi) - mid)
+// (three planes), the split pre-pass's arithmetic -- as one 16-byte row
+// chunk per plane at dst, dst + plane_bytes, ...
+template <int PLANES>
+__device__ __forceinline__ void store_split8(uint8_t* dst, uint32_t plane_bytes, const float (&v)[8]) {
+  uint32_t w[PLANES][4];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    uint16_t h[2], m[2], l[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      h[q] = bf16_bits(v[e + q]);
+      const float d = v[e + q] - bf16_value(h[q]);
+      m[q] = bf16_bits(d);
+      l[q] = bf16_bits(d - bf16_value(m[q]));
+    }
+    w[0][e / 2] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    w[1][e / 2] = (uint32_t)m[0] | ((uint32_t)m[1] << 16);   // two planes: lo = bf16(x - hi); three: mid
+    if constexpr (PLANES == 3) w[2][e / 2] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+  }
+#pragma unroll
+  for (int p = 0; p < PLANES; ++p)
+    *reinterpret_cast<uint4*>(dst + p * plane_bytes) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+template <int BM_T, int STAGES, int MODE, int CG, class Sched, bool FUSED = false>
 __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long timeout_ns, int* status,
                                              int debug_withhold, const float* scale_a, const float* scale_b) {
   using T = TcTraits<MODE>;
-  using Cfg = TcConfig<BM_T, STAGES, MODE, CG>;
+  using Cfg = TcConfig<BM_T, STAGES, MODE, CG, FUSED>;
   constexpr bool kPair = (CG == 2);
   constexpr bool kIntChunked = (MODE == TC_I8EMU);
   static_assert(!kIntChunked || Cfg::kEpiRows <= 128,
@@ -398,7 +480,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
+      mbar_init(&full[s], FUSED ? Cfg::kConvWarpsPerGroup : 1);   // FUSED: the group's warps arrive
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < (int)Cfg::kNumBufs; ++a) {
@@ -445,7 +527,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane == 0) {
+    if (!FUSED && lane == 0) {
       uint32_t it = 0;
       bool ok = true;
       for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
@@ -607,7 +689,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       while (!mbar_try_wait(drain, 0))
         if (globaltimer_ns() - t0 > timeout_ns) { atomicCAS(status, 0, WD_DRAIN); break; }
     }
-  } else {
+  } else if (warp < 2 + Cfg::kEpiWarps) {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;                  // TMEM lane quarter this warp may access
     float scale = 1.0f;
@@ -846,6 +928,76 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       }   // accumulation chunks
     }
     if (threadIdx.x == 64) bulk_wait_group_all();   // every TMA store of C has completed
+  } else if constexpr (FUSED) {
+    // ------------------------------------------------------------ loader-converters
+    // Group g (kConvWarpsPerGroup warps) fills the stages of the k-blocks whose
+    // iteration index is g mod 2.  A k-block of a 64-row tile is 64 x 64 FP32
+    // elements of A and 64 x 128 of B, i.e. 512 + 1024 runs of eight along the
+    // contiguous dimension, shared out evenly over the group's threads and
+    // loaded into registers before the stage is free, then split and stored --
+    // A's runs in its K-major rows (row r, 16-byte chunk c at chunk position
+    // c ^ (r % 8)), B's in the MN-major boxes of 64 columns (k-row kk, chunk of
+    // 8 columns c at position c ^ (kk % 8)): the 128-byte swizzle TMA applies.
+    constexpr int kGroupThreads = 32 * Cfg::kConvWarpsPerGroup;
+    constexpr int kARuns = BM_T * (T::kBK / 8);            // 512
+    constexpr int kBRuns = T::kBK * (128 / 8);             // 1024
+    static_assert(kARuns % kGroupThreads == 0 && kBRuns % kGroupThreads == 0, "runs per thread");
+    constexpr int kAPer = kARuns / kGroupThreads, kBPer = kBRuns / kGroupThreads;
+    const int cw = warp - 2 - Cfg::kEpiWarps;
+    const uint32_t grp = (uint32_t)(cw / Cfg::kConvWarpsPerGroup);
+    const int gt = (cw % Cfg::kConvWarpsPerGroup) * 32 + lane;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
+      const TileJob j = S.tile(t);
+      if (j.kb1 <= j.kb0) continue;
+      const GroupDesc* d = S.desc(j);
+      const float* A = d->A;
+      const float* B = d->B;
+      const long long lda = d->lda, ldb = d->ldb;
+      const int m = d->m, n = d->n, k = d->k;
+      for (int kb = j.kb0; kb < j.kb1; ++kb, ++it) {
+        if ((it & 1u) != grp) continue;
+        const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
+        const int k0 = kb * T::kBK;
+        float va[kAPer][8], vb[kBPer][8];
+#pragma unroll
+        for (int i = 0; i < kAPer; ++i) {
+          const int u = gt + i * kGroupThreads;
+          load_run8(A, lda, j.m0 + (u >> 3), m, k0 + (u & 7) * 8, k, va[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kBPer; ++i) {
+          const int u = gt + i * kGroupThreads;
+          load_run8(B, ldb, k0 + (u >> 4), k, j.n0 + (u & 15) * 8, n, vb[i]);
+        }
+        bool free_ok = wait_parity(&empty[stage], ph ^ 1u, wd, WD_PRODUCER_EMPTY);
+        free_ok = __all_sync(0xffffffffu, free_ok);
+        if (!free_ok) {
+          ok = false;
+          break;
+        }
+        if ((int)it == debug_withhold) continue;   // failure-detection test: the stage never fills
+        uint8_t* st = smem + stage * Cfg::kStageBytes;
+#pragma unroll
+        for (int i = 0; i < kAPer; ++i) {
+          const int u = gt + i * kGroupThreads;
+          const int r = u >> 3, c = u & 7;
+          store_split8<T::kPlanes>(st + T::kBtBytes + r * 128 + ((c ^ (r & 7)) << 4), Cfg::kPlaneBytes, va[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kBPer; ++i) {
+          const int u = gt + i * kGroupThreads;
+          const int kk = u >> 4, c = u & 15;
+          store_split8<T::kPlanes>(st + (c >> 3) * (T::kBK * 128) + kk * 128 + (((c & 7) ^ (kk & 7)) << 4),
+                                   Cfg::kPlaneBytes, vb[i]);
+        }
+        // the tensor core reads the stage through the async proxy
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[stage]);
+      }
+    }
   }
 
   tc_fence_before();
@@ -881,6 +1033,16 @@ __global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE, CG>::kThreads, 1)
   const int n_off = (CG == 2) ? 128 * (int)cluster_ctarank() : 0;
   const SingleSched<BM_T, CG, TcStreamK<BM_T, MODE>::value> S{&p, {&tmA, &tmB, &tmA1, &tmB1, &tmA2, &tmB2}, p.c_tma ? &tmC : nullptr, n_off};
   tc_gemm_body<BM_T, STAGES, MODE, CG>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
+}
+
+// The same with the FP32-accurate split inside the kernel (loader-converter
+// warps in place of TMA loads; C by plain stores).
+template <int BM_T, int STAGES, int MODE>
+__global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE, 1, true>::kThreads, 1)
+    tc_grouped_fused_kernel(const __grid_constant__ GroupedParams gp) {
+  const GroupedSched S{&gp};
+  tc_gemm_body<BM_T, STAGES, MODE, 1, GroupedSched, true>(S, gp.timeout_ns, gp.status, gp.debug_withhold, nullptr,
+                                                          nullptr);
 }
 
 // Many independent problems in one persistent launch: every CTA walks the

@@ -104,6 +104,17 @@ def enumerate_family():
 # buffers are sized for bm_max = 128; one member per mode with the deepest ring.
 GROUPED_MODES = ("bf16", "3xbf16", "6xbf16", "fp8")
 GROUPED_BM_MAX = 128
+# Grouped FP32-accurate members that split inside the kernel: loader-converter
+# warps read the FP32 operands and write the bf16 parts into the stages
+# themselves (no TMA loads, no split pre-pass); 64-row tiles keep a k-block's
+# runs in the registers of two groups of eight warps, and there is no C
+# staging (grouped launches write C with plain stores).
+GROUPED_FUSED_MODES = ("3xbf16", "6xbf16")
+GROUPED_FUSED_BM = 64
+
+
+def smem_bytes_fused(mode: str, bm: int, stages: int) -> int:
+    return ALIGN_SLACK + stages * stage_bytes(mode, bm) + BAR_BYTES
 
 
 def enumerate_grouped():
@@ -112,7 +123,12 @@ def enumerate_grouped():
         fits = [s for s in range(2, 9) if smem_bytes(mode, GROUPED_BM_MAX, s) <= SMEM_LIMIT]
         st = max(fits)
         out.append({"index": len(out), "mode": mode, "bm_max": GROUPED_BM_MAX, "stages": st,
-                    "smem": smem_bytes(mode, GROUPED_BM_MAX, st)})
+                    "smem": smem_bytes(mode, GROUPED_BM_MAX, st), "fused": 0})
+    for mode in GROUPED_FUSED_MODES:
+        fits = [s for s in range(2, 9) if smem_bytes_fused(mode, GROUPED_FUSED_BM, s) <= SMEM_LIMIT]
+        st = max(fits)
+        out.append({"index": len(out), "mode": mode, "bm_max": GROUPED_FUSED_BM, "stages": st,
+                    "smem": smem_bytes_fused(mode, GROUPED_FUSED_BM, st), "fused": 1})
     return out
 
 
@@ -127,10 +143,11 @@ def write(out_dir: str) -> list:
     lines.append("")
     lines.append(f"#define G3_FAMILY_SIZE {len(members)}")
     lines.append("")
-    lines.append("// X(index, mode, bm_max, stages): persistent grouped kernels")
+    lines.append("// X(index, mode, bm_max, stages, fused): persistent grouped kernels (fused = 1: the")
+    lines.append("// FP32-accurate split inside the kernel)")
     lines.append("#define G3_GROUPED_LIST(X) \\")
     for g in grouped:
-        lines.append(f"  X({g['index']}, {MODE_ENUM[g['mode']]}, {g['bm_max']}, {g['stages']}) \\")
+        lines.append(f"  X({g['index']}, {MODE_ENUM[g['mode']]}, {g['bm_max']}, {g['stages']}, {g['fused']}) \\")
     lines.append("")
     lines.append(f"#define G3_GROUPED_SIZE {len(grouped)}")
     text = "\n".join(lines) + "\n"

@@ -176,9 +176,11 @@ class GroupedPlan:
     """A g3_grouped_plan over (A, B, C, alpha, beta) tuples of torch tensors
     -- (A, B, C, alpha, beta, scale_a, scale_b) for G3_FP8_E4M3, the scales
     as Python floats or one-element tensors (read once here).  The tensors
-    must stay alive while the plan exists."""
+    must stay alive while the plan exists.  split_in_kernel=True: an
+    FP32-accurate plan splits inside the grouped kernels
+    (G3_GROUPED_SPLIT_IN_KERNEL) instead of in a pre-pass."""
 
-    def __init__(self, problems, dtype):
+    def __init__(self, problems, dtype, split_in_kernel=False):
         in_t = _ELEM[dtype][0]
         descs = []
         self._keep = []
@@ -200,7 +202,7 @@ class GroupedPlan:
             d.scale_b = float(sb.item()) if torch.is_tensor(sb) else float(sb)
             descs.append(d)
             self._keep.append((A, B, C))
-        st, plan = _lib.g3_grouped_plan_create(descs, dtype)
+        st, plan = _lib.g3_grouped_plan_create(descs, dtype, _lib.G3_GROUPED_SPLIT_IN_KERNEL if split_in_kernel else None)
         check(st, "g3_grouped_plan_create")
         self.plan = plan
 

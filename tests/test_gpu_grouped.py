@@ -281,3 +281,72 @@ def test_autotune_grouped_records_the_bucket(dtype):
     assert _lib.g3_grouped_plan_describe(plan.plan, 0)[1:] == (bm, 1 if dtype == G3_F32_3XBF16 else 0)
     plan.close()
     _lib.g3_tune_cache_clear()
+
+
+def _outputs(probs, host):
+    """Reset every C to its initial value (or to zero where beta = 0)."""
+    for (A, B, C, a, b), (p, full) in zip(probs, host):
+        C.copy_(torch.from_numpy(p.C) if p.C is not None else torch.zeros(p.m, p.n))
+
+
+def test_grouped_split_in_kernel_matches_the_pre_split_plan():
+    # On request FP32-accurate plans split inside the grouped kernels: the
+    # loader-converter warps read FP32 rows of any alignment (every second
+    # problem has rows that are not 16-byte multiples) and write the bf16 parts
+    # the split pre-pass would write, so each problem equals the default plan's
+    # result bit for bit where that plan also takes 64-row tiles (m <= 64), and
+    # every problem passes the oracle checks.  k spans both sides of 512
+    # (three- and two-part splits) and ragged k-blocks; the split-in-kernel
+    # plan runs no preparation kernel.
+    probs, host = make_batch(48, seed=7, lo=1, hi=900, dtype=G3_F32_3XBF16, unaligned_every=2)
+    assert any(p.k <= 512 for p, _ in host) and any(p.k > 512 for p, _ in host)
+    fused = torch_api.GroupedPlan(probs, G3_F32_3XBF16, split_in_kernel=True)
+    pre = torch_api.GroupedPlan(probs, G3_F32_3XBF16)
+    kinds = set()
+    for i, (p, _) in enumerate(host):
+        st, bm, kind = _lib.g3_grouped_plan_describe(fused.plan, i)
+        assert st == 0 and bm == 64, (i, bm)
+        kinds.add(kind)
+    l0 = _lib.g3_launch_count()
+    fused.execute()
+    assert _lib.g3_launch_count() - l0 == len(kinds)
+    torch.cuda.synchronize()
+    got_fused = [C.cpu().numpy().copy() for (_, _, C, _, _) in probs]
+    check_batch(probs, host, G3_F32_3XBF16)
+    _outputs(probs, host)
+    l0 = _lib.g3_launch_count()
+    pre.execute()
+    assert _lib.g3_launch_count() - l0 == len(kinds) + 1
+    torch.cuda.synchronize()
+    check_batch(probs, host, G3_F32_3XBF16)
+    same = 0
+    for i, ((_, _, C, _, _), (p, _)) in enumerate(zip(probs, host)):
+        if _lib.g3_grouped_plan_describe(pre.plan, i)[1] == 64:
+            assert np.array_equal(C.cpu().numpy().view(np.uint32), got_fused[i].view(np.uint32)), (p.m, p.n, p.k)
+            same += 1
+    assert same >= 10, same
+    fused.close()
+    pre.close()
+
+
+def test_grouped_split_in_kernel_watchdog_and_flags():
+    # a stage the loader-converter warps never fill: the MMA issuer's wait
+    # expires, the status reports it, and the next execution is correct;
+    # unknown flag bits are rejected
+    probs, host = make_batch(10, seed=8, lo=64, hi=700, dtype=G3_F32_3XBF16, unaligned_every=3)
+    plan = torch_api.GroupedPlan(probs, G3_F32_3XBF16, split_in_kernel=True)
+    assert _lib.g3_debug_withhold_next(200) == 0
+    plan.execute()
+    st, code = torch_api.device_status()
+    assert st == _lib.G3_ERR_TIMEOUT and code != 0
+    _outputs(probs, host)
+    plan.execute()
+    torch.cuda.synchronize()
+    check_batch(probs, host, G3_F32_3XBF16)
+    assert torch_api.device_status()[0] == 0
+    plan.close()
+    d = _lib.g3_gemm_desc()
+    d.m = d.n = d.k = 0
+    d.lda = d.ldb = d.ldc = 1
+    st, _ = _lib.g3_grouped_plan_create([d], G3_F32_3XBF16, 2)
+    assert st == _lib.G3_ERR_ARG
