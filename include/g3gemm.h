@@ -64,6 +64,10 @@ extern "C" {
  *                  C float32 = alpha*scale_a*scale_b*(Aq Bq) + beta*C.
  *   G3_INT8        A, B int8; C int32; alpha must be 1 and beta 0 or 1; exact
  *                  (k <= 131072 so that no int32 overflow is possible).
+ *                  Single-CTA tiles read the int8 operands as they are (an
+ *                  aligned copy only for rows that are not 16-byte
+ *                  multiples) and convert them in the kernel; CTA pairs and
+ *                  deep 128-row tiles convert them in a pre-pass.
  *   G3_FP16        A, B IEEE binary16 (raw 16-bit patterns); C float32.
  *   G3_TF32        A, B, C float32; A and B rounded to TF32 (10 fraction
  *                  bits, nearest even) by a pre-pass, products on kind::tf32

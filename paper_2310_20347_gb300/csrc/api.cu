@@ -212,6 +212,23 @@ int encode_2d(CUtensorMap* map, const void* base, int esize, uint64_t inner, uin
   return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
 }
 
+// A row-major int8 matrix (outer rows x inner bytes, leading dimension ld
+// bytes) in unswizzled boxes of box_inner x box_outer: the raw tiles of the
+// RAW8 members; out-of-range bytes read as zero.
+int encode_raw8_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_inner,
+                   uint32_t box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return G3_ERR_CUDA;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? G3_OK : G3_ERR_CUDA;
+}
+
 // C (m rows x n columns of 4-byte elements, leading dimension ldc) for TMA
 // stores of 32-row x 128-column boxes, no swizzle (row-major staging tile).
 int encode_c_2d(CUtensorMap* map, void* base, bool is_int, uint64_t n, uint64_t m, uint64_t ldc) {
@@ -377,12 +394,14 @@ void tune_env_once() {
 Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_member, int force_split,
                int force_raster, bool allow_splitk = true) {
   Plan pl;
+  bool automatic = force_member < 0;   // the member is the planner's own choice
   if (force_member < 0 && force_split == 0) {
     tune_env_once();
     auto it = g_tune.find(tune_key(m, n, k, dtype));
     if (it != g_tune.end()) {
       force_member = it->second.member;
       force_split = it->second.split;
+      automatic = false;
     }
   }
   const int mode = tc_mode_of(dtype, k);
@@ -427,7 +446,7 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     double best = 1e300;
     for (int i = 0; i < G3_FAMILY_SIZE; ++i) {
       const FamilyEntry& f = g_family[i];
-      if (!f.launch || f.mode != mode) continue;
+      if (!f.launch || f.mode != mode || f.raw8) continue;
       // first (deepest) variant per (bm, cg)
       if (pl.member >= 0 && g_family[pl.member].bm == f.bm && g_family[pl.member].cg == f.cg) continue;
       splits_for(f, [&](int s) {
@@ -437,6 +456,22 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     }
   }
   if (pl.member < 0) return pl;
+  // INT8 on one CTA: the member's twin that reads the int8 operands as they
+  // are (tiles of at most 128 rows) replaces the int8 -> bf16 conversion
+  // pass.  Its tiles convert their own blocks of A and B, k (bm + 128) / (128
+  // bm) elements per output against the pass's (mk + kn) / mn, which on
+  // 128-row tiles deep in k with many rows of A costs more than the pass
+  // saves (measured on the im2col layers: 512 x 3136 x 1024 and 2048 x 784 x
+  // 1024 ran 18 us against 15): those, and CTA pairs, keep the pass.
+  const bool deep128 = std::min(g_family[pl.member].bm, 128) == 128 && k >= 1024 && m > 128;
+  if (automatic && mode == TC_I8EMU && g_family[pl.member].cg == 1 && !g_family[pl.member].raw8 && !deep128) {
+    const int want = std::min(g_family[pl.member].bm, 128);
+    for (int i = 0; i < G3_FAMILY_SIZE; ++i)
+      if (g_family[i].launch && g_family[i].raw8 && g_family[i].bm == want) {
+        pl.member = i;
+        break;
+      }
+  }
   const int bm = g_family[pl.member].bm;
   const int cg = g_family[pl.member].cg;
   pl.tiles_n = (int)((n + 128LL * cg - 1) / (128LL * cg));
@@ -546,6 +581,16 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl, bool b_prepared = fals
       L.b_lo = take((size_t)n * L.ldb_p * 4);
       break;
     case G3_INT8:
+      if (pl.member >= 0 && g_family[pl.member].raw8) {
+        // int8 read as it is: only rows TMA cannot address get an aligned copy
+        L.pack_a = !tma_ok(a.A, a.lda, 1);
+        L.pack_b = !tma_ok(a.B, a.ldb, 1);
+        L.lda_p = L.pack_a ? round_up(k, 16) : a.lda;
+        L.ldb_p = L.pack_b ? round_up(n, 16) : a.ldb;
+        if (L.pack_a) L.a_hi = take((size_t)m * L.lda_p);
+        if (L.pack_b) L.b_hi = take((size_t)k * L.ldb_p);
+        break;
+      }
       L.pack_a = L.pack_b = true;
       L.lda_p = round_up(k, 8);
       L.ldb_p = round_up(n, 8);
@@ -838,6 +883,17 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
     A_hi = ah; A_lo = al; B_hi = bh; B_lo = bl;
     lda = L.lda_p;
     ldb = L.ldb_p;
+  } else if (a.dtype == G3_INT8 && fam.raw8) {
+    if (L.pack_a) {
+      G3_CHECK_CUDA(launch_pack_rows(a.A, (int)m, k, a.lda, ws + L.a_hi, L.lda_p, s));
+      A_hi = ws + L.a_hi;
+    }
+    if (L.pack_b) {
+      G3_CHECK_CUDA(launch_pack_rows(a.B, (int)k, n, a.ldb, ws + L.b_hi, L.ldb_p, s));
+      B_hi = ws + L.b_hi;
+    }
+    lda = L.lda_p;
+    ldb = L.ldb_p;
   } else if (a.dtype == G3_INT8) {
     uint16_t *ah = (uint16_t*)(ws + L.a_hi), *bh = (uint16_t*)(ws + L.b_hi);
     G3_CHECK_CUDA(launch_int8_to_bf16_pair((const int8_t*)a.A, (int)m, (int)k, a.lda, ah, L.lda_p,
@@ -868,7 +924,10 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   CUtensorMap maps[7];
   std::memset(maps, 0, sizeof(maps));
   const uint32_t arows = fam.bm / fam.cg;   // rows of A one CTA stages (half the tile in a pair)
-  if (conv) {
+  if (fam.raw8) {
+    // raw int8 tiles: A as 64 bytes of k x bm rows, B as 128 columns x 64 k-rows
+    if ((st = encode_raw8_2d(&maps[0], A_hi, k, m, lda, 64, fam.bm)) != G3_OK) return st;
+  } else if (conv) {
     if ((st = encode_im2col(&maps[0], a.A, es, *conv, arows)) != G3_OK) return st;
   } else if (a.trans_a) {   // A stored k x m: boxes of (128 bytes of m) x bk
     if ((st = encode_2d(&maps[0], A_hi, es, m, k, lda, boxn, bk)) != G3_OK) return st;
@@ -876,7 +935,9 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
     return st;
   }
   const bool b_kmajor = a.dtype == G3_TF32 || a.dtype == G3_F32_3XTF32 || a.trans_b;
-  if (b_kmajor) {   // B stored n x k: boxes of bk (k) x 128 (n rows)
+  if (fam.raw8) {
+    if ((st = encode_raw8_2d(&maps[1], B_hi, n, k, ldb, 128, 64)) != G3_OK) return st;
+  } else if (b_kmajor) {   // B stored n x k: boxes of bk (k) x 128 (n rows)
     if ((st = encode_2d(&maps[1], B_hi, es, k, n, ldb, bk, 128)) != G3_OK) return st;
   } else if ((st = encode_2d(&maps[1], B_hi, es, n, k, ldb, boxn, bk)) != G3_OK) {
     return st;

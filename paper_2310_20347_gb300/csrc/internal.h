@@ -28,6 +28,7 @@ struct FamilyEntry {
   TcLaunchFn launch;
   int (*slots)(int sms);   // CTAs (pairs) that can be resident at once; 0 on error
   bool stream_k;           // takes a stream-K tail (TcParams::sk_*)
+  bool raw8;               // INT8 member reading the int8 operands as they are (converted in the kernel)
 };
 
 void register_family_bf16(FamilyEntry* table);

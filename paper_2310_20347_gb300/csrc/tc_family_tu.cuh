@@ -64,12 +64,11 @@ int tc_slots(int sms) {
 
 // Persistent grid: one CTA (or CTA pair) per tile up to the member's slots;
 // with a stream-K tail exactly p.sk_streams of them (one per stream).
-template <int BM, int ST, int MODE, int CG>
+// RAW8 members (single-CTA INT8 reading the int8 operands as they are) take
+// the raw int8 maps of A and B and C's map.
+template <int BM, int ST, int MODE, int CG, bool RAW8>
 cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int sms, cudaStream_t s) {
-  using Cfg = TcConfig<BM, ST, MODE, CG>;
-  auto kern = tc_gemm_kernel<BM, ST, MODE, CG>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
-  if (e != cudaSuccess) return e;
+  using Cfg = TcConfig<BM, ST, MODE, CG, false, RAW8>;
   const int slots = tc_slots<BM, ST, MODE, CG>(sms);
   if (slots <= 0) return cudaErrorInvalidConfiguration;
   const long long work = (long long)p.tiles_m * p.tiles_n * p.splits;
@@ -77,17 +76,29 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcParams& p, int sms, cudaS
   cudaLaunchAttribute attr[2];
   cudaLaunchConfig_t cfg = pdl_config((int)(CG * clusters), Cfg::kThreads, Cfg::kSmemBytes, s, attr);
   if constexpr (CG > 1) set_cluster(cfg, attr, CG);
-  e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], p);
+  cudaError_t e;
+  if constexpr (RAW8) {
+    auto kern = tc_gemm_raw8_kernel<BM, ST, MODE>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[6], p);
+  } else {
+    auto kern = tc_gemm_kernel<BM, ST, MODE, CG>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], maps[6], p);
+  }
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int IDX, int MODE, int BM, int ST, int CG>
+template <int IDX, int MODE, int BM, int ST, int CG, int RAW8>
 void add_member(FamilyEntry* t) {
   if constexpr (MODE == G3_TU_MODE) {
-    using Cfg = TcConfig<BM, ST, MODE, CG>;
-    t[IDX] = FamilyEntry{IDX, MODE, BM, ST, (int)Cfg::kSmemBytes, (int)Cfg::kNumBufs, CG, &launch_tc<BM, ST, MODE, CG>,
-                         &tc_slots<BM, ST, MODE, CG>, TcStreamK<BM, MODE>::value};
+    using Cfg = TcConfig<BM, ST, MODE, CG, false, RAW8 != 0>;
+    t[IDX] = FamilyEntry{IDX, MODE, BM, ST, (int)Cfg::kSmemBytes, (int)Cfg::kNumBufs, CG,
+                         &launch_tc<BM, ST, MODE, CG, RAW8 != 0>, &tc_slots<BM, ST, MODE, CG>,
+                         TcStreamK<BM, MODE>::value, RAW8 != 0};
   }
 }
 
@@ -116,7 +127,7 @@ void add_grouped(GroupedEntry* t) {
 
 }  // namespace
 
-#define G3_ADD_MEMBER(idx, mode, bm, st, cg) add_member<idx, mode, bm, st, cg>(table);
+#define G3_ADD_MEMBER(idx, mode, bm, st, cg, raw8) add_member<idx, mode, bm, st, cg, raw8>(table);
 void G3_TU_REGISTER(FamilyEntry* table) { G3_FAMILY_LIST(G3_ADD_MEMBER) }
 #undef G3_ADD_MEMBER
 

@@ -54,6 +54,13 @@
 // the FP32 operands cross the memory system once instead of three times
 // (read, planes written, planes read).
 //
+// INT8 read as int8 (RAW8 members): TMA loads the raw int8 tiles of A and B
+// into a small ring of their own, and converter warps write their exact
+// binary16 values into the stage in the swizzled layout (kind::f16 with the
+// F16 format: products and the chunked FP32 sums stay exact), so the operands
+// cross HBM once at one byte per element instead of through a conversion pass
+// that writes and re-reads two.
+//
 // Implicit-GEMM convolution (TcParams::conv): A is an NHWC activation tensor;
 // the producer loads each k-block of A (64 channels of one filter tap for bm
 // output pixels) with a TMA im2col load, so the convolution runs through the
@@ -190,7 +197,7 @@ struct TcTraits {
   static constexpr bool kTransOk = kPlanes == 1 && !kTf32 && MODE != TC_I8EMU;
 };
 
-template <int BM_T, int STAGES, int MODE, int CG = 1, bool FUSED = false>
+template <int BM_T, int STAGES, int MODE, int CG = 1, bool FUSED = false, bool RAW8 = false>
 struct TcConfig {
   using T = TcTraits<MODE>;
   static constexpr uint32_t kABytes = BM_T * 128 / CG;                 // this CTA's rows of A x 128 B
@@ -225,21 +232,32 @@ struct TcConfig {
   // registers that hold them: six runs of eight per thread here (measured:
   // 0.75 ms for the 1000-problem batch against 1.20 ms with groups of four
   // and twelve runs per thread, which spill).
-  static constexpr int kConvWarpsPerGroup = 8;
-  static constexpr int kConvWarps = FUSED ? 2 * kConvWarpsPerGroup : 0;
+  // RAW8: eight converter warps for 64-row tiles, four for 128 (whose 128
+  // int32 register sums per epilogue thread spill beside eight; measured on
+  // the 20 im2col layers: 64 rows 8 warps up to 1.3x faster than 4, 128 rows
+  // 4 warps up to 1.6x faster than 8; two warps, converting at half the rate,
+  // lost everywhere).
+  static constexpr int kConvWarpsPerGroup = RAW8 ? (BM_T == 64 ? 8 : 4) : 8;
+  static constexpr int kConvWarps = FUSED ? 2 * kConvWarpsPerGroup : (RAW8 ? kConvWarpsPerGroup : 0);
+  // RAW8 members: a ring of raw int8 tiles (bm rows x 64 bytes of A, 64
+  // k-rows x 128 bytes of B per k-block) between the TMA and the converters.
+  static constexpr int kRawStages = RAW8 ? 4 : 0;
+  static constexpr uint32_t kRawBytes = RAW8 ? (uint32_t)(BM_T * 64 + 64 * 128) : 0u;
   // Epilogue staging for TMA stores of C: two buffers of 32 rows x 128
   // columns x 4 bytes (none for the FUSED members, whose grouped launches
   // write C with plain stores).
   static constexpr uint32_t kCStageBytes = FUSED ? 0 : 2 * 32 * 128 * 4;
   static constexpr uint32_t kBarBytes = 256;
-  static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kCStageBytes + kBarBytes;
+  static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kRawStages * kRawBytes + kCStageBytes + kBarBytes;
   static constexpr int kThreads = 64 + 32 * kEpiWarps + 32 * kConvWarps;
   static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair");
   static_assert(kNumBufs >= 1, "TMEM budget");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
   static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32 && kTmemCols <= 512, "TMEM allocation");
-  static_assert(8 * (2 * STAGES + 2 * kMaxBufs + 1) + 8 <= (int)kBarBytes, "barrier area");
+  static_assert(8 * (2 * STAGES + 2 * kMaxBufs + 1) + 8 + 16 * kRawStages <= (int)kBarBytes, "barrier area");
+  static_assert(!RAW8 || (MODE == TC_I8EMU && CG == 1 && BM_T <= 128 && !FUSED),
+                "raw int8 staging: single-CTA INT8 members of at most 128 rows");
   static_assert(!FUSED || (CG == 1 && BM_T == 64 && (MODE == TC_3XBF16 || MODE == TC_6XBF16)),
                 "in-kernel split: single-CTA FP32-accurate members with 64-row tiles");
 };
@@ -424,6 +442,22 @@ __device__ __forceinline__ void load_run8(const float* __restrict__ x, long long
   }
 }
 
+// Eight int8 values (8 bytes) as IEEE binary16, exact, in one 16-byte row
+// chunk at dst, two values per instruction: each byte, biased by 128, becomes
+// the low mantissa byte of 1024 in a half2 (one byte permute per pair), and
+// one packed subtraction of 1024 + 128 leaves the pair exactly (|x| <= 128
+// needs 8 of binary16's 11 significant bits).
+__device__ __forceinline__ void store_i8_as_f16(uint8_t* dst, const uint2& v) {
+  const uint32_t b[2] = {v.x ^ 0x80808080u, v.y ^ 0x80808080u};
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t biased = __byte_perm(b[q >> 1], 0x64646464u, (q & 1) ? 0x4342u : 0x4140u);
+    asm("sub.f16x2 %0, %1, %2;" : "=r"(w[q]) : "r"(biased), "r"(0x64806480u));
+  }
+  *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // The bfloat16 parts of eight FP32 values -- hi = bf16(x), then lo =
 // bf16(x - hi) (two planes) or mid = bf16(x - hi), lo = bf16((x - hi) - mid)
 // (three planes), the split pre-pass's arithmetic -- as one 16-byte row
@@ -450,11 +484,11 @@ __device__ __forceinline__ void store_split8(uint8_t* dst, uint32_t plane_bytes,
     *reinterpret_cast<uint4*>(dst + p * plane_bytes) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
-template <int BM_T, int STAGES, int MODE, int CG, class Sched, bool FUSED = false>
+template <int BM_T, int STAGES, int MODE, int CG, class Sched, bool FUSED = false, bool RAW8 = false>
 __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long timeout_ns, int* status,
                                              int debug_withhold, const float* scale_a, const float* scale_b) {
   using T = TcTraits<MODE>;
-  using Cfg = TcConfig<BM_T, STAGES, MODE, CG, FUSED>;
+  using Cfg = TcConfig<BM_T, STAGES, MODE, CG, FUSED, RAW8>;
   constexpr bool kPair = (CG == 2);
   constexpr bool kIntChunked = (MODE == TC_I8EMU);
   static_assert(!kIntChunked || Cfg::kEpiRows <= 128,
@@ -462,14 +496,17 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  float* cstage = reinterpret_cast<float*>(smem + STAGES * Cfg::kStageBytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::kStageBytes + Cfg::kCStageBytes);
+  uint8_t* ring8 = smem + STAGES * Cfg::kStageBytes;   // RAW8: the int8 ring
+  float* cstage = reinterpret_cast<float*>(ring8 + Cfg::kRawStages * Cfg::kRawBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring8 + Cfg::kRawStages * Cfg::kRawBytes + Cfg::kCStageBytes);
   uint64_t* empty = full + STAGES;
   uint64_t* tmem_full = empty + STAGES;
   uint64_t* tmem_empty = tmem_full + Cfg::kMaxBufs;
   uint64_t* drain = tmem_empty + Cfg::kMaxBufs;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(tmem_slot + 2);   // RAW8 only
+  uint64_t* raw_empty = raw_full + Cfg::kRawStages;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -480,8 +517,13 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], FUSED ? Cfg::kConvWarpsPerGroup : 1);   // FUSED: the group's warps arrive
+      // FUSED: the group's warps arrive; RAW8: the converter warps
+      mbar_init(&full[s], (FUSED || RAW8) ? Cfg::kConvWarpsPerGroup : 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int r = 0; r < Cfg::kRawStages; ++r) {
+      mbar_init(&raw_full[r], 1);
+      mbar_init(&raw_empty[r], Cfg::kConvWarpsPerGroup);
     }
     for (int a = 0; a < (int)Cfg::kNumBufs; ++a) {
       mbar_init(&tmem_full[a], 1);
@@ -527,7 +569,33 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (!FUSED && lane == 0) {
+    if (RAW8 && lane == 0) {
+      // raw int8 boxes: A (64 bytes of k x bm rows) and B (128 columns x 64
+      // k-rows), unswizzled, into the raw ring
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
+        const TileJob j = S.tile(t);
+        if (j.kb1 <= j.kb0) continue;
+        for (int kb = j.kb0; kb < j.kb1; ++kb, ++it) {
+          const uint32_t rs = it % Cfg::kRawStages, rph = (it / Cfg::kRawStages) & 1u;
+          if (!wait_parity(&raw_empty[rs], rph ^ 1u, wd, WD_PRODUCER_EMPTY)) { ok = false; break; }
+          if ((int)it == debug_withhold) continue;   // failure-detection test: never arrive
+          mbar_arrive_expect_tx(&raw_full[rs], Cfg::kRawBytes);
+          uint8_t* rb = ring8 + rs * Cfg::kRawBytes;
+          tma_load_2d(rb, S.map(j, 0), kb * 64, j.m0, &raw_full[rs]);
+          tma_load_2d(rb + BM_T * 64, S.map(j, 1), j.n0, kb * 64, &raw_full[rs]);
+        }
+      }
+      // the last raw loads have landed before the CTA can retire
+      const uint32_t first = it > (uint32_t)Cfg::kRawStages ? it - Cfg::kRawStages : 0u;
+      for (uint32_t q = first; q < it; ++q) {
+        uint64_t t0 = globaltimer_ns();
+        while (!mbar_try_wait(&raw_full[q % Cfg::kRawStages], (q / Cfg::kRawStages) & 1u))
+          if (globaltimer_ns() - t0 > timeout_ns) { atomicCAS(status, 0, WD_DRAIN); break; }
+      }
+    }
+    if (!FUSED && !RAW8 && lane == 0) {
       uint32_t it = 0;
       bool ok = true;
       for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
@@ -610,7 +678,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
         const TileJob j = S.tile(t);
         if (j.kb1 <= j.kb0) continue;
-        const uint32_t idesc = make_idesc(T::kAFmt, T::kAFmt, /*a_mn=*/!bt_km, /*b_mn=*/a_mn, 128 * CG, j.bm);
+        // RAW8 stages hold binary16 (exact int8 values), the others T's format
+        constexpr uint32_t kFmt = RAW8 ? 0u : T::kAFmt;
+        const uint32_t idesc = make_idesc(kFmt, kFmt, /*a_mn=*/!bt_km, /*b_mn=*/a_mn, 128 * CG, j.bm);
         const int span = j.kchunk > 0 ? j.kchunk : j.kb1 - j.kb0;
         for (int c0 = j.kb0; ok && c0 < j.kb1; c0 += span, ++lt) {
         const int c1 = min(j.kb1, c0 + span);
@@ -928,6 +998,57 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       }   // accumulation chunks
     }
     if (threadIdx.x == 64) bulk_wait_group_all();   // every TMA store of C has completed
+  } else if constexpr (RAW8) {
+    // ------------------------------------------------------------ int8 converters
+    // The converter warps turn each raw k-block into the stage's binary16 tile: run u of
+    // eight int8 values -- A: row r = u / 8, bytes 8*(u % 8) of its 64; B:
+    // k-row kk = u / 16, columns 8*(u % 16) of its 128 -- read from the raw
+    // tile and stored as binary16 where TMA puts the 16-bit operands (A: row r, chunk c at
+    // c ^ (r % 8); B: box of 64 columns, k-row kk, chunk at c ^ (kk % 8)).
+    constexpr int kThreadsC = 32 * Cfg::kConvWarpsPerGroup;
+    constexpr int kARuns = BM_T * 8, kBRuns = 64 * 16;
+    static_assert(kARuns % kThreadsC == 0 && kBRuns % kThreadsC == 0, "runs per thread");
+    const int ct = (warp - 2 - Cfg::kEpiWarps) * 32 + lane;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
+      const TileJob j = S.tile(t);
+      if (j.kb1 <= j.kb0) continue;
+      for (int kb = j.kb0; kb < j.kb1; ++kb, ++it) {
+        const uint32_t stage = it % STAGES, ph = (it / STAGES) & 1u;
+        const uint32_t rs = it % Cfg::kRawStages, rph = (it / Cfg::kRawStages) & 1u;
+        bool w_ok = wait_parity(&raw_full[rs], rph, wd, WD_MMA_FULL);
+        w_ok = w_ok && wait_parity(&empty[stage], ph ^ 1u, wd, WD_PRODUCER_EMPTY);
+        w_ok = __all_sync(0xffffffffu, w_ok);
+        if (!w_ok) {
+          ok = false;
+          break;
+        }
+        const uint8_t* rb = ring8 + rs * Cfg::kRawBytes;
+        uint8_t* st = smem + stage * Cfg::kStageBytes;
+#pragma unroll
+        for (int i = 0; i < kARuns / kThreadsC; ++i) {
+          const int u = ct + i * kThreadsC;
+          const int r = u >> 3, c = u & 7;
+          store_i8_as_f16(st + T::kBtBytes + r * 128 + ((c ^ (r & 7)) << 4),
+                          *reinterpret_cast<const uint2*>(rb + r * 64 + c * 8));
+        }
+#pragma unroll
+        for (int i = 0; i < kBRuns / kThreadsC; ++i) {
+          const int u = ct + i * kThreadsC;
+          const int kk = u >> 4, c = u & 15;
+          store_i8_as_f16(st + (c >> 3) * (T::kBK * 128) + kk * 128 + (((c & 7) ^ (kk & 7)) << 4),
+                          *reinterpret_cast<const uint2*>(rb + BM_T * 64 + kk * 128 + c * 8));
+        }
+        // the tensor core reads the stage through the async proxy
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&full[stage]);
+          mbar_arrive(&raw_empty[rs]);
+        }
+      }
+    }
   } else if constexpr (FUSED) {
     // ------------------------------------------------------------ loader-converters
     // Group g (kConvWarpsPerGroup warps) fills the stages of the k-blocks whose
@@ -1033,6 +1154,23 @@ __global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE, CG>::kThreads, 1)
   const int n_off = (CG == 2) ? 128 * (int)cluster_ctarank() : 0;
   const SingleSched<BM_T, CG, TcStreamK<BM_T, MODE>::value> S{&p, {&tmA, &tmB, &tmA1, &tmB1, &tmA2, &tmB2}, p.c_tma ? &tmC : nullptr, n_off};
   tc_gemm_body<BM_T, STAGES, MODE, CG>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a, p.scale_b);
+}
+
+// INT8 members that read the int8 operands as they are (RAW8): tmA / tmB
+// address the raw int8 matrices.
+template <int BM_T, int STAGES, int MODE>
+__global__ void __launch_bounds__(TcConfig<BM_T, STAGES, MODE, 1, false, true>::kThreads, 1)
+    tc_gemm_raw8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmC, const __grid_constant__ TcParams p) {
+  if (threadIdx.x == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+    if (p.c_tma) tma_prefetch_desc(&tmC);
+  }
+  using Sch = SingleSched<BM_T, 1, TcStreamK<BM_T, MODE>::value>;
+  const Sch S{&p, {&tmA, &tmB, &tmA, &tmB, &tmA, &tmB}, p.c_tma ? &tmC : nullptr, 0};
+  tc_gemm_body<BM_T, STAGES, MODE, 1, Sch, false, true>(S, p.timeout_ns, p.status, p.debug_withhold, p.scale_a,
+                                                        p.scale_b);
 }
 
 // The same with the FP32-accurate split inside the kernel (loader-converter

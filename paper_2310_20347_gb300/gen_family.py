@@ -56,6 +56,8 @@ MAX_BM = {"int8emu": 256}
 # CTA-pair members: tile heights worth pairing (a pair of bm = 64 tiles would
 # stage 32-row halves of A, no better than a single bm = 128 CTA)
 PAIR_BMS = (256, 128)
+RAW8_BMS = (128, 64)
+RAW8_STAGES = 4
 # TMEM columns one CTA of a pair allocates (the pair allocates collectively:
 # both CTAs receive the same address, which the kernel checks)
 PAIR_TMEM_COLUMNS = 512
@@ -93,7 +95,18 @@ def enumerate_family():
                 bufs = min(4, tmem // acc_cols)                     # accumulator sets across tiles
                 for st in chosen:
                     members.append({"mode": mode, "bm": bm, "stages": st, "cg": cg,
-                                    "smem": smem_bytes(mode, bm, st, cg), "tmem_bufs": bufs})
+                                    "smem": smem_bytes(mode, bm, st, cg), "tmem_bufs": bufs, "raw8": 0})
+    # INT8 members that read the int8 operands as they are: TMA fills a ring
+    # of raw int8 tiles (RAW8_STAGES k-blocks of bm x 64 + 64 x 128 bytes) and
+    # converter warps write the exact bfloat16 tile into the stage; single-CTA,
+    # at most 128 rows; the deepest bf16 ring that fits beside the raw ring
+    for bm in RAW8_BMS:
+        raw = RAW8_STAGES * (bm * 64 + 64 * 128)
+        fits = [s for s in range(2, 9) if smem_bytes("int8emu", bm, s, 1) + raw <= SMEM_LIMIT]
+        st = max(fits)
+        members.append({"mode": "int8emu", "bm": bm, "stages": st, "cg": 1,
+                        "smem": smem_bytes("int8emu", bm, st, 1) + raw, "tmem_bufs": min(4, TMEM_COLUMNS // bm),
+                        "raw8": 1})
     for i, m in enumerate(members):
         m["index"] = i
     return members
@@ -136,10 +149,10 @@ def write(out_dir: str) -> list:
     members = enumerate_family()
     grouped = enumerate_grouped()
     lines = ["// Generated by gen_family.py -- do not edit.",
-             "// X(index, mode, bm, stages, cg)",
+             "// X(index, mode, bm, stages, cg, raw8): raw8 = 1 reads int8 operands as they are",
              "#define G3_FAMILY_LIST(X) \\"]
     for m in members:
-        lines.append(f"  X({m['index']}, {MODE_ENUM[m['mode']]}, {m['bm']}, {m['stages']}, {m['cg']}) \\")
+        lines.append(f"  X({m['index']}, {MODE_ENUM[m['mode']]}, {m['bm']}, {m['stages']}, {m['cg']}, {m['raw8']}) \\")
     lines.append("")
     lines.append(f"#define G3_FAMILY_SIZE {len(members)}")
     lines.append("")
