@@ -66,8 +66,9 @@ extern "C" {
  *                  (k <= 131072 so that no int32 overflow is possible).
  *                  Single-CTA tiles read the int8 operands as they are (an
  *                  aligned copy only for rows that are not 16-byte
- *                  multiples) and convert them in the kernel; CTA pairs and
- *                  deep 128-row tiles convert them in a pre-pass.
+ *                  multiples) and convert them in the kernel, k split so
+ *                  that each split sums at most 1024 products; CTA pairs
+ *                  and deeper splits convert them in a pre-pass.
  *   G3_FP16        A, B IEEE binary16 (raw 16-bit patterns); C float32.
  *   G3_TF32        A, B, C float32; A and B rounded to TF32 (10 fraction
  *                  bits, nearest even) by a pre-pass, products on kind::tf32

@@ -458,13 +458,11 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   if (pl.member < 0) return pl;
   // INT8 on one CTA: the member's twin that reads the int8 operands as they
   // are (tiles of at most 128 rows) replaces the int8 -> bf16 conversion
-  // pass.  Its tiles convert their own blocks of A and B, k (bm + 128) / (128
-  // bm) elements per output against the pass's (mk + kn) / mn, which on
-  // 128-row tiles deep in k with many rows of A costs more than the pass
-  // saves (measured on the im2col layers: 512 x 3136 x 1024 and 2048 x 784 x
-  // 1024 ran 18 us against 15): those, and CTA pairs, keep the pass.
-  const bool deep128 = std::min(g_family[pl.member].bm, 128) == 128 && k >= 1024 && m > 128;
-  if (automatic && mode == TC_I8EMU && g_family[pl.member].cg == 1 && !g_family[pl.member].raw8 && !deep128) {
+  // pass where the planner's split already keeps every split within one
+  // exact accumulation chunk (16 k-blocks, 1024 products), which RAW8 members
+  // require; deeper splits, and CTA pairs, keep the pass.
+  const bool one_chunk = (pl.num_kb + best_split - 1) / std::max(best_split, 1) <= 16;
+  if (automatic && mode == TC_I8EMU && g_family[pl.member].cg == 1 && !g_family[pl.member].raw8 && one_chunk) {
     const int want = std::min(g_family[pl.member].bm, 128);
     for (int i = 0; i < G3_FAMILY_SIZE; ++i)
       if (g_family[i].launch && g_family[i].raw8 && g_family[i].bm == want) {
@@ -491,6 +489,8 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
   // (3xTF32) per accumulator; split-K beyond.
   if (force_split == 0 && mode == TC_3XTF32) splits = std::max(splits, (pl.num_kb + 255) / 256);
   if (force_split == 0 && mode == TC_3XBF16) splits = std::max(splits, (pl.num_kb + 511) / 512);
+  // RAW8 members: every split within one exact FP32 chunk of 16 k-blocks
+  if (g_family[pl.member].raw8) splits = std::max(splits, (pl.num_kb + 15) / 16);
   splits = std::min(splits, pl.num_kb);
   pl.kb_per_split = (pl.num_kb + splits - 1) / splits;
   pl.splits = (pl.num_kb + pl.kb_per_split - 1) / pl.kb_per_split;
@@ -980,7 +980,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   p.a_mn = a.trans_a ? 1 : 0;
   p.b_km = a.trans_b ? 1 : 0;
   // INT8: at most 16 k-blocks (1024 products, |sum| <= 2^24) per FP32 accumulator
-  p.kchunk = (a.dtype == G3_INT8) ? 16 : 0;
+  p.kchunk = (a.dtype == G3_INT8 && !fam.raw8) ? 16 : 0;
   if (conv) {
     p.conv = 1;
     p.conv_pq = (int)(conv->P * conv->Q);

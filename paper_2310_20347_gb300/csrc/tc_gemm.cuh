@@ -232,12 +232,9 @@ struct TcConfig {
   // registers that hold them: six runs of eight per thread here (measured:
   // 0.75 ms for the 1000-problem batch against 1.20 ms with groups of four
   // and twelve runs per thread, which spill).
-  // RAW8: eight converter warps for 64-row tiles, four for 128 (whose 128
-  // int32 register sums per epilogue thread spill beside eight; measured on
-  // the 20 im2col layers: 64 rows 8 warps up to 1.3x faster than 4, 128 rows
-  // 4 warps up to 1.6x faster than 8; two warps, converting at half the rate,
-  // lost everywhere).
-  static constexpr int kConvWarpsPerGroup = RAW8 ? (BM_T == 64 ? 8 : 4) : 8;
+  // RAW8: eight converter warps (two, converting at a quarter of the rate,
+  // lost everywhere on the 20 im2col layers; four lost on 64-row tiles).
+  static constexpr int kConvWarpsPerGroup = 8;
   static constexpr int kConvWarps = FUSED ? 2 * kConvWarpsPerGroup : (RAW8 ? kConvWarpsPerGroup : 0);
   // RAW8 members: a ring of raw int8 tiles (bm rows x 64 bytes of A, 64
   // k-rows x 128 bytes of B per k-block) between the TMA and the converters.
@@ -490,7 +487,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   using T = TcTraits<MODE>;
   using Cfg = TcConfig<BM_T, STAGES, MODE, CG, FUSED, RAW8>;
   constexpr bool kPair = (CG == 2);
-  constexpr bool kIntChunked = (MODE == TC_I8EMU);
+  // INT8 members sum k in exact chunks of at most 1024 products, added in
+  // int32 registers by the epilogue; RAW8 members instead keep every tile's
+  // k range (every split) within one chunk, so their FP32 accumulator is exact
+  // as it stands and the epilogue converts it to int32 once.
+  constexpr bool kIntChunked = (MODE == TC_I8EMU) && !RAW8;
+  constexpr bool kIntOut = (MODE == TC_I8EMU);
   static_assert(!kIntChunked || Cfg::kEpiRows <= 128,
                 "int32 running sums in registers: <= 128 rows");
   extern __shared__ uint8_t smem_raw[];
@@ -916,7 +918,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             for (int i = 0; i < 32; ++i) buf[i * 128] = __int_as_float(__float2int_rn(__uint_as_float(r[i])));
           } else if (e.out_mode == OUT_PARTIAL) {   // the raw sum: alpha is applied by the reduction
 #pragma unroll
-            for (int i = 0; i < 32; ++i) buf[i * 128] = __uint_as_float(r[i]);
+            for (int i = 0; i < 32; ++i)
+              buf[i * 128] = kIntOut ? __int_as_float(__float2int_rn(__uint_as_float(r[i]))) : __uint_as_float(r[i]);
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i) buf[i * 128] = alpha * __uint_as_float(r[i]);
@@ -954,7 +957,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
             float* pp = e.partial + (long long)i0 * e.ldp + col;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (i < iend) pp[(long long)i * e.ldp] = __uint_as_float(r[i]);
+              if (i < iend)
+                pp[(long long)i * e.ldp] =
+                    kIntOut ? __int_as_float(__float2int_rn(__uint_as_float(r[i]))) : __uint_as_float(r[i]);
           }
         }
       };
