@@ -68,7 +68,7 @@ extern "C" {
  *                  aligned copy only for rows that are not 16-byte
  *                  multiples) and convert them in the kernel, k split so
  *                  that each split sums at most 1024 products; CTA pairs
- *                  and deeper splits convert them in a pre-pass.
+ *                  convert them in a pre-pass.
  *   G3_FP16        A, B IEEE binary16 (raw 16-bit patterns); C float32.
  *   G3_TF32        A, B, C float32; A and B rounded to TF32 (10 fraction
  *                  bits, nearest even) by a pre-pass, products on kind::tf32

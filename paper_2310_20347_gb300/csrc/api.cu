@@ -456,14 +456,15 @@ Plan make_plan(int64_t m, int64_t n, int64_t k, int dtype, int sms, int force_me
     }
   }
   if (pl.member < 0) return pl;
-  // INT8 on one CTA: the member's twin that reads the int8 operands as they
-  // are (tiles of at most 128 rows) replaces the int8 -> bf16 conversion
-  // pass where the planner's split already keeps every split within one
-  // exact accumulation chunk (16 k-blocks, 1024 products), which RAW8 members
-  // require; deeper splits, and CTA pairs, keep the pass.
-  const bool one_chunk = (pl.num_kb + best_split - 1) / std::max(best_split, 1) <= 16;
-  if (automatic && mode == TC_I8EMU && g_family[pl.member].cg == 1 && !g_family[pl.member].raw8 && one_chunk) {
-    const int want = std::min(g_family[pl.member].bm, 128);
+  // INT8 on one CTA: a twin that reads the int8 operands as they are
+  // replaces the int8 -> bf16 conversion pass (CTA pairs keep it).  RAW8
+  // members split k so that every split is one exact accumulation chunk (16
+  // k-blocks, 1024 products); past one chunk the 128-row twin, whose tiles
+  // convert fewer blocks of B per output (measured on the deep im2col layers:
+  // 256 x 3136 x 2304 15.8 us against 18.9 with 64 rows and 20.3 with the
+  // pass; 512 x 784 x 4608 16.5 against 25.5).
+  if (automatic && mode == TC_I8EMU && g_family[pl.member].cg == 1 && !g_family[pl.member].raw8) {
+    const int want = pl.num_kb > 16 ? 128 : std::min(g_family[pl.member].bm, 128);
     for (int i = 0; i < G3_FAMILY_SIZE; ++i)
       if (g_family[i].launch && g_family[i].raw8 && g_family[i].bm == want) {
         pl.member = i;

@@ -52,11 +52,11 @@ def test_planner_reads_int8_as_is_for_single_cta_shapes(m, n, k, beta):
         # pass, only copies of unaligned operands and the split-K reduction
         copies = int(k % 16 != 0) + int(n % 16 != 0)
         assert launches == 1 + copies + (1 if split > 1 else 0), (launches, split, copies)
+        # every split one exact accumulation chunk
+        assert -(-(-(-k // 64)) // max(split, 1)) <= 16, (k, split)
     else:
-        # the conversion pass stays for CTA pairs and where a split would hold
-        # more than one exact accumulation chunk (16 k-blocks)
-        kb = -(-k // 64)
-        assert FAMILY[cfg]["cg"] == 2 or -(-kb // max(split, 1)) > 16, (m, n, k, cfg, split)
+        # the conversion pass stays for CTA pairs only
+        assert FAMILY[cfg]["cg"] == 2, (m, n, k, cfg, split)
         assert launches == 2 + (1 if split > 1 else 0), (launches, split)
 
 
