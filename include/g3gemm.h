@@ -320,9 +320,13 @@ G3_API int g3_grouped_plan_create_ex(int count, const g3_gemm_desc* descs, int d
 
 /* Run every problem of the plan: pre-passes (if any) and one persistent
  * kernel launch per kernel kind (BF16, FP8: one; FP32-accurate: one for the
- * problems with k > 512 and one for those with k <= 512).  No host
- * synchronisation and no allocation, so the call can be captured into a CUDA
- * graph.                                                                    */
+ * problems with k > 512 and one for those with k <= 512).  A plan with two
+ * kinds that both have split jobs runs the first kind (its jobs and launch)
+ * on a stream of its own, forked from `cuda_stream` by an event and joined
+ * back into it before the call returns, beside the second kind's; all of the
+ * plan's work is ordered on `cuda_stream`.  No
+ * host synchronisation and no allocation, so the call can be captured into
+ * a CUDA graph.                                                             */
 G3_API int g3_grouped_plan_execute(g3_grouped_plan* plan, void* cuda_stream);
 
 G3_API int g3_grouped_plan_destroy(g3_grouped_plan* plan);

@@ -181,6 +181,12 @@ struct g3_grouped_plan {
   // the three-part split), -1 / -1 for problems without products
   std::vector<int> bms, kinds;
   bool fused = false;   // FP32-accurate split inside the grouped kernels
+  // Two kernel kinds with preparation jobs each (FP32-accurate, split in a
+  // pre-pass): kind 0's jobs and launch run on a plan-owned side stream,
+  // forked from and joined back into the caller's stream, beside kind 1's.
+  int njobs0 = 0;       // jobs of kind 0 (and the C := beta*C jobs) first, then kind 1's
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -243,6 +249,7 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, i
   // ---- per-problem tiling, jobs and plane sizes (host)
   std::vector<GroupDesc> groups(count);
   std::vector<PrepJob> jobs;
+  std::vector<int> job_kind;   // kernel kind whose launch reads the job's output (0 for C := beta*C)
   struct Operands { size_t a_off = 0, a_lo_off = 0, b_off = 0, b_lo_off = 0, a_mid_off = 0, b_mid_off = 0;
                     int64_t lda = 0, ldb = 0;
                     bool pack_a = false, pack_b = false; bool active = false; };
@@ -272,6 +279,7 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, i
       PrepJob J{};
       J.src = d.C; J.ld_src = d.ldc; J.rows = g.m; J.cols = g.n; J.kind = PREP_SCALE_C; J.beta = (float)d.beta;
       jobs.push_back(J);
+      job_kind.push_back(0);
       continue;
     }
     Operands& o = ops[i];
@@ -344,15 +352,19 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, i
       const int va = aligned16(d.A, d.lda, 4) ? 1 : 0, vb = aligned16(d.B, d.ldb, 4) ? 1 : 0;
       jobs.push_back(PrepJob{d.A, d.lda, (void*)a, (void*)a_lo, (void*)a_mid, o.lda, g.m, g.k, kind, 0.f, va});
       jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, (void*)b_lo, (void*)b_mid, o.ldb, g.k, g.n, kind, 0.f, vb});
+      job_kind.push_back(part_of(d.k));
+      job_kind.push_back(part_of(d.k));
     } else {
       const int copy = fp8 ? PREP_COPY8 : PREP_COPY16;
       if (o.pack_a) {
         a = d_planes + o.a_off;
         jobs.push_back(PrepJob{d.A, d.lda, (void*)a, nullptr, nullptr, o.lda, g.m, g.k, copy, 0.f, 0});
+        job_kind.push_back(0);
       }
       if (o.pack_b) {
         b = d_planes + o.b_off;
         jobs.push_back(PrepJob{d.B, d.ldb, (void*)b, nullptr, nullptr, o.ldb, g.k, g.n, copy, 0.f, 0});
+        job_kind.push_back(0);
       }
     }
     // maps 2p, 2p+1 = A, B of plane p: hi; then lo (two-part) or mid, lo
@@ -397,6 +409,14 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, i
       part_tiles[part] += nt;
     }
 
+  // kind 0's jobs first, then kind 1's (order kept within each)
+  std::vector<PrepJob> ordered;
+  ordered.reserve(jobs.size());
+  for (int kind = 0; kind < 2; ++kind)
+    for (size_t q = 0; q < jobs.size(); ++q)
+      if (job_kind[q] == kind) ordered.push_back(jobs[q]);
+  const int njobs0 = (int)std::count(job_kind.begin(), job_kind.end(), 0);
+  jobs.swap(ordered);
   bool ok = true;
   ok = ok && cudaMemcpy(d_maps, maps.data(), sizeof(CUtensorMap) * kMapsPerProblem * (size_t)count,
                         cudaMemcpyHostToDevice) ==
@@ -426,6 +446,7 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, i
   plan->count = count;
   plan->total_tiles = (int)total_tiles;
   plan->njobs = (int)jobs.size();
+  plan->njobs0 = njobs0;
   plan->sms = dev.sms;
   plan->d_jobs = d_jobs;
   int first = 0;
@@ -442,6 +463,15 @@ int plan_create(int count, const g3_gemm_desc* descs, int dtype, int force_bm, i
     plan->entry[plan->nparts] = entries[part];
     ++plan->nparts;
     first += part_tiles[part];
+  }
+  if (plan->nparts == 2 && plan->njobs0 > 0 && plan->njobs > plan->njobs0) {
+    if (cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      g3_grouped_plan_destroy(plan);
+      return G3_ERR_CUDA;
+    }
   }
   *out = plan;
   return G3_OK;
@@ -475,12 +505,15 @@ int g3_grouped_plan_execute(g3_grouped_plan* plan, void* stream) {
     cudaGetLastError();
     return G3_ERR_ARG;
   }
-  if (plan->njobs > 0) {
-    const dim3 grid(16, (unsigned)std::min(plan->njobs, 65535));
-    grouped_prep_kernel<<<grid, 256, 0, s>>>(plan->d_jobs, plan->njobs);
+  auto prep = [&](const PrepJob* jobs, int n, cudaStream_t st) -> bool {
+    if (n <= 0) return true;
+    const dim3 grid(16, (unsigned)std::min(n, 65535));
+    grouped_prep_kernel<<<grid, 256, 0, st>>>(jobs, n);
     count_launch();
-    if (cudaGetLastError() != cudaSuccess) return G3_ERR_CUDA;
-  }
+    return cudaGetLastError() == cudaSuccess;
+  };
+  const bool forked = plan->side != nullptr && plan->total_tiles > 0;
+  if (!forked && !prep(plan->d_jobs, plan->njobs, s)) return G3_ERR_CUDA;
   if (plan->total_tiles == 0) return G3_OK;
   GroupedParams p[2] = {plan->params[0], plan->params[1]};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -498,9 +531,25 @@ int g3_grouped_plan_execute(g3_grouped_plan* plan, void* stream) {
   }
   if (e0) cudaEventRecord(e0, s);
   cudaError_t e = cudaSuccess;
-  for (int part = 0; part < plan->nparts && e == cudaSuccess; ++part) {
-    const int grid = std::min(p[part].total_tiles, plan->sms);
-    e = g_grouped[plan->entry[part]].launch(p[part], grid, s);
+  if (forked) {
+    // kind 0's jobs and launch on the side stream, kind 1's on the caller's
+    // (measured: the two kinds' split passes together reach more bandwidth
+    // than one; kind 0's jobs first, then its launch beside kind 1's jobs,
+    // gained nothing), then join
+    if (cudaEventRecord(plan->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(plan->side, plan->ev_fork, 0) != cudaSuccess)
+      return G3_ERR_CUDA;
+    if (!prep(plan->d_jobs, plan->njobs0, plan->side)) return G3_ERR_CUDA;
+    e = g_grouped[plan->entry[0]].launch(p[0], std::min(p[0].total_tiles, plan->sms), plan->side);
+    if (e == cudaSuccess && !prep(plan->d_jobs + plan->njobs0, plan->njobs - plan->njobs0, s)) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = g_grouped[plan->entry[1]].launch(p[1], std::min(p[1].total_tiles, plan->sms), s);
+    if (e == cudaSuccess && (cudaEventRecord(plan->ev_join, plan->side) != cudaSuccess ||
+                             cudaStreamWaitEvent(s, plan->ev_join, 0) != cudaSuccess))
+      e = cudaErrorUnknown;
+  } else {
+    for (int part = 0; part < plan->nparts && e == cudaSuccess; ++part) {
+      const int grid = std::min(p[part].total_tiles, plan->sms);
+      e = g_grouped[plan->entry[part]].launch(p[part], grid, s);
+    }
   }
   if (e1) {
     cudaEventRecord(e1, s);
@@ -520,6 +569,10 @@ int g3_grouped_plan_destroy(g3_grouped_plan* plan) {
     cudaFree(plan->dmem);   // synchronises with work still using the plan
     cudaGetLastError();
   }
+  if (plan->side) cudaStreamDestroy(plan->side);
+  if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+  if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+  cudaGetLastError();
   delete plan;
   return G3_OK;
 }
