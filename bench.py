@@ -203,12 +203,18 @@ TRAFFIC_RECORD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profi
 
 
 def kernel_sources_hash():
+    """SHA-256 of the headline kernel's sources with comments and whitespace
+    removed: the code the DRAM-traffic record was taken with."""
     import hashlib
+    import re
     pkg = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2310_20347_gb300")
     h = hashlib.sha256()
     for rel in TRAFFIC_SOURCES:
-        with open(os.path.join(pkg, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(pkg, rel)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 
