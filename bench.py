@@ -197,7 +197,7 @@ NOMINAL_TFLOPS = {"bf16": 2250.0, "fp8": 4500.0, "tf32": 1125.0}
 # only while these files hash to the recorded value and the member and size
 # match the record.
 TRAFFIC_SOURCES = ("csrc/tc_gemm.cuh", "csrc/ptx.cuh", "csrc/sched.cuh", "csrc/tc_family_tu.cuh",
-                   "csrc/tc_family_3xbf16.cu")
+                   "csrc/tc_family_3xbf16.cu", "csrc/api.cu")
 TRAFFIC_RECORD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                               "tc_gemm_3xbf16_16384_dram.md")
 

@@ -194,8 +194,19 @@ G3_API int g3_set_stream(void* cuda_stream);
  *                      through distributed shared memory in a fixed order (no
  *                      workspace); 1 forbids it; 0 lets the planner take it
  *                      when fewer 64 x 64 blocks than SMs would run.
- *   raster             0: the planner's choice; >= 1 the band width (in tiles)
- *                      of the tile walk.
+ *   raster             0: the planner's choice (8 tile rows; for a claimed
+ *                      walk 2-8, as many as keep the band's panels of A
+ *                      within 80 MiB of L2); >= 1 the band width (in tiles)
+ *                      of the tile walk.  Launches of at least 16 waves of
+ *                      tiles claim their tiles in walk order from a counter
+ *                      (one int in the workspace, zeroed by a memset before
+ *                      the call's first launch) rather than each CTA taking
+ *                      every grid-th tile, so that the tiles running at one
+ *                      time stay neighbours in the walk and share their
+ *                      operand panels in L2; a caller workspace without the
+ *                      256 bytes for it (g3_gemm_workspace_size counts them)
+ *                      keeps the static walk, as does G3_STATIC_WALK=1 in
+ *                      the environment.  Results are the same bit for bit.
  *   trans_a, trans_b   0: A is m x k (lda >= k), B is k x n (ldb >= n);
  *                      1: the operand is stored transposed -- A as k x m
  *                      (lda >= m), B as n x k (ldb >= k) -- and C := beta*C
@@ -360,7 +371,8 @@ G3_API int g3_gemm_grouped(int count, const g3_gemm_desc* descs, int dtype, void
  * raw device code is stored in *code when code != NULL: 0x101-0x105 name the
  * wait that expired (producer, MMA stage, MMA accumulator, epilogue, drain);
  * 0x106: the two CTAs of a CTA-pair member were given different TMEM
- * addresses, and the kernel did no work.                                     */
+ * addresses, and the kernel did no work; 0x107: the wait for a claimed tile
+ * number (or for a free entry of the queue that passes it on).              */
 G3_API int g3_get_last_device_status(int* code);
 
 G3_API const char* g3_status_string(int status);

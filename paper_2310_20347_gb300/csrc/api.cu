@@ -623,6 +623,58 @@ Layout make_layout(const g3_gemm_args& a, const Plan& pl, bool b_prepared = fals
   return L;
 }
 
+// Long launches claim their tiles (TcParams::tile_ctr) instead of walking
+// them statically: at least kClaimMinWaves waves of work items, no stream-K
+// tail, not a RAW8 member.  Over a long launch the CTAs of a static walk
+// drift apart by more than the time L2 keeps a panel, so the tiles sharing a
+// panel of B read it from DRAM one by one; claimed tiles run together in
+// claim order.  The counter (one int, zeroed by a memset before the call's
+// first launch) sits in the 256 bytes after the call's workspace layout; a
+// caller-provided workspace without room for it keeps the static walk.
+// G3_STATIC_WALK=1 in the environment forces the static walk (A/B timing).
+constexpr int kClaimMinWaves = 16;
+constexpr size_t kClaimBytes = 256;
+
+bool claims_tiles(const Plan& pl, int sms) {
+  if (pl.member < 0 || pl.sk_streams > 0) return false;
+  const FamilyEntry& f = g_family[pl.member];
+  if (f.raw8) return false;
+  const char* e = std::getenv("G3_STATIC_WALK");
+  if (e && e[0] == '1') return false;
+  const int slots = f.slots(sms);
+  const long long work = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
+  return slots > 0 && work >= (long long)kClaimMinWaves * slots;
+}
+
+// Band width of a claimed walk unless the caller forces one: as many tile
+// rows (2 to 8) as keep the band's panels of A within 80 MiB of the 129 MB
+// L2, so that they stay there while the B panels stream past, each read by
+// the band's tiles claimed one after another.  Measured on the FP32-accurate
+// 16384^3 pair member (16 MB of bf16 planes per 256-row panel), per launch:
+// bands of 3, 4, 5, 6 rows 14.37, 14.06, 13.96, 13.92 ms, 8 rows 14.15-14.76
+// ms (the static walk: 14.63-15.56 ms); 80 MiB gives 5 there.
+constexpr double kClaimBandBytes = 80.0 * (1 << 20);
+
+// Bytes of A one tile row of k holds in shared memory (all planes).
+int staged_a_bytes(int mode) {
+  switch (mode) {
+    case TC_3XBF16: return 4;
+    case TC_6XBF16: return 6;
+    case TC_FP8: return 1;
+    case TC_TF32: return 4;
+    case TC_3XTF32: return 8;
+    default: return 2;   // BF16, FP16, INT8 staged as bf16
+  }
+}
+
+int walk_raster(const Plan& pl, bool claim, int forced) {
+  if (!claim || forced > 0) return pl.raster;
+  const FamilyEntry& f = g_family[pl.member];
+  const double panel = (double)f.bm * pl.kb_per_split * kblock_of(f.mode) * staged_a_bytes(f.mode);
+  const int band = std::max(2, std::min(8, (int)(kClaimBandBytes / std::max(panel, 1.0))));
+  return std::min(band, pl.tiles_m);
+}
+
 int get_workspace(DevState& d, const g3_gemm_args& a, size_t need, uint8_t** out) {
   *out = nullptr;
   if (need == 0) return G3_OK;
@@ -834,9 +886,12 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   }
   if (pb && tc_mode_of(a.dtype, a.k) != TC_3XBF16) return G3_ERR_ARG;   // only the two-part split
   const Layout L = make_layout(a, pl, pb != nullptr);
+  const bool claim = claims_tiles(pl, d.sms) && (!a.workspace || a.workspace_bytes >= L.total + kClaimBytes);
   uint8_t* ws = nullptr;
-  int st = get_workspace(d, a, L.total, &ws);
+  int st = get_workspace(d, a, L.total + (claim ? kClaimBytes : 0), &ws);
   if (st != G3_OK) return st;
+  int* tile_ctr = claim ? reinterpret_cast<int*>(ws + L.total) : nullptr;
+  if (claim) G3_CHECK_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(int), s));
 
   const int64_t m = a.m, n = a.n, k = a.k;
   const int es = (a.dtype == G3_FP8_E4M3) ? 1 : ((a.dtype == G3_TF32 || a.dtype == G3_F32_3XTF32) ? 4 : 2);
@@ -968,7 +1023,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   p.splits = pl.splits;
   p.kb_per_split = pl.kb_per_split;
   p.num_kb = pl.num_kb;
-  p.raster = pl.raster;
+  p.raster = walk_raster(pl, claim, a.raster);
   p.alpha = (float)a.alpha;
   p.beta = (float)a.beta;
   p.scale_a = (a.dtype == G3_FP8_E4M3) ? a.scale_a : nullptr;
@@ -980,6 +1035,7 @@ int run_tc(DevState& d, const g3_gemm_args& a, cudaStream_t s, const ConvDesc* c
   p.debug_withhold = -1;
   p.a_mn = a.trans_a ? 1 : 0;
   p.b_km = a.trans_b ? 1 : 0;
+  p.tile_ctr = tile_ctr;
   // INT8: at most 16 k-blocks (1024 products, |sum| <= 2^24) per FP32 accumulator
   p.kchunk = (a.dtype == G3_INT8 && !fam.raw8) ? 16 : 0;
   if (conv) {
@@ -1307,7 +1363,8 @@ static int gemm_host_impl(const g3_gemm_args& a, cudaStream_t s) {
     if (products && d->sms > 0 && a.dtype != G3_F32 && a.dtype != G3_F64 && a.dtype != G3_INT16) {
       auto need_of = [&](const g3_gemm_args& blk, bool prepared) {
         const Plan pl = make_plan(blk.m, blk.n, blk.k, blk.dtype, d->sms, blk.config, blk.split_k, blk.raster, true);
-        return pl.member < 0 ? size_t(0) : make_layout(blk, pl, prepared).total;
+        return pl.member < 0 ? size_t(0)
+                             : make_layout(blk, pl, prepared).total + (claims_tiles(pl, d->sms) ? kClaimBytes : 0);
       };
       for (int b = 0; b < nb; ++b) {
         int64_t r0, r1;
@@ -1543,6 +1600,7 @@ int g3_gemm_workspace_size(const g3_gemm_args* args, size_t* bytes) {
   if (a.trans_b) { a.B = d->ws ? d->ws : reinterpret_cast<void*>(uintptr_t(256)); a.ldb = round_up(a.n, 16); }
   const Plan pl = make_plan(a.m, a.n, a.k, a.dtype, d->sms, a.config, a.split_k, a.raster, !dev_scales);
   *bytes = make_layout(a, pl).total;
+  if (claims_tiles(pl, d->sms)) *bytes += kClaimBytes;
   return G3_OK;
 }
 
@@ -1691,7 +1749,7 @@ int g3_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int* config, int* 
   const Plan pl = make_plan(m, n, std::max<int64_t>(k, 1), dtype, sms, -1, 0, 0, dtype != G3_FP8_E4M3);
   if (config) *config = pl.member;
   if (split_k) *split_k = pl.sk_streams > 0 ? G3_SPLIT_STREAM_K : pl.splits;
-  if (raster) *raster = pl.raster;
+  if (raster) *raster = walk_raster(pl, claims_tiles(pl, sms), 0);
   return G3_OK;
 }
 

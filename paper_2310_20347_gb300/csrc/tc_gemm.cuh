@@ -98,6 +98,7 @@ enum : int {
   WD_EPI_TMEM_FULL = 0x104,
   WD_DRAIN = 0x105,
   WD_PAIR_TMEM = 0x106,   // the two CTAs of a pair did not receive the same TMEM address
+  WD_TILE_QUEUE = 0x107,  // a claimed tile number (or a free entry for one) never arrived
 };
 
 struct TcParams {
@@ -138,6 +139,10 @@ struct TcParams {
   // 16-bit modes only): a_mn = 1, A stored k x m (lda >= m) and staged
   // MN-major; b_km = 1, B stored n x k (ldb >= k) and staged K-major.
   int a_mn, b_km;
+  // Claimed tile walk (non-null; zeroed before the launch): the tiles past each
+  // CTA's (or pair's) first are claimed from this counter in claim order
+  // instead of the static every-gridDim-th walk (not with a stream-K tail).
+  int* tile_ctr;
 };
 
 // One problem of a grouped launch (device table entry).
@@ -246,6 +251,9 @@ struct TcConfig {
   // write C with plain stores).
   static constexpr uint32_t kCStageBytes = FUSED ? 0 : 2 * 32 * 128 * 4;
   static constexpr uint32_t kBarBytes = 256;
+  // Entries of the claimed-tile queue (tile number + full / empty barriers);
+  // the RAW8 and FUSED members always walk statically.
+  static constexpr int kTileQ = (RAW8 || FUSED) ? 0 : 2;
   static constexpr uint32_t kSmemBytes = 1024 + STAGES * kStageBytes + kRawStages * kRawBytes + kCStageBytes + kBarBytes;
   static constexpr int kThreads = 64 + 32 * kEpiWarps + 32 * kConvWarps;
   static_assert(BM_T == 64 || BM_T == 128 || BM_T == 256, "MMA N must be 64, 128 or 256");
@@ -253,7 +261,8 @@ struct TcConfig {
   static_assert(kNumBufs >= 1, "TMEM budget");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
   static_assert((kTmemCols & (kTmemCols - 1)) == 0 && kTmemCols >= 32 && kTmemCols <= 512, "TMEM allocation");
-  static_assert(8 * (2 * STAGES + 2 * kMaxBufs + 1) + 8 + 16 * kRawStages <= (int)kBarBytes, "barrier area");
+  static_assert(8 * (2 * STAGES + 2 * kMaxBufs + 1) + 8 + 16 * kRawStages + 20 * kTileQ <= (int)kBarBytes,
+                "barrier area");
   static_assert(!RAW8 || (MODE == TC_I8EMU && CG == 1 && BM_T <= 128 && !FUSED),
                 "raw int8 staging: single-CTA INT8 members of at most 128 rows");
   static_assert(!FUSED || (CG == 1 && BM_T == 64 && (MODE == TC_3XBF16 || MODE == TC_6XBF16)),
@@ -321,6 +330,10 @@ struct SingleSched {
     return kStreamK && p->sk_streams > 0 ? p->sk_dp + p->sk_streams * p->sk_segs
                                          : p->tiles_m * p->tiles_n * p->splits;
   }
+  // counter of the claimed walk, or null for the static walk
+  __device__ __forceinline__ int* claim_ctr() const {
+    return kStreamK && p->sk_streams > 0 ? nullptr : p->tile_ctr;
+  }
 
   __device__ __forceinline__ TileJob tile(int t) const {
     int tm, tn;
@@ -379,6 +392,7 @@ struct GroupedSched {
   const GroupedParams* gp;
 
   __device__ __forceinline__ int total() const { return gp->total_tiles; }
+  __device__ __forceinline__ int* claim_ctr() const { return nullptr; }   // grouped launches walk statically
 
   __device__ __forceinline__ TileJob tile(int t) const {
     const int2 ti = __ldg(gp->tile_info + t);
@@ -510,6 +524,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint64_t* raw_full = reinterpret_cast<uint64_t*>(tmem_slot + 2);   // RAW8 only
   uint64_t* raw_empty = raw_full + Cfg::kRawStages;
+  uint64_t* tq_full = raw_empty + Cfg::kRawStages;   // claimed-tile queue
+  uint64_t* tq_empty = tq_full + Cfg::kTileQ;
+  volatile int* tq = reinterpret_cast<volatile int*>(tq_empty + Cfg::kTileQ);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -531,6 +548,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
     for (int a = 0; a < (int)Cfg::kNumBufs; ++a) {
       mbar_init(&tmem_full[a], 1);
       mbar_init(&tmem_empty[a], CG * Cfg::kEpiWarps);   // the epilogue warps of every CTA of the pair
+    }
+    for (int q = 0; q < Cfg::kTileQ; ++q) {
+      mbar_init(&tq_full[q], 1);   // the leader's producer publishes
+      // read by the MMA issuer (leader) or producer (peer) and the epilogue
+      // warps of every CTA of the pair; only the leader's barrier is used
+      mbar_init(&tq_empty[q], CG * (1 + Cfg::kEpiWarps));
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -560,6 +583,48 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
 
   Watchdog wd{timeout_ns, status, abort_flag};
   const int total_tiles = pair_ok ? S.total() : 0;
+
+  // Tile walk.  Static: this CTA's (pair's) first tile, then every
+  // tile_stride-th work item.  Claimed (a counter from the host, zeroed
+  // before the launch): the first tile as above, each further one claimed
+  // from the counter by the pair leader's producer as it moves on, so the
+  // tiles in flight are always the most recently claimed -- neighbours in
+  // the banded raster, whose panels of A and B are then read from L2 at
+  // about the same time however far the CTAs of a long launch drift apart.
+  // The producer hands each claimed number to the other roles, and to the
+  // peer CTA of a pair, through a kTileQ-entry queue in shared memory.
+  int* const claim_ctr = Cfg::kTileQ > 0 ? S.claim_ctr() : nullptr;
+  // role 0: the claimer (leader's producer); 1: one thread of a warp; 2: a whole warp
+  auto next_tile = [&](int t, uint32_t& qn, int role) -> int {
+    if constexpr (Cfg::kTileQ == 0) {
+      return t + tile_stride;
+    } else {
+      if (claim_ctr == nullptr) return t + tile_stride;
+      const uint32_t slot = qn % (uint32_t)Cfg::kTileQ, ph = (qn / (uint32_t)Cfg::kTileQ) & 1u;
+      ++qn;
+      if (role == 0) {
+        if (!wait_parity<kPair>(&tq_empty[slot], ph ^ 1u, wd, WD_TILE_QUEUE)) return total_tiles;
+        const int nt = tile_stride + atomicAdd(claim_ctr, 1);
+        tq[slot] = nt;
+        if constexpr (kPair) {
+          st_shared_cluster_u32(mapa_shared(smem_u32(const_cast<int*>(&tq[slot])), 1u), (uint32_t)nt);
+          mbar_arrive_cluster(mapa_shared(smem_u32(&tq_full[slot]), 1u));
+        }
+        mbar_arrive(&tq_full[slot]);
+        return nt;
+      }
+      bool got = wait_parity<kPair>(&tq_full[slot], ph, wd, WD_TILE_QUEUE);
+      if (role == 2) got = __all_sync(0xffffffffu, got);
+      if (!got) return total_tiles;
+      const int nt = tq[slot];
+      if (role == 2) __syncwarp();   // every lane has read the entry before it is released
+      if (role == 1 || lane == 0) {
+        if constexpr (kPair) mbar_arrive_cluster(mapa_shared(smem_u32(&tq_empty[slot]), 0u));
+        else mbar_arrive(&tq_empty[slot]);
+      }
+      return nt;
+    }
+  };
   // Operand layouts of this launch.  Bt (the instruction's A, 128*CG columns
   // of C) is MN-major when B is stored k x n, K-major when stored n x k (and
   // always for TF32).  The A tile (the instruction's B, bm rows of C) is
@@ -599,9 +664,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
       }
     }
     if (!FUSED && !RAW8 && lane == 0) {
-      uint32_t it = 0;
+      uint32_t it = 0, qn = 0;
       bool ok = true;
-      for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
+      for (int t = first_tile; ok && t < total_tiles; t = next_tile(t, qn, leader ? 0 : 1)) {
         const TileJob j = S.tile(t);
         if (j.kb1 <= j.kb0) continue;   // an empty stream-K slot (every role skips it)
         // bytes this CTA stages per k-block; a pair's leader counts both CTAs'
@@ -678,7 +743,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
         if constexpr (kPair) mma_commit_pair(bar, 0x3);
         else mma_commit(bar);
       };
-      for (int t = first_tile; ok && t < total_tiles; t += tile_stride) {
+      uint32_t qn = 0;
+      for (int t = first_tile; ok && t < total_tiles; t = next_tile(t, qn, 1)) {
         const TileJob j = S.tile(t);
         if (j.kb1 <= j.kb0) continue;
         // RAW8 stages hold binary16 (exact int8 values), the others T's format
@@ -774,7 +840,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& S, unsigned long long 
     uint32_t lt = 0;   // accumulation chunks consumed, in the MMA issuer's order
     uint32_t schunk = 0;   // 32-row chunks staged for TMA stores (selects the staging buffer)
     bool alive = true;
-    for (int t = first_tile; alive && t < total_tiles; t += tile_stride) {
+    uint32_t qn = 0;
+    for (int t = first_tile; alive && t < total_tiles; t = next_tile(t, qn, 2)) {
       const TileJob j = S.tile(t);
       if (j.kb1 <= j.kb0) continue;
       const EpiJob e = S.epi(j);

@@ -82,7 +82,7 @@ static void streamk(int tail, int num_kb, int streams) {
 int main() {
   for (int tm = 1; tm <= 9; ++tm)
     for (int tn = 1; tn <= 7; ++tn)
-      for (int band : {1, 2, 3, 8, 16}) raster(tm, tn, band);
+      for (int band : {1, 2, 3, 4, 8, 16}) raster(tm, tn, band);
   raster(64, 64, 8);
   const int streams_list[] = {1, 2, 3, 7, 74, 76, 148, 152};
   const int kb_list[] = {1, 2, 3, 5, 16, 17, 32, 128, 256};
