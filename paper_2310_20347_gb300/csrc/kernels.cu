@@ -283,16 +283,22 @@ cudaError_t launch_splitk_reduce(const float* P, int splits, int rows, int cols,
   // 16-byte accesses of C when its rows allow (the partial planes always do)
   const bool vec = reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0 && ldp % 4 == 0 &&
                    reinterpret_cast<uintptr_t>(P) % 16 == 0;
-  const dim3 grid = rows_grid(rows, cols, 4);
-  if (is_int) {
-    if (vec) splitk_reduce_kernel<true, true><<<grid, 256, 0, s>>>(P, splits, rows, cols, ldp, alpha, beta, C, ldc);
-    else splitk_reduce_kernel<true, false><<<grid, 256, 0, s>>>(P, splits, rows, cols, ldp, alpha, beta, C, ldc);
-  } else {
-    if (vec) splitk_reduce_kernel<false, true><<<grid, 256, 0, s>>>(P, splits, rows, cols, ldp, alpha, beta, C, ldc);
-    else splitk_reduce_kernel<false, false><<<grid, 256, 0, s>>>(P, splits, rows, cols, ldp, alpha, beta, C, ldc);
-  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = rows_grid(rows, cols, 4);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // a dependent of the GEMM
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void (*kern)(const float*, int, int, int, long long, float, float, void*, long long) =
+      is_int ? (vec ? splitk_reduce_kernel<true, true> : splitk_reduce_kernel<true, false>)
+             : (vec ? splitk_reduce_kernel<false, true> : splitk_reduce_kernel<false, false>);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, P, splits, rows, cols, ldp, alpha, beta, C, ldc);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Stream-K fix-up (sched.cuh).  Block (t, y) covers a strip of 256 x 4

@@ -433,10 +433,15 @@ __global__ void scale_c_kernel(TC* __restrict__ C, int rows, int cols, long long
 // Plane s holds rows of ldp elements (whole 128-byte lines).  Each thread
 // takes 4 consecutive columns of a row; VEC: 16-byte loads of the partials
 // and 16-byte accesses of C (columns beyond the last full group of 4 one by
-// one).
+// one).  Launched as a programmatic dependent of the GEMM that writes the
+// partials: its blocks are placed while that grid drains and wait for it (and
+// its memory) before the first read; the next kernel may place its own
+// blocks once these have started.
 template <bool INT, bool VEC>
 __global__ void splitk_reduce_kernel(const float* __restrict__ P, int splits, int rows, int cols, long long ldp,
                                      float alpha, float beta, void* C, long long ldc) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const long long plane = (long long)rows * ldp;
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) * 4; c < cols; c += gridDim.x * blockDim.x * 4) {
