@@ -154,6 +154,12 @@ __device__ __forceinline__ float4 ld_cluster_f4(uint32_t caddr) {
 __device__ __forceinline__ void simt_cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// The same without the release fence: for a barrier that only has to keep
+// this CTA's shared memory alive until the other CTAs have finished reading
+// it (their loads have returned before they arrive).
+__device__ __forceinline__ void simt_cluster_sync_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
 
 // Epilogue of one row of four: C = alpha * v + beta * C (C not read when
 // beta == 0), float4 when the row is 16-byte aligned and whole.
@@ -322,7 +328,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // (deterministic), applies alpha and beta and stores them.  A second cluster
 // barrier keeps every partial readable until all sums are taken.
 template <bool VEC, bool SPLIT>
-__global__ void __launch_bounds__(256, SPLIT ? 3 : 4) simt_sgemm64_kernel(const SimtParams p) {
+__global__ void __launch_bounds__(256, SPLIT ? 2 : 4) simt_sgemm64_kernel(const SimtParams p) {
   constexpr int BM = 64, BN = 64, BK = 16, APAD = 4, STAGES = 4;
   constexpr int LDA_S = BK + APAD;   // 20 floats: rows 4 apart fall 16 banks apart
   constexpr int A_STAGE = BM * LDA_S, B_STAGE = BK * BN;
@@ -386,6 +392,43 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 4) simt_sgemm64_kernel(const 
     cp_async_commit();
     const float* as = As + (kb % STAGES) * A_STAGE + ty * 4 * LDA_S;
     const float* bs = Bs + (kb % STAGES) * B_STAGE + tx * 4;
+    if constexpr (SPLIT) {
+      // At most two CTAs per SM leave few warps to hide shared-memory
+      // latency: the fragments of step k4 + 4 are loaded while step k4's
+      // outer products run (same products, same order per element).
+      float a[2][4][4], b[2][4][4];   // a[.][i][u]: row 4ty + i, k = k4 + u; b[.][u][j]: k4 + u, column 4tx + j
+      auto load = [&](int buf, int k4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 v = *reinterpret_cast<const float4*>(as + i * LDA_S + k4);
+          a[buf][i][0] = v.x;
+          a[buf][i][1] = v.y;
+          a[buf][i][2] = v.z;
+          a[buf][i][3] = v.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 v = *reinterpret_cast<const float4*>(bs + (k4 + u) * BN);
+          b[buf][u][0] = v.x;
+          b[buf][u][1] = v.y;
+          b[buf][u][2] = v.z;
+          b[buf][u][3] = v.w;
+        }
+      };
+      load(0, 0);
+#pragma unroll
+      for (int s4 = 0; s4 < BK / 4; ++s4) {
+        const int cur = s4 & 1;
+        if (s4 + 1 < BK / 4) load(cur ^ 1, (s4 + 1) * 4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[cur][i][u], b[cur][u][j], acc[i][j]);
+      }
+      continue;
+    }
 #pragma unroll
     for (int k4 = 0; k4 < BK; k4 += 4) {
       float a[4][4];   // a[i][u]: row 4ty + i, k = k4 + u
@@ -439,7 +482,7 @@ __global__ void __launch_bounds__(256, SPLIT ? 3 : 4) simt_sgemm64_kernel(const 
       }
       store4_epilogue<VEC>(p, m0 + r, n0 + c, sum);
     }
-    simt_cluster_sync();
+    simt_cluster_sync_relaxed();
   }
 }
 
